@@ -1,0 +1,110 @@
+"""Algorithm 1, coarse to fine, in float64 (oracle).
+
+Test infrastructure only (see ``oracle/__init__``).
+
+Order of operations (Algorithm 1 inside the pyramid of Sec. IV-B, after the
+pre-rotation of Sec. IV-A):
+
+  pre-rotate I1 by the calibration field (t = 0)            Sec. IV-A
+  build the image pyramids and the per-level masks          Sec. IV-B
+  for each level, coarsest first:
+      trajectory field gamma' of the level                  Sec. III-B
+      tensor T^1/2 and step sizes                           Eq. 12, 11
+      u, w <- 2 x upsampled previous level (0 at the top); p <- 0
+      for each warp omega < N:
+          warp I1 by w, linearise along gamma'              Eq. 3, 5, 9
+          ubar <- u;  nIters primal-dual iterations          Eq. 11, 13
+          clip delta-u, u_{w+1} = u_w + du, w += du g        Eq. 8, 9
+  triangulate x and x + w at full resolution                Sec. III-D
+
+The dual p carries over between the warps of one level and restarts at 0 on
+a new level.  All state is float64.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .camera import calib_from_dict
+from .geometry import (calibration_field, prerotate, trajectory_field,
+                       triangulate_range, virtual_translation)
+from .pyramid import downsample_fast, fov_mask, level_sizes, scaled_calib, upsample
+from .variational import (Params, clip_update, grad_masks, pd_iteration,
+                          precondition, tensor_sqrt, warp_linearize)
+
+
+def level_data(I0l, M, prm: Params):
+    a, b, c = tensor_sqrt(I0l, M, prm.beta, prm.eta)
+    m1, m2 = grad_masks(M)
+    tau, sig1, sig2 = precondition(a, b, c, M, m1, m2, prm.precond)
+    return dict(a=a, b=b, c=c, m1=m1, m2=m2, M=M, tau=tau, sig1=sig1, sig2=sig2)
+
+
+def solve_level_warps(I0l, I1l, gamma, lv, u, w, p1, p2, warps, iters,
+                      prm: Params, on_iter=None, level=0):
+    """Run `warps` warps of `iters` primal-dual iterations on one level."""
+    M = lv["M"]
+    for om in range(warps):
+        Iu, rho0, g = warp_linearize(I0l, I1l, w, gamma, M)
+        st = dict(u=u.copy(), ubar=u.copy(), p1=p1, p2=p2, Iu=Iu, rho0=rho0,
+                  u_w=u.copy())
+        if on_iter is not None:
+            on_iter(level, om, -1, st, lv)
+        for k in range(iters):
+            pd_iteration(st, lv, prm)
+            if on_iter is not None:
+                on_iter(level, om, k, st, lv)
+        u, w = clip_update(st["u"], st["u_w"], w, g, prm.du_max, M)
+        p1, p2 = st["p1"], st["p2"]
+    return u, w, p1, p2
+
+
+def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params(),
+          on_iter=None, keep_levels=False):
+    """Full method on one pair; returns disparity (px), range (m), w and more."""
+    cam0 = calib_from_dict(cam0)
+    cam1 = calib_from_dict(cam1)
+    I0 = np.asarray(I0, dtype=np.float64)
+    I1 = np.asarray(I1, dtype=np.float64)
+    H, W = I0.shape
+    M0 = fov_mask(cam0, W, H)
+    cfield = calibration_field(cam0, cam1, R, W, H, M0)
+    I1p = prerotate(I1, cfield)
+    tp = virtual_translation(R, t)
+
+    sizes = level_sizes(W, H, levels)
+    calibs = [scaled_calib(cam0, l) for l in range(levels)]
+    masks = [fov_mask(calibs[l], *sizes[l]) for l in range(levels)]
+    pyr0, pyr1 = [I0], [I1p]
+    for l in range(1, levels):
+        pyr0.append(downsample_fast(pyr0[-1], masks[l - 1], *sizes[l]))
+        pyr1.append(downsample_fast(pyr1[-1], masks[l - 1], *sizes[l]))
+
+    u = w = None
+    per_level = []
+    for l in range(levels - 1, -1, -1):
+        Wl, Hl = sizes[l]
+        M = masks[l]
+        gamma = trajectory_field(calibs[l], tp, Wl, Hl, M)
+        lv = level_data(pyr0[l], M, prm)
+        if u is None:
+            u = np.zeros((Hl, Wl))
+            w = np.zeros((Hl, Wl, 2))
+        else:
+            u = upsample(u, masks[l + 1], Wl, Hl, M)
+            w = upsample(w, masks[l + 1], Wl, Hl, M)
+        p1 = np.zeros((Hl, Wl))
+        p2 = np.zeros((Hl, Wl))
+        u, w, p1, p2 = solve_level_warps(pyr0[l], pyr1[l], gamma, lv, u, w, p1, p2,
+                                         warps, iters, prm, on_iter, l)
+        if keep_levels:
+            per_level.append(dict(level=l, u=u.copy(), w=w.copy(), gamma=gamma,
+                                  I0=pyr0[l], I1=pyr1[l], **lv))
+
+    py, px = np.mgrid[0:H, 0:W].astype(np.float64)
+    rng = triangulate_range(cam0, px, py, w[..., 0], w[..., 1], tp)
+    depth = np.where(M0, rng, np.nan)
+    out = dict(disp=np.where(M0, u, 0.0), depth=depth, w=w, mask=M0, I1p=I1p,
+               cfield=cfield, tprime=tp)
+    if keep_levels:
+        out["levels"] = per_level
+    return out

@@ -1,0 +1,103 @@
+"""Seeded synthetic workloads: fisheye stereo pairs with known geometry.
+
+The paper's datasets are not available; these scenes stand in for them with
+the shapes and value ranges of the evaluated workloads (textured planes and
+spheres seen by 180-190 degree fisheye lenses, intensities in [0, 1]).
+Every pair is a pure function of (workload, seed, size).
+
+Each pair is a dict:
+  I0, I1      float64 (H, W) images in [0, 1], 0 outside the lens FOV
+  cam0, cam1  calibration dicts {model, fx, fy, cx, cy, k, fov_deg}
+  R, t        pose, X1 = R X0 + t
+  gt_range    camera-0 range (m) at pixel centres, NaN outside the FOV
+  levels, warps, iters, lam, eps   solver settings of the workload
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .render import (kb_is_monotone, make_plane_scene, make_scene, render,
+                     rotation)
+
+
+def _cam(model, W, H, f, fov, k=(0.0, 0.0, 0.0, 0.0)):
+    return dict(model=model, fx=float(f), fy=float(f), cx=(W - 1) / 2.0,
+                cy=(H - 1) / 2.0, k=[float(v) for v in k], fov_deg=float(fov))
+
+
+def draw_kb(rng, half_angle, bound=0.05):
+    """k1..k4 ~ U(-bound, bound), redrawn until r(theta) is monotone."""
+    while True:
+        k = rng.uniform(-bound, bound, size=4)
+        if kb_is_monotone(k, half_angle):
+            return [float(v) for v in k]
+
+
+def _pair(scene, cam0, cam1, R, C1, W, H, supersample, noise, rng):
+    t = -R @ C1
+    I0, gt = render(scene, cam0, np.eye(3), np.zeros(3), W, H, supersample, noise, rng)
+    I1, _ = render(scene, cam1, R, C1, W, H, supersample, noise, rng)
+    return dict(I0=I0, I1=I1, cam0=cam0, cam1=cam1, R=R, t=t, gt_range=gt)
+
+
+def plain_small(seed=0, W=256, H=256, supersample=2):
+    """Equidistant f=80 px 180 deg, 3 planes at 1-5 m, 0.1 m baseline along x."""
+    rng = np.random.default_rng(seed)
+    f = 80.0 * W / 256.0
+    cam = _cam("equidistant", W, H, f, 180.0)
+    scene = make_scene(rng, 3, (1.0, 5.0), 5.0, f, kinds=("plane",))
+    p = _pair(scene, cam, dict(cam), np.eye(3), np.array([0.1, 0.0, 0.0]), W, H,
+              supersample, 0.0, rng)
+    p.update(levels=3, warps=5, iters=50, lam=50.0, eps=0.01, name="plain_small_256")
+    return p
+
+
+def plain_kb(seed=0, W=1024, H=1024, supersample=2, levels=5):
+    """Kannala-Brandt f=320 px (at 1024) 190 deg, 20 objects 0.5-20 m, 0.12 m
+    baseline + rotation <= 2 deg, Gaussian noise 0.01."""
+    rng = np.random.default_rng(seed)
+    f = 320.0 * W / 1024.0
+    half = math.radians(190.0) / 2.0
+    k = draw_kb(rng, half)
+    cam = _cam("kb", W, H, f, 190.0, k)
+    axis = rng.normal(size=3)
+    R = rotation(axis, math.radians(rng.uniform(0.0, 2.0)))
+    scene = make_scene(rng, 20, (0.5, 20.0), 20.0, f, kinds=("plane", "sphere"))
+    p = _pair(scene, cam, dict(cam), R, np.array([0.12, 0.0, 0.0]), W, H,
+              supersample, 0.01, rng)
+    p.update(levels=levels, warps=10, iters=100, lam=50.0, eps=0.01,
+             name=f"plain_kb_{W}")
+    return p
+
+
+def mixed_2048(seed=0, supersample=2):
+    """The 180-degree equidistant generator at 2048 x 2048, 6 levels."""
+    p = plain_small(seed, 2048, 2048, supersample)
+    p.update(levels=6, warps=10, iters=100, name="equidistant_2048")
+    return p
+
+
+def auto_levels(W, min_width=40):
+    L = 1
+    while W / 2 ** L >= min_width:
+        L += 1
+    return L
+
+
+def fronto_plane(seed=0, model="equidistant", W=192, H=192, f=None, depth=2.0,
+                 baseline=0.1, supersample=2, cycles_per_px=0.25):
+    """A single textured plane Z = depth seen with a pure x translation."""
+    rng = np.random.default_rng(seed)
+    if model == "pinhole":
+        f = f or W / 2.0
+        cam = _cam("pinhole", W, H, f, 100.0)
+    else:
+        f = f or 60.0 * W / 192.0
+        cam = _cam("equidistant", W, H, f, 180.0)
+    scene = make_plane_scene(rng, depth, f, cycles_per_px=cycles_per_px)
+    p = _pair(scene, cam, dict(cam), np.eye(3), np.array([baseline, 0.0, 0.0]), W, H,
+              supersample, 0.0, rng)
+    p.update(levels=4, warps=8, iters=60, lam=50.0, eps=0.01, name=f"plane_{model}")
+    return p

@@ -1,0 +1,65 @@
+"""End-to-end pins for the oracle: paper parameters, renderer/pose convention,
+and a rendered fronto-parallel plane recovered at its known depth."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.ndimage as nd
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.json")
+
+
+def test_default_parameters_are_the_papers():
+    g = json.load(open(GOLDEN))
+    prm = oracle.Params()
+    assert prm.beta == g["beta"]["value"]
+    assert prm.eta == g["eta"]["value"]
+    assert prm.du_max == g["du_max_px"]["value"]
+    # an 800 x 800 image at scale 2 with minimum width 50 has 5 levels
+    sizes = oracle.level_sizes(800, 800, g["pyramid_levels_800"]["value"])
+    assert sizes[-1][0] >= g["min_width_px"]["value"]
+    assert sizes[-1][0] / g["pyramid_scale"]["value"] < g["min_width_px"]["value"]
+
+
+def test_renderer_pose_convention_matches_oracle_geometry(small_pair):
+    # the ground-truth correspondence pi(P + t') predicted by the oracle's
+    # geometry must look at the same scene point in the rendered I1
+    p = small_pair
+    cam = oracle.calib_from_dict(p["cam0"])
+    H, W = p["I0"].shape
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    r = oracle.unproject(cam, px, py)
+    P = p["gt_range"][..., None] * r
+    tp = oracle.virtual_translation(p["R"], p["t"])
+    x1 = oracle.project(cam, P + tp)
+    M = nd.binary_erosion(oracle.fov_mask(cam, W, H), iterations=6)
+    I1s = oracle.bilinear(p["I1"], x1[..., 0], x1[..., 1])
+    err = np.abs(I1s - p["I0"])[M]
+    wrong = np.abs(oracle.bilinear(p["I1"], px - (x1[..., 0] - px), py)[M] - p["I0"][M])
+    assert np.median(err) < 0.01
+    assert np.median(wrong) > 3 * np.median(err)
+
+
+@pytest.mark.parametrize("model", ["equidistant", "pinhole"])
+@pytest.mark.parametrize("depth", [1.0, 2.0, 4.0])
+def test_fronto_parallel_plane_depth(model, depth):
+    p = synth.fronto_plane(0, model=model, depth=depth, cycles_per_px=0.05,
+                           baseline=0.2, supersample=4)
+    prm = oracle.Params(lam=p["lam"], eps=p["eps"])
+    out = oracle.solve(p["I0"], p["I1"], p["cam0"], p["cam1"], p["R"], p["t"],
+                       p["levels"], p["warps"], p["iters"], prm)
+    cam = oracle.calib_from_dict(p["cam0"])
+    H, W = p["I0"].shape
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    r = oracle.unproject(cam, px, py)
+    Z = out["depth"] * r[..., 2]
+    theta = np.arccos(np.clip(r[..., 2], -1, 1))
+    # eroded mask, away from the epipoles at 90 degrees
+    sel = nd.binary_erosion(out["mask"], iterations=4) & (theta < np.radians(60))
+    rel = Z[sel] / depth - 1.0
+    assert abs(np.median(rel)) <= 0.01
+    assert np.median(np.abs(rel)) <= 0.025
