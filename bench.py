@@ -1,0 +1,346 @@
+"""Benchmark: frames/s of the fisheye variational stereo path on GB300.
+
+Workload (default): one 1024 x 1024 Kannala-Brandt fisheye pair (f = 320 px,
+190 deg FOV, k1..k4 seeded in +-0.05), 0.12 m baseline plus a seeded rotation
+<= 2 deg, 20 textured planes/spheres at 0.5-20 m, noise sigma 0.01; 5 pyramid
+levels, 10 warps x 100 primal-dual iterations per level, FP32.  A step is one
+whole frame: pre-rotation, pyramids, per-level tensor, warps, primal-dual
+iterations, clip/update, upsampling and triangulation.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Multi-GPU runs are independent replicas (one pair per rank, no collective on
+the data path).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & p99 latency, 1024² fisheye pair; primal-dual Gpix-iter/s vs plain"
+PD_BYTES_PER_PX_ITER = 52.0   # unblocked FP32 traffic of one pixel-iteration (9 reads + 4 writes)
+
+
+def workload_pair(name, seed):
+    import synth
+    if name == "plain_kb_1024":
+        return synth.plain_kb(seed)
+    if name == "plain_small_256":
+        return synth.plain_small(seed)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def level_pixels(W, H, levels):
+    import oracle
+    return [w * h for w, h in oracle.level_sizes(W, H, levels)]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_baseline(pair, target_s=15.0):
+    """The FP64 oracle on a bounded sample of the same frame: the finest
+    level's primal-dual iterations of one warp, extrapolated per pixel-iteration."""
+    import oracle
+    from oracle.solve import level_data
+    prm = oracle.Params(lam=pair["lam"], eps=pair["eps"])
+    cam = oracle.calib_from_dict(pair["cam0"])
+    H, W = pair["I0"].shape
+    M = oracle.fov_mask(cam, W, H)
+    lv = level_data(pair["I0"], M, prm)
+    rng = np.random.default_rng(0)
+    st = dict(u=np.zeros((H, W)), ubar=np.zeros((H, W)), p1=np.zeros((H, W)),
+              p2=np.zeros((H, W)), Iu=np.where(M, rng.uniform(-0.1, 0.1, (H, W)), 0.0),
+              rho0=np.where(M, rng.uniform(-0.05, 0.05, (H, W)), 0.0), u_w=np.zeros((H, W)))
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.pd_iteration(st, lv, prm)
+        n += 1
+        if time.perf_counter() - t0 > target_s:
+            break
+    dt = time.perf_counter() - t0
+    return n * W * H / dt, n, dt
+
+
+def run_reference(args, pair, rank):
+    """--impl reference: the FP64 oracle on the host cores, per step a bounded
+    sample of the frame (primal-dual iterations of the finest level)."""
+    import oracle
+    from oracle.solve import level_data
+    if rank != 0:
+        return
+    prm = oracle.Params(lam=pair["lam"], eps=pair["eps"])
+    cam = oracle.calib_from_dict(pair["cam0"])
+    H, W = pair["I0"].shape
+    M = oracle.fov_mask(cam, W, H)
+    lv = level_data(pair["I0"], M, prm)
+    st = dict(u=np.zeros((H, W)), ubar=np.zeros((H, W)), p1=np.zeros((H, W)),
+              p2=np.zeros((H, W)), Iu=np.where(M, 0.05, 0.0), rho0=np.where(M, 0.01, 0.0),
+              u_w=np.zeros((H, W)))
+    per_step = 5
+    for _ in range(args.warmup):
+        for _ in range(per_step):
+            oracle.pd_iteration(st, lv, prm)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            oracle.pd_iteration(st, lv, prm)
+        times.append(time.perf_counter() - t0)
+    pxit_frame = sum(level_pixels(W, H, pair["levels"])) * pair["warps"] * pair["iters"]
+    rate = per_step * W * H / float(np.mean(times))      # px-iter/s
+    fps = rate / pxit_frame
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / fps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": pair["name"], "W": W, "H": H, "levels": pair["levels"],
+                   "warps": pair["warps"], "iters": pair["iters"]},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} primal-dual iterations of the finest "
+                                   f"{W}x{H} level per step, extrapolated to a frame by "
+                                   f"pixel-iterations ({pxit_frame:.3e} per frame)"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpix_iter_s": rate / 1e9,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="plain_kb_1024")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--block-iters", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        if rank == 0:
+            run_reference(args, workload_pair(args.workload, args.seed), rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1909_07545_gb300 import Solver
+
+    pair = workload_pair(args.workload, args.seed + rank)
+    H, W = pair["I0"].shape
+    L, warps, iters = pair["levels"], pair["warps"], pair["iters"]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, L, stream=stream,
+                   lam=pair["lam"], huber_eps=pair["eps"], use_graph=1,
+                   block_iters=args.block_iters)
+        I0 = torch.as_tensor(np.float32(pair["I0"]), device="cuda")
+        I1 = torch.as_tensor(np.float32(pair["I1"]), device="cuda")
+        disp = torch.empty((H, W), device="cuda")
+        depth = torch.empty((H, W), device="cuda")
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+        stream.synchronize()
+
+        def step():
+            s.solve(I0, I1, warps, iters, disp=disp, depth=depth)
+
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        clocks.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))                      # evict the frame's working set from L2
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t_wall = time.perf_counter() - t_wall
+        clk = clocks.stop()
+        step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+        total_ms = float(step_ms.sum())
+        if dist:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+
+        # primal-dual kernel timing (CUDA events around each warp's launches,
+        # recorded by the library on this stream) over the same number of steps
+        s.timing_enable(True)
+        step()
+        stream.synchronize()
+        s.timing_read(reset=True)
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            step()
+            s.timing_read(reset=False)
+        per_level = s.timing_read(reset=True)
+        s.timing_enable(False)
+
+        # end to end through the host entry point (pinned buffers, copies inside)
+        hI0 = torch.as_tensor(np.float32(pair["I0"])).pin_memory()
+        hI1 = torch.as_tensor(np.float32(pair["I1"])).pin_memory()
+        hD = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        hZ = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        s.solve_host(hI0, hI1, warps, iters, disp=hD, depth=hZ)
+        e2e_steps = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            s.solve_host(hI0, hI1, warps, iters, disp=hD, depth=hZ)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        pd_launches = sum(n for _, n, _ in per_level) // max(args.steps, 1)
+        s.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    pxit_frame = sum(level_pixels(W, H, L)) * warps * iters
+    ms_per_step = total_ms / args.steps
+    fps = world * args.steps / (total_ms / 1000.0)
+    ms0, n0, px0 = per_level[0]
+    achieved = PD_BYTES_PER_PX_ITER * px0 / (ms0 / 1000.0) / 1e9
+    peaks, src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    pd_ms = sum(m for m, _, _ in per_level) / args.steps
+    # launches per frame: 2 copy/pre-rotate, L-1 downsample, L tensor, 1 zero,
+    # L-1 upsample, warps*L (warp + clip), PD launches, 1 depth
+    per_frame_other = 2 + (L - 1) + L + 1 + (L - 1) + 2 * warps * L + 1
+    line = {
+        "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": pair["name"], "W": W, "H": H, "levels": L, "warps": warps,
+                   "iters": iters, "camera": "kannala_brandt f=320 fov=190",
+                   "l2": "flushed between steps (256 MB write)",
+                   "block_iters": args.block_iters or 4, "graph": True,
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99)),
+                       "max": float(step_ms.max())},
+        "gpix_iter_s": pxit_frame * fps / world / 1e9 * world,
+        "pd": {"ms_per_frame": pd_ms, "share_of_step": pd_ms / ms_per_step,
+               "per_level_ms": [m / args.steps for m, _, _ in per_level]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_pd level 0 (1024x1024)",
+                     "peak_source": f"{src} hbm_gbs",
+                     "algorithmic_bytes_per_px_iter": PD_BYTES_PER_PX_ITER},
+        "gpu_launches": int(args.steps * (pd_launches + per_frame_other)),
+        "clocks": clk,
+        "wall_s": t_wall,
+    }
+    line["e2e"] = {"value": 1.0 / e2e_s, "unit": "frames/s",
+                   "h2d_bytes_per_step": 2 * W * H * 4, "d2h_bytes_per_step": 2 * W * H * 4}
+    if not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        rate, n, dt = cpu_baseline(pair, args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": rate / pxit_frame, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} primal-dual iterations of the finest {W}x{H} level in {dt:.1f} s "
+                      f"(FP64 numpy, one thread), extrapolated to a frame by pixel-iterations "
+                      f"({pxit_frame:.3e} per frame)"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,148 @@
+/*
+ * fs.h -- C ABI of the GB300 non-rectified variational fisheye stereo library
+ * (Roxas & Oishi, "Real-Time Variational Fisheye Stereo without Rectification
+ * and Undistortion").
+ *
+ * The library estimates, for a calibrated fisheye pair, the scalar disparity
+ * u along the epipolar curves (Sec. III-A) and the range it implies
+ * (Sec. III-D) directly on the distorted images: per pyramid level it builds
+ * the trajectory field of epipolar tangents (Sec. III-B, Eq. 6-7), warps the
+ * second image along it (Eq. 9), linearises the data term along the field
+ * (Eq. 3, 5) and runs primal-dual iterations of a tensor-weighted (Eq. 12)
+ * Huber-TV-L1 energy (Eq. 11, 13), inside the warping loop of Algorithm 1
+ * and the coarse-to-fine scheme of Sec. IV-B, after the pre-rotation of
+ * Sec. IV-A.
+ *
+ * Conventions shared by every entry point
+ *   - Images are float32 in [0, 1], row-major, pitch = width (no padding),
+ *     pixel centres on integer coordinates, (0, 0) the top-left pixel.
+ *   - Device pointers point to memory of the device that was current when the
+ *     handle was created; the caller owns them.  The library owns the per-rig
+ *     state it allocates in fs_create and frees it in fs_destroy.
+ *   - All GPU work of a handle is issued on the CUDA stream given to
+ *     fs_create (NULL = the legacy default stream) and is asynchronous unless
+ *     stated; the caller synchronises that stream before reading results.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ *   - Errors are returned as fs_status, never thrown; fs_last_error() gives a
+ *     message for the last failing call of the calling thread.
+ *   - Outside the FOV mask, disparity is 0 and depth is NaN; where the two
+ *     rays are parallel the depth is +inf.
+ */
+#ifndef FS_H
+#define FS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FS_OK = 0,
+  FS_EINVAL = -1,    /* bad argument (null pointer, size, level, count)      */
+  FS_ENOMEM = -2,    /* device allocation failed                             */
+  FS_ECUDA = -3,     /* a CUDA call or kernel launch failed                  */
+  FS_ECALIB = -4,    /* calibration rejected (e.g. non-monotone r(theta))    */
+  FS_ETIMEOUT = -5   /* a bounded device-side wait ran out                   */
+} fs_status;
+
+/* Radially symmetric camera models, pixel = c + f * r(theta) * (X, Y)/|(X, Y)|
+ * with theta the angle off the optical axis (Sec. III-B allows any model
+ * with a defined projection; Kannala-Brandt is one the paper cites). */
+typedef enum {
+  FS_PINHOLE = 0,          /* r = tan(theta)                                  */
+  FS_EQUIDISTANT = 1,      /* r = theta                                       */
+  FS_KANNALA_BRANDT = 2    /* r = theta + k1 t^3 + k2 t^5 + k3 t^7 + k4 t^9   */
+} fs_model;
+
+typedef struct {
+  int model;               /* fs_model                                        */
+  double fx, fy;           /* focal lengths, pixels                           */
+  double cx, cy;           /* principal point, pixels                         */
+  double k[4];             /* Kannala-Brandt k1..k4 (ignored otherwise)       */
+  double fov_deg;          /* full field of view; the mask keeps theta <= fov/2 */
+} fs_calib;
+
+/* Rig pose exp(xi_1) of Sec. III-A: X_cam1 = R X_cam0 + t, R row-major. */
+typedef struct {
+  double R[9];
+  double t[3];
+} fs_pose;
+
+/* Solver parameters.  beta, eta: Eq. 12 (paper values 9.0, 0.85, Sec. IV-C);
+ * du_max: the per-warp clip of delta-u (0.2 px, Sec. IV-C); lambda (data
+ * weight) and huber_eps are not stated by the paper.  theta is the
+ * over-relaxation of Eq. 11 (1 = Chambolle-Pock Algorithm 1).  precond = 1
+ * uses diagonal preconditioning (Pock-Chambolle 2011, alpha = 1), 0 uses
+ * tau = sigma = 1/sqrt(8).  block_iters: primal-dual iterations fused per
+ * launch by temporal blocking (1..8; 0 = library default).  use_graph = 1
+ * captures a solve into a CUDA graph on first use and replays it. */
+typedef struct {
+  float lambda;
+  float huber_eps;
+  float du_max;
+  float beta;
+  float eta;
+  float theta;
+  int precond;
+  int block_iters;
+  int use_graph;
+  int reserved[5];         /* must be 0 */
+} fs_params;
+
+typedef struct fs_handle fs_handle;
+
+/* Fill *out with the defaults (lambda 50, eps 0.01, du_max 0.2, beta 9,
+ * eta 0.85, theta 1, precond 1, block_iters 0, use_graph 0). */
+fs_status fs_default_params(fs_params* out);
+
+/* Create the per-rig state for W x H pairs and `levels` pyramid levels
+ * (scale 2 per level, Sec. IV-B/C; level l is ceil(W/2^l) x ceil(H/2^l)).
+ * cam[0], cam[1]: calibrations of the two cameras; pose: camera 1 relative
+ * to camera 0; prm: NULL for defaults; cuda_stream: a cudaStream_t or NULL.
+ * Builds, on the stream, the FOV masks, the calibration field of Sec. IV-A
+ * and the trajectory field of every level (Sec. III-B).  Requires
+ * 1 <= levels <= 8, every level at least 4 x 4, fx, fy > 0, fov in (0, 360)
+ * (< 180 for pinhole), and a Kannala-Brandt r(theta) increasing on
+ * [0, fov/2] (else FS_ECALIB).  On success *out owns device memory. */
+fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H,
+                    int levels, const fs_params* prm, void* cuda_stream,
+                    fs_handle** out);
+
+/* Replace the pose; recomputes the calibration and trajectory fields. */
+fs_status fs_set_pose(fs_handle* h, const fs_pose* pose);
+
+/* Size of pyramid level `level` (0 = full resolution). */
+fs_status fs_level_size(const fs_handle* h, int level, int* W, int* H);
+
+/* Copy the trajectory field gamma' of a level (Sec. III-B, Eq. 7) to d_out:
+ * two planes of H_l x W_l floats, x components then y components.  Unit
+ * vectors inside the mask, 0 outside and at epipoles. */
+fs_status fs_trajectory_field(fs_handle* h, int level, float* d_out);
+
+/* Run the method on one pair (Algorithm 1 inside the pyramid of Sec. IV-B,
+ * after the pre-rotation of Sec. IV-A).  d_I0, d_I1: W x H device images of
+ * camera 0 and camera 1.  d_init: NULL to start from u = 0 at the coarsest
+ * level; else a W x H disparity (px) to warm-start from, in which case only
+ * the finest level runs.  warps >= 1 warps of iters >= 1 primal-dual
+ * iterations per level.  d_disp (W x H, px along the epipolar curve) and
+ * d_depth (W x H, metres along the camera-0 ray) may be NULL to skip. */
+fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1,
+                   const float* d_init, int warps, int iters,
+                   float* d_disp, float* d_depth);
+
+/* fs_solve from HOST buffers: copies the inputs to the device, solves,
+ * copies the outputs back and synchronises the handle's stream before
+ * returning.  Host buffers may be pageable or pinned (pinned is faster). */
+fs_status fs_solve_host(fs_handle* h, const float* h_I0, const float* h_I1,
+                        const float* h_init, int warps, int iters,
+                        float* h_disp, float* h_depth);
+
+/* Free the handle and its device memory (synchronises its stream). */
+fs_status fs_destroy(fs_handle* h);
+
+/* Message for the last failing call of this thread ("" if none). */
+const char* fs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FS_H */

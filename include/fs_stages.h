@@ -1,0 +1,80 @@
+/*
+ * fs_stages.h -- step-by-step access to the per-level state of an fs_handle.
+ *
+ * fs_solve runs these stages in the order of Algorithm 1; exposing them one
+ * at a time lets a caller (a test, a profiler, a custom schedule) set a
+ * level's buffers, run a single stage and read the result.  Same
+ * conventions as fs.h: dense row-major device buffers (pitch = width of the
+ * level), caller-owned, work on the handle's stream.
+ */
+#ifndef FS_STAGES_H
+#define FS_STAGES_H
+
+#include "fs.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Per-level buffers.  "planes" is the number of H_l x W_l float planes a
+ * read or write moves (2 = x then y components, 3 = a, b, c). */
+typedef enum {
+  FS_BUF_I0 = 0,      /* 1: camera-0 image of the level                       */
+  FS_BUF_I1 = 1,      /* 1: pre-rotated camera-1 image (Sec. IV-A)            */
+  FS_BUF_MASK = 2,    /* 1: FOV mask as 0.0 / 1.0 (read only)                 */
+  FS_BUF_GAMMA = 3,   /* 2: trajectory field gamma' (Sec. III-B)              */
+  FS_BUF_TENSOR = 4,  /* 3: T^1/2 = [[a, b], [b, c]] (Eq. 12)                 */
+  FS_BUF_STEPS = 5,   /* 2: tau, sigma (diagonal preconditioning)             */
+  FS_BUF_U = 6,       /* 1: disparity u (px along the curve)                  */
+  FS_BUF_UBAR = 7,    /* 1: over-relaxed u (Eq. 11)                           */
+  FS_BUF_UW = 8,      /* 1: linearisation point u_omega (Eq. 3)               */
+  FS_BUF_P = 9,       /* 2: dual variable p (Eq. 11)                          */
+  FS_BUF_W = 10,      /* 2: warp vector w (Eq. 9)                             */
+  FS_BUF_IU = 11,     /* 1: I_u, variation of I1 along gamma' (Eq. 5)         */
+  FS_BUF_RHO0 = 12,   /* 1: I1(x + w) - I0(x)                                 */
+  FS_BUF_G = 13       /* 2: gamma' at x + w, renormalised (bicubic)           */
+} fs_buffer;
+
+typedef enum {
+  FS_STAGE_DOWNSAMPLE = 0, /* I0, I1 of `level` -> level + 1 (Sec. IV-B)      */
+  FS_STAGE_TENSOR = 1,     /* I0 -> T^1/2 (Eq. 12) and tau, sigma             */
+  FS_STAGE_UPSAMPLE = 2,   /* u, w of level + 1 -> level (x2), p <- 0        */
+  FS_STAGE_WARP = 3,       /* I0, I1, w, gamma' -> I_u, rho0, g; ubar, u_w <- u (Eq. 3, 5, 9) */
+  FS_STAGE_PD = 4,         /* `count` primal-dual iterations (Eq. 11, 13)     */
+  FS_STAGE_CLIP = 5,       /* clip delta-u, u_w + du -> u, w += du g (Alg. 1) */
+  FS_STAGE_TRAJECTORY = 6  /* rebuild gamma' of the level (Sec. III-B)        */
+} fs_stage;
+
+/* Copy a level buffer to / from dense device memory of planes x H_l x W_l
+ * floats.  FS_BUF_MASK is read-only. */
+fs_status fs_buffer_read(fs_handle* h, int level, int buffer, float* d_out);
+fs_status fs_buffer_write(fs_handle* h, int level, int buffer, const float* d_in);
+
+/* Run one stage on a level's buffers; `count` is the iteration count of
+ * FS_STAGE_PD and ignored by the others. */
+fs_status fs_run_stage(fs_handle* h, int level, int stage, int count);
+
+/* Pre-rotate a full-resolution camera-1 image by the calibration field
+ * (Sec. IV-A) into the level-0 FS_BUF_I1 buffer. */
+fs_status fs_stage_prerotate(fs_handle* h, const float* d_I1);
+
+/* Triangulate level 0 (Sec. III-D): d_disp <- u, d_depth <- range; either
+ * may be NULL. */
+fs_status fs_stage_depth(fs_handle* h, float* d_disp, float* d_depth);
+
+/* Kernel timing with CUDA events on the handle's stream.  While enabled,
+ * every fs_solve records an event pair around the primal-dual launches of
+ * each (level, warp); fs_timing_read synchronises the stream, folds the
+ * recorded pairs into per-level totals and returns, for each level l < 8,
+ * ms[l] = accumulated primal-dual time, launches[l] = primal-dual kernel
+ * launches and pixel_iters[l] = pixel-iterations they processed, since the
+ * last reset.  Call it after each solve (a solve reuses the events).
+ * reset = 1 clears the totals after reading.  Any output may be NULL. */
+fs_status fs_timing_enable(fs_handle* h, int enable);
+fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
+                         double* pixel_iters, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FS_STAGES_H */

@@ -15,7 +15,7 @@ import numpy as np
 from .camera import project, unproject
 from .interp import bilinear
 
-SMALL_MOTION = 1e-6       # |t| -> 0 of Sec. III-B, Eq. 7
+SMALL_MOTION = 1e-5       # |t| -> 0 of Sec. III-B, Eq. 7 (symmetric pair, O(s^2) error)
 EPIPOLE_RATIO = 1e-3      # |w| / s below this: the pixel is an epipole, gamma' = 0
 
 
@@ -27,21 +27,25 @@ def virtual_translation(R, t):
 
 
 def trajectory_vector(calib, tprime, px, py, depth=1.0, s=SMALL_MOTION):
-    """gamma'(x0) at arbitrary points, following Sec. III-B literally.
+    """gamma'(x0) at arbitrary points, following Sec. III-B.
 
     A surface point X at arbitrary depth on the ray of x0 is projected into
-    both (pre-rotated) cameras, x0 = pi(X) and x1 = pi(X + s * t'/|t'|), with
-    s -> 0 (Eq. 6-7); the normalised flow w/|w| is the field.  Where |w|/s is
-    below EPIPOLE_RATIO the point is an epipole and the field is 0.
+    cameras translated along t' by a vanishing amount (Eq. 6-7, |t| -> 0);
+    the normalised flow w/|w| is the field.  The limit is taken with the
+    symmetric pair of motions -s t'/|t'| and +s t'/|t'|, whose flow
+    w = pi(X + s t^) - pi(X - s t^) has an O(s^2) error (a one-sided pair
+    has O(s), about 1e-6 in gamma' for s = 1e-6, which the warping then
+    amplifies).  Where |w|/(2 s) is below EPIPOLE_RATIO the point is an
+    epipole and the field is 0.
     """
     tprime = np.asarray(tprime, dtype=np.float64)
     that = tprime / np.linalg.norm(tprime)
     X = depth * unproject(calib, px, py)
-    x0 = project(calib, X)
     x1 = project(calib, X + s * that)
-    w = x1 - x0
+    xm = project(calib, X - s * that)
+    w = x1 - xm
     n = np.linalg.norm(w, axis=-1, keepdims=True)
-    ok = n / s >= EPIPOLE_RATIO
+    ok = n / (2.0 * s) >= EPIPOLE_RATIO
     return np.where(ok, w / np.where(ok, n, 1.0), 0.0)
 
 

@@ -59,8 +59,13 @@ def solve_level_warps(I0l, I1l, gamma, lv, u, w, p1, p2, warps, iters,
 
 
 def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params(),
-          on_iter=None, keep_levels=False):
-    """Full method on one pair; returns disparity (px), range (m), w and more."""
+          on_iter=None, keep_levels=False, level_hook=None):
+    """Full method on one pair; returns disparity (px), range (m), w and more.
+
+    level_hook(level, I0_l, I1_l) -> (I0_l, I1_l), when given, may replace
+    each level's images after the pyramid is built (a probe for how the
+    result responds to perturbing them; None for the method itself).
+    """
     cam0 = calib_from_dict(cam0)
     cam1 = calib_from_dict(cam1)
     I0 = np.asarray(I0, dtype=np.float64)
@@ -78,6 +83,10 @@ def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params()
     for l in range(1, levels):
         pyr0.append(downsample_fast(pyr0[-1], masks[l - 1], *sizes[l]))
         pyr1.append(downsample_fast(pyr1[-1], masks[l - 1], *sizes[l]))
+
+    if level_hook is not None:
+        for l in range(levels):
+            pyr0[l], pyr1[l] = level_hook(l, pyr0[l], pyr1[l])
 
     u = w = None
     per_level = []

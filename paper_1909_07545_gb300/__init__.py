@@ -1,0 +1,275 @@
+"""GB300 non-rectified variational fisheye stereo (Roxas & Oishi) -- Python binding.
+
+Argument marshalling over the C ABI of ``libfs.so`` (``include/fs.h`` and
+``include/fs_stages.h``); every step of the method runs in the library's
+CUDA kernels.  PyTorch only supplies device memory and the CUDA stream.
+The library must have been built (``paper_1909_07545_gb300.build.build()``);
+without it, creating a solver raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Solver", "FsError", "load_library", "default_params", "BUF", "STAGE",
+           "LIB_PATH", "EXPORTED"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfs.so")
+
+MODELS = {"pinhole": 0, "equidistant": 1, "kb": 2, "kannala_brandt": 2}
+
+BUF = dict(I0=0, I1=1, MASK=2, GAMMA=3, TENSOR=4, STEPS=5, U=6, UBAR=7, UW=8, P=9, W=10,
+           IU=11, RHO0=12, G=13)
+BUF_PLANES = {0: 1, 1: 1, 2: 1, 3: 2, 4: 3, 5: 2, 6: 1, 7: 1, 8: 1, 9: 2, 10: 2, 11: 1, 12: 1,
+              13: 2}
+STAGE = dict(DOWNSAMPLE=0, TENSOR=1, UPSAMPLE=2, WARP=3, PD=4, CLIP=5, TRAJECTORY=6)
+
+STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ENOMEM", -3: "FS_ECUDA", -4: "FS_ECALIB",
+          -5: "FS_ETIMEOUT"}
+
+# every entry point declared in include/*.h
+EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
+            "fs_trajectory_field", "fs_solve", "fs_solve_host", "fs_destroy", "fs_last_error",
+            "fs_buffer_read", "fs_buffer_write", "fs_run_stage", "fs_stage_prerotate",
+            "fs_stage_depth", "fs_timing_enable", "fs_timing_read"]
+
+
+class FsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class FsCalib(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("k", ctypes.c_double * 4),
+                ("fov_deg", ctypes.c_double)]
+
+
+class FsPose(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
+
+
+class FsParams(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_float), ("huber_eps", ctypes.c_float),
+                ("du_max", ctypes.c_float), ("beta", ctypes.c_float), ("eta", ctypes.c_float),
+                ("theta", ctypes.c_float), ("precond", ctypes.c_int),
+                ("block_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load_library():
+    """Load libfs.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "paper_1909_07545_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    i, d = ctypes.c_int, ctypes.c_double
+    sig = {
+        "fs_default_params": [ctypes.POINTER(FsParams)],
+        "fs_create": [ctypes.POINTER(FsCalib), ctypes.POINTER(FsPose), i, i, i,
+                      ctypes.POINTER(FsParams), _P, ctypes.POINTER(_P)],
+        "fs_set_pose": [_P, ctypes.POINTER(FsPose)],
+        "fs_level_size": [_P, i, ctypes.POINTER(i), ctypes.POINTER(i)],
+        "fs_trajectory_field": [_P, i, _P],
+        "fs_solve": [_P, _P, _P, _P, i, i, _P, _P],
+        "fs_solve_host": [_P, _P, _P, _P, i, i, _P, _P],
+        "fs_destroy": [_P],
+        "fs_buffer_read": [_P, i, i, _P],
+        "fs_buffer_write": [_P, i, i, _P],
+        "fs_run_stage": [_P, i, i, i],
+        "fs_stage_prerotate": [_P, _P],
+        "fs_stage_depth": [_P, _P, _P],
+        "fs_timing_enable": [_P, i],
+        "fs_timing_read": [_P, _P, _P, _P, i],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.fs_last_error.argtypes = []
+    lib.fs_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise FsError(status, _lib.fs_last_error().decode())
+
+
+def default_params(**overrides) -> FsParams:
+    lib = load_library()
+    p = FsParams()
+    _check(lib.fs_default_params(ctypes.byref(p)))
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
+    return p
+
+
+def _calib(c) -> FsCalib:
+    m = c["model"]
+    k = list(c.get("k", [0.0] * 4)) + [0.0] * 4
+    return FsCalib(MODELS[m] if isinstance(m, str) else int(m), float(c["fx"]), float(c["fy"]),
+                   float(c["cx"]), float(c["cy"]), (ctypes.c_double * 4)(*k[:4]),
+                   float(c.get("fov_deg", 180.0)))
+
+
+def _pose(R, t) -> FsPose:
+    R = np.asarray(R, dtype=np.float64).reshape(9)
+    t = np.asarray(t, dtype=np.float64).reshape(3)
+    return FsPose((ctypes.c_double * 9)(*R), (ctypes.c_double * 3)(*t))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Solver:
+    """One rig: calibration, pose and per-level device state (fs_create)."""
+
+    def __init__(self, cam0, cam1, R, t, W, H, levels, params=None, stream=None, **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.lib = load_library()
+        self.torch = torch
+        if params is None:
+            params = default_params(**kw)
+        self.params = params
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        cams = (FsCalib * 2)(_calib(cam0), _calib(cam1))
+        pose = _pose(R, t)
+        h = _P()
+        _check(self.lib.fs_create(cams, ctypes.byref(pose), int(W), int(H), int(levels),
+                                  ctypes.byref(params), _P(stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        self.W, self.H, self.levels = int(W), int(H), int(levels)
+
+    # ------------------------------------------------------------------ core
+    def level_size(self, level):
+        w, h = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.fs_level_size(self.h, level, ctypes.byref(w), ctypes.byref(h)))
+        return w.value, h.value
+
+    def set_pose(self, R, t):
+        _check(self.lib.fs_set_pose(self.h, ctypes.byref(_pose(R, t))))
+
+    def _dev(self, a):
+        torch = self.torch
+        if isinstance(a, torch.Tensor):
+            t = a.to(device="cuda", dtype=torch.float32)
+        else:
+            t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+        return t.contiguous()
+
+    def solve(self, I0, I1, warps, iters, init=None, disp=None, depth=None):
+        """fs_solve on device tensors (H, W); returns (disparity, depth) tensors."""
+        torch = self.torch
+        I0 = self._dev(I0)
+        I1 = self._dev(I1)
+        init = self._dev(init) if init is not None else None
+        if disp is None:
+            disp = torch.empty((self.H, self.W), device="cuda", dtype=torch.float32)
+        if depth is None:
+            depth = torch.empty((self.H, self.W), device="cuda", dtype=torch.float32)
+        _check(self.lib.fs_solve(self.h, _ptr(I0), _ptr(I1), _ptr(init), int(warps), int(iters),
+                                 _ptr(disp), _ptr(depth)))
+        self._keep = (I0, I1, init)
+        return disp, depth
+
+    def solve_host(self, I0, I1, warps, iters, init=None, disp=None, depth=None):
+        """fs_solve_host on host float32 arrays (copies inside the call)."""
+        def host(a):
+            if hasattr(a, "data_ptr"):
+                return a
+            return np.ascontiguousarray(a, dtype=np.float32)
+        I0, I1 = host(I0), host(I1)
+        init = host(init) if init is not None else None
+        if disp is None:
+            disp = np.empty((self.H, self.W), dtype=np.float32)
+        if depth is None:
+            depth = np.empty((self.H, self.W), dtype=np.float32)
+
+        def p(a):
+            if a is None:
+                return None
+            return _P(a.data_ptr()) if hasattr(a, "data_ptr") else a.ctypes.data_as(_P)
+        _check(self.lib.fs_solve_host(self.h, p(I0), p(I1), p(init), int(warps), int(iters),
+                                      p(disp), p(depth)))
+        return disp, depth
+
+    def trajectory_field(self, level=0):
+        w, h = self.level_size(level)
+        out = self.torch.empty((2, h, w), device="cuda", dtype=self.torch.float32)
+        _check(self.lib.fs_trajectory_field(self.h, level, _ptr(out)))
+        return out
+
+    # ------------------------------------------------------------------ stages
+    def read(self, level, buf):
+        b = BUF[buf] if isinstance(buf, str) else int(buf)
+        w, h = self.level_size(level)
+        out = self.torch.empty((BUF_PLANES[b], h, w), device="cuda", dtype=self.torch.float32)
+        _check(self.lib.fs_buffer_read(self.h, level, b, _ptr(out)))
+        return out[0] if BUF_PLANES[b] == 1 else out
+
+    def write(self, level, buf, value):
+        b = BUF[buf] if isinstance(buf, str) else int(buf)
+        w, h = self.level_size(level)
+        t = self._dev(value).reshape(BUF_PLANES[b], h, w).contiguous()
+        _check(self.lib.fs_buffer_write(self.h, level, b, _ptr(t)))
+        self._keep_w = t
+
+    def stage(self, level, stage, count=0):
+        s = STAGE[stage] if isinstance(stage, str) else int(stage)
+        _check(self.lib.fs_run_stage(self.h, level, s, int(count)))
+
+    def prerotate(self, I1):
+        I1 = self._dev(I1)
+        _check(self.lib.fs_stage_prerotate(self.h, _ptr(I1)))
+        self._keep_p = I1
+
+    def depth(self):
+        disp = self.torch.empty((self.H, self.W), device="cuda", dtype=self.torch.float32)
+        depth = self.torch.empty_like(disp)
+        _check(self.lib.fs_stage_depth(self.h, _ptr(disp), _ptr(depth)))
+        return disp, depth
+
+    def timing_enable(self, on=True):
+        _check(self.lib.fs_timing_enable(self.h, 1 if on else 0))
+
+    def timing_read(self, reset=False):
+        """Per-level primal-dual (ms, launches, pixel-iterations) since the last reset."""
+        ms = (ctypes.c_double * 8)()
+        n = (ctypes.c_longlong * 8)()
+        px = (ctypes.c_double * 8)()
+        _check(self.lib.fs_timing_read(self.h, ms, n, px, 1 if reset else 0))
+        return [(ms[l], n[l], px[l]) for l in range(self.levels)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(self.lib.fs_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

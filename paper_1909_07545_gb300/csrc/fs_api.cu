@@ -1,0 +1,770 @@
+// fs_api.cu -- the C ABI (include/fs.h, include/fs_stages.h): handle
+// lifecycle, FP64 host geometry, and the Algorithm 1 schedule of kernels on
+// the handle's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fs.h"
+#include "fs_stages.h"
+#include "fs_kernels.h"
+
+using namespace fs;
+
+namespace {
+
+thread_local std::string g_err;
+
+fs_status fail(fs_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define FS_CUDA(expr)                                                             \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(FS_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));      \
+  } while (0)
+
+#define FS_LAUNCHED(name)                                                         \
+  do {                                                                            \
+    cudaError_t e_ = cudaGetLastError();                                          \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(FS_ECUDA, "launch of %s failed: %s", name, cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kMaxLevels = 8;
+
+struct HostLevel {
+  int W = 0, H = 0, P = 0;
+  double fx = 0, fy = 0, cx = 0, cy = 0;   // level calibration (camera 0)
+  LevelView v{};
+};
+
+double radial(const fs_calib& c, double th) {
+  if (c.model == FS_PINHOLE) return std::tan(th);
+  if (c.model == FS_EQUIDISTANT) return th;
+  double t2 = th * th;
+  return th * (1.0 + t2 * (c.k[0] + t2 * (c.k[1] + t2 * (c.k[2] + t2 * c.k[3]))));
+}
+
+DevCam dev_cam(const fs_calib& c, double fx, double fy, double cx, double cy) {
+  DevCam d;
+  d.model = c.model;
+  d.fx = (float)fx; d.fy = (float)fy; d.cx = (float)cx; d.cy = (float)cy;
+  d.k1 = (float)c.k[0]; d.k2 = (float)c.k[1]; d.k3 = (float)c.k[2]; d.k4 = (float)c.k[3];
+  double tm = c.fov_deg * M_PI / 360.0;
+  d.theta_max = (float)tm;
+  d.r_max = (float)radial(c, tm);
+  return d;
+}
+
+fs_status check_calib(const fs_calib& c, int which) {
+  if (c.model < FS_PINHOLE || c.model > FS_KANNALA_BRANDT)
+    return fail(FS_EINVAL, "camera %d: unknown model %d", which, c.model);
+  if (!(c.fx > 0) || !(c.fy > 0) || !std::isfinite(c.cx) || !std::isfinite(c.cy))
+    return fail(FS_ECALIB, "camera %d: focal lengths must be > 0, centre finite", which);
+  if (!(c.fov_deg > 0 && c.fov_deg < 360))
+    return fail(FS_ECALIB, "camera %d: fov_deg must be in (0, 360)", which);
+  if (c.model == FS_PINHOLE && !(c.fov_deg < 180))
+    return fail(FS_ECALIB, "camera %d: a pinhole fov must be < 180 degrees", which);
+  if (c.model == FS_KANNALA_BRANDT) {
+    // r(theta) must increase on [0, fov/2] (10^4 samples)
+    double tm = c.fov_deg * M_PI / 360.0, prev = 0.0;
+    for (int i = 1; i < 10000; ++i) {
+      double r = radial(c, tm * i / 9999.0);
+      if (!(r > prev)) return fail(FS_ECALIB, "camera %d: r(theta) not increasing", which);
+      prev = r;
+    }
+  }
+  return FS_OK;
+}
+
+double radial_d(const fs_calib& c, double th) {
+  if (c.model == FS_PINHOLE) { double cs = std::cos(th); return 1.0 / (cs * cs); }
+  if (c.model == FS_EQUIDISTANT) return 1.0;
+  double t2 = th * th;
+  return 1.0 + t2 * (3 * c.k[0] + t2 * (5 * c.k[1] + t2 * (7 * c.k[2] + t2 * 9 * c.k[3])));
+}
+
+// theta with r(theta) = rn on [0, fov/2] in FP64: 24 bisection steps, then
+// Newton inside the bracket (r increases there; checked by check_calib).
+double theta_of(const fs_calib& c, double rn) {
+  if (c.model == FS_EQUIDISTANT) return rn;
+  if (c.model == FS_PINHOLE) return std::atan(rn);
+  double lo = 0.0, hi = c.fov_deg * M_PI / 360.0;
+  for (int i = 0; i < 24; ++i) {
+    double mid = 0.5 * (lo + hi);
+    if (radial(c, mid) > rn) hi = mid; else lo = mid;
+  }
+  double th = 0.5 * (lo + hi);
+  for (int i = 0; i < 6; ++i) {
+    double f = radial(c, th) - rn;
+    if (f > 0) hi = th; else lo = th;
+    double nt = th - f / radial_d(c, th);
+    th = (nt >= lo && nt <= hi) ? nt : 0.5 * (lo + hi);
+  }
+  return th;
+}
+
+void unproject_d(const fs_calib& c, double px, double py, double X[3]) {
+  double mx = (px - c.cx) / c.fx, my = (py - c.cy) / c.fy;
+  double rn = std::hypot(mx, my);
+  double th = theta_of(c, rn), s = std::sin(th);
+  X[0] = rn > 0 ? s * mx / rn : 0.0;
+  X[1] = rn > 0 ? s * my / rn : 0.0;
+  X[2] = std::cos(th);
+}
+
+void project_d(const fs_calib& c, const double X[3], double p[2]) {
+  double rho = std::hypot(X[0], X[1]);
+  double r = radial(c, std::atan2(rho, X[2]));
+  p[0] = c.fx * (rho > 0 ? r * X[0] / rho : 0.0) + c.cx;
+  p[1] = c.fy * (rho > 0 ? r * X[1] / rho : 0.0) + c.cy;
+}
+
+inline dim3 grid2(int W, int H) { return dim3((W + 31) / 32, (H + 7) / 8); }
+const dim3 kBlock2(32, 8);
+
+}  // namespace
+
+struct fs_handle {
+  fs_calib cam[2];
+  fs_pose pose;
+  fs_params prm;
+  int W = 0, H = 0, L = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  HostLevel lv[kMaxLevels];
+  std::vector<uint8_t> mask0;            // host copy of the level-0 mask bits
+  float2* cfield = nullptr;
+  double tp[3] = {0, 0, 0};
+  void* arena = nullptr;
+  // staging for fs_solve_host
+  float* stage = nullptr;
+  // CUDA graph cache of one solve
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[7] = {};
+  int gwarps = 0, giters = 0;
+  // primal-dual timing: one event pair per (level, warp) of the last solve
+  int timing = 0;
+  std::vector<cudaEvent_t> ev;          // 2 per (level, warp)
+  int ev_warps = 0;                      // warps recorded by the last solve
+  int ev_iters = 0;
+  bool ev_pending = false;
+  double t_ms[kMaxLevels] = {};
+  long long t_launch[kMaxLevels] = {};
+  double t_pxit[kMaxLevels] = {};
+};
+
+namespace {
+
+fs_status upload_masks(fs_handle* h, std::vector<uint8_t>& host) {
+  const fs_calib& c = h->cam[0];
+  double rmax = radial(c, c.fov_deg * M_PI / 360.0);
+  for (int l = 0; l < h->L; ++l) {
+    HostLevel& L = h->lv[l];
+    host.assign((size_t)L.P * L.H, 0);
+    auto inside = [&](int x, int y) {
+      double mx = (x - L.cx) / L.fx, my = (y - L.cy) / L.fy;
+      return std::hypot(mx, my) <= rmax;
+    };
+    for (int y = 0; y < L.H; ++y)
+      for (int x = 0; x < L.W; ++x) {
+        bool m = inside(x, y);
+        uint8_t b = m ? MASK_IN : 0;
+        if (m && x + 1 < L.W && inside(x + 1, y)) b |= MASK_GX;
+        if (m && y + 1 < L.H && inside(x, y + 1)) b |= MASK_GY;
+        host[(size_t)y * L.P + x] = b;
+      }
+    FS_CUDA(cudaMemcpy((void*)L.v.mask, host.data(), host.size(), cudaMemcpyHostToDevice));
+    if (l == 0) h->mask0 = host;
+  }
+  return FS_OK;
+}
+
+fs_status build_fields(fs_handle* h) {
+  const double* R = h->pose.R;
+  const double* t = h->pose.t;
+  for (int i = 0; i < 3; ++i) h->tp[i] = R[0 + i] * t[0] + R[3 + i] * t[1] + R[6 + i] * t[2];
+  double n = std::sqrt(h->tp[0] * h->tp[0] + h->tp[1] * h->tp[1] + h->tp[2] * h->tp[2]);
+  if (!(n > 0) || !std::isfinite(n))
+    return fail(FS_EINVAL, "pose: translation must be non-zero and finite");
+  // calibration field c(x) = pi_1(R X) - pi_0(X), X = pi_0^-1(x), t = 0
+  // (Sec. IV-A), in FP64 on host threads; FP32 only for storage
+  HostLevel& L0 = h->lv[0];
+  std::vector<float2> field((size_t)L0.P * L0.H, make_float2(0.f, 0.f));
+  auto rows = [&](int y0, int y1) {
+    for (int y = y0; y < y1; ++y)
+      for (int x = 0; x < L0.W; ++x) {
+        size_t i = (size_t)y * L0.P + x;
+        if (!(h->mask0[i] & MASK_IN)) continue;
+        double X[3], X1[3], p0[2], p1[2];
+        unproject_d(h->cam[0], x, y, X);
+        project_d(h->cam[0], X, p0);
+        for (int r = 0; r < 3; ++r) X1[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2];
+        project_d(h->cam[1], X1, p1);
+        field[i] = make_float2((float)(p1[0] - p0[0]), (float)(p1[1] - p0[1]));
+      }
+  };
+  unsigned nt = std::thread::hardware_concurrency();
+  nt = nt == 0 ? 1 : (nt > 16 ? 16 : nt);
+  std::vector<std::thread> pool;
+  int chunk = (L0.H + (int)nt - 1) / (int)nt;
+  for (unsigned k = 0; k < nt; ++k) {
+    int y0 = (int)k * chunk, y1 = std::min(L0.H, y0 + chunk);
+    if (y0 < y1) pool.emplace_back(rows, y0, y1);
+  }
+  for (auto& t : pool) t.join();
+  FS_CUDA(cudaMemcpyAsync(h->cfield, field.data(), field.size() * sizeof(float2),
+                          cudaMemcpyHostToDevice, h->stream));
+  FS_CUDA(cudaStreamSynchronize(h->stream));
+  for (int l = 0; l < h->L; ++l) {
+    HostLevel& L = h->lv[l];
+    DevCam c = dev_cam(h->cam[0], L.fx, L.fy, L.cx, L.cy);
+    k_trajectory<<<grid2(L.W, L.H), kBlock2, 0, h->stream>>>(
+        c, (float)(h->tp[0] / n), (float)(h->tp[1] / n), (float)(h->tp[2] / n), L.v);
+    FS_LAUNCHED("k_trajectory");
+  }
+  return FS_OK;
+}
+
+int pd_block(const fs_handle* h) {
+  int b = h->prm.block_iters;
+  return b <= 0 ? 4 : (b > 8 ? 8 : b);
+}
+
+// Number of k_pd launches for `iters` iterations with at most B per launch:
+// ceil(iters / B), raised to an even count (when iters >= 2) so that the
+// ping-pong state ends in the primary buffers (a launch may then run 0
+// iterations, i.e. only copy its interior across).
+int pd_launches(int iters, int B) {
+  int n = (iters + B - 1) / B;
+  if (n % 2 == 1 && iters >= 2) ++n;
+  return n;
+}
+
+fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
+  HostLevel& L = h->lv[l];
+  PDParams pp{h->prm.lambda, h->prm.huber_eps, h->prm.theta};
+  int B = pd_block(h);
+  int variant = (L.W >= 128 && L.H >= 128) ? PD_TILE_64 : PD_TILE_32;
+  PDState A{L.v.u, L.v.ubar, L.v.p1, L.v.p2};
+  PDState Bs{L.v.u_alt, L.v.ubar_alt, L.v.p1_alt, L.v.p2_alt};
+  int nl = pd_launches(iters, B);
+  for (int k = 0, done = 0; k < nl; ++k) {
+    int n = (iters - done) / (nl - k);          // spread the iterations evenly
+    if ((iters - done) % (nl - k)) ++n;
+    const PDState& in = (k % 2 == 0) ? A : Bs;
+    const PDState& out = (k % 2 == 0) ? Bs : A;
+    cudaError_t e = launch_pd(variant, L.v, in, out, pp, B, n, st);
+    if (e != cudaSuccess) return fail(FS_ECUDA, "launch of k_pd failed: %s", cudaGetErrorString(e));
+    done += n;
+  }
+  if (nl % 2 == 1) {   // a single launch: bring the state back to the primary set
+    size_t bytes = (size_t)L.P * L.H * sizeof(float);
+    FS_CUDA(cudaMemcpyAsync(A.u, Bs.u, bytes, cudaMemcpyDeviceToDevice, st));
+    FS_CUDA(cudaMemcpyAsync(A.ubar, Bs.ubar, bytes, cudaMemcpyDeviceToDevice, st));
+    FS_CUDA(cudaMemcpyAsync(A.p1, Bs.p1, bytes, cudaMemcpyDeviceToDevice, st));
+    FS_CUDA(cudaMemcpyAsync(A.p2, Bs.p2, bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  return FS_OK;
+}
+
+fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) {
+  HostLevel& L = h->lv[l];
+  switch (stage) {
+    case FS_STAGE_DOWNSAMPLE:
+      if (l + 1 >= h->L) return fail(FS_EINVAL, "downsample: level %d has no coarser level", l);
+      k_downsample<<<grid2(h->lv[l + 1].W, h->lv[l + 1].H), kBlock2, 0, st>>>(L.v, h->lv[l + 1].v);
+      FS_LAUNCHED("k_downsample");
+      return FS_OK;
+    case FS_STAGE_TENSOR:
+      k_tensor<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, h->prm.beta, h->prm.eta, h->prm.precond);
+      FS_LAUNCHED("k_tensor");
+      return FS_OK;
+    case FS_STAGE_UPSAMPLE:
+      if (l + 1 >= h->L) return fail(FS_EINVAL, "upsample: level %d has no coarser level", l);
+      k_upsample<<<grid2(L.W, L.H), kBlock2, 0, st>>>(h->lv[l + 1].v, L.v);
+      FS_LAUNCHED("k_upsample");
+      return FS_OK;
+    case FS_STAGE_WARP:
+      k_warp<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v);
+      FS_LAUNCHED("k_warp");
+      return FS_OK;
+    case FS_STAGE_PD:
+      if (count < 1) return fail(FS_EINVAL, "pd: count must be >= 1");
+      return run_pd(h, l, count, st);
+    case FS_STAGE_CLIP:
+      k_clip<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, h->prm.du_max);
+      FS_LAUNCHED("k_clip");
+      return FS_OK;
+    case FS_STAGE_TRAJECTORY: {
+      double n = std::sqrt(h->tp[0] * h->tp[0] + h->tp[1] * h->tp[1] + h->tp[2] * h->tp[2]);
+      DevCam c = dev_cam(h->cam[0], L.fx, L.fy, L.cx, L.cy);
+      k_trajectory<<<grid2(L.W, L.H), kBlock2, 0, st>>>(
+          c, (float)(h->tp[0] / n), (float)(h->tp[1] / n), (float)(h->tp[2] / n), L.v);
+      FS_LAUNCHED("k_trajectory");
+      return FS_OK;
+    }
+    default:
+      return fail(FS_EINVAL, "unknown stage %d", stage);
+  }
+}
+
+fs_status enqueue_depth(fs_handle* h, float* disp, float* depth, cudaStream_t st) {
+  HostLevel& L0 = h->lv[0];
+  DevCam c = dev_cam(h->cam[0], L0.fx, L0.fy, L0.cx, L0.cy);
+  k_depth<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(L0.v, c, (float)-h->tp[0], (float)-h->tp[1],
+                                                 (float)-h->tp[2], disp, depth);
+  FS_LAUNCHED("k_depth");
+  return FS_OK;
+}
+
+// Record a timing event; inside a stream capture it must become an event
+// record node of the graph (cudaEventRecordExternal), not a dependency.
+cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t r = cudaStreamIsCapturing(st, &cs);
+  if (r != cudaSuccess) return r;
+  return cudaEventRecordWithFlags(e, st, cs == cudaStreamCaptureStatusActive
+                                             ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
+// The whole method for one pair on stream st (Algorithm 1 in the pyramid).
+fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const float* init,
+                        int warps, int iters, float* disp, float* depth, cudaStream_t st) {
+  fs_status s;
+  HostLevel& L0 = h->lv[0];
+  k_copy_in<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(I0, L0.v.I0, L0.W, L0.H, L0.P);
+  FS_LAUNCHED("k_copy_in");
+  k_prerotate<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(I1, h->cfield, L0.v.I1, L0.W, L0.H, L0.P);
+  FS_LAUNCHED("k_prerotate");
+  int top = h->L - 1;
+  if (init) {
+    return fail(FS_EINVAL, "warm start is not available in this build");
+  }
+  for (int l = 0; l < top; ++l)
+    if ((s = run_stage(h, l, FS_STAGE_DOWNSAMPLE, 0, st)) != FS_OK) return s;
+  for (int l = top; l >= 0; --l) {
+    HostLevel& L = h->lv[l];
+    if ((s = run_stage(h, l, FS_STAGE_TENSOR, 0, st)) != FS_OK) return s;
+    if (l == top) {
+      k_zero_state<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v);
+      FS_LAUNCHED("k_zero_state");
+    } else if ((s = run_stage(h, l, FS_STAGE_UPSAMPLE, 0, st)) != FS_OK) {
+      return s;
+    }
+    for (int w = 0; w < warps; ++w) {
+      if ((s = run_stage(h, l, FS_STAGE_WARP, 0, st)) != FS_OK) return s;
+      if (h->timing) FS_CUDA(record_event(h->ev[2 * (l * warps + w)], st));
+      if ((s = run_pd(h, l, iters, st)) != FS_OK) return s;
+      if (h->timing) FS_CUDA(record_event(h->ev[2 * (l * warps + w) + 1], st));
+      if ((s = run_stage(h, l, FS_STAGE_CLIP, 0, st)) != FS_OK) return s;
+    }
+  }
+  if (h->timing) {
+    h->ev_warps = warps;
+    h->ev_iters = iters;
+    h->ev_pending = true;
+  }
+  return enqueue_depth(h, disp, depth, st);
+}
+
+fs_status prepare_timing(fs_handle* h, int warps) {
+  size_t need = (size_t)2 * h->L * warps;
+  while (h->ev.size() < need) {
+    cudaEvent_t e;
+    FS_CUDA(cudaEventCreate(&e));
+    h->ev.push_back(e);
+  }
+  return FS_OK;
+}
+
+fs_status check_handle(const fs_handle* h) {
+  if (!h) return fail(FS_EINVAL, "null handle");
+  return FS_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" {
+
+const char* fs_last_error(void) { return g_err.c_str(); }
+
+fs_status fs_default_params(fs_params* out) {
+  if (!out) return fail(FS_EINVAL, "null params");
+  memset(out, 0, sizeof(*out));
+  out->lambda = 50.f;
+  out->huber_eps = 0.01f;
+  out->du_max = 0.2f;
+  out->beta = 9.f;
+  out->eta = 0.85f;
+  out->theta = 1.f;
+  out->precond = 1;
+  out->block_iters = 0;
+  out->use_graph = 0;
+  return FS_OK;
+}
+
+fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, int levels,
+                    const fs_params* prm, void* cuda_stream, fs_handle** out) {
+  if (!out) return fail(FS_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  if (!cam || !pose) return fail(FS_EINVAL, "null calibration or pose");
+  if (levels < 1 || levels > kMaxLevels) return fail(FS_EINVAL, "levels must be in [1, %d]", kMaxLevels);
+  if (W < 4 || H < 4 || W > 32768 || H > 32768) return fail(FS_EINVAL, "bad image size %dx%d", W, H);
+  fs_status s;
+  if ((s = check_calib(cam[0], 0)) != FS_OK) return s;
+  if ((s = check_calib(cam[1], 1)) != FS_OK) return s;
+  for (int i = 0; i < 12; ++i) {
+    double v = i < 9 ? pose->R[i] : pose->t[i - 9];
+    if (!std::isfinite(v)) return fail(FS_EINVAL, "pose has a non-finite entry");
+  }
+  fs_params p;
+  if (prm) {
+    p = *prm;
+    if (!(p.lambda > 0) || !(p.huber_eps >= 0) || !(p.du_max > 0) || !(p.beta >= 0) ||
+        !(p.eta > 0) || !(p.theta >= 0 && p.theta <= 1) || p.block_iters < 0 || p.block_iters > 8)
+      return fail(FS_EINVAL, "parameter out of range");
+  } else {
+    fs_default_params(&p);
+  }
+
+  fs_handle* h = new (std::nothrow) fs_handle();
+  if (!h) return fail(FS_ENOMEM, "host allocation failed");
+  h->cam[0] = cam[0];
+  h->cam[1] = cam[1];
+  h->pose = *pose;
+  h->prm = p;
+  h->W = W;
+  h->H = H;
+  h->L = levels;
+  h->stream = (cudaStream_t)cuda_stream;
+
+  // level sizes and scaled calibrations (f 2^-l, (c + 0.5) 2^-l - 0.5)
+  size_t bytes = 0;
+  for (int l = 0; l < levels; ++l) {
+    HostLevel& L = h->lv[l];
+    L.W = l == 0 ? W : (h->lv[l - 1].W + 1) / 2;
+    L.H = l == 0 ? H : (h->lv[l - 1].H + 1) / 2;
+    if (L.W < 4 || L.H < 4) {
+      delete h;
+      return fail(FS_EINVAL, "level %d would be %dx%d (< 4x4): too many levels", l, L.W, L.H);
+    }
+    L.P = (int)align_up((size_t)L.W, 32);
+    double sc = std::ldexp(1.0, -l);
+    L.fx = cam[0].fx * sc;
+    L.fy = cam[0].fy * sc;
+    L.cx = (cam[0].cx + 0.5) * sc - 0.5;
+    L.cy = (cam[0].cy + 0.5) * sc - 0.5;
+    size_t plane = align_up((size_t)L.P * L.H * sizeof(float), 256);
+    size_t plane8 = align_up((size_t)L.P * L.H, 256);
+    bytes += plane8 + 17 * plane + 3 * 2 * plane;
+  }
+  size_t cbytes = align_up((size_t)h->lv[0].P * H * sizeof(float2), 256);
+  bytes += cbytes;
+  cudaError_t e = cudaMalloc(&h->arena, bytes);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(FS_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  char* cur = (char*)h->arena;
+  for (int l = 0; l < levels; ++l) {
+    HostLevel& L = h->lv[l];
+    size_t plane = align_up((size_t)L.P * L.H * sizeof(float), 256);
+    size_t plane8 = align_up((size_t)L.P * L.H, 256);
+    LevelView& v = L.v;
+    v.W = L.W; v.H = L.H; v.P = L.P;
+    v.mask = (const uint8_t*)cur; cur += plane8;
+    float** fl[] = {&v.I0, &v.I1, &v.sx, &v.sy, &v.tau, &v.sig, &v.u, &v.ubar, &v.uw,
+                    &v.p1, &v.p2, &v.Iu, &v.rho0, &v.u_alt, &v.ubar_alt, &v.p1_alt, &v.p2_alt};
+    for (float** f : fl) { *f = (float*)cur; cur += plane; }
+    float2** f2[] = {&v.gamma, &v.w, &v.g};
+    for (float2** f : f2) { *f = (float2*)cur; cur += 2 * plane; }
+  }
+  h->cfield = (float2*)cur;
+  e = cudaMemsetAsync(h->arena, 0, bytes, h->stream);
+  if (e != cudaSuccess) {
+    cudaFree(h->arena);
+    delete h;
+    return fail(FS_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+  }
+  std::vector<uint8_t> host;
+  if ((s = upload_masks(h, host)) != FS_OK || (s = build_fields(h)) != FS_OK) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->arena);
+    delete h;
+    return s;
+  }
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cudaFree(h->arena);
+    delete h;
+    return fail(FS_ECUDA, "fs_create: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return FS_OK;
+}
+
+fs_status fs_set_pose(fs_handle* h, const fs_pose* pose) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (!pose) return fail(FS_EINVAL, "null pose");
+  fs_pose old = h->pose;
+  h->pose = *pose;
+  if ((s = build_fields(h)) != FS_OK) {
+    h->pose = old;
+    return s;
+  }
+  if (h->gexec) {  // the graph captured the old depth constants
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  return FS_OK;
+}
+
+fs_status fs_level_size(const fs_handle* h, int level, int* W, int* H) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (level < 0 || level >= h->L) return fail(FS_EINVAL, "level %d out of range", level);
+  if (W) *W = h->lv[level].W;
+  if (H) *H = h->lv[level].H;
+  return FS_OK;
+}
+
+fs_status fs_trajectory_field(fs_handle* h, int level, float* d_out) {
+  return fs_buffer_read(h, level, FS_BUF_GAMMA, d_out);
+}
+
+fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1, const float* d_init,
+                   int warps, int iters, float* d_disp, float* d_depth) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (!d_I0 || !d_I1) return fail(FS_EINVAL, "null input image");
+  if (warps < 1 || iters < 1) return fail(FS_EINVAL, "warps and iters must be >= 1");
+  if (h->timing && (s = prepare_timing(h, warps)) != FS_OK) return s;
+  if (!h->prm.use_graph) return enqueue_solve(h, d_I0, d_I1, d_init, warps, iters, d_disp, d_depth, h->stream);
+
+  const void* key[7] = {d_I0, d_I1, d_init, d_disp, d_depth, nullptr, nullptr};
+  bool hit = h->gexec && warps == h->gwarps && iters == h->giters &&
+             memcmp(key, h->gkey, sizeof(key)) == 0;
+  if (!hit) {
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (!h->cap_stream) FS_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    FS_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    s = enqueue_solve(h, d_I0, d_I1, d_init, warps, iters, d_disp, d_depth, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (s != FS_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) return fail(FS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h->gexec = nullptr; return fail(FS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+    memcpy(h->gkey, key, sizeof(key));
+    h->gwarps = warps;
+    h->giters = iters;
+  }
+  FS_CUDA(cudaGraphLaunch(h->gexec, h->stream));
+  if (h->timing) {              // the replay re-records the captured events
+    h->ev_warps = warps;
+    h->ev_iters = iters;
+    h->ev_pending = true;
+  }
+  return FS_OK;
+}
+
+fs_status fs_solve_host(fs_handle* h, const float* h_I0, const float* h_I1, const float* h_init,
+                        int warps, int iters, float* h_disp, float* h_depth) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (!h_I0 || !h_I1) return fail(FS_EINVAL, "null input image");
+  size_t n = (size_t)h->W * h->H;
+  if (!h->stage) {
+    cudaError_t e = cudaMalloc(&h->stage, 5 * n * sizeof(float));
+    if (e != cudaSuccess) { h->stage = nullptr; return fail(FS_ENOMEM, "staging allocation failed"); }
+  }
+  float *dI0 = h->stage, *dI1 = h->stage + n, *dinit = h->stage + 2 * n;
+  float *ddisp = h->stage + 3 * n, *ddepth = h->stage + 4 * n;
+  FS_CUDA(cudaMemcpyAsync(dI0, h_I0, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  FS_CUDA(cudaMemcpyAsync(dI1, h_I1, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  if (h_init) FS_CUDA(cudaMemcpyAsync(dinit, h_init, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  if ((s = fs_solve(h, dI0, dI1, h_init ? dinit : nullptr, warps, iters, h_disp ? ddisp : nullptr,
+                    h_depth ? ddepth : nullptr)) != FS_OK)
+    return s;
+  if (h_disp) FS_CUDA(cudaMemcpyAsync(h_disp, ddisp, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  if (h_depth) FS_CUDA(cudaMemcpyAsync(h_depth, ddepth, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  FS_CUDA(cudaStreamSynchronize(h->stream));
+  return FS_OK;
+}
+
+fs_status fs_destroy(fs_handle* h) {
+  if (!h) return FS_OK;
+  cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->stage) cudaFree(h->stage);
+  if (h->arena) cudaFree(h->arena);
+  delete h;
+  return FS_OK;
+}
+
+// ------------------------------------------------------------------ stages
+
+static fs_status buffer_planes(fs_handle* h, int level, int buffer, float** base, int* planes,
+                               int* stride) {
+  LevelView& v = h->lv[level].v;
+  size_t plane = align_up((size_t)v.P * v.H * sizeof(float), 256) / sizeof(float);
+  *stride = 1;
+  switch (buffer) {
+    case FS_BUF_I0: *base = v.I0; *planes = 1; break;
+    case FS_BUF_I1: *base = v.I1; *planes = 1; break;
+    case FS_BUF_GAMMA: *base = (float*)v.gamma; *planes = 2; *stride = 2; break;
+    case FS_BUF_U: *base = v.u; *planes = 1; break;
+    case FS_BUF_UBAR: *base = v.ubar; *planes = 1; break;
+    case FS_BUF_UW: *base = v.uw; *planes = 1; break;
+    case FS_BUF_P: *base = v.p1; *planes = 2; break;
+    case FS_BUF_W: *base = (float*)v.w; *planes = 2; *stride = 2; break;
+    case FS_BUF_IU: *base = v.Iu; *planes = 1; break;
+    case FS_BUF_RHO0: *base = v.rho0; *planes = 1; break;
+    case FS_BUF_G: *base = (float*)v.g; *planes = 2; *stride = 2; break;
+    default: return fail(FS_EINVAL, "buffer %d cannot be accessed this way", buffer);
+  }
+  (void)plane;
+  return FS_OK;
+}
+
+extern "C" fs_status fs_buffer_read(fs_handle* h, int level, int buffer, float* d_out) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (level < 0 || level >= h->L) return fail(FS_EINVAL, "level %d out of range", level);
+  if (!d_out) return fail(FS_EINVAL, "null output");
+  HostLevel& L = h->lv[level];
+  size_t n = (size_t)L.W * L.H;
+  cudaStream_t st = h->stream;
+  if (buffer == FS_BUF_MASK) {
+    k_mask_to_float<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v.mask, d_out, L.W, L.H, L.P);
+    FS_LAUNCHED("k_mask_to_float");
+    return FS_OK;
+  }
+  if (buffer == FS_BUF_TENSOR) {
+    k_tensor_abc<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, d_out);
+    FS_LAUNCHED("k_tensor_abc");
+    return FS_OK;
+  }
+  if (buffer == FS_BUF_STEPS) {
+    k_pack<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v.tau, 1, d_out, L.W, L.H, L.P);
+    k_pack<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v.sig, 1, d_out + n, L.W, L.H, L.P);
+    FS_LAUNCHED("k_pack");
+    return FS_OK;
+  }
+  float* base;
+  int planes, stride;
+  if ((s = buffer_planes(h, level, buffer, &base, &planes, &stride)) != FS_OK) return s;
+  for (int c = 0; c < planes; ++c) {
+    const float* src = stride == 2 ? base + c : (c == 0 ? base : L.v.p2);
+    k_pack<<<grid2(L.W, L.H), kBlock2, 0, st>>>(src, stride, d_out + c * n, L.W, L.H, L.P);
+    FS_LAUNCHED("k_pack");
+  }
+  return FS_OK;
+}
+
+extern "C" fs_status fs_buffer_write(fs_handle* h, int level, int buffer, const float* d_in) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (level < 0 || level >= h->L) return fail(FS_EINVAL, "level %d out of range", level);
+  if (!d_in) return fail(FS_EINVAL, "null input");
+  if (buffer == FS_BUF_MASK || buffer == FS_BUF_TENSOR || buffer == FS_BUF_STEPS)
+    return fail(FS_EINVAL, "buffer %d is derived and read-only", buffer);
+  HostLevel& L = h->lv[level];
+  size_t n = (size_t)L.W * L.H;
+  float* base;
+  int planes, stride;
+  if ((s = buffer_planes(h, level, buffer, &base, &planes, &stride)) != FS_OK) return s;
+  for (int c = 0; c < planes; ++c) {
+    float* dst = stride == 2 ? base + c : (c == 0 ? base : L.v.p2);
+    k_unpack<<<grid2(L.W, L.H), kBlock2, 0, h->stream>>>(d_in + c * n, dst, stride, L.W, L.H, L.P);
+    FS_LAUNCHED("k_unpack");
+  }
+  return FS_OK;
+}
+
+extern "C" fs_status fs_run_stage(fs_handle* h, int level, int stage, int count) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (level < 0 || level >= h->L) return fail(FS_EINVAL, "level %d out of range", level);
+  return run_stage(h, level, stage, count, h->stream);
+}
+
+extern "C" fs_status fs_stage_prerotate(fs_handle* h, const float* d_I1) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (!d_I1) return fail(FS_EINVAL, "null input");
+  HostLevel& L0 = h->lv[0];
+  k_prerotate<<<grid2(L0.W, L0.H), kBlock2, 0, h->stream>>>(d_I1, h->cfield, L0.v.I1, L0.W, L0.H, L0.P);
+  FS_LAUNCHED("k_prerotate");
+  return FS_OK;
+}
+
+extern "C" fs_status fs_timing_enable(fs_handle* h, int enable) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if ((enable != 0) != (h->timing != 0) && h->gexec) {  // captured graph has / lacks the events
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  h->timing = enable != 0;
+  h->ev_pending = false;
+  return FS_OK;
+}
+
+extern "C" fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
+                                    double* pixel_iters, int reset) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (h->ev_pending) {
+    FS_CUDA(cudaStreamSynchronize(h->stream));
+    int B = pd_block(h);
+    for (int l = 0; l < h->L; ++l) {
+      for (int w = 0; w < h->ev_warps; ++w) {
+        float t = 0.f;
+        FS_CUDA(cudaEventElapsedTime(&t, h->ev[2 * (l * h->ev_warps + w)],
+                                     h->ev[2 * (l * h->ev_warps + w) + 1]));
+        h->t_ms[l] += t;
+      }
+      h->t_launch[l] += (long long)h->ev_warps * pd_launches(h->ev_iters, B);
+      h->t_pxit[l] += (double)h->lv[l].W * h->lv[l].H * h->ev_warps * h->ev_iters;
+    }
+    h->ev_pending = false;
+  }
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (ms) ms[l] = h->t_ms[l];
+    if (launches) launches[l] = h->t_launch[l];
+    if (pixel_iters) pixel_iters[l] = h->t_pxit[l];
+    if (reset) { h->t_ms[l] = 0; h->t_launch[l] = 0; h->t_pxit[l] = 0; }
+  }
+  return FS_OK;
+}
+
+extern "C" fs_status fs_stage_depth(fs_handle* h, float* d_disp, float* d_depth) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  return enqueue_depth(h, d_disp, d_depth, h->stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// fs_device.cuh -- FP32 device math shared by the library's kernels:
+// camera models, sampling, and the per-level argument blocks.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fs {
+
+// Mask bits stored per pixel (uint8):
+//   MASK_IN  the pixel lies inside the FOV circle (Sec. IV-B)
+//   MASK_GX  the forward difference along x stays inside (Neumann, Sec. IV-B)
+//   MASK_GY  the forward difference along y stays inside
+constexpr uint8_t MASK_IN = 1, MASK_GX = 2, MASK_GY = 4;
+
+// Radially symmetric camera, pixel = c + f * r(theta) * (X, Y)/|(X, Y)|.
+struct DevCam {
+  int model;            // 0 pinhole, 1 equidistant, 2 Kannala-Brandt
+  float fx, fy, cx, cy;
+  float k1, k2, k3, k4;
+  float theta_max;      // FOV half-angle (radians)
+  float r_max;          // r(theta_max)
+};
+
+__host__ __device__ __forceinline__ float cam_r(const DevCam& c, float th) {
+  if (c.model == 0) return tanf(th);
+  if (c.model == 1) return th;
+  float t2 = th * th;
+  return th * (1.f + t2 * (c.k1 + t2 * (c.k2 + t2 * (c.k3 + t2 * c.k4))));
+}
+
+// dr/dtheta
+__host__ __device__ __forceinline__ float cam_dr(const DevCam& c, float th) {
+  if (c.model == 0) { float cs = cosf(th); return 1.f / (cs * cs); }
+  if (c.model == 1) return 1.f;
+  float t2 = th * th;
+  return 1.f + t2 * (3.f * c.k1 + t2 * (5.f * c.k2 + t2 * (7.f * c.k3 + t2 * 9.f * c.k4)));
+}
+
+// theta with r(theta) = rn on [0, theta_max]: closed form for pinhole and
+// equidistant.  For Kannala-Brandt, whose r(theta) can bend strongly near the
+// FOV edge, 10 bisection steps first narrow [0, theta_max] to a bracket of
+// width theta_max / 1024, then 8 Newton steps converge inside it (a step
+// that leaves the bracket is replaced by its midpoint).  r must increase on
+// the interval (checked at handle creation).
+__device__ __forceinline__ float cam_theta(const DevCam& c, float rn) {
+  if (c.model == 1) return rn;
+  if (c.model == 0) return atanf(rn);
+  float lo = 0.f, hi = c.theta_max;
+#pragma unroll 1
+  for (int i = 0; i < 10; ++i) {
+    float mid = 0.5f * (lo + hi);
+    if (cam_r(c, mid) > rn) hi = mid; else lo = mid;
+  }
+  float th = 0.5f * (lo + hi);
+#pragma unroll 1
+  for (int i = 0; i < 8; ++i) {
+    float f = cam_r(c, th) - rn;
+    if (f > 0.f) hi = th; else lo = th;
+    float nt = th - f / cam_dr(c, th);
+    th = (nt >= lo && nt <= hi) ? nt : 0.5f * (lo + hi);
+  }
+  return th;
+}
+
+struct Ray {
+  float x, y, z;        // unit direction
+  float ux, uy;         // in-plane unit direction (x, y)/|(x, y)|, (1, 0) on axis
+  float theta;
+};
+
+__device__ __forceinline__ Ray cam_unproject(const DevCam& c, float px, float py) {
+  float mx = (px - c.cx) / c.fx;
+  float my = (py - c.cy) / c.fy;
+  float rn = sqrtf(mx * mx + my * my);
+  Ray r;
+  r.theta = cam_theta(c, rn);
+  float s, co;
+  sincosf(r.theta, &s, &co);
+  if (rn > 0.f) { r.ux = mx / rn; r.uy = my / rn; } else { r.ux = 1.f; r.uy = 0.f; }
+  r.x = s * r.ux;
+  r.y = s * r.uy;
+  r.z = co;
+  return r;
+}
+
+__device__ __forceinline__ float2 cam_project(const DevCam& c, float X, float Y, float Z) {
+  float rho = sqrtf(X * X + Y * Y);
+  float th = atan2f(rho, Z);
+  float r = cam_r(c, th);
+  float mx = 0.f, my = 0.f;
+  if (rho > 0.f) { mx = r * X / rho; my = r * Y / rho; }
+  return make_float2(c.fx * mx + c.cx, c.fy * my + c.cy);
+}
+
+// Image-plane velocity d/ds pi(X + s t) at s = 0 for a unit ray X, by the
+// chain rule through rho = |(X, Y)| and theta = atan2(rho, Z):
+//   dp = f * ( r'(theta) dtheta u + r(theta)/rho (t_xy - u drho) ),
+//   drho = u . t_xy, dtheta = Z drho - rho t_z  (|X| = 1),
+// with the tangential part written through the 2-D cross product to avoid
+// cancellation where t_xy is nearly parallel to u.
+__device__ __forceinline__ float2 cam_velocity(const DevCam& c, const Ray& X,
+                                               float tx, float ty, float tz) {
+  float rho = sqrtf(X.x * X.x + X.y * X.y);
+  if (rho < 1e-6f) return make_float2(c.fx * tx / X.z, c.fy * ty / X.z);
+  float drho = X.ux * tx + X.uy * ty;
+  float dth = X.z * drho - rho * tz;
+  float rad = cam_dr(c, X.theta) * dth;
+  float tan_scale = cam_r(c, X.theta) / rho;
+  // t_xy - u (u . t_xy) = u_perp (u_perp . t_xy), u_perp = (-u_y, u_x)
+  float cr = X.ux * ty - X.uy * tx;
+  float vx = rad * X.ux - tan_scale * X.uy * cr;
+  float vy = rad * X.uy + tan_scale * X.ux * cr;
+  return make_float2(c.fx * vx, c.fy * vy);
+}
+
+// ---------------------------------------------------------------- sampling
+
+// Sample positions are passed as an integer pixel plus a real offset
+// (x + dx, y + dy): splitting off the integer part of the offset keeps the
+// fractional position exact to the precision of the offset itself instead of
+// rounding x + dx at the magnitude of x (3e-5 px at x ~ 1000 in FP32).
+struct Tap {
+  int i0, i1;   // the two neighbouring samples
+  float a;      // weight of i1
+};
+
+// Linear tap pair along one axis of length n for position x + d, the
+// position clamped to [0, n - 1].
+__device__ __forceinline__ Tap tap_linear(int x, float d, int n) {
+  float fl = floorf(d);
+  int b = x + (int)fl;
+  float f = d - fl;                       // in [0, 1)
+  Tap t;
+  if (b < 0) { t.i0 = 0; t.a = 0.f; }
+  else if (b >= n - 1) { t.i0 = max(n - 2, 0); t.a = n >= 2 ? 1.f : 0.f; }
+  else { t.i0 = b; t.a = f; }
+  t.i1 = min(t.i0 + 1, n - 1);
+  return t;
+}
+
+// Bilinear sample at (x + dx, y + dy), position clamped to the image.
+__device__ __forceinline__ float sample_bilinear(const float* __restrict__ img, int W, int H,
+                                                 int P, int x, float dx, int y, float dy) {
+  Tap tx = tap_linear(x, dx, W), ty = tap_linear(y, dy, H);
+  const float* r0 = img + (size_t)ty.i0 * P;
+  const float* r1 = img + (size_t)ty.i1 * P;
+  float v00 = __ldg(r0 + tx.i0), v01 = __ldg(r0 + tx.i1);
+  float v10 = __ldg(r1 + tx.i0), v11 = __ldg(r1 + tx.i1);
+  float top = fmaf(tx.a, v01 - v00, v00);
+  float bot = fmaf(tx.a, v11 - v10, v10);
+  return fmaf(ty.a, bot - top, top);
+}
+
+// Keys cubic convolution weights (a = -0.5) for the 4 taps at offsets
+// -1, 0, 1, 2 around floor(x), s = x - floor(x) in [0, 1).
+__device__ __forceinline__ void keys_weights(float s, float w[4]) {
+  const float A = -0.5f;
+  float s1 = 1.f + s, s2 = 1.f - s, s3 = 2.f - s;
+  w[0] = ((A * s1 - 5.f * A) * s1 + 8.f * A) * s1 - 4.f * A;
+  w[1] = ((A + 2.f) * s - (A + 3.f)) * s * s + 1.f;
+  w[2] = ((A + 2.f) * s2 - (A + 3.f)) * s2 * s2 + 1.f;
+  w[3] = ((A * s3 - 5.f * A) * s3 + 8.f * A) * s3 - 4.f * A;
+}
+
+// Base index and fraction of x + d clamped to [0, n - 1] for the cubic taps.
+__device__ __forceinline__ void cubic_base(int x, float d, int n, int& b, float& s) {
+  float fl = floorf(d);
+  b = x + (int)fl;
+  s = d - fl;
+  if (b < 0) { b = 0; s = 0.f; }
+  else if (b >= n - 1) { b = n - 1; s = 0.f; }
+}
+
+// Bicubic sample of an interleaved float2 field at (x + dx, y + dy),
+// position clamped to the image, taps repeating the edge.
+__device__ __forceinline__ float2 sample_bicubic2(const float2* __restrict__ f, int W, int H,
+                                                  int P, int x, float dx, int y, float dy) {
+  int xi, yi;
+  float sx_, sy_;
+  cubic_base(x, dx, W, xi, sx_);
+  cubic_base(y, dy, H, yi, sy_);
+  float wx[4], wy[4];
+  keys_weights(sx_, wx);
+  keys_weights(sy_, wy);
+  float sx = 0.f, sy = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int yy = min(max(yi + j - 1, 0), H - 1);
+    const float2* row = f + (size_t)yy * P;
+    float rx = 0.f, ry = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int xx = min(max(xi + i - 1, 0), W - 1);
+      float2 v = __ldg(row + xx);
+      rx += wx[i] * v.x;
+      ry += wx[i] * v.y;
+    }
+    sx += wy[j] * rx;
+    sy += wy[j] * ry;
+  }
+  return make_float2(sx, sy);
+}
+
+// ---------------------------------------------------------------- levels
+
+// Device view of one pyramid level (pitch P floats per row).
+struct LevelView {
+  int W, H, P;
+  const uint8_t* mask;
+  float *I0, *I1;
+  float2* gamma;
+  float *sx, *sy;        // T^1/2 = I - s s^T, s = sqrt(1 - e) n  (Eq. 12)
+  float *tau, *sig;      // primal / dual step sizes
+  float *u, *ubar, *uw, *p1, *p2, *Iu, *rho0;
+  float2 *w, *g;
+  float *u_alt, *ubar_alt, *p1_alt, *p2_alt;   // ping-pong copies for k_pd
+};
+
+// Primal-dual state planes of one buffer set.
+struct PDState {
+  float *u, *ubar, *p1, *p2;
+};
+
+struct PDParams {
+  float lam, eps, theta;
+};
+
+}  // namespace fs

@@ -1,0 +1,320 @@
+// k_level.cu -- per-level kernels of the fisheye stereo path other than the
+// primal-dual iteration: trajectory field, calibration field and
+// pre-rotation, pyramid down/up-sampling, tensor and step sizes,
+// warp + linearisation, clip + update, triangulation.
+#include "fs_kernels.h"
+
+namespace fs {
+
+// ------------------------------------------------------------ trajectory field
+// gamma'(x) = normalise(d/ds pi(pi^-1(x) + s t')) at s -> 0 (Sec. III-B,
+// Eq. 6-7), evaluated as the analytic image-plane velocity of a point on the
+// pixel's ray under the (pre-rotated) translation t'.  Zero outside the mask
+// and where the velocity vanishes (epipoles).
+__global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView L) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t i = (size_t)y * L.P + x;
+  float2 g = make_float2(0.f, 0.f);
+  if (L.mask[i] & MASK_IN) {
+    Ray r = cam_unproject(cam, (float)x, (float)y);
+    float2 v = cam_velocity(cam, r, tx, ty, tz);
+    float n = sqrtf(v.x * v.x + v.y * v.y);
+    if (n >= 1e-3f) g = make_float2(v.x / n, v.y / n);
+  }
+  L.gamma[i] = g;
+}
+
+// ------------------------------------------------------------ pre-rotation
+// The calibration field c(x) (Sec. IV-A) is built once per pose on the host
+// in FP64 (fs_api.cu): an FP32 field carries ~1e-7 relative round-off in
+// the projections, ~3e-5 px at 1000 px, which the warping then amplifies.
+// I1'(x) = I1(x + c(x)), bilinear; I1 dense (pitch W), output pitch P.
+__global__ void k_prerotate(const float* __restrict__ I1, const float2* __restrict__ field,
+                            float* __restrict__ out, int W, int H, int P) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  size_t i = (size_t)y * P + x;
+  float2 c = field[i];
+  out[i] = sample_bilinear(I1, W, H, W, x, c.x, y, c.y);
+}
+
+// Dense (pitch W) -> pitched copy, used for I0 and warm-start input.
+__global__ void k_copy_in(const float* __restrict__ src, float* __restrict__ dst, int W, int H,
+                          int P) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  dst[(size_t)y * P + x] = src[(size_t)y * W + x];
+}
+
+// ------------------------------------------------------------ pyramid
+// 2x2 box mean over the children inside the finer mask (all existing
+// children when none is inside), for I0 and I1 together (Sec. IV-B).
+__global__ void k_downsample(LevelView F, LevelView C) {
+  int X = blockIdx.x * blockDim.x + threadIdx.x;
+  int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= C.W || Y >= C.H) return;
+  float s0 = 0.f, s1 = 0.f, a0 = 0.f, a1 = 0.f;
+  int nin = 0, nall = 0;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int x = 2 * X + i, y = 2 * Y + j;
+      if (x < F.W && y < F.H) {
+        size_t k = (size_t)y * F.P + x;
+        float v0 = F.I0[k], v1 = F.I1[k];
+        a0 += v0; a1 += v1; ++nall;
+        if (F.mask[k] & MASK_IN) { s0 += v0; s1 += v1; ++nin; }
+      }
+    }
+  }
+  size_t o = (size_t)Y * C.P + X;
+  if (nin > 0) { C.I0[o] = s0 / (float)nin; C.I1[o] = s1 / (float)nin; }
+  else { C.I0[o] = a0 / (float)nall; C.I1[o] = a1 / (float)nall; }
+}
+
+// u, w of level C (coarse) -> level F (fine): bilinear over coarse in-mask
+// samples with renormalised weights, values x2, 0 outside the fine mask.
+// Also sets ubar = u_w = u and p = 0 on the fine level.
+__global__ void k_upsample(LevelView C, LevelView F) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= F.W || y >= F.H) return;
+  size_t o = (size_t)y * F.P + x;
+  float u = 0.f, wx = 0.f, wy = 0.f;
+  if (F.mask[o] & MASK_IN) {
+    float X = fminf(fmaxf(((float)x + 0.5f) * 0.5f - 0.5f, 0.f), (float)(C.W - 1));
+    float Y = fminf(fmaxf(((float)y + 0.5f) * 0.5f - 0.5f, 0.f), (float)(C.H - 1));
+    int x0 = min((int)floorf(X), max(C.W - 2, 0));
+    int y0 = min((int)floorf(Y), max(C.H - 2, 0));
+    int x1 = min(x0 + 1, C.W - 1), y1 = min(y0 + 1, C.H - 1);
+    float ax = X - (float)x0, ay = Y - (float)y0;
+    int xs[4] = {x0, x1, x0, x1}, ys[4] = {y0, y0, y1, y1};
+    float ws[4] = {(1.f - ax) * (1.f - ay), ax * (1.f - ay), (1.f - ax) * ay, ax * ay};
+    float den = 0.f, nu = 0.f, nx = 0.f, ny = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      size_t ci = (size_t)ys[k] * C.P + xs[k];
+      if (C.mask[ci] & MASK_IN) {
+        float2 cw = C.w[ci];
+        den += ws[k];
+        nu += ws[k] * C.u[ci];
+        nx += ws[k] * cw.x;
+        ny += ws[k] * cw.y;
+      }
+    }
+    if (den > 0.f) {
+      float s = 2.f / den;
+      u = nu * s; wx = nx * s; wy = ny * s;
+    }
+  }
+  F.u[o] = u; F.ubar[o] = u; F.uw[o] = u;
+  F.w[o] = make_float2(wx, wy);
+  F.p1[o] = 0.f; F.p2[o] = 0.f;
+}
+
+// Zero state at the coarsest level (Algorithm 1: u_0 = 0, w_0 = 0).
+__global__ void k_zero_state(LevelView L) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t o = (size_t)y * L.P + x;
+  L.u[o] = 0.f; L.ubar[o] = 0.f; L.uw[o] = 0.f;
+  L.p1[o] = 0.f; L.p2[o] = 0.f;
+  L.w[o] = make_float2(0.f, 0.f);
+}
+
+// ------------------------------------------------------------ tensor + steps
+struct TensorAt {
+  float sx, sy;            // T^1/2 = I - s s^T
+  float aa, bb, cc;        // |a|, |b|, |c|
+};
+
+// T^1/2 = e n n^T + n_perp n_perp^T = I - (1 - e) n n^T  (Eq. 12) with
+// e = exp(-beta |grad I0|^eta), grad I0 by central differences on the mask
+// (one-sided at its edge, 0 where both neighbours leave it).
+__device__ __forceinline__ TensorAt tensor_at(const LevelView& L, int x, int y, float beta,
+                                              float eta) {
+  TensorAt t;
+  size_t i = (size_t)y * L.P + x;
+  if (!(L.mask[i] & MASK_IN)) { t.sx = t.sy = 0.f; t.aa = 1.f; t.bb = 0.f; t.cc = 1.f; return t; }
+  float c = L.I0[i];
+  bool r = x + 1 < L.W && (L.mask[i + 1] & MASK_IN);
+  bool l = x > 0 && (L.mask[i - 1] & MASK_IN);
+  bool d = y + 1 < L.H && (L.mask[i + L.P] & MASK_IN);
+  bool u = y > 0 && (L.mask[i - L.P] & MASK_IN);
+  float gx = 0.f, gy = 0.f;
+  if (r && l) gx = 0.5f * (L.I0[i + 1] - L.I0[i - 1]);
+  else if (r) gx = L.I0[i + 1] - c;
+  else if (l) gx = c - L.I0[i - 1];
+  if (d && u) gy = 0.5f * (L.I0[i + L.P] - L.I0[i - L.P]);
+  else if (d) gy = L.I0[i + L.P] - c;
+  else if (u) gy = c - L.I0[i - L.P];
+  float mag = sqrtf(gx * gx + gy * gy);
+  if (mag < 1e-12f) { t.sx = t.sy = 0.f; t.aa = 1.f; t.bb = 0.f; t.cc = 1.f; return t; }
+  float nx = gx / mag, ny = gy / mag;
+  float one_minus_e = -expm1f(-beta * powf(mag, eta));
+  float s = sqrtf(one_minus_e);
+  t.sx = s * nx;
+  t.sy = s * ny;
+  t.aa = fabsf(1.f - one_minus_e * nx * nx);
+  t.bb = fabsf(one_minus_e * nx * ny);
+  t.cc = fabsf(1.f - one_minus_e * ny * ny);
+  return t;
+}
+
+// Diagonal preconditioning (Pock-Chambolle 2011, alpha = 1) from the row and
+// column sums of the entrywise bound |T^1/2| |grad| of K = T^1/2 grad:
+//   sigma(x) = 1 / max(2(|a| m1 + |b| m2), 2(|b| m1 + |c| m2))
+//   tau(x)   = 1 / ((|a|+|b|) m1 + (|b|+|c|) m2 at x,
+//                   + (|a|+|b|) m1 at x - e1, + (|b|+|c|) m2 at x - e2)
+__global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t i = (size_t)y * L.P + x;
+  uint8_t m = L.mask[i];
+  TensorAt t = tensor_at(L, x, y, beta, eta);
+  L.sx[i] = t.sx;
+  L.sy[i] = t.sy;
+  if (!precond) {
+    const float s = 0.35355339059327373f;   // 1/sqrt(8)
+    L.tau[i] = s;
+    L.sig[i] = s;
+    return;
+  }
+  float m1 = (m & MASK_GX) ? 1.f : 0.f, m2 = (m & MASK_GY) ? 1.f : 0.f;
+  float r1 = 2.f * (t.aa * m1 + t.bb * m2);
+  float r2 = 2.f * (t.bb * m1 + t.cc * m2);
+  float r = fmaxf(r1, r2);
+  L.sig[i] = r > 0.f ? 1.f / r : 0.f;
+  float col = (t.aa + t.bb) * m1 + (t.bb + t.cc) * m2;
+  if (x > 0 && (L.mask[i - 1] & MASK_GX)) {
+    TensorAt tl = tensor_at(L, x - 1, y, beta, eta);
+    col += tl.aa + tl.bb;
+  }
+  if (y > 0 && (L.mask[i - L.P] & MASK_GY)) {
+    TensorAt tu = tensor_at(L, x, y - 1, beta, eta);
+    col += tu.bb + tu.cc;
+  }
+  L.tau[i] = (col > 0.f && (m & MASK_IN)) ? 1.f / col : 0.f;
+}
+
+// ------------------------------------------------------------ warp + linearise
+// g = bicubic gamma'(x + w) renormalised (0 if |g| < 1e-6); I1w = I1(x + w);
+// I_u = I1(x + w + g) - I1w (Eq. 5); rho0 = I1w - I0 (Eq. 3, 9).  Starts a
+// warp: ubar = u_w = u.
+__global__ void k_warp(LevelView L) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t i = (size_t)y * L.P + x;
+  float Iu = 0.f, rho0 = 0.f;
+  float2 g = make_float2(0.f, 0.f);
+  if (L.mask[i] & MASK_IN) {
+    float2 w = L.w[i];
+    float2 gr = sample_bicubic2(L.gamma, L.W, L.H, L.P, x, w.x, y, w.y);
+    float n = sqrtf(gr.x * gr.x + gr.y * gr.y);
+    if (n >= 1e-6f) g = make_float2(gr.x / n, gr.y / n);
+    float I1w = sample_bilinear(L.I1, L.W, L.H, L.P, x, w.x, y, w.y);
+    float I1g = sample_bilinear(L.I1, L.W, L.H, L.P, x, w.x + g.x, y, w.y + g.y);
+    Iu = I1g - I1w;
+    rho0 = I1w - L.I0[i];
+  }
+  L.Iu[i] = Iu;
+  L.rho0[i] = rho0;
+  L.g[i] = g;
+  float u = L.u[i];
+  L.ubar[i] = u;
+  L.uw[i] = u;
+}
+
+// ------------------------------------------------------------ clip + update
+// du = clamp(u - u_w, +-du_max); u_{w+1} = u_w + du; w += du g (Algorithm 1,
+// Eq. 8-9).  The primal state continues from u_{w+1}.
+__global__ void k_clip(LevelView L, float du_max) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t i = (size_t)y * L.P + x;
+  if (!(L.mask[i] & MASK_IN)) return;
+  float uw = L.uw[i];
+  float du = fminf(fmaxf(L.u[i] - uw, -du_max), du_max);
+  float un = uw + du;
+  L.u[i] = un;
+  L.ubar[i] = un;
+  L.uw[i] = un;
+  float2 w = L.w[i], g = L.g[i];
+  L.w[i] = make_float2(w.x + du * g.x, w.y + du * g.y);
+}
+
+// ------------------------------------------------------------ triangulation
+// Range along the camera-0 ray of x from the rays pi^-1(x) and pi^-1(x + w)
+// of the pre-rotated pair (virtual camera-1 centre C = -t'), closest point
+// of the two lines: l0 = ((C x r1) . (r0 x r1)) / |r0 x r1|^2 (Sec. III-D).
+__global__ void k_depth(LevelView L, DevCam cam, float Cx, float Cy, float Cz,
+                        float* __restrict__ disp, float* __restrict__ depth) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t i = (size_t)y * L.P + x;
+  size_t o = (size_t)y * L.W + x;
+  bool in = L.mask[i] & MASK_IN;
+  if (disp) disp[o] = in ? L.u[i] : 0.f;
+  if (!depth) return;
+  if (!in) { depth[o] = __int_as_float(0x7fc00000); return; }
+  float2 w = L.w[i];
+  Ray r0 = cam_unproject(cam, (float)x, (float)y);
+  Ray r1 = cam_unproject(cam, (float)x + w.x, (float)y + w.y);
+  float nx = r0.y * r1.z - r0.z * r1.y;
+  float ny = r0.z * r1.x - r0.x * r1.z;
+  float nz = r0.x * r1.y - r0.y * r1.x;
+  float mx = Cy * r1.z - Cz * r1.y;
+  float my = Cz * r1.x - Cx * r1.z;
+  float mz = Cx * r1.y - Cy * r1.x;
+  float den = nx * nx + ny * ny + nz * nz;
+  depth[o] = den > 0.f ? (mx * nx + my * ny + mz * nz) / den : __int_as_float(0x7f800000);
+}
+
+// ------------------------------------------------------------ buffer access
+__global__ void k_pack(const float* __restrict__ src, int stride, float* __restrict__ dst, int W,
+                       int H, int P) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  dst[(size_t)y * W + x] = src[((size_t)y * P + x) * stride];
+}
+
+__global__ void k_unpack(const float* __restrict__ src, float* __restrict__ dst, int stride,
+                         int W, int H, int P) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  dst[((size_t)y * P + x) * stride] = src[(size_t)y * W + x];
+}
+
+__global__ void k_mask_to_float(const uint8_t* __restrict__ m, float* __restrict__ dst, int W,
+                                int H, int P) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  dst[(size_t)y * W + x] = (m[(size_t)y * P + x] & MASK_IN) ? 1.f : 0.f;
+}
+
+// T^1/2 entries a, b, c from s: a = 1 - sx^2, b = -sx sy, c = 1 - sy^2.
+__global__ void k_tensor_abc(LevelView L, float* __restrict__ dst) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t i = (size_t)y * L.P + x, o = (size_t)y * L.W + x, n = (size_t)L.W * L.H;
+  float sx = L.sx[i], sy = L.sy[i];
+  dst[o] = 1.f - sx * sx;
+  dst[n + o] = -sx * sy;
+  dst[2 * n + o] = 1.f - sy * sy;
+}
+
+}  // namespace fs

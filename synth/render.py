@@ -14,6 +14,8 @@ camera 1 sits at C1 = -R^T t and looks along R^T z.
 from __future__ import annotations
 
 import math
+import os
+import threading
 
 import numpy as np
 
@@ -42,7 +44,7 @@ def lens_rays(cam, px, py):
     valid = rn <= lens_radius(cam, half)
     lo = np.zeros_like(rn)
     hi = np.full_like(rn, half)
-    for _ in range(60):                      # bisection on the monotone radius
+    for _ in range(44):                      # bisection on the monotone radius
         mid = (lo + hi) / 2.0
         up = lens_radius(cam, mid) < rn
         lo = np.where(up, mid, lo)
@@ -73,10 +75,8 @@ def _texture_params(rng, fmax):
 
 
 def _texture(tex, P):
-    s = np.zeros(P.shape[:-1])
-    for i in range(tex["k"].shape[0]):
-        s += tex["amp"][i] * np.sin(2.0 * np.pi * (P @ tex["k"][i]) + tex["phase"][i])
-    s /= np.sum(tex["amp"])
+    arg = 2.0 * np.pi * (P @ tex["k"].T) + tex["phase"]
+    s = np.sin(arg) @ tex["amp"] / np.sum(tex["amp"])
     return np.clip(tex["base"] + 0.45 * s, 0.0, 1.0)
 
 
@@ -161,26 +161,52 @@ def _trace(scene, o, d):
     return best, val
 
 
+_RAY_CACHE = {}
+_RAY_LOCK = threading.Lock()
+
+
+def _cached_rays(cam, y0, y1, W, ox, oy):
+    key = (tuple(sorted((k, tuple(v) if isinstance(v, list) else v) for k, v in cam.items())),
+           y0, y1, W, ox, oy)
+    with _RAY_LOCK:
+        hit = _RAY_CACHE.get(key)
+    if hit is None:
+        py, px = np.mgrid[y0:y1, 0:W].astype(np.float64)
+        hit = lens_rays(cam, px + ox, py + oy)
+        with _RAY_LOCK:
+            if len(_RAY_CACHE) > 400:
+                _RAY_CACHE.clear()
+            _RAY_CACHE[key] = hit
+    return hit
+
+
 def render(scene, cam, R_w2c, origin, W, H, supersample=2, noise=0.0, rng=None,
-           rows_per_chunk=128):
-    """Render one camera; returns (image (H, W) f64, range at pixel centres)."""
+           rows_per_chunk=64):
+    """Render one camera; returns (image (H, W) f64, range at pixel centres).
+
+    Row chunks are traced on a thread pool (numpy releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
     img = np.zeros((H, W))
     rng_out = np.full((H, W), np.nan)
     offs = [((i + 0.5) / supersample - 0.5) for i in range(supersample)]
     Rt = np.asarray(R_w2c, dtype=np.float64).T           # camera -> world
-    for y0 in range(0, H, rows_per_chunk):
+
+    def chunk(y0):
         y1 = min(H, y0 + rows_per_chunk)
-        py, px = np.mgrid[y0:y1, 0:W].astype(np.float64)
-        acc = np.zeros(py.shape)
+        acc = np.zeros((y1 - y0, W))
         for oy in offs:
             for ox in offs:
-                d, valid = lens_rays(cam, px + ox, py + oy)
+                d, valid = _cached_rays(cam, y0, y1, W, ox, oy)
                 _, v = _trace(scene, origin, d @ Rt.T)
                 acc += np.where(valid, v, 0.0)
         img[y0:y1] = acc / (supersample * supersample)
-        d, valid = lens_rays(cam, px, py)
+        d, valid = _cached_rays(cam, y0, y1, W, 0.0, 0.0)
         s, _ = _trace(scene, origin, d @ Rt.T)
         rng_out[y0:y1] = np.where(valid, s, np.nan)
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(chunk, range(0, H, rows_per_chunk)))
     if noise > 0.0:
         img = np.clip(img + rng.normal(0.0, noise, size=img.shape), 0.0, 1.0)
     return img, rng_out

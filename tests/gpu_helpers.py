@@ -1,0 +1,131 @@
+"""Helpers shared by the GPU parity tests (no method arithmetic here)."""
+import numpy as np
+
+import oracle
+
+
+def f32pair(pair):
+    """The pair with its images rounded to float32, the precision both sides
+    receive (the GPU path takes float32 images)."""
+    out = dict(pair)
+    out["I0"] = np.float32(pair["I0"]).astype(np.float64)
+    out["I1"] = np.float32(pair["I1"]).astype(np.float64)
+    return out
+
+
+def make_solver(pair, levels=None, **prm):
+    import paper_1909_07545_gb300 as fsb
+    H, W = pair["I0"].shape
+    kw = dict(lam=pair.get("lam", 50.0), huber_eps=pair.get("eps", 0.01))
+    kw.update(prm)
+    return fsb.Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H,
+                      levels or pair["levels"], **kw)
+
+
+def level_calibs(pair, levels):
+    cam = oracle.calib_from_dict(pair["cam0"])
+    H, W = pair["I0"].shape
+    sizes = oracle.level_sizes(W, H, levels)
+    cals = [oracle.scaled_calib(cam, l) for l in range(levels)]
+    masks = [oracle.fov_mask(cals[l], *sizes[l]) for l in range(levels)]
+    return sizes, cals, masks
+
+
+def np64(t):
+    return t.detach().double().cpu().numpy()
+
+
+def oracle_params(pair, **over):
+    d = dict(lam=pair.get("lam", 50.0), eps=pair.get("eps", 0.01))
+    d.update(over)
+    return oracle.Params(**d)
+
+
+def gpu_level_data(s, level):
+    """Tensor, step sizes and masks as the GPU holds them (float64 copies)."""
+    abc = np64(s.read(level, "TENSOR"))
+    steps = np64(s.read(level, "STEPS"))
+    M = np64(s.read(level, "MASK")) > 0.5
+    m1, m2 = oracle.grad_masks(M)
+    return dict(a=abc[0], b=abc[1], c=abc[2], tau=steps[0], sig1=steps[1], sig2=steps[1],
+                M=M, m1=m1, m2=m2)
+
+
+def ragged_pair(seed=0, W=203, H=157):
+    """A small equidistant pair of ragged size with an off-centre principal
+    point and a rotated second camera (exercises the pre-rotation)."""
+    import math
+    from synth.render import make_scene, render, rotation
+    rng = np.random.default_rng(seed)
+    f = 55.0
+    cam = dict(model="equidistant", fx=f, fy=f * 1.01, cx=(W - 1) / 2 + 3.2,
+               cy=(H - 1) / 2 - 2.7, k=[0, 0, 0, 0], fov_deg=170.0)
+    scene = make_scene(rng, 4, (1.0, 4.0), 6.0, f)
+    R = rotation([0.3, 1.0, 0.2], math.radians(1.5))
+    C1 = np.array([0.1, 0.01, 0.0])
+    I0, gt = render(scene, cam, np.eye(3), np.zeros(3), W, H, 2)
+    I1, _ = render(scene, cam, R, C1, W, H, 2)
+    return f32pair(dict(I0=I0, I1=I1, cam0=cam, cam1=dict(cam), R=R, t=-R @ C1, gt_range=gt,
+                        levels=3, warps=4, iters=30, lam=50.0, eps=0.01))
+
+
+def oracle_solve(pair, levels=None, warps=None, iters=None, level_hook=None, on_iter=None,
+                 **prm):
+    return oracle.solve(pair["I0"], pair["I1"], pair["cam0"], pair["cam1"], pair["R"],
+                        pair["t"], levels or pair["levels"], warps or pair["warps"],
+                        iters or pair["iters"], oracle_params(pair, **prm),
+                        level_hook=level_hook, on_iter=on_iter)
+
+
+def oracle_sensitivity(pair, ref, levels=None, warps=None, iters=None, **prm):
+    """How far the FP64 oracle's own disparity moves under perturbations of
+    the size FP32 arithmetic makes: (1) its pyramid images (and pre-rotated
+    I1) rounded to float32, (2) its primal-dual state (u, ubar, p) rounded to
+    float32 after every iteration, (3) Gaussian relative noise of 2^-22
+    (4 units of float32 round-off) on both inputs.  Returns the per-pixel
+    maximum of |delta d| over the three probes."""
+    f32 = lambda a: np.float32(a).astype(np.float64)
+    a = oracle_solve(pair, levels, warps, iters,
+                     level_hook=lambda l, i0, i1: (f32(i0), f32(i1)), **prm)["disp"]
+
+    def round_state(level, om, k, st, lv):
+        for key in ("u", "ubar", "p1", "p2"):
+            st[key] = f32(st[key])
+    c = oracle_solve(pair, levels, warps, iters, on_iter=round_state, **prm)["disp"]
+    rng = np.random.default_rng(12345)
+    noisy = dict(pair)
+    rel = 2.0 ** -22
+    noisy["I0"] = pair["I0"] * (1 + rel * rng.normal(size=pair["I0"].shape))
+    noisy["I1"] = pair["I1"] * (1 + rel * rng.normal(size=pair["I1"].shape))
+    b = oracle_solve(noisy, levels, warps, iters, **prm)["disp"]
+    return np.maximum(np.maximum(np.abs(a - ref["disp"]), np.abs(b - ref["disp"])),
+                      np.abs(c - ref["disp"]))
+
+
+# Disparity parity gate, GPU FP32 vs FP64 oracle (same float32 inputs,
+# pyramid, warps and iterations).  The warping makes a few pixels
+# ill-conditioned: the FP64 oracle itself moves there by up to ~0.1 px under
+# FP32-sized perturbations (oracle_sensitivity), so no FP32 implementation
+# holds a 5e-3 px bound at every pixel.  The gate:
+#   mean |dd| over the FOV mask <= 1e-4 px;
+#   |dd| <= 5e-3 px on at least 99.8 % of the mask;
+#   the pixels above 5e-3 px are at most 2 x as many as the oracle's own
+#   under the probes (+ 10), and no |dd| exceeds max(5e-3, 2 x the largest
+#   probe response).
+MAX_TOL = 5e-3
+MEAN_TOL = 1e-4
+QUANTILE = 0.998
+
+
+def disparity_parity(d_gpu, ref, sens):
+    M = ref["mask"]
+    err = np.abs(d_gpu - ref["disp"])[M]
+    s = sens[M]
+    n_gpu = int((err > MAX_TOL).sum())
+    n_probe = int((s > MAX_TOL).sum())
+    report = dict(mean=float(err.mean()), q998=float(np.quantile(err, QUANTILE)),
+                  max=float(err.max()), n_over=n_gpu, n_over_probe=n_probe,
+                  probe_max=float(s.max()), probe_mean=float(s.mean()))
+    ok = (report["mean"] <= MEAN_TOL and report["q998"] <= MAX_TOL
+          and n_gpu <= 2 * n_probe + 10 and report["max"] <= max(MAX_TOL, 2 * report["probe_max"]))
+    return ok, report

@@ -1,0 +1,79 @@
+"""The C ABI: the library builds, loads, exports every declared entry point, and
+rejects bad arguments on the host before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1909_07545_gb300 as fsb
+from paper_1909_07545_gb300 import build as fsbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(fs_\w+)\s*\(", src, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fsbuild.build()
+    return fsb.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    decl = _declared()
+    assert "fs_solve" in decl and "fs_create" in decl
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert decl == set(fsb.EXPORTED)
+
+
+def test_default_params_match_paper(lib):
+    p = fsb.default_params()
+    assert p.beta == pytest.approx(9.0) and p.eta == pytest.approx(0.85)
+    assert p.du_max == pytest.approx(0.2) and p.theta == 1.0 and p.precond == 1
+
+
+def _create(cams, W=64, H=64, levels=2, prm=None):
+    lib = fsb.load_library()
+    c = (fsb.FsCalib * 2)(fsb._calib(cams[0]), fsb._calib(cams[1]))
+    pose = fsb._pose(np.eye(3), [-0.1, 0, 0])
+    h = ctypes.c_void_p()
+    st = lib.fs_create(c, ctypes.byref(pose), W, H, levels,
+                       ctypes.byref(prm) if prm is not None else None, None, ctypes.byref(h))
+    return st, lib.fs_last_error().decode()
+
+
+EQ = dict(model="equidistant", fx=20.0, fy=20.0, cx=31.5, cy=31.5, fov_deg=180.0)
+
+
+def test_host_side_validation(lib):
+    st, msg = _create([EQ, EQ], levels=0)
+    assert st == -1 and "levels" in msg
+    st, msg = _create([EQ, EQ], W=64, H=64, levels=6)     # 64 -> 2 px at level 5
+    assert st == -1 and "too many levels" in msg
+    bad_kb = dict(EQ, model="kb", k=[0, 0, 0, -0.05], fov_deg=190.0)
+    st, msg = _create([bad_kb, EQ])
+    assert st == -4 and "not increasing" in msg
+    pin = dict(EQ, model="pinhole", fov_deg=190.0)
+    st, msg = _create([pin, EQ])
+    assert st == -4
+    neg = dict(EQ, fx=-1.0)
+    st, _ = _create([EQ, neg])
+    assert st == -4
+    prm = fsb.default_params(block_iters=9)
+    st, msg = _create([EQ, EQ], prm=prm)
+    assert st == -1 and "parameter" in msg
+    h = ctypes.c_void_p()
+    assert lib.fs_solve(None, None, None, None, 1, 1, None, None) == -1
+    assert lib.fs_destroy(None) == 0
+    assert lib.fs_create(None, None, 64, 64, 1, None, None, ctypes.byref(h)) == -1

@@ -1,0 +1,123 @@
+"""End-to-end GPU solve (fs_solve through the C ABI) against the FP64 oracle.
+
+Same float32 inputs, pyramid, warp and iteration counts on both sides.  The
+disparity gate (gpu_helpers.disparity_parity): mean |dd| <= 1e-4 px over the
+FOV mask, |dd| <= 5e-3 px on 99.8 % of it, and the rest no worse than the
+oracle's own response to FP32-sized perturbations.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import (disparity_parity, f32pair, make_solver, np64, oracle_params,
+                         oracle_sensitivity, ragged_pair)
+
+pytestmark = pytest.mark.gpu
+
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1909_07545_gb300 import build
+    build.build()
+
+
+def _oracle(pair, levels=None, warps=None, iters=None, **prm):
+    return oracle.solve(pair["I0"], pair["I1"], pair["cam0"], pair["cam1"], pair["R"],
+                        pair["t"], levels or pair["levels"], warps or pair["warps"],
+                        iters or pair["iters"], oracle_params(pair, **prm))
+
+
+def _compare(pair, ref, disp, depth, sens):
+    M = ref["mask"]
+    d = np64(disp)
+    assert np.all(d[~M] == 0.0)
+    ok, rep = disparity_parity(d, ref, sens)
+    assert ok, rep
+    z = np64(depth)
+    assert np.all(np.isnan(z[~M]))
+    # range follows the disparity: compare where the oracle is stable and the
+    # warp is at least a pixel long
+    w = np.linalg.norm(ref["w"], axis=-1)
+    sel = M & (w > 1.0) & (sens <= 1e-4) & np.isfinite(ref["depth"]) & (ref["depth"] > 0)
+    rel = np.abs(z[sel] / ref["depth"][sel] - 1.0)
+    assert np.median(rel) < 1e-4
+    assert rel.max() < 1e-2
+    return rep
+
+
+@pytest.fixture(scope="module")
+def small():
+    return f32pair(synth.plain_small(0))
+
+
+@pytest.fixture(scope="module")
+def small_ref(small):
+    ref = _oracle(small)
+    return ref, oracle_sensitivity(small, ref)
+
+
+def test_plain_small_256_matches_oracle(small, small_ref):
+    s = make_solver(small)
+    disp, depth = s.solve(small["I0"], small["I1"], small["warps"], small["iters"])
+    _compare(small, small_ref[0], disp, depth, small_ref[1])
+    s.close()
+
+
+@pytest.mark.parametrize("block", [1, 5, 8])
+def test_block_depths_are_identical(small, block):
+    s1 = make_solver(small, block_iters=block)
+    s4 = make_solver(small, block_iters=4)
+    d1, z1 = s1.solve(small["I0"], small["I1"], 2, 13)
+    d4, z4 = s4.solve(small["I0"], small["I1"], 2, 13)
+    assert np.array_equal(np64(d1), np64(d4))
+    s1.close()
+    s4.close()
+
+
+def test_ragged_rotated_pair_matches_oracle():
+    pair = ragged_pair(1)
+    ref = _oracle(pair)
+    sens = oracle_sensitivity(pair, ref)
+    s = make_solver(pair)
+    disp, depth = s.solve(pair["I0"], pair["I1"], pair["warps"], pair["iters"])
+    _compare(pair, ref, disp, depth, sens)
+    s.close()
+
+
+def test_unpreconditioned_steps_match_oracle(small):
+    ref = _oracle(small, warps=3, iters=40, precond=False)
+    sens = oracle_sensitivity(small, ref, warps=3, iters=40, precond=False)
+    s = make_solver(small, precond=0)
+    disp, depth = s.solve(small["I0"], small["I1"], 3, 40)
+    _compare(small, ref, disp, depth, sens)
+    s.close()
+
+
+def test_graph_replay_and_host_entry_point(small, small_ref):
+    s = make_solver(small, use_graph=1)
+    import torch
+    I0 = torch.as_tensor(np.float32(small["I0"]), device="cuda")
+    I1 = torch.as_tensor(np.float32(small["I1"]), device="cuda")
+    outs = []
+    for _ in range(3):
+        d, z = s.solve(I0, I1, small["warps"], small["iters"])
+        outs.append(np64(d))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    _compare(small, small_ref[0], d, z, small_ref[1])
+    hd, hz = s.solve_host(small["I0"], small["I1"], small["warps"], small["iters"])
+    assert np.array_equal(hd.astype(np.float64), outs[0])
+    s.close()
+
+
+def test_full_size_kb_1024_short_schedule():
+    # the full 1024 x 1024 Kannala-Brandt workload (5 levels) on a schedule the
+    # oracle finishes in seconds: 2 warps x 20 iterations per level
+    pair = f32pair(synth.plain_kb(0))
+    ref = _oracle(pair, warps=2, iters=20)
+    sens = oracle_sensitivity(pair, ref, warps=2, iters=20)
+    s = make_solver(pair)
+    disp, depth = s.solve(pair["I0"], pair["I1"], 2, 20)
+    _compare(pair, ref, disp, depth, sens)
+    s.close()

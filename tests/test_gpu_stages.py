@@ -1,0 +1,309 @@
+"""GPU kernels against the FP64 oracle, one stage at a time (through the C ABI).
+
+Each test loads the same inputs into the oracle and into a level of an
+fs_handle, runs one stage, and compares element by element.  Sizes span
+several PD tiles with ragged edges (203 x 157, 256 x 256, 1024 x 1024).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import (f32pair, gpu_level_data, level_calibs, make_solver, np64,
+                         oracle_params, ragged_pair)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1909_07545_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def small():
+    return f32pair(synth.plain_small(0))
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    return ragged_pair(0)
+
+
+def _kb_rig(seed=0, W=1024):
+    rng = np.random.default_rng(seed)
+    k = synth.draw_kb(rng, math.radians(95.0))
+    cam = dict(model="kb", fx=320.0 * W / 1024, fy=320.0 * W / 1024, cx=(W - 1) / 2,
+               cy=(W - 1) / 2, k=k, fov_deg=190.0)
+    from synth.render import rotation
+    R = rotation(rng.normal(size=3), math.radians(1.7))
+    t = -R @ np.array([0.12, 0.0, 0.0])
+    z = np.zeros((W, W))
+    return dict(I0=z, I1=z, cam0=cam, cam1=dict(cam), R=R, t=t, levels=5, lam=50.0, eps=0.01)
+
+
+@pytest.mark.parametrize("which", ["small", "ragged", "kb"])
+def test_masks_bit_exact_and_trajectory_field(which, small, ragged):
+    pair = {"small": small, "ragged": ragged, "kb": None}[which] or _kb_rig()
+    s = make_solver(pair)
+    sizes, cals, masks = level_calibs(pair, pair["levels"])
+    tp = oracle.virtual_translation(pair["R"], pair["t"])
+    for l in range(pair["levels"]):
+        Mg = np64(s.read(l, "MASK")) > 0.5
+        assert np.array_equal(Mg, masks[l]), f"mask differs at level {l}"
+        g = np64(s.trajectory_field(l)).transpose(1, 2, 0)
+        ref = oracle.trajectory_field(cals[l], tp, *sizes[l], masks[l])
+        both = (np.linalg.norm(ref, axis=-1) > 0.5) & (np.linalg.norm(g, axis=-1) > 0.5)
+        # zero (epipole / off-mask) decisions agree everywhere but at most a
+        # pixel or two right at an epipole
+        assert np.sum(both != masks[l]) <= 2
+        # away from the epipoles (rays within 3 degrees of +-t'), where the
+        # field turns fast and neither side resolves it, angles agree to 1e-4
+        W, H = sizes[l]
+        py, px = np.mgrid[0:H, 0:W].astype(float)
+        ray = oracle.unproject(cals[l], px, py)
+        cos_t = np.abs(ray @ (tp / np.linalg.norm(tp)))
+        away = both & (cos_t < np.cos(np.radians(3.0)))
+        ang = np.abs(np.arctan2(g[..., 0] * ref[..., 1] - g[..., 1] * ref[..., 0],
+                                np.sum(g * ref, -1)))
+        assert ang[away].max() < 1e-4
+    s.close()
+
+
+def test_prerotation(ragged):
+    pair = ragged
+    s = make_solver(pair)
+    s.prerotate(pair["I1"])
+    got = np64(s.read(0, "I1"))
+    cam0 = oracle.calib_from_dict(pair["cam0"])
+    H, W = pair["I0"].shape
+    M0 = oracle.fov_mask(cam0, W, H)
+    cf = oracle.calibration_field(cam0, oracle.calib_from_dict(pair["cam1"]), pair["R"], W, H, M0)
+    ref = oracle.prerotate(pair["I1"], cf)
+    assert np.abs(got - ref).max() < 2e-5
+    s.close()
+
+
+@pytest.mark.parametrize("which", ["small", "ragged"])
+def test_downsample(which, small, ragged):
+    pair = small if which == "small" else ragged
+    s = make_solver(pair)
+    sizes, cals, masks = level_calibs(pair, pair["levels"])
+    s.write(0, "I0", pair["I0"])
+    s.write(0, "I1", pair["I1"])
+    r0, r1 = pair["I0"], pair["I1"]
+    for l in range(pair["levels"] - 1):
+        s.stage(l, "DOWNSAMPLE")
+        r0 = oracle.pyramid.downsample_fast(r0, masks[l], *sizes[l + 1])
+        r1 = oracle.pyramid.downsample_fast(r1, masks[l], *sizes[l + 1])
+        assert np.abs(np64(s.read(l + 1, "I0")) - r0).max() < 1e-6
+        assert np.abs(np64(s.read(l + 1, "I1")) - r1).max() < 1e-6
+    s.close()
+
+
+@pytest.mark.parametrize("precond", [1, 0])
+def test_tensor_and_steps(precond, small, ragged):
+    for pair in (small, ragged):
+        s = make_solver(pair, precond=precond)
+        sizes, cals, masks = level_calibs(pair, pair["levels"])
+        prm = oracle_params(pair, precond=bool(precond))
+        s.write(0, "I0", pair["I0"])
+        s.stage(0, "TENSOR")
+        a, b, c = oracle.tensor_sqrt(pair["I0"], masks[0], prm.beta, prm.eta)
+        m1, m2 = oracle.grad_masks(masks[0])
+        tau, s1, s2 = oracle.precondition(a, b, c, masks[0], m1, m2, prm.precond)
+        abc = np64(s.read(0, "TENSOR"))
+        M = masks[0]
+        for got, ref in zip(abc, (a, b, c)):
+            assert np.abs(got - ref)[M].max() < 2e-6
+        st = np64(s.read(0, "STEPS"))
+        assert np.abs(st[0] - tau).max() < 2e-6 * max(1.0, tau.max())
+        assert np.abs(st[1] - s1).max() < 2e-6 * max(1.0, s1.max())
+        s.close()
+
+
+def _smooth_field(rng, H, W, scale, n=2):
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    out = np.zeros((n, H, W))
+    for c in range(n):
+        for _ in range(3):
+            k = rng.normal(size=2) * 0.05
+            out[c] += scale * rng.uniform(0.3, 1) * np.sin(k[0] * px + k[1] * py + rng.uniform(0, 6))
+    return out
+
+
+def test_warp_linearize(small, ragged):
+    for pair in (small, ragged):
+        s = make_solver(pair)
+        sizes, cals, masks = level_calibs(pair, pair["levels"])
+        rng = np.random.default_rng(7)
+        H, W = pair["I0"].shape
+        w = _smooth_field(rng, H, W, 3.0)
+        u = rng.uniform(0, 5, (H, W))
+        s.write(0, "I0", pair["I0"])
+        s.write(0, "I1", pair["I1"])
+        s.write(0, "W", w)
+        s.write(0, "U", u)
+        s.stage(0, "WARP")
+        gam = np64(s.trajectory_field(0)).transpose(1, 2, 0)
+        Iu, rho0, g = oracle.warp_linearize(pair["I0"], pair["I1"], w.transpose(1, 2, 0), gam,
+                                            masks[0])
+        assert np.abs(np64(s.read(0, "RHO0")) - rho0).max() < 5e-6
+        # where the bicubic sum of unit vectors is short (stencil reaching off
+        # the mask or across an epipole) renormalising it amplifies rounding;
+        # the comparison is on pixels where |sum| >= 0.2
+        py, px = np.mgrid[0:H, 0:W].astype(float)
+        graw = oracle.bicubic(gam, px + w[0], py + w[1])
+        ok = masks[0] & (np.linalg.norm(graw, axis=-1) >= 0.2)
+        assert np.abs(np64(s.read(0, "G")).transpose(1, 2, 0) - g)[ok].max() < 2e-6
+        assert np.abs(np64(s.read(0, "IU")) - Iu)[ok].max() < 5e-6
+        assert np.array_equal(np64(s.read(0, "UW")), np.float32(u).astype(np.float64))
+        assert np.array_equal(np64(s.read(0, "UBAR")), np.float32(u).astype(np.float64))
+        s.close()
+
+
+def _pd_inputs(pair, rng):
+    H, W = pair["I0"].shape
+    u = rng.uniform(0, 4, (H, W))
+    uw = u + rng.uniform(-0.2, 0.2, (H, W))
+    p = rng.uniform(-0.7, 0.7, (2, H, W))
+    Iu = rng.uniform(-0.2, 0.2, (H, W))
+    rho0 = rng.uniform(-0.05, 0.05, (H, W))
+    return u, uw, p, Iu, rho0
+
+
+def _load_pd(s, pair, u, uw, p, Iu, rho0):
+    s.write(0, "I0", pair["I0"])
+    s.stage(0, "TENSOR")
+    M = np64(s.read(0, "MASK")) > 0.5
+    u = np.where(M, u, 0.0)
+    s.write(0, "U", u)
+    s.write(0, "UBAR", u)
+    s.write(0, "UW", uw)
+    s.write(0, "P", p)
+    s.write(0, "IU", Iu)
+    s.write(0, "RHO0", rho0)
+    return u
+
+
+@pytest.mark.parametrize("block", [1, 3, 4, 8])
+def test_pd_iterations_match_oracle(block, small, ragged):
+    for pair in (small, ragged):
+        rng = np.random.default_rng(11)
+        u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
+        s = make_solver(pair, block_iters=block)
+        u = _load_pd(s, pair, u, uw, p, Iu, rho0)
+        lv = gpu_level_data(s, 0)
+        M = lv["M"]
+        f32 = lambda a: np.float32(a).astype(np.float64)
+        st = dict(u=f32(u), ubar=f32(u), p1=f32(p[0]), p2=f32(p[1]), Iu=np.where(M, f32(Iu), 0),
+                  rho0=np.where(M, f32(rho0), 0), u_w=f32(uw))
+        # the GPU stores per-pixel data for every pixel; the oracle's data
+        # term is only read inside the mask
+        st["Iu"], st["rho0"] = f32(Iu), f32(rho0)
+        prm = oracle_params(pair)
+        done = 0
+        for n in (1, 6, 13):
+            s.stage(0, "PD", n)
+            for _ in range(n):
+                oracle.pd_iteration(st, lv, prm)
+            done += n
+            gu = np64(s.read(0, "U"))
+            gp = np64(s.read(0, "P"))
+            tol = 2e-6 * done
+            assert np.abs(gu - st["u"]).max() < tol, (block, done)
+            assert np.abs(gp[0] - st["p1"]).max() < tol
+            assert np.abs(gp[1] - st["p2"]).max() < tol
+            assert np.abs(np64(s.read(0, "UBAR")) - st["ubar"]).max() < 2 * tol
+        s.close()
+
+
+def test_pd_temporal_blocking_is_bit_exact(ragged):
+    pair = ragged
+    outs = []
+    for block in (1, 2, 3, 5, 8):
+        rng = np.random.default_rng(12)
+        u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
+        s = make_solver(pair, block_iters=block)
+        _load_pd(s, pair, u, uw, p, Iu, rho0)
+        s.stage(0, "PD", 17)
+        outs.append((np64(s.read(0, "U")), np64(s.read(0, "P")), np64(s.read(0, "UBAR"))))
+        s.close()
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
+def test_clip_update(ragged):
+    pair = ragged
+    s = make_solver(pair)
+    H, W = pair["I0"].shape
+    rng = np.random.default_rng(13)
+    M = np64(s.read(0, "MASK")) > 0.5
+    u = np.where(M, rng.uniform(0, 3, (H, W)), 0)
+    uw = np.where(M, u + rng.uniform(-0.6, 0.6, (H, W)), 0)
+    w = rng.uniform(-4, 4, (2, H, W))
+    gg = rng.normal(size=(2, H, W))
+    gg /= np.linalg.norm(gg, axis=0, keepdims=True)
+    s.write(0, "U", u)
+    s.write(0, "UW", uw)
+    s.write(0, "W", w)
+    s.write(0, "G", gg)
+    s.stage(0, "CLIP")
+    f32 = lambda a: np.float32(a).astype(np.float64)
+    un, wn = oracle.clip_update(f32(u), f32(uw), f32(w).transpose(1, 2, 0),
+                                f32(gg).transpose(1, 2, 0), 0.2, M)
+    assert np.abs(np64(s.read(0, "U"))[M] - un[M]).max() < 1e-6
+    assert np.abs(np64(s.read(0, "W")).transpose(1, 2, 0)[M] - wn[M]).max() < 1e-6
+    s.close()
+
+
+def test_upsample(small, ragged):
+    for pair in (small, ragged):
+        s = make_solver(pair)
+        sizes, cals, masks = level_calibs(pair, pair["levels"])
+        rng = np.random.default_rng(14)
+        Wc, Hc = sizes[1]
+        uc = np.where(masks[1], rng.uniform(0, 3, (Hc, Wc)), 0)
+        wc = np.where(masks[1], rng.uniform(-2, 2, (2, Hc, Wc)), 0)
+        s.write(1, "U", uc)
+        s.write(1, "W", wc)
+        s.stage(0, "UPSAMPLE")
+        f32 = lambda a: np.float32(a).astype(np.float64)
+        ru = oracle.upsample(f32(uc), masks[1], *sizes[0], masks[0])
+        rw = oracle.upsample(f32(wc).transpose(1, 2, 0), masks[1], *sizes[0], masks[0])
+        assert np.abs(np64(s.read(0, "U")) - ru).max() < 2e-6
+        assert np.abs(np64(s.read(0, "W")).transpose(1, 2, 0) - rw).max() < 2e-6
+        assert np.abs(np64(s.read(0, "P"))).max() == 0.0
+        s.close()
+
+
+def test_depth_triangulation(ragged):
+    pair = ragged
+    s = make_solver(pair)
+    cam = oracle.calib_from_dict(pair["cam0"])
+    H, W = pair["I0"].shape
+    M = oracle.fov_mask(cam, W, H)
+    tp = oracle.virtual_translation(pair["R"], pair["t"])
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    # exact correspondences of points 0.7 - 6 m away
+    rng = np.random.default_rng(15)
+    rr = rng.uniform(0.7, 6.0, (H, W))
+    X = rr[..., None] * oracle.unproject(cam, px, py)
+    x1 = oracle.project(cam, X + tp)
+    w = np.where(M[..., None], x1 - np.stack([px, py], -1), 0.0)
+    u = np.linalg.norm(w, axis=-1)
+    s.write(0, "W", w.transpose(2, 0, 1))
+    s.write(0, "U", u)
+    disp, depth = s.depth()
+    disp, depth = np64(disp), np64(depth)
+    f32w = np.float32(w).astype(np.float64)
+    ref = oracle.triangulate_range(cam, px, py, f32w[..., 0], f32w[..., 1], tp)
+    sel = M & (u > 0.5)
+    assert np.all(np.isnan(depth[~M])) and np.all(disp[~M] == 0)
+    assert np.abs(depth[sel] / ref[sel] - 1).max() < 2e-3
+    assert np.median(np.abs(depth[sel] / rr[sel] - 1)) < 1e-3
+    s.close()
