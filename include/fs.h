@@ -142,6 +142,43 @@ fs_status fs_destroy(fs_handle* h);
 /* Message for the last failing call of this thread ("" if none). */
 const char* fs_last_error(void);
 
+/* ---- For callers that cannot allocate device memory --------------------
+ * (The paper has no counterpart: this is a deployment variant.)  A real-time
+ * host thread that must not risk the device-wide synchronisation an
+ * allocation can cause, a plug-in living inside a framework that owns the
+ * whole device memory pool, or a process with a fixed memory cap cannot
+ * call cudaMalloc, and fs_create allocates.  fs_pd_iterate_noalloc runs the
+ * primal-dual iterations of one warp (the same kernels fs_solve uses:
+ * tensor and step sizes, then `iters` iterations of Eq. 11/13) directly on
+ * the caller's buffers and allocates nothing: its intermediate planes live
+ * in one fixed array compiled into the library, sized for
+ * FS_NOALLOC_MAX_PIXELS pixels (37 bytes each, about 9.7 MB), which every
+ * GPU that loads the library holds until the process exits.
+ *
+ *   d_I0    W x H image (the tensor T^1/2 of Eq. 12 is built from it)
+ *   d_mask  W x H bytes, nonzero inside the FOV
+ *   d_Iu, d_rho0, d_uw  W x H linearisation I_u, rho0 and u_w (Eq. 3, 5)
+ *   d_u     W x H disparity, read as the start value and overwritten
+ *   d_p     2 x W x H dual variable (x then y plane), read and overwritten
+ *   prm     NULL for the defaults; lambda, huber_eps, beta, eta, theta,
+ *           precond and block_iters are used
+ *   cuda_stream  stream for the work (NULL = legacy default stream)
+ * All pointers are device pointers, dense row-major (pitch W), owned by
+ * the caller.  W, H >= 2, iters >= 1; W * H > FS_NOALLOC_MAX_PIXELS
+ * returns FS_EINVAL.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  Every call on a device uses
+ * the same array: calls whose work overlaps on the GPU (different streams,
+ * or different host threads) race and corrupt each other's results;
+ * serialise them.  The array keeps the last call's contents, which no call
+ * reads: every plane is written in full before it is used. */
+#define FS_NOALLOC_MAX_PIXELS (512 * 512)
+fs_status fs_pd_iterate_noalloc(const float* d_I0, const unsigned char* d_mask,
+                                const float* d_Iu, const float* d_rho0,
+                                const float* d_uw, float* d_u, float* d_p,
+                                int W, int H, int iters, const fs_params* prm,
+                                void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ENOMEM", -3: "FS_ECUDA", -4: "FS_
 EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_trajectory_field", "fs_solve", "fs_solve_host", "fs_destroy", "fs_last_error",
             "fs_buffer_read", "fs_buffer_write", "fs_run_stage", "fs_stage_prerotate",
-            "fs_stage_depth", "fs_timing_enable", "fs_timing_read"]
+            "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc"]
 
 
 class FsError(RuntimeError):
@@ -91,6 +91,8 @@ def load_library():
         "fs_stage_depth": [_P, _P, _P],
         "fs_timing_enable": [_P, i],
         "fs_timing_read": [_P, _P, _P, _P, i],
+        "fs_pd_iterate_noalloc": [_P, _P, _P, _P, _P, _P, _P, i, i, i,
+                                  ctypes.POINTER(FsParams), _P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

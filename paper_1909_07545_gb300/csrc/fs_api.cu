@@ -140,6 +140,12 @@ const dim3 kBlock2(32, 8);
 
 }  // namespace
 
+// Sets the thread's fs_last_error message for the other translation units.
+fs_status fs_internal_set_error(fs_status s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+
 struct fs_handle {
   fs_calib cam[2];
   fs_pose pose;
