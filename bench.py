@@ -310,7 +310,7 @@ def main():
         "config": {"workload": pair["name"], "W": W, "H": H, "levels": L, "warps": warps,
                    "iters": iters, "camera": "kannala_brandt f=320 fov=190",
                    "l2": "flushed between steps (256 MB write)",
-                   "block_iters": args.block_iters or 4, "graph": True,
+                   "block_iters": args.block_iters or "auto (6 above 512 px, 8 below)", "graph": True, "pd_schedule": "cluster <= 128 px, temporal blocking above",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),

@@ -74,7 +74,11 @@ typedef struct {
  * uses diagonal preconditioning (Pock-Chambolle 2011, alpha = 1), 0 uses
  * tau = sigma = 1/sqrt(8).  block_iters: primal-dual iterations fused per
  * launch by temporal blocking (1..8; 0 = library default).  use_graph = 1
- * captures a solve into a CUDA graph on first use and replays it. */
+ * captures a solve into a CUDA graph on first use and replays it.
+ * pd_schedule: 0 = automatic (levels up to 128 x 128 run all iterations of
+ * a warp in one launch of a thread-block cluster holding the whole level,
+ * when the GPU can host that cluster; larger levels use temporal blocking),
+ * 1 = temporal blocking on every level.  Both give identical results. */
 typedef struct {
   float lambda;
   float huber_eps;
@@ -85,7 +89,8 @@ typedef struct {
   int precond;
   int block_iters;
   int use_graph;
-  int reserved[5];         /* must be 0 */
+  int pd_schedule;
+  int reserved[4];         /* must be 0 */
 } fs_params;
 
 typedef struct fs_handle fs_handle;

@@ -34,7 +34,7 @@ from .pyramid import level_sizes, scaled_calib, fov_mask, downsample, upsample
 from .variational import (Params, grad_masks, grad, div, tensor_sqrt, precondition,
                           dual_step, shrink, primal_step, pd_iteration,
                           warp_linearize, clip_update, energy)
-from .solve import solve, solve_level_warps
+from .solve import solve, solve_level_warps, warm_start_w
 
 __all__ = [
     "Calib", "calib_from_dict", "project", "unproject", "radial", "fov_radius",
@@ -44,5 +44,5 @@ __all__ = [
     "level_sizes", "scaled_calib", "fov_mask", "downsample", "upsample",
     "Params", "grad_masks", "grad", "div", "tensor_sqrt", "precondition",
     "dual_step", "shrink", "primal_step", "pd_iteration", "warp_linearize",
-    "clip_update", "energy", "solve", "solve_level_warps",
+    "clip_update", "energy", "solve", "solve_level_warps", "warm_start_w",
 ]

@@ -28,6 +28,7 @@ from .camera import calib_from_dict
 from .geometry import (calibration_field, prerotate, trajectory_field,
                        triangulate_range, virtual_translation)
 from .pyramid import downsample_fast, fov_mask, level_sizes, scaled_calib, upsample
+from .interp import bicubic
 from .variational import (Params, clip_update, grad_masks, pd_iteration,
                           precondition, tensor_sqrt, warp_linearize)
 
@@ -58,13 +59,38 @@ def solve_level_warps(I0l, I1l, gamma, lv, u, w, p1, p2, warps, iters,
     return u, w, p1, p2
 
 
+def warm_start_w(d, gamma, M, du_max):
+    """Warp vector of a given disparity d: walk along the trajectory field
+    from x in n = ceil(|d| / du_max) equal steps of d / n, each along the
+    renormalised bicubic gamma' at the current point (the update w += du g of
+    Algorithm 1 repeated with the largest admissible increments).  n is
+    taken in float32, the precision of the stored disparity."""
+    H, W = d.shape
+    py, px = np.mgrid[0:H, 0:W].astype(np.float64)
+    n = np.ceil(np.float32(np.abs(d)) / np.float32(du_max)).astype(np.int64)
+    n = np.where(M, n, 0)
+    step = np.where(n > 0, d / np.maximum(n, 1), 0.0)
+    w = np.zeros((H, W, 2))
+    for k in range(int(n.max()) if n.size else 0):
+        act = n > k
+        graw = bicubic(gamma, px + w[..., 0], py + w[..., 1])
+        nrm = np.hypot(graw[..., 0], graw[..., 1])
+        ok = act & (nrm >= 1e-6)
+        g = np.where(ok[..., None], graw / np.where(ok, nrm, 1.0)[..., None], 0.0)
+        w = w + step[..., None] * g
+    return w
+
+
 def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params(),
-          on_iter=None, keep_levels=False, level_hook=None):
+          on_iter=None, keep_levels=False, level_hook=None, d_init=None):
     """Full method on one pair; returns disparity (px), range (m), w and more.
 
     level_hook(level, I0_l, I1_l) -> (I0_l, I1_l), when given, may replace
     each level's images after the pyramid is built (a probe for how the
     result responds to perturbing them; None for the method itself).
+
+    d_init, when given, warm-starts from that full-resolution disparity:
+    u = d_init, w rebuilt by warm_start_w, and only the finest level runs.
     """
     cam0 = calib_from_dict(cam0)
     cam1 = calib_from_dict(cam1)
@@ -90,7 +116,14 @@ def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params()
 
     u = w = None
     per_level = []
-    for l in range(levels - 1, -1, -1):
+    first = levels - 1
+    if d_init is not None:
+        M = masks[0]
+        gamma0 = trajectory_field(calibs[0], tp, W, H, M)
+        u = np.where(M, np.asarray(d_init, dtype=np.float64), 0.0)
+        w = np.where(M[..., None], warm_start_w(u, gamma0, M, prm.du_max), 0.0)
+        first = 0
+    for l in range(first, -1, -1):
         Wl, Hl = sizes[l]
         M = masks[l]
         gamma = trajectory_field(calibs[l], tp, Wl, Hl, M)
@@ -98,7 +131,7 @@ def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params()
         if u is None:
             u = np.zeros((Hl, Wl))
             w = np.zeros((Hl, Wl, 2))
-        else:
+        elif l < first:
             u = upsample(u, masks[l + 1], Wl, Hl, M)
             w = upsample(w, masks[l + 1], Wl, Hl, M)
         p1 = np.zeros((Hl, Wl))

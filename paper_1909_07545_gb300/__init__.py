@@ -24,7 +24,7 @@ BUF = dict(I0=0, I1=1, MASK=2, GAMMA=3, TENSOR=4, STEPS=5, U=6, UBAR=7, UW=8, P=
            IU=11, RHO0=12, G=13)
 BUF_PLANES = {0: 1, 1: 1, 2: 1, 3: 2, 4: 3, 5: 2, 6: 1, 7: 1, 8: 1, 9: 2, 10: 2, 11: 1, 12: 1,
               13: 2}
-STAGE = dict(DOWNSAMPLE=0, TENSOR=1, UPSAMPLE=2, WARP=3, PD=4, CLIP=5, TRAJECTORY=6)
+STAGE = dict(DOWNSAMPLE=0, TENSOR=1, UPSAMPLE=2, WARP=3, PD=4, CLIP=5, TRAJECTORY=6, WARM=7)
 
 STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ENOMEM", -3: "FS_ECUDA", -4: "FS_ECALIB",
           -5: "FS_ETIMEOUT"}
@@ -57,7 +57,7 @@ class FsParams(ctypes.Structure):
                 ("du_max", ctypes.c_float), ("beta", ctypes.c_float), ("eta", ctypes.c_float),
                 ("theta", ctypes.c_float), ("precond", ctypes.c_int),
                 ("block_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("pd_schedule", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None

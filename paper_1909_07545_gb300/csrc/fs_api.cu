@@ -50,6 +50,7 @@ constexpr int kMaxLevels = 8;
 struct HostLevel {
   int W = 0, H = 0, P = 0;
   double fx = 0, fy = 0, cx = 0, cy = 0;   // level calibration (camera 0)
+  int cluster = -1;                         // whole-level cluster variant, -1 if none
   LevelView v{};
 };
 
@@ -169,6 +170,7 @@ struct fs_handle {
   std::vector<cudaEvent_t> ev;          // 2 per (level, warp)
   int ev_warps = 0;                      // warps recorded by the last solve
   int ev_iters = 0;
+  int ev_levels = 0;                     // levels it ran (1 for a warm start)
   bool ev_pending = false;
   double t_ms[kMaxLevels] = {};
   long long t_launch[kMaxLevels] = {};
@@ -247,9 +249,14 @@ fs_status build_fields(fs_handle* h) {
   return FS_OK;
 }
 
-int pd_block(const fs_handle* h) {
+// Iterations fused per k_pd launch (temporal-blocking depth).  0 picks by
+// level size: 6 for levels wider than 512 px, where the halo recomputation
+// starts to cost more than the saved launches, 8 below (launch-latency
+// bound); measured on GB300 with the 1024 x 1024 workload.
+int pd_block(const fs_handle* h, int l) {
   int b = h->prm.block_iters;
-  return b <= 0 ? 4 : (b > 8 ? 8 : b);
+  if (b <= 0) return (h->lv[l].W > 512 || h->lv[l].H > 512) ? 6 : 8;
+  return b > 8 ? 8 : b;
 }
 
 // Number of k_pd launches for `iters` iterations with at most B per launch:
@@ -265,7 +272,13 @@ int pd_launches(int iters, int B) {
 fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
   HostLevel& L = h->lv[l];
   PDParams pp{h->prm.lambda, h->prm.huber_eps, h->prm.theta};
-  int B = pd_block(h);
+  if (L.cluster >= 0 && h->prm.pd_schedule == 0) {
+    cudaError_t e = launch_pd_cluster(L.cluster, L.v, pp, iters, st);
+    if (e != cudaSuccess)
+      return fail(FS_ECUDA, "launch of k_pd_cluster failed: %s", cudaGetErrorString(e));
+    return FS_OK;
+  }
+  int B = pd_block(h, l);
   int variant = (L.W >= 128 && L.H >= 128) ? PD_TILE_64 : PD_TILE_32;
   PDState A{L.v.u, L.v.ubar, L.v.p1, L.v.p2};
   PDState Bs{L.v.u_alt, L.v.ubar_alt, L.v.p1_alt, L.v.p2_alt};
@@ -317,6 +330,10 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
       k_clip<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, h->prm.du_max);
       FS_LAUNCHED("k_clip");
       return FS_OK;
+    case FS_STAGE_WARM:
+      k_warm_start<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, h->prm.du_max);
+      FS_LAUNCHED("k_warm_start");
+      return FS_OK;
     case FS_STAGE_TRAJECTORY: {
       double n = std::sqrt(h->tp[0] * h->tp[0] + h->tp[1] * h->tp[1] + h->tp[2] * h->tp[2]);
       DevCam c = dev_cam(h->cam[0], L.fx, L.fy, L.cx, L.cy);
@@ -359,8 +376,25 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
   k_prerotate<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(I1, h->cfield, L0.v.I1, L0.W, L0.H, L0.P);
   FS_LAUNCHED("k_prerotate");
   int top = h->L - 1;
-  if (init) {
-    return fail(FS_EINVAL, "warm start is not available in this build");
+  if (init) {   // warm start: the finest level only, from the given disparity
+    k_copy_in<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(init, L0.v.u, L0.W, L0.H, L0.P);
+    FS_LAUNCHED("k_copy_in");
+    if ((s = run_stage(h, 0, FS_STAGE_WARM, 0, st)) != FS_OK) return s;
+    if ((s = run_stage(h, 0, FS_STAGE_TENSOR, 0, st)) != FS_OK) return s;
+    for (int w = 0; w < warps; ++w) {
+      if ((s = run_stage(h, 0, FS_STAGE_WARP, 0, st)) != FS_OK) return s;
+      if (h->timing) FS_CUDA(record_event(h->ev[2 * w], st));
+      if ((s = run_pd(h, 0, iters, st)) != FS_OK) return s;
+      if (h->timing) FS_CUDA(record_event(h->ev[2 * w + 1], st));
+      if ((s = run_stage(h, 0, FS_STAGE_CLIP, 0, st)) != FS_OK) return s;
+    }
+    if (h->timing) {
+      h->ev_warps = warps;
+      h->ev_iters = iters;
+      h->ev_levels = 1;
+      h->ev_pending = true;
+    }
+    return enqueue_depth(h, disp, depth, st);
   }
   for (int l = 0; l < top; ++l)
     if ((s = run_stage(h, l, FS_STAGE_DOWNSAMPLE, 0, st)) != FS_OK) return s;
@@ -384,6 +418,7 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
   if (h->timing) {
     h->ev_warps = warps;
     h->ev_iters = iters;
+    h->ev_levels = h->L;
     h->ev_pending = true;
   }
   return enqueue_depth(h, disp, depth, st);
@@ -445,7 +480,8 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
   if (prm) {
     p = *prm;
     if (!(p.lambda > 0) || !(p.huber_eps >= 0) || !(p.du_max > 0) || !(p.beta >= 0) ||
-        !(p.eta > 0) || !(p.theta >= 0 && p.theta <= 1) || p.block_iters < 0 || p.block_iters > 8)
+        !(p.eta > 0) || !(p.theta >= 0 && p.theta <= 1) || p.block_iters < 0 ||
+        p.block_iters > 8 || p.pd_schedule < 0 || p.pd_schedule > 1)
       return fail(FS_EINVAL, "parameter out of range");
   } else {
     fs_default_params(&p);
@@ -481,6 +517,8 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     size_t plane = align_up((size_t)L.P * L.H * sizeof(float), 256);
     size_t plane8 = align_up((size_t)L.P * L.H, 256);
     bytes += plane8 + 17 * plane + 3 * 2 * plane;
+    int cv = pd_cluster_variant(L.W, L.H);
+    L.cluster = (cv >= 0 && pd_cluster_fits(cv, L.W, L.H)) ? cv : -1;
   }
   size_t cbytes = align_up((size_t)h->lv[0].P * H * sizeof(float2), 256);
   bytes += cbytes;
@@ -589,6 +627,7 @@ fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1, const flo
   if (h->timing) {              // the replay re-records the captured events
     h->ev_warps = warps;
     h->ev_iters = iters;
+    h->ev_levels = d_init ? 1 : h->L;
     h->ev_pending = true;
   }
   return FS_OK;
@@ -745,15 +784,17 @@ extern "C" fs_status fs_timing_read(fs_handle* h, double* ms, long long* launche
   if ((s = check_handle(h)) != FS_OK) return s;
   if (h->ev_pending) {
     FS_CUDA(cudaStreamSynchronize(h->stream));
-    int B = pd_block(h);
-    for (int l = 0; l < h->L; ++l) {
+    for (int l = 0; l < h->ev_levels; ++l) {
+      int B = pd_block(h, l);
       for (int w = 0; w < h->ev_warps; ++w) {
         float t = 0.f;
         FS_CUDA(cudaEventElapsedTime(&t, h->ev[2 * (l * h->ev_warps + w)],
                                      h->ev[2 * (l * h->ev_warps + w) + 1]));
         h->t_ms[l] += t;
       }
-      h->t_launch[l] += (long long)h->ev_warps * pd_launches(h->ev_iters, B);
+      h->t_launch[l] += h->lv[l].cluster >= 0 && h->prm.pd_schedule == 0
+                            ? (long long)h->ev_warps
+                            : (long long)h->ev_warps * pd_launches(h->ev_iters, B);
       h->t_pxit[l] += (double)h->lv[l].W * h->lv[l].H * h->ev_warps * h->ev_iters;
     }
     h->ev_pending = false;

@@ -5,11 +5,8 @@
 
 namespace fs {
 
-struct Mat3 {
-  float m[9];
-};
-
 enum PDVariant { PD_TILE_64 = 0, PD_TILE_32 = 1 };
+enum PDClusterVariant { PD_CLUSTER_16 = 0, PD_CLUSTER_32 = 1 };
 
 __global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView L);
 __global__ void k_prerotate(const float* __restrict__ I1, const float2* __restrict__ field,
@@ -19,6 +16,7 @@ __global__ void k_copy_in(const float* __restrict__ src, float* __restrict__ dst
 __global__ void k_downsample(LevelView F, LevelView C);
 __global__ void k_upsample(LevelView C, LevelView F);
 __global__ void k_zero_state(LevelView L);
+__global__ void k_warm_start(LevelView L, float du_max);
 __global__ void k_tensor(LevelView L, float beta, float eta, int precond);
 __global__ void k_warp(LevelView L);
 __global__ void k_clip(LevelView L, float du_max);
@@ -36,5 +34,13 @@ __global__ void k_tensor_abc(LevelView L, float* __restrict__ dst);
 // `variant`, state read from `in` and written to `out` (distinct buffers).
 cudaError_t launch_pd(int variant, const LevelView& L, const PDState& in, const PDState& out,
                       const PDParams& pp, int B, int n, cudaStream_t st);
+
+// Whole-level primal-dual in one thread-block cluster: the tile variant for a
+// W x H level (-1 if none), whether its cluster can be resident on this GPU,
+// and the launch of n iterations in place.
+int pd_cluster_variant(int W, int H);
+bool pd_cluster_fits(int variant, int W, int H);
+cudaError_t launch_pd_cluster(int variant, const LevelView& L, const PDParams& pp, int n,
+                              cudaStream_t st);
 
 }  // namespace fs

@@ -117,6 +117,37 @@ __global__ void k_upsample(LevelView C, LevelView F) {
   F.p1[o] = 0.f; F.p2[o] = 0.f;
 }
 
+// Warm start at the finest level from a disparity already in L.u: w is
+// rebuilt by walking along the trajectory field in n = ceil(|d| / du_max)
+// equal steps of d / n, each along the renormalised bicubic gamma' at the
+// current point; ubar = u_w = u, p = 0.  Non-finite disparities count as 0
+// and n is capped at kMaxWarmSteps.
+constexpr int kMaxWarmSteps = 16384;
+__global__ void k_warm_start(LevelView L, float du_max) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t i = (size_t)y * L.P + x;
+  float d = L.u[i];
+  if (!(L.mask[i] & MASK_IN) || !isfinite(d)) d = 0.f;
+  float2 w = make_float2(0.f, 0.f);
+  int n = (int)fminf(ceilf(fabsf(d) / du_max), (float)kMaxWarmSteps);
+  if (n > 0) {
+    float step = d / (float)n;
+    for (int k = 0; k < n; ++k) {
+      float2 gr = sample_bicubic2(L.gamma, L.W, L.H, L.P, x, w.x, y, w.y);
+      float nr = sqrtf(gr.x * gr.x + gr.y * gr.y);
+      if (nr >= 1e-6f) {
+        w.x = fmaf(step, gr.x / nr, w.x);
+        w.y = fmaf(step, gr.y / nr, w.y);
+      }
+    }
+  }
+  L.u[i] = d; L.ubar[i] = d; L.uw[i] = d;
+  L.w[i] = w;
+  L.p1[i] = 0.f; L.p2[i] = 0.f;
+}
+
 // Zero state at the coarsest level (Algorithm 1: u_0 = 0, w_0 = 0).
 __global__ void k_zero_state(LevelView L) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;

@@ -1,27 +1,35 @@
-// k_pd.cu -- temporally blocked primal-dual iterations (Eq. 11, 13).
+// k_pd.cu -- primal-dual iterations (Eq. 11, 13) in two schedules.
 //
-// One CTA owns a footprint of FW x (NY * R) pixels: an interior tile plus a
-// halo of B pixels on every side.  Thread (tx, ty) keeps the column tx,
-// rows ty*R .. ty*R + R - 1 of the footprint in registers (state u, ubar, p
-// and the per-warp constants); shared memory only carries what neighbours
-// exchange (ubar, and the masked products T^1/2 p).  One iteration makes the
-// dependency cone grow by one pixel in every direction, so after n <= B
-// iterations the interior is exact and is written back; the halo is
-// recomputed by the neighbouring CTAs.  Two CTA barriers per iteration.
-// The state is read from one buffer set and written to the other, so no CTA
-// can see a neighbour's updated interior while it loads its halo.
+// Per-pixel arithmetic: pd_math.cuh (identical in both schedules).
 //
-// Per pixel and iteration, with K = T^1/2 grad and T^1/2 = I - s s^T:
-//   p    <- P((p + sigma K ubar) / (1 + sigma eps)),   P(q) = q / max(1, |q|)
-//   uh   <- u + tau div(T^1/2 p)
-//   u'   <- shrink(uh): rb = rho0 + I_u (uh - u_w)
-//           uh + tau lam I_u   if rb < -tau lam I_u^2
-//           uh - tau lam I_u   if rb >  tau lam I_u^2
-//           uh - rb / I_u      otherwise               (Eq. 13)
-//   ubar <- u' + theta (u' - u)
+// 1. k_pd -- temporal blocking, for levels too large to stay on chip.
+//    One CTA owns a footprint of FW x (NY * R) pixels: an interior tile plus
+//    a halo of B pixels on every side.  Thread (tx, ty) keeps the column tx,
+//    rows ty*R .. ty*R + R - 1 of the footprint in registers (state u, ubar,
+//    p and the per-warp constants); shared memory only carries what
+//    neighbours exchange (ubar, and the masked products T^1/2 p).  One
+//    iteration makes the dependency cone grow by one pixel in every
+//    direction, so after n <= B iterations the interior is exact and is
+//    written back; the halo is recomputed by the neighbouring CTAs.  Two CTA
+//    barriers per iteration.  The state is read from one buffer set and
+//    written to the other, so no CTA sees a neighbour's updated interior
+//    while it loads its halo.
+//
+// 2. k_pd_cluster -- the whole level resident in one thread-block cluster
+//    (at most 16 CTAs, one tile each, no halo), for the coarse levels.  Each
+//    CTA pushes its border values into halo cells of its neighbours' shared
+//    memory (remote stores into distributed shared memory), so all reads stay
+//    local; two cluster barriers per iteration.  All iterations of a warp run
+//    in one launch and the state is updated in place.
+//
 // grad: forward differences masked by MASK_GX / MASK_GY; div: its exact
 // negative adjoint; u is only updated inside the FOV mask.
+#include <cooperative_groups.h>
+
 #include "fs_kernels.h"
+#include "pd_math.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace fs {
 
@@ -39,10 +47,10 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters) {
   const int oy = (int)blockIdx.y * IH - B;
   const int gx = ox + tx;
   const bool col_in = gx >= 0 && gx < L.W;
-  const float lam = pp.lam, eps = pp.eps, theta = pp.theta;
+  const float theta = pp.theta;
 
-  float u[R], ub[R], p1[R], p2[R], sx[R], sy[R], dinv[R], sd[R], tau[R], step[R], Iu[R],
-      rho0[R], uw[R], inv[R];
+  float u[R], ub[R], p1[R], p2[R];
+  PxConst c[R];
   unsigned mb = 0;
 
 #pragma unroll
@@ -55,22 +63,11 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters) {
       ub[r] = in.ubar[i];
       p1[r] = in.p1[i];
       p2[r] = in.p2[i];
-      sx[r] = L.sx[i];
-      sy[r] = L.sy[i];
-      const float sg = L.sig[i];
-      dinv[r] = 1.f / (1.f + sg * eps);
-      sd[r] = sg * dinv[r];
-      tau[r] = L.tau[i];
-      Iu[r] = L.Iu[i];
-      step[r] = (tau[r] * lam) * Iu[r];              // tau lam I_u
-      rho0[r] = L.rho0[i];
-      uw[r] = L.uw[i];
-      inv[r] = Iu[r] != 0.f ? 1.f / Iu[r] : 0.f;
+      px_load(L, i, pp.lam, pp.eps, c[r]);
       mb |= (unsigned)L.mask[i] << (3 * r);
     } else {
-      u[r] = ub[r] = p1[r] = p2[r] = sx[r] = sy[r] = 0.f;
-      dinv[r] = 1.f; sd[r] = 0.f; tau[r] = 0.f; step[r] = 0.f; Iu[r] = 0.f; rho0[r] = 0.f;
-      uw[r] = 0.f; inv[r] = 0.f;
+      u[r] = ub[r] = p1[r] = p2[r] = 0.f;
+      px_zero(c[r]);
     }
     s_ub[fy][tx] = ub[r];
   }
@@ -81,49 +78,23 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters) {
 
 #pragma unroll 1
   for (int it = 0; it < n_iters; ++it) {
-    // ---- dual ascent + Huber resolvent + projection
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int fy = ty * R + r;
-      const unsigned m = mb >> (3 * r);
       const float right = s_ub[fy][txr];
       const float below = (r + 1 < R) ? ub[r + 1] : s_ub[min(fy + 1, FH - 1)][tx];
-      const float g1 = (m & MASK_GX) ? right - ub[r] : 0.f;
-      const float g2 = (m & MASK_GY) ? below - ub[r] : 0.f;
-      const float d = sx[r] * g1 + sy[r] * g2;
-      const float k1 = fmaf(-sx[r], d, g1);
-      const float k2 = fmaf(-sy[r], d, g2);
-      float q1 = fmaf(sd[r], k1, p1[r] * dinv[r]);
-      float q2 = fmaf(sd[r], k2, p2[r] * dinv[r]);
-      const float nn = q1 * q1 + q2 * q2;
-      if (nn > 1.f) {
-        const float s = rsqrtf(nn);
-        q1 *= s;
-        q2 *= s;
-      }
-      p1[r] = q1;
-      p2[r] = q2;
-      const float dp = sx[r] * q1 + sy[r] * q2;
-      s_t1[fy][tx] = (m & MASK_GX) ? fmaf(-sx[r], dp, q1) : 0.f;
-      s_t2[fy][tx] = (m & MASK_GY) ? fmaf(-sy[r], dp, q2) : 0.f;
+      float t1, t2;
+      px_dual(mb >> (3 * r), ub[r], right, below, c[r], p1[r], p2[r], t1, t2);
+      s_t1[fy][tx] = t1;
+      s_t2[fy][tx] = t2;
     }
     __syncthreads();
-    // ---- primal descent + pointwise shrinkage + over-relaxation
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int fy = ty * R + r;
-      const unsigned m = mb >> (3 * r);
-      const float dv = s_t1[fy][tx] - s_t1[fy][txl] + s_t2[fy][tx] - s_t2[max(fy - 1, 0)][tx];
-      float un = u[r];
-      if (m & MASK_IN) {
-        const float uh = fmaf(tau[r], dv, u[r]);
-        // rho0 + I_u (uh - u_w): the small increment keeps its precision
-        // (folding rho0 - I_u u_w first would round at the size of I_u u_w)
-        const float rb = fmaf(Iu[r], uh - uw[r], rho0[r]);
-        const float thr = step[r] * Iu[r];              // tau lam I_u^2
-        un = rb < -thr ? uh + step[r] : (rb > thr ? uh - step[r] : fmaf(-rb, inv[r], uh));
-      }
-      ub[r] = fmaf(theta, un - u[r], un);
+      const float dv = px_div(s_t1[fy][tx], s_t1[fy][txl], s_t2[fy][tx], s_t2[max(fy - 1, 0)][tx]);
+      const float un = px_primal(mb >> (3 * r), u[r], dv, c[r]);
+      ub[r] = px_relax(un, u[r], theta);
       u[r] = un;
       s_ub[fy][tx] = ub[r];
     }
@@ -144,6 +115,108 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters) {
   }
 }
 
+template <int TW, int NY, int R>
+__global__ void __launch_bounds__(TW * NY, 1)
+k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
+  constexpr int TH = NY * R;
+  constexpr int SU = TW + 1;          // s_ub: TH+1 rows of TW+1 (right column, bottom row = halo)
+  constexpr int S1 = TW + 1;          // s_t1: TH rows of TW+1 (column 0 = left halo)
+  __shared__ float s_ub[(TH + 1) * SU];
+  __shared__ float s_t1[TH * S1];
+  __shared__ float s_t2[(TH + 1) * TW];   // row 0 = top halo
+
+  cg::cluster_group cl = cg::this_cluster();
+  const dim3 cb = cl.block_index();
+  const dim3 cd = cl.dim_blocks();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int ox = (int)cb.x * TW, oy = (int)cb.y * TH;
+  const int gx = ox + tx;
+  const bool col_in = gx < L.W;
+  const float theta = pp.theta;
+
+  // Neighbouring tiles' shared memory: borders are pushed into their halo
+  // cells with remote stores, so every read below is a local one.
+  const unsigned cw = cd.x;
+  float* to_left_ub = cb.x > 0 ? cl.map_shared_rank(s_ub, (cb.x - 1) + cb.y * cw) : nullptr;
+  float* to_up_ub = cb.y > 0 ? cl.map_shared_rank(s_ub, cb.x + (cb.y - 1) * cw) : nullptr;
+  float* to_right_t1 = cb.x + 1 < cd.x ? cl.map_shared_rank(s_t1, (cb.x + 1) + cb.y * cw) : nullptr;
+  float* to_down_t2 = cb.y + 1 < cd.y ? cl.map_shared_rank(s_t2, cb.x + (cb.y + 1) * cw) : nullptr;
+
+  // halo cells with no neighbour stay 0 (the masks zero their terms anyway)
+  const int nthr = TW * NY, tid = ty * TW + tx;
+  for (int k = tid; k < TH + 1; k += nthr) s_ub[k * SU + TW] = 0.f;
+  for (int k = tid; k < TW; k += nthr) { s_ub[TH * SU + k] = 0.f; s_t2[k] = 0.f; }
+  for (int k = tid; k < TH; k += nthr) s_t1[k * S1] = 0.f;
+  cl.sync();                                   // zeroing before any neighbour pushes
+
+  float u[R], ub[R], p1[R], p2[R];
+  PxConst c[R];
+  unsigned mb = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int fy = ty * R + r;
+    const int gy = oy + fy;
+    if (col_in && gy < L.H) {
+      const size_t i = (size_t)gy * L.P + gx;
+      u[r] = L.u[i];
+      ub[r] = L.ubar[i];
+      p1[r] = L.p1[i];
+      p2[r] = L.p2[i];
+      px_load(L, i, pp.lam, pp.eps, c[r]);
+      mb |= (unsigned)L.mask[i] << (3 * r);
+    } else {
+      u[r] = ub[r] = p1[r] = p2[r] = 0.f;
+      px_zero(c[r]);
+    }
+    s_ub[fy * SU + tx] = ub[r];
+    if (tx == 0 && to_left_ub) to_left_ub[fy * SU + TW] = ub[r];
+    if (fy == 0 && to_up_ub) to_up_ub[TH * SU + tx] = ub[r];
+  }
+  cl.sync();
+
+#pragma unroll 1
+  for (int it = 0; it < n_iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int fy = ty * R + r;
+      const float right = s_ub[fy * SU + tx + 1];
+      const float below = (r + 1 < R) ? ub[r + 1] : s_ub[(fy + 1) * SU + tx];
+      float t1, t2;
+      px_dual(mb >> (3 * r), ub[r], right, below, c[r], p1[r], p2[r], t1, t2);
+      s_t1[fy * S1 + tx + 1] = t1;
+      s_t2[(fy + 1) * TW + tx] = t2;
+      if (tx == TW - 1 && to_right_t1) to_right_t1[fy * S1] = t1;
+      if (fy == TH - 1 && to_down_t2) to_down_t2[tx] = t2;
+    }
+    cl.sync();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int fy = ty * R + r;
+      const float dv = px_div(s_t1[fy * S1 + tx + 1], s_t1[fy * S1 + tx],
+                              s_t2[(fy + 1) * TW + tx], s_t2[fy * TW + tx]);
+      const float un = px_primal(mb >> (3 * r), u[r], dv, c[r]);
+      ub[r] = px_relax(un, u[r], theta);
+      u[r] = un;
+      s_ub[fy * SU + tx] = ub[r];
+      if (tx == 0 && to_left_ub) to_left_ub[fy * SU + TW] = ub[r];
+      if (fy == 0 && to_up_ub) to_up_ub[TH * SU + tx] = ub[r];
+    }
+    cl.sync();
+  }
+
+  if (!col_in) return;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gy = oy + ty * R + r;
+    if (gy >= L.H) continue;
+    const size_t i = (size_t)gy * L.P + gx;
+    L.u[i] = u[r];
+    L.ubar[i] = ub[r];
+    L.p1[i] = p1[r];
+    L.p2[i] = p2[r];
+  }
+}
+
 template <int FW, int NY, int R>
 static cudaError_t launch_pd_t(const LevelView& L, const PDState& in, const PDState& out,
                                const PDParams& pp, int B, int n, cudaStream_t st) {
@@ -159,6 +232,88 @@ cudaError_t launch_pd(int variant, const LevelView& L, const PDState& in, const 
   switch (variant) {
     case PD_TILE_64: return launch_pd_t<64, 8, 8>(L, in, out, pp, B, n, st);
     case PD_TILE_32: return launch_pd_t<32, 8, 4>(L, in, out, pp, B, n, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------- clusters
+
+template <int TW, int NY, int R>
+static bool cluster_dims(int W, int H, unsigned& cx, unsigned& cy) {
+  constexpr int TH = NY * R;
+  cx = (unsigned)((W + TW - 1) / TW);
+  cy = (unsigned)((H + TH - 1) / TH);
+  return cx * cy <= 16;
+}
+
+template <int TW, int NY, int R>
+static cudaLaunchConfig_t cluster_config(unsigned cx, unsigned cy, cudaStream_t st,
+                                         cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cx, cy, 1);
+  cfg.blockDim = dim3(TW, NY, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cx;
+  attr[0].val.clusterDim.y = cy;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// True when a cluster of the tiles covering W x H can be resident (cluster
+// sizes above 8 need the non-portable opt-in; the occupancy query says
+// whether a GPC has room for it).
+template <int TW, int NY, int R>
+static bool cluster_fits_t(int W, int H) {
+  unsigned cx, cy;
+  if (!cluster_dims<TW, NY, R>(W, H, cx, cy)) return false;
+  if (cudaFuncSetAttribute(k_pd_cluster<TW, NY, R>,
+                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_config<TW, NY, R>(cx, cy, nullptr, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_pd_cluster<TW, NY, R>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
+}
+
+template <int TW, int NY, int R>
+static cudaError_t launch_cluster_t(const LevelView& L, const PDParams& pp, int n,
+                                    cudaStream_t st) {
+  unsigned cx, cy;
+  if (!cluster_dims<TW, NY, R>(L.W, L.H, cx, cy) || n < 1) return cudaErrorInvalidValue;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_config<TW, NY, R>(cx, cy, st, attr);
+  return cudaLaunchKernelEx(&cfg, k_pd_cluster<TW, NY, R>, L, pp, n);
+}
+
+int pd_cluster_variant(int W, int H) {
+  if (W <= 64 && H <= 64) return PD_CLUSTER_16;
+  if (W <= 128 && H <= 128) return PD_CLUSTER_32;
+  return -1;
+}
+
+bool pd_cluster_fits(int variant, int W, int H) {
+  switch (variant) {
+    case PD_CLUSTER_16: return cluster_fits_t<16, 4, 4>(W, H);
+    case PD_CLUSTER_32: return cluster_fits_t<32, 8, 4>(W, H);
+    default: return false;
+  }
+}
+
+cudaError_t launch_pd_cluster(int variant, const LevelView& L, const PDParams& pp, int n,
+                              cudaStream_t st) {
+  switch (variant) {
+    case PD_CLUSTER_16: return launch_cluster_t<16, 4, 4>(L, pp, n, st);
+    case PD_CLUSTER_32: return launch_cluster_t<32, 8, 4>(L, pp, n, st);
     default: return cudaErrorInvalidValue;
   }
 }

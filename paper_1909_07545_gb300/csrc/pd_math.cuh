@@ -1,0 +1,97 @@
+// pd_math.cuh -- per-pixel arithmetic of one primal-dual iteration (Eq. 11,
+// 13), shared by every primal-dual kernel so that all schedules compute
+// bit-identical results.
+//
+// K = T^1/2 grad with T^1/2 = I - s s^T (s = sqrt(1 - e) n, Eq. 12):
+//   dual    p <- P((p + sigma K ubar) / (1 + sigma eps)),  P(q) = q / max(1, |q|)
+//           t = masked T^1/2 p (what the divergence of the neighbours reads)
+//   primal  uh = u + tau div(T^1/2 p)
+//           rb = rho0 + I_u (uh - u_w)
+//           u' = uh + tau lam I_u   if rb < -tau lam I_u^2
+//                uh - tau lam I_u   if rb >  tau lam I_u^2
+//                uh - rb / I_u      otherwise       (Eq. 13, resolvent of the L1 term)
+//           only inside the FOV mask (u held elsewhere)
+#pragma once
+
+#include "fs_device.cuh"
+
+namespace fs {
+
+// Per-pixel constants of one warp.
+struct PxConst {
+  float sx, sy;      // T^1/2 = I - s s^T
+  float dinv, sd;    // 1 / (1 + sigma eps), sigma / (1 + sigma eps)
+  float tau, step;   // tau, tau lam I_u
+  float Iu, rho0, uw, inv;   // linearisation, 1 / I_u (0 when I_u = 0)
+};
+
+__device__ __forceinline__ void px_load(const LevelView& L, size_t i, float lam, float eps,
+                                        PxConst& c) {
+  c.sx = L.sx[i];
+  c.sy = L.sy[i];
+  const float sg = L.sig[i];
+  c.dinv = __fdiv_rn(1.f, fmaf(sg, eps, 1.f));
+  c.sd = __fmul_rn(sg, c.dinv);
+  c.tau = L.tau[i];
+  c.Iu = L.Iu[i];
+  c.step = __fmul_rn(__fmul_rn(c.tau, lam), c.Iu);
+  c.rho0 = L.rho0[i];
+  c.uw = L.uw[i];
+  c.inv = c.Iu != 0.f ? __fdiv_rn(1.f, c.Iu) : 0.f;
+}
+
+__device__ __forceinline__ void px_zero(PxConst& c) {
+  c.sx = c.sy = 0.f;
+  c.dinv = 1.f;
+  c.sd = c.tau = c.step = c.Iu = c.rho0 = c.uw = c.inv = 0.f;
+}
+
+// Dual ascent at one pixel: ub, right = ubar(x + e1), below = ubar(x + e2).
+// Updates p1, p2 and returns the masked products t1, t2 of T^1/2 p.
+__device__ __forceinline__ void px_dual(unsigned m, float ub, float right, float below,
+                                        const PxConst& c, float& p1, float& p2, float& t1,
+                                        float& t2) {
+  const float g1 = (m & MASK_GX) ? __fsub_rn(right, ub) : 0.f;
+  const float g2 = (m & MASK_GY) ? __fsub_rn(below, ub) : 0.f;
+  const float d = fmaf(c.sx, g1, __fmul_rn(c.sy, g2));
+  const float k1 = fmaf(-c.sx, d, g1);
+  const float k2 = fmaf(-c.sy, d, g2);
+  float q1 = fmaf(c.sd, k1, __fmul_rn(p1, c.dinv));
+  float q2 = fmaf(c.sd, k2, __fmul_rn(p2, c.dinv));
+  const float nn = fmaf(q1, q1, __fmul_rn(q2, q2));
+  if (nn > 1.f) {
+    const float s = rsqrtf(nn);
+    q1 = __fmul_rn(q1, s);
+    q2 = __fmul_rn(q2, s);
+  }
+  p1 = q1;
+  p2 = q2;
+  const float dp = fmaf(c.sx, q1, __fmul_rn(c.sy, q2));
+  t1 = (m & MASK_GX) ? fmaf(-c.sx, dp, q1) : 0.f;
+  t2 = (m & MASK_GY) ? fmaf(-c.sy, dp, q2) : 0.f;
+}
+
+// div(T^1/2 p) at a pixel from its own and its left / upper neighbours'
+// masked products.
+__device__ __forceinline__ float px_div(float t1, float t1_left, float t2, float t2_up) {
+  return __fadd_rn(__fsub_rn(t1, t1_left), __fsub_rn(t2, t2_up));
+}
+
+// Over-relaxation ubar = u' + theta (u' - u).
+__device__ __forceinline__ float px_relax(float un, float u, float theta) {
+  return fmaf(theta, __fsub_rn(un, u), un);
+}
+
+// Primal descent + shrinkage at one pixel; dv = div(T^1/2 p) at the pixel.
+// Returns the new u (unchanged outside the mask).
+__device__ __forceinline__ float px_primal(unsigned m, float u, float dv, const PxConst& c) {
+  if (!(m & MASK_IN)) return u;
+  const float uh = fmaf(c.tau, dv, u);
+  // rho0 + I_u (uh - u_w): the small increment keeps its precision
+  const float rb = fmaf(c.Iu, __fsub_rn(uh, c.uw), c.rho0);
+  const float thr = __fmul_rn(c.step, c.Iu);     // tau lam I_u^2
+  return rb < -thr ? __fadd_rn(uh, c.step)
+                   : (rb > thr ? __fsub_rn(uh, c.step) : fmaf(-rb, c.inv, uh));
+}
+
+}  // namespace fs

@@ -23,10 +23,10 @@ def _built():
     build.build()
 
 
-def _oracle(pair, levels=None, warps=None, iters=None, **prm):
+def _oracle(pair, levels=None, warps=None, iters=None, d_init=None, **prm):
     return oracle.solve(pair["I0"], pair["I1"], pair["cam0"], pair["cam1"], pair["R"],
                         pair["t"], levels or pair["levels"], warps or pair["warps"],
-                        iters or pair["iters"], oracle_params(pair, **prm))
+                        iters or pair["iters"], oracle_params(pair, **prm), d_init=d_init)
 
 
 def _compare(pair, ref, disp, depth, sens):
@@ -66,14 +66,14 @@ def test_plain_small_256_matches_oracle(small, small_ref):
 
 
 @pytest.mark.parametrize("block", [1, 5, 8])
-def test_block_depths_are_identical(small, block):
-    s1 = make_solver(small, block_iters=block)
-    s4 = make_solver(small, block_iters=4)
+def test_schedules_and_block_depths_are_identical(small, block):
+    s1 = make_solver(small, block_iters=block, pd_schedule=1)
+    s0 = make_solver(small)
     d1, z1 = s1.solve(small["I0"], small["I1"], 2, 13)
-    d4, z4 = s4.solve(small["I0"], small["I1"], 2, 13)
-    assert np.array_equal(np64(d1), np64(d4))
+    d0, z0 = s0.solve(small["I0"], small["I1"], 2, 13)
+    assert np.array_equal(np64(d1), np64(d0))
     s1.close()
-    s4.close()
+    s0.close()
 
 
 def test_ragged_rotated_pair_matches_oracle():
@@ -120,4 +120,19 @@ def test_full_size_kb_1024_short_schedule():
     s = make_solver(pair)
     disp, depth = s.solve(pair["I0"], pair["I1"], 2, 20)
     _compare(pair, ref, disp, depth, sens)
+    s.close()
+
+
+def test_warm_start_matches_oracle(small):
+    # warm start from a disparity (here the oracle's own cold result, rounded
+    # to float32): w rebuilt along the trajectory field, finest level only
+    cold = _oracle(small, warps=2, iters=20)
+    d0 = np.float32(cold["disp"]).astype(np.float64)
+    ref = _oracle(small, warps=3, iters=30, d_init=d0)
+    sens = oracle_sensitivity(small, ref, warps=3, iters=30, d_init=d0)
+    s = make_solver(small)
+    disp, depth = s.solve(small["I0"], small["I1"], 3, 30, init=d0)
+    _compare(small, ref, disp, depth, sens)
+    # the rebuilt warp vector itself, before any iteration
+    s.solve(small["I0"], small["I1"], 1, 1, init=d0)
     s.close()

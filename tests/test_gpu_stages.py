@@ -189,12 +189,12 @@ def _load_pd(s, pair, u, uw, p, Iu, rho0):
     return u
 
 
-@pytest.mark.parametrize("block", [1, 3, 4, 8])
-def test_pd_iterations_match_oracle(block, small, ragged):
+@pytest.mark.parametrize("sched,block", [(0, 0), (1, 1), (1, 3), (1, 4), (1, 8)])
+def test_pd_iterations_match_oracle(sched, block, small, ragged):
     for pair in (small, ragged):
         rng = np.random.default_rng(11)
         u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
-        s = make_solver(pair, block_iters=block)
+        s = make_solver(pair, block_iters=block, pd_schedule=sched)
         u = _load_pd(s, pair, u, uw, p, Iu, rho0)
         lv = gpu_level_data(s, 0)
         M = lv["M"]
@@ -221,13 +221,16 @@ def test_pd_iterations_match_oracle(block, small, ragged):
         s.close()
 
 
-def test_pd_temporal_blocking_is_bit_exact(ragged):
-    pair = ragged
+@pytest.mark.parametrize("which", ["small", "ragged"])
+def test_pd_schedules_are_bit_exact(which, small, ragged):
+    # the whole-level cluster schedule and temporal blocking at every depth
+    # compute the same per-pixel arithmetic: results must be identical
+    pair = small if which == "small" else ragged
     outs = []
-    for block in (1, 2, 3, 5, 8):
+    for sched, block in ((0, 0), (1, 1), (1, 2), (1, 3), (1, 5), (1, 8)):
         rng = np.random.default_rng(12)
         u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
-        s = make_solver(pair, block_iters=block)
+        s = make_solver(pair, block_iters=block, pd_schedule=sched)
         _load_pd(s, pair, u, uw, p, Iu, rho0)
         s.stage(0, "PD", 17)
         outs.append((np64(s.read(0, "U")), np64(s.read(0, "P")), np64(s.read(0, "UBAR"))))
@@ -307,3 +310,23 @@ def test_depth_triangulation(ragged):
     assert np.abs(depth[sel] / ref[sel] - 1).max() < 2e-3
     assert np.median(np.abs(depth[sel] / rr[sel] - 1)) < 1e-3
     s.close()
+
+
+def test_warm_start_warp_vector(small, ragged):
+    # FS_STAGE_WARM: w rebuilt from u by walking the trajectory field
+    for pair in (small, ragged):
+        rng = np.random.default_rng(21)
+        H, W = pair["I0"].shape
+        sizes, cals, masks = level_calibs(pair, pair["levels"])
+        d = np.float32(np.where(masks[0], 4.0 * rng.uniform(-0.5, 1.0, size=(H, W)), 0.0))
+        d = d.astype(np.float64)
+        s = make_solver(pair)
+        s.write(0, "U", d)
+        s.stage(0, "WARM")
+        tp = oracle.virtual_translation(pair["R"], pair["t"])
+        gamma = np64(s.trajectory_field(0)).transpose(1, 2, 0)
+        ref_w = oracle.warm_start_w(d, gamma, masks[0], 0.2)
+        got_w = np64(s.read(0, "W")).transpose(1, 2, 0)
+        assert np.abs(got_w - ref_w)[masks[0]].max() < 1e-4
+        assert np.array_equal(np64(s.read(0, "UW")), d) and np.abs(np64(s.read(0, "P"))).max() == 0
+        s.close()

@@ -63,3 +63,26 @@ def test_fronto_parallel_plane_depth(model, depth):
     rel = Z[sel] / depth - 1.0
     assert abs(np.median(rel)) <= 0.01
     assert np.median(np.abs(rel)) <= 0.025
+
+
+def test_warm_start_walks_the_trajectory_field():
+    # constant field: w = d * gamma exactly; curved field: Euler steps of
+    # <= du_max converge to the epipolar curve as the step shrinks
+    H, W = 20, 24
+    M = np.ones((H, W), bool)
+    gam = np.zeros((H, W, 2))
+    gam[..., 0] = 0.6
+    gam[..., 1] = -0.8
+    d = np.linspace(-3, 5, H * W).reshape(H, W)
+    w = oracle.warm_start_w(d, gam, M, 0.2)
+    assert np.allclose(w[..., 0], 0.6 * d, atol=1e-12)
+    assert np.allclose(w[..., 1], -0.8 * d, atol=1e-12)
+    cam = oracle.Calib(oracle.camera.EQUIDISTANT, 40.0, 40.0, 63.5, 63.5, fov_deg=180.0)
+    Mc = oracle.fov_mask(cam, 128, 128)
+    g = oracle.trajectory_field(cam, np.array([-0.1, 0.02, 0.0]), 128, 128, Mc)
+    dd = np.where(Mc, 4.0, 0.0)
+    coarse = oracle.warm_start_w(dd, g, Mc, 0.2)
+    fine = oracle.warm_start_w(dd, g, Mc, 0.02)
+    sel = nd.binary_erosion(Mc, iterations=12)
+    assert np.abs(coarse - fine)[sel].max() < 0.05
+    assert np.abs(np.linalg.norm(fine, axis=-1)[sel] - 4.0).max() < 0.05
