@@ -100,6 +100,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank values over all ranks (replicas time
+    the same number of steps; the job is as slow as its slowest rank)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rate(world, steps, max_ms):
+    """Whole-job frames/s: every rank solves `steps` frames of its own pair."""
+    return world * steps / (max_ms / 1000.0)
+
+
+def replica_seed(seed, rank):
+    """Each replica solves its own seeded pair (no data is shared)."""
+    return seed + rank
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -190,6 +211,8 @@ def main():
     ap.add_argument("--block-iters", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batch", type=int, default=8,
+                    help="pairs per fs_batch for the batched-throughput figure (<= 1 skips)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -212,7 +235,7 @@ def main():
 
     from paper_1909_07545_gb300 import Solver
 
-    pair = workload_pair(args.workload, args.seed + rank)
+    pair = workload_pair(args.workload, replica_seed(args.seed, rank))
     H, W = pair["I0"].shape
     L, warps, iters = pair["levels"], pair["warps"], pair["iters"]
     stream = torch.cuda.Stream()
@@ -253,11 +276,7 @@ def main():
         t_wall = time.perf_counter() - t_wall
         clk = clocks.stop()
         step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-        total_ms = float(step_ms.sum())
-        if dist:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms, = reduce_max([float(step_ms.sum())], dist, "cuda")
 
         # primal-dual kernel timing (CUDA events around each warp's launches,
         # recorded by the library on this stream) over the same number of steps
@@ -283,8 +302,43 @@ def main():
         for _ in range(e2e_steps):
             s.solve_host(hI0, hI1, warps, iters, disp=hD, depth=hZ)
         e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_s, = reduce_max([e2e_s], dist, "cuda")
         pd_launches = sum(n for _, n, _ in per_level) // max(args.steps, 1)
         s.close()
+
+        # batched throughput: args.batch independent 1024^2 handles solved
+        # concurrently through one fs_batch graph (same pair on every handle)
+        batched = None
+        if args.batch > 1:
+            from paper_1909_07545_gb300 import Batch
+            sols = [Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, L,
+                           stream=stream, lam=pair["lam"], huber_eps=pair["eps"])
+                    for _ in range(args.batch)]
+            bt = Batch(sols, stream=stream)
+            outs_d = [torch.empty((H, W), device="cuda") for _ in sols]
+            outs_z = [torch.empty((H, W), device="cuda") for _ in sols]
+            bstep = lambda: bt.solve([I0] * len(sols), [I1] * len(sols), warps, iters,
+                                     disps=outs_d, depths=outs_z)
+            for _ in range(args.warmup):
+                bstep()
+            stream.synchronize()
+            bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                bev[i][0].record(stream)
+                bstep()
+                bev[i][1].record(stream)
+            stream.synchronize()
+            bms = np.array([a.elapsed_time(b) for a, b in bev])
+            btot, = reduce_max([float(bms.sum())], dist, "cuda")
+            batched = {"pairs_per_batch": len(sols),
+                       "value": job_rate(world, args.steps * len(sols), btot),
+                       "unit": "frames/s", "ms_per_batch": btot / args.steps,
+                       "note": "independent handles, one fs_batch graph per step"}
+            bt.close()
+            for x in sols:
+                x.close()
 
     if rank != 0:
         if dist:
@@ -293,7 +347,7 @@ def main():
 
     pxit_frame = sum(level_pixels(W, H, L)) * warps * iters
     ms_per_step = total_ms / args.steps
-    fps = world * args.steps / (total_ms / 1000.0)
+    fps = job_rate(world, args.steps, total_ms)
     ms0, n0, px0 = per_level[0]
     achieved = PD_BYTES_PER_PX_ITER * px0 / (ms0 / 1000.0) / 1e9
     peaks, src = measured_peaks()
@@ -327,7 +381,8 @@ def main():
         "clocks": clk,
         "wall_s": t_wall,
     }
-    line["e2e"] = {"value": 1.0 / e2e_s, "unit": "frames/s",
+    line["batched"] = batched
+    line["e2e"] = {"value": world / e2e_s, "unit": "frames/s",
                    "h2d_bytes_per_step": 2 * W * H * 4, "d2h_bytes_per_step": 2 * W * H * 4}
     if not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", "1")

@@ -147,6 +147,34 @@ fs_status fs_destroy(fs_handle* h);
 /* Message for the last failing call of this thread ("" if none). */
 const char* fs_last_error(void);
 
+/* ---- Batches: many independent pairs per call -------------------------
+ * A batch groups n handles (each from fs_create: any sizes, calibrations
+ * and poses, all on one device) and solves one pair per handle at once.
+ * Handle i's work runs on its own internal stream, forked from the batch
+ * stream and joined back to it, so the pairs' kernels overlap on the GPU;
+ * the whole fork/join schedule is captured into one CUDA graph the first
+ * time a set of buffers is seen and replayed afterwards.  Each pair's result
+ * is bit-identical to a lone fs_solve of that pair.  A handle may belong to
+ * one batch at a time and must not be used alone while a batch solve that
+ * includes it is in flight. */
+typedef struct fs_batch fs_batch;
+
+/* handles: n >= 1 distinct handles; cuda_stream: the stream the batch's
+ * graph is launched on (NULL = legacy default stream). */
+fs_status fs_batch_create(fs_handle* const* handles, int n, void* cuda_stream,
+                          fs_batch** out);
+
+/* Arrays of n device pointers, as for fs_solve per pair; d_init may be NULL
+ * (all cold starts) or hold NULL entries; d_disp / d_depth entries may be
+ * NULL.  warps >= 1, iters >= 1 for every pair.  Asynchronous on the batch
+ * stream. */
+fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0, const float* const* d_I1,
+                         const float* const* d_init, int warps, int iters,
+                         float* const* d_disp, float* const* d_depth);
+
+/* Free the batch (its streams, events and graph; not the handles). */
+fs_status fs_batch_destroy(fs_batch* b);
+
 /* ---- For callers that cannot allocate device memory --------------------
  * (The paper has no counterpart: this is a deployment variant.)  A real-time
  * host thread that must not risk the device-wide synchronisation an

@@ -13,7 +13,7 @@ import os
 
 import numpy as np
 
-__all__ = ["Solver", "FsError", "load_library", "default_params", "BUF", "STAGE",
+__all__ = ["Solver", "Batch", "FsError", "load_library", "default_params", "BUF", "STAGE",
            "LIB_PATH", "EXPORTED"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfs.so")
@@ -33,7 +33,8 @@ STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ENOMEM", -3: "FS_ECUDA", -4: "FS_
 EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_trajectory_field", "fs_solve", "fs_solve_host", "fs_destroy", "fs_last_error",
             "fs_buffer_read", "fs_buffer_write", "fs_run_stage", "fs_stage_prerotate",
-            "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc"]
+            "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc",
+            "fs_batch_create", "fs_batch_solve", "fs_batch_destroy"]
 
 
 class FsError(RuntimeError):
@@ -93,6 +94,10 @@ def load_library():
         "fs_timing_read": [_P, _P, _P, _P, i],
         "fs_pd_iterate_noalloc": [_P, _P, _P, _P, _P, _P, _P, i, i, i,
                                   ctypes.POINTER(FsParams), _P],
+        "fs_batch_create": [ctypes.POINTER(_P), i, _P, ctypes.POINTER(_P)],
+        "fs_batch_solve": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), i, i,
+                           ctypes.POINTER(_P), ctypes.POINTER(_P)],
+        "fs_batch_destroy": [_P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -275,3 +280,50 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """fs_batch: one concurrent solve over several Solvers (one pair each)."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.lib = load_library()
+        self.torch = torch
+        self.solvers = list(solvers)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        hs = (_P * len(self.solvers))(*[s.h for s in self.solvers])
+        b = _P()
+        _check(self.lib.fs_batch_create(hs, len(self.solvers), _P(stream.cuda_stream),
+                                        ctypes.byref(b)))
+        self.b = b
+
+    def solve(self, I0s, I1s, warps, iters, inits=None, disps=None, depths=None):
+        """Device tensors per pair; returns lists of (disparity, depth) tensors."""
+        torch = self.torch
+        n = len(self.solvers)
+        I0s = [s._dev(a) for s, a in zip(self.solvers, I0s)]
+        I1s = [s._dev(a) for s, a in zip(self.solvers, I1s)]
+        inits = [None] * n if inits is None else \
+            [None if a is None else s._dev(a) for s, a in zip(self.solvers, inits)]
+        if disps is None:
+            disps = [torch.empty((s.H, s.W), device="cuda") for s in self.solvers]
+        if depths is None:
+            depths = [torch.empty((s.H, s.W), device="cuda") for s in self.solvers]
+        arr = lambda ts: (_P * n)(*[None if t is None else t.data_ptr() for t in ts])
+        _check(self.lib.fs_batch_solve(self.b, arr(I0s), arr(I1s), arr(inits), int(warps),
+                                       int(iters), arr(disps), arr(depths)))
+        self._keep = (I0s, I1s, inits)
+        return disps, depths
+
+    def close(self):
+        if getattr(self, "b", None):
+            _check(self.lib.fs_batch_destroy(self.b))
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

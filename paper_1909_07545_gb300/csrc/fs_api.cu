@@ -669,6 +669,135 @@ fs_status fs_destroy(fs_handle* h) {
   return FS_OK;
 }
 
+// ------------------------------------------------------------------ batches
+
+struct fs_batch {
+  std::vector<fs_handle*> h;
+  cudaStream_t stream = nullptr;          // user stream the graph is launched on
+  cudaStream_t origin = nullptr;          // capture origin
+  std::vector<cudaStream_t> lanes;        // one per pair
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> key;
+  int warps = 0, iters = 0;
+};
+
+static void batch_free(fs_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaStream_t s : b->lanes) cudaStreamDestroy(s);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+extern "C" fs_status fs_batch_create(fs_handle* const* handles, int n, void* cuda_stream,
+                                     fs_batch** out) {
+  if (!out) return fail(FS_EINVAL, "null output batch pointer");
+  *out = nullptr;
+  if (!handles || n < 1) return fail(FS_EINVAL, "a batch needs n >= 1 handles");
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i]) return fail(FS_EINVAL, "batch handle %d is null", i);
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return fail(FS_EINVAL, "handle %d appears twice", i);
+  }
+  fs_batch* b = new (std::nothrow) fs_batch();
+  if (!b) return fail(FS_ENOMEM, "host allocation failed");
+  b->h.assign(handles, handles + n);
+  b->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    cudaStream_t s;
+    cudaEvent_t j;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    b->lanes.push_back(s);
+    e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    b->joins.push_back(j);
+  }
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return fail(FS_ECUDA, "fs_batch_create: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return FS_OK;
+}
+
+extern "C" fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0,
+                                    const float* const* d_I1, const float* const* d_init,
+                                    int warps, int iters, float* const* d_disp,
+                                    float* const* d_depth) {
+  if (!b) return fail(FS_EINVAL, "null batch");
+  if (!d_I0 || !d_I1 || !d_disp || !d_depth) return fail(FS_EINVAL, "null pointer array");
+  if (warps < 1 || iters < 1) return fail(FS_EINVAL, "warps and iters must be >= 1");
+  const int n = (int)b->h.size();
+  std::vector<const void*> key;
+  key.reserve(5 * n);
+  for (int i = 0; i < n; ++i) {
+    if (!d_I0[i] || !d_I1[i]) return fail(FS_EINVAL, "null input image for pair %d", i);
+    key.push_back(d_I0[i]);
+    key.push_back(d_I1[i]);
+    key.push_back(d_init ? d_init[i] : nullptr);
+    key.push_back(d_disp[i]);
+    key.push_back(d_depth[i]);
+  }
+  bool hit = b->gexec && warps == b->warps && iters == b->iters && key == b->key;
+  if (!hit) {
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    for (int i = 0; i < n; ++i) {
+      fs_status s;
+      if (b->h[i]->timing && (s = prepare_timing(b->h[i], warps)) != FS_OK) return s;
+    }
+    FS_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    fs_status s = FS_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->origin);
+    for (int i = 0; i < n && s == FS_OK && e == cudaSuccess; ++i) {
+      e = cudaStreamWaitEvent(b->lanes[i], b->fork, 0);
+      if (e != cudaSuccess) break;
+      s = enqueue_solve(b->h[i], d_I0[i], d_I1[i], d_init ? d_init[i] : nullptr, warps, iters,
+                        d_disp[i], d_depth[i], b->lanes[i]);
+      if (s != FS_OK) break;
+      e = cudaEventRecord(b->joins[i], b->lanes[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->joins[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->origin, &g);
+    if (s != FS_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return fail(FS_ECUDA, "batch capture failed: %s",
+                  cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->gexec = nullptr; return fail(FS_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e)); }
+    b->key = key;
+    b->warps = warps;
+    b->iters = iters;
+  }
+  FS_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+  for (int i = 0; i < n; ++i) {
+    fs_handle* h = b->h[i];
+    if (h->timing) {
+      h->ev_warps = warps;
+      h->ev_iters = iters;
+      h->ev_levels = (d_init && d_init[i]) ? 1 : h->L;
+      h->ev_pending = true;
+    }
+  }
+  return FS_OK;
+}
+
+extern "C" fs_status fs_batch_destroy(fs_batch* b) {
+  if (!b) return FS_OK;
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  return FS_OK;
+}
+
 // ------------------------------------------------------------------ stages
 
 static fs_status buffer_planes(fs_handle* h, int level, int buffer, float** base, int* planes,

@@ -214,7 +214,7 @@ __global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
   L.sy[i] = t.sy;
   if (!precond) {
     const float s = 0.35355339059327373f;   // 1/sqrt(8)
-    L.tau[i] = s;
+    L.tau[i] = (m & MASK_IN) ? s : 0.f;       // tau = 0 holds u outside the mask
     L.sig[i] = s;
     return;
   }

@@ -93,7 +93,7 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters) {
     for (int r = 0; r < R; ++r) {
       const int fy = ty * R + r;
       const float dv = px_div(s_t1[fy][tx], s_t1[fy][txl], s_t2[fy][tx], s_t2[max(fy - 1, 0)][tx]);
-      const float un = px_primal(mb >> (3 * r), u[r], dv, c[r]);
+      const float un = px_primal(u[r], dv, c[r]);
       ub[r] = px_relax(un, u[r], theta);
       u[r] = un;
       s_ub[fy][tx] = ub[r];
@@ -194,7 +194,7 @@ k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
       const int fy = ty * R + r;
       const float dv = px_div(s_t1[fy * S1 + tx + 1], s_t1[fy * S1 + tx],
                               s_t2[(fy + 1) * TW + tx], s_t2[fy * TW + tx]);
-      const float un = px_primal(mb >> (3 * r), u[r], dv, c[r]);
+      const float un = px_primal(u[r], dv, c[r]);
       ub[r] = px_relax(un, u[r], theta);
       u[r] = un;
       s_ub[fy * SU + tx] = ub[r];

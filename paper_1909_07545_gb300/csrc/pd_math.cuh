@@ -10,7 +10,9 @@
 //           u' = uh + tau lam I_u   if rb < -tau lam I_u^2
 //                uh - tau lam I_u   if rb >  tau lam I_u^2
 //                uh - rb / I_u      otherwise       (Eq. 13, resolvent of the L1 term)
-//           only inside the FOV mask (u held elsewhere)
+//              = uh + clamp(-rb / I_u, -|tau lam I_u|, |tau lam I_u|)
+//           (the three cases are the clamp of the unconstrained step; I_u = 0
+//           gives uh).  tau = 0 outside the FOV mask, so u is held there.
 #pragma once
 
 #include "fs_device.cuh"
@@ -21,7 +23,7 @@ namespace fs {
 struct PxConst {
   float sx, sy;      // T^1/2 = I - s s^T
   float dinv, sd;    // 1 / (1 + sigma eps), sigma / (1 + sigma eps)
-  float tau, step;   // tau, tau lam I_u
+  float tau, step;   // tau, |tau lam I_u|
   float Iu, rho0, uw, inv;   // linearisation, 1 / I_u (0 when I_u = 0)
 };
 
@@ -34,7 +36,7 @@ __device__ __forceinline__ void px_load(const LevelView& L, size_t i, float lam,
   c.sd = __fmul_rn(sg, c.dinv);
   c.tau = L.tau[i];
   c.Iu = L.Iu[i];
-  c.step = __fmul_rn(__fmul_rn(c.tau, lam), c.Iu);
+  c.step = fabsf(__fmul_rn(__fmul_rn(c.tau, lam), c.Iu));
   c.rho0 = L.rho0[i];
   c.uw = L.uw[i];
   c.inv = c.Iu != 0.f ? __fdiv_rn(1.f, c.Iu) : 0.f;
@@ -58,12 +60,10 @@ __device__ __forceinline__ void px_dual(unsigned m, float ub, float right, float
   const float k2 = fmaf(-c.sy, d, g2);
   float q1 = fmaf(c.sd, k1, __fmul_rn(p1, c.dinv));
   float q2 = fmaf(c.sd, k2, __fmul_rn(p2, c.dinv));
-  const float nn = fmaf(q1, q1, __fmul_rn(q2, q2));
-  if (nn > 1.f) {
-    const float s = rsqrtf(nn);
-    q1 = __fmul_rn(q1, s);
-    q2 = __fmul_rn(q2, s);
-  }
+  // P(q) = q / max(1, |q|): scale by min(1, 1/|q|) (1 for |q| <= 1, also q = 0)
+  const float s = fminf(1.f, rsqrtf(fmaf(q1, q1, __fmul_rn(q2, q2))));
+  q1 = __fmul_rn(q1, s);
+  q2 = __fmul_rn(q2, s);
   p1 = q1;
   p2 = q2;
   const float dp = fmaf(c.sx, q1, __fmul_rn(c.sy, q2));
@@ -83,15 +83,13 @@ __device__ __forceinline__ float px_relax(float un, float u, float theta) {
 }
 
 // Primal descent + shrinkage at one pixel; dv = div(T^1/2 p) at the pixel.
-// Returns the new u (unchanged outside the mask).
-__device__ __forceinline__ float px_primal(unsigned m, float u, float dv, const PxConst& c) {
-  if (!(m & MASK_IN)) return u;
+// Returns the new u (unchanged where tau = 0, i.e. outside the mask).
+__device__ __forceinline__ float px_primal(float u, float dv, const PxConst& c) {
   const float uh = fmaf(c.tau, dv, u);
   // rho0 + I_u (uh - u_w): the small increment keeps its precision
   const float rb = fmaf(c.Iu, __fsub_rn(uh, c.uw), c.rho0);
-  const float thr = __fmul_rn(c.step, c.Iu);     // tau lam I_u^2
-  return rb < -thr ? __fadd_rn(uh, c.step)
-                   : (rb > thr ? __fsub_rn(uh, c.step) : fmaf(-rb, c.inv, uh));
+  const float du = fminf(fmaxf(__fmul_rn(-rb, c.inv), -c.step), c.step);
+  return __fadd_rn(uh, du);
 }
 
 }  // namespace fs

@@ -75,5 +75,11 @@ def test_host_side_validation(lib):
     assert st == -1 and "parameter" in msg
     h = ctypes.c_void_p()
     assert lib.fs_solve(None, None, None, None, 1, 1, None, None) == -1
+    b = ctypes.c_void_p()
+    assert lib.fs_batch_create(None, 0, None, ctypes.byref(b)) == -1
+    two = (ctypes.c_void_p * 2)(16, 16)
+    assert lib.fs_batch_create(two, 2, None, ctypes.byref(b)) == -1     # duplicate handle
+    assert "twice" in lib.fs_last_error().decode()
+    assert lib.fs_batch_destroy(None) == 0
     assert lib.fs_destroy(None) == 0
     assert lib.fs_create(None, None, 64, 64, 1, None, None, ctypes.byref(h)) == -1

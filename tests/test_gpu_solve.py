@@ -136,3 +136,28 @@ def test_warm_start_matches_oracle(small):
     # the rebuilt warp vector itself, before any iteration
     s.solve(small["I0"], small["I1"], 1, 1, init=d0)
     s.close()
+
+
+def test_batch_results_equal_lone_solves(small):
+    # pairs of three sizes (256^2, ragged 203x157, 128^2) solved concurrently
+    # through one batch graph: each result is bit-identical to its lone solve
+    import paper_1909_07545_gb300 as fsb
+    pairs = [small, ragged_pair(2), f32pair(synth.plain_small(3, W=128, H=128))]
+    for p in pairs[1:]:
+        p.setdefault("warps", 3)
+    alone = []
+    for p in pairs:
+        s = make_solver(p)
+        d, z = s.solve(p["I0"], p["I1"], 3, 25)
+        alone.append((np64(d), np64(z)))
+        s.close()
+    solvers = [make_solver(p) for p in pairs]
+    batch = fsb.Batch(solvers)
+    for rep in range(2):                     # capture, then replay
+        ds, zs = batch.solve([p["I0"] for p in pairs], [p["I1"] for p in pairs], 3, 25)
+        for (d, z), (ad, az) in zip(zip(ds, zs), alone):
+            assert np.array_equal(np64(d), ad)
+            assert np.array_equal(np64(z), az, equal_nan=True)
+    batch.close()
+    for s in solvers:
+        s.close()
