@@ -288,7 +288,7 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
     if ((iters - done) % (nl - k)) ++n;
     const PDState& in = (k % 2 == 0) ? A : Bs;
     const PDState& out = (k % 2 == 0) ? Bs : A;
-    cudaError_t e = launch_pd(variant, L.v, in, out, pp, B, n, st);
+    cudaError_t e = launch_pd(variant, L.v, in, out, pp, B, n, st, k > 0);
     if (e != cudaSuccess) return fail(FS_ECUDA, "launch of k_pd failed: %s", cudaGetErrorString(e));
     done += n;
   }

@@ -32,8 +32,12 @@ __global__ void k_tensor_abc(LevelView L, float* __restrict__ dst);
 
 // Primal-dual iterations: n <= B iterations with halo B, tile variant
 // `variant`, state read from `in` and written to `out` (distinct buffers).
+// chained = true when the launch directly follows another k_pd launch on
+// the stream: it is then a programmatic dependent launch that loads its
+// per-warp constants while the preceding launch drains, and waits for it
+// before reading the state.
 cudaError_t launch_pd(int variant, const LevelView& L, const PDState& in, const PDState& out,
-                      const PDParams& pp, int B, int n, cudaStream_t st);
+                      const PDParams& pp, int B, int n, cudaStream_t st, bool chained = false);
 
 // Whole-level primal-dual in one thread-block cluster: the tile variant for a
 // W x H level (-1 if none), whether its cluster can be resident on this GPU,

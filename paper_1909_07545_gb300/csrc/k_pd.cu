@@ -35,7 +35,7 @@ namespace fs {
 
 template <int FW, int NY, int R>
 __global__ void __launch_bounds__(FW * NY, 1)
-k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters) {
+k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int chained) {
   constexpr int FH = NY * R;
   __shared__ float s_ub[FH][FW];
   __shared__ float s_t1[FH][FW];
@@ -49,10 +49,29 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters) {
   const bool col_in = gx >= 0 && gx < L.W;
   const float theta = pp.theta;
 
+  // Let the next launch of the chain be scheduled as soon as every CTA of
+  // this one is resident (it waits for this grid's completion before it
+  // reads the state, below).
+  if (chained) cudaTriggerProgrammaticLaunchCompletion();
+
   float u[R], ub[R], p1[R], p2[R];
   PxConst c[R];
   unsigned mb = 0;
-
+  // per-warp constants first: written by earlier kernels, not by the
+  // preceding launch of this chain
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gy = oy + ty * R + r;
+    if (col_in && gy >= 0 && gy < L.H) {
+      const size_t i = (size_t)gy * L.P + gx;
+      px_load(L, i, pp.lam, pp.eps, c[r]);
+      mb |= (unsigned)L.mask[i] << (3 * r);
+    } else {
+      px_zero(c[r]);
+    }
+  }
+  // the state is the preceding launch's output
+  if (chained) cudaGridDependencySynchronize();
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int fy = ty * R + r;
@@ -63,11 +82,8 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters) {
       ub[r] = in.ubar[i];
       p1[r] = in.p1[i];
       p2[r] = in.p2[i];
-      px_load(L, i, pp.lam, pp.eps, c[r]);
-      mb |= (unsigned)L.mask[i] << (3 * r);
     } else {
       u[r] = ub[r] = p1[r] = p2[r] = 0.f;
-      px_zero(c[r]);
     }
     s_ub[fy][tx] = ub[r];
   }
@@ -219,19 +235,27 @@ k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
 
 template <int FW, int NY, int R>
 static cudaError_t launch_pd_t(const LevelView& L, const PDState& in, const PDState& out,
-                               const PDParams& pp, int B, int n, cudaStream_t st) {
+                               const PDParams& pp, int B, int n, bool chained,
+                               cudaStream_t st) {
   const int IW = FW - 2 * B, IH = NY * R - 2 * B;
   if (IW <= 0 || IH <= 0 || n < 0 || n > B) return cudaErrorInvalidValue;
-  dim3 grid((L.W + IW - 1) / IW, (L.H + IH - 1) / IH);
-  k_pd<FW, NY, R><<<grid, dim3(FW, NY), 0, st>>>(L, in, out, pp, B, n);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((L.W + IW - 1) / IW, (L.H + IH - 1) / IH, 1);
+  cfg.blockDim = dim3(FW, NY, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_pd<FW, NY, R>, L, in, out, pp, B, n, chained ? 1 : 0);
 }
 
 cudaError_t launch_pd(int variant, const LevelView& L, const PDState& in, const PDState& out,
-                      const PDParams& pp, int B, int n, cudaStream_t st) {
+                      const PDParams& pp, int B, int n, cudaStream_t st, bool chained) {
   switch (variant) {
-    case PD_TILE_64: return launch_pd_t<64, 8, 8>(L, in, out, pp, B, n, st);
-    case PD_TILE_32: return launch_pd_t<32, 8, 4>(L, in, out, pp, B, n, st);
+    case PD_TILE_64: return launch_pd_t<64, 8, 8>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_32: return launch_pd_t<32, 8, 4>(L, in, out, pp, B, n, chained, st);
     default: return cudaErrorInvalidValue;
   }
 }
