@@ -211,6 +211,8 @@ def main():
     ap.add_argument("--block-iters", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip fs_autotune (default schedule per level)")
     ap.add_argument("--batch", type=int, default=8,
                     help="pairs per fs_batch for the batched-throughput figure (<= 1 skips)")
     args = ap.parse_args()
@@ -243,6 +245,7 @@ def main():
         s = Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, L, stream=stream,
                    lam=pair["lam"], huber_eps=pair["eps"], use_graph=1,
                    block_iters=args.block_iters)
+        tuned = s.autotune(iters) if args.autotune else None
         I0 = torch.as_tensor(np.float32(pair["I0"]), device="cuda")
         I1 = torch.as_tensor(np.float32(pair["I1"]), device="cuda")
         disp = torch.empty((H, W), device="cuda")
@@ -314,6 +317,9 @@ def main():
             sols = [Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, L,
                            stream=stream, lam=pair["lam"], huber_eps=pair["eps"])
                     for _ in range(args.batch)]
+            if args.autotune:
+                for x in sols:
+                    x.autotune(iters)
             bt = Batch(sols, stream=stream)
             outs_d = [torch.empty((H, W), device="cuda") for _ in sols]
             outs_z = [torch.empty((H, W), device="cuda") for _ in sols]
@@ -364,7 +370,10 @@ def main():
         "config": {"workload": pair["name"], "W": W, "H": H, "levels": L, "warps": warps,
                    "iters": iters, "camera": "kannala_brandt f=320 fov=190",
                    "l2": "flushed between steps (256 MB write)",
-                   "block_iters": args.block_iters or "auto (6 above 512 px, 8 below)", "graph": True, "pd_schedule": "cluster <= 128 px, temporal blocking above",
+                   "pd_schedule_per_level": (
+                       ["cluster" if c == 0 else f"blocking x{c}" for c in tuned]
+                       if tuned else "default (cluster <= 128 px, blocking 6 / 8 above)"),
+                   "autotuned": bool(tuned), "graph": True,
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),

@@ -76,6 +76,16 @@ fs_status fs_timing_enable(fs_handle* h, int enable);
 fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
                          double* pixel_iters, int reset);
 
+/* Autotuner of the primal-dual schedule.  For every level, times `iters`
+ * iterations (best of 3 after a warm-up, CUDA events on the handle's
+ * stream) of each candidate -- the whole-level cluster schedule where the
+ * level fits one cluster, and temporal blocking with 1..8 iterations per
+ * launch -- and keeps the fastest for later solves when block_iters = 0 and
+ * pd_schedule = 0.  choice (may be NULL) receives per level 0 = cluster or
+ * the depth 1..8.  Overwrites the levels' state; synchronises the stream.
+ * All candidates give identical results. */
+fs_status fs_autotune(fs_handle* h, int iters, int* choice);
+
 #ifdef __cplusplus
 }
 #endif

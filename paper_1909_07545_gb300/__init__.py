@@ -34,7 +34,7 @@ EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_trajectory_field", "fs_solve", "fs_solve_host", "fs_destroy", "fs_last_error",
             "fs_buffer_read", "fs_buffer_write", "fs_run_stage", "fs_stage_prerotate",
             "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc",
-            "fs_batch_create", "fs_batch_solve", "fs_batch_destroy"]
+            "fs_batch_create", "fs_batch_solve", "fs_batch_destroy", "fs_autotune"]
 
 
 class FsError(RuntimeError):
@@ -98,6 +98,7 @@ def load_library():
         "fs_batch_solve": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), i, i,
                            ctypes.POINTER(_P), ctypes.POINTER(_P)],
         "fs_batch_destroy": [_P],
+        "fs_autotune": [_P, i, _P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -252,6 +253,13 @@ class Solver:
         depth = self.torch.empty_like(disp)
         _check(self.lib.fs_stage_depth(self.h, _ptr(disp), _ptr(depth)))
         return disp, depth
+
+    def autotune(self, iters=20):
+        """Pick the primal-dual schedule per level by timing (fs_autotune).
+        Returns per level 0 = cluster or the temporal-blocking depth."""
+        out = (ctypes.c_int * 8)()
+        _check(self.lib.fs_autotune(self.h, int(iters), out))
+        return [out[l] for l in range(self.levels)]
 
     def timing_enable(self, on=True):
         _check(self.lib.fs_timing_enable(self.h, 1 if on else 0))

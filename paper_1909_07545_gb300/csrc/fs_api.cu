@@ -51,6 +51,7 @@ struct HostLevel {
   int W = 0, H = 0, P = 0;
   double fx = 0, fy = 0, cx = 0, cy = 0;   // level calibration (camera 0)
   int cluster = -1;                         // whole-level cluster variant, -1 if none
+  int tuned = -1;                           // autotuned choice: 0 cluster, 1..8 depth, -1 none
   LevelView v{};
 };
 
@@ -255,8 +256,17 @@ fs_status build_fields(fs_handle* h) {
 // bound); measured on GB300 with the 1024 x 1024 workload.
 int pd_block(const fs_handle* h, int l) {
   int b = h->prm.block_iters;
+  if (b <= 0 && h->lv[l].tuned >= 1) return h->lv[l].tuned;
   if (b <= 0) return (h->lv[l].W > 512 || h->lv[l].H > 512) ? 6 : 8;
   return b > 8 ? 8 : b;
+}
+
+// Whether level l runs the whole-level cluster schedule.
+bool use_cluster(const fs_handle* h, int l) {
+  const HostLevel& L = h->lv[l];
+  if (L.cluster < 0 || h->prm.pd_schedule != 0) return false;
+  if (h->prm.block_iters <= 0 && L.tuned >= 1) return false;   // tuner chose blocking
+  return true;
 }
 
 // Number of k_pd launches for `iters` iterations with at most B per launch:
@@ -272,7 +282,7 @@ int pd_launches(int iters, int B) {
 fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
   HostLevel& L = h->lv[l];
   PDParams pp{h->prm.lambda, h->prm.huber_eps, h->prm.theta};
-  if (L.cluster >= 0 && h->prm.pd_schedule == 0) {
+  if (use_cluster(h, l)) {
     cudaError_t e = launch_pd_cluster(L.cluster, L.v, pp, iters, st);
     if (e != cudaSuccess)
       return fail(FS_ECUDA, "launch of k_pd_cluster failed: %s", cudaGetErrorString(e));
@@ -921,7 +931,7 @@ extern "C" fs_status fs_timing_read(fs_handle* h, double* ms, long long* launche
                                      h->ev[2 * (l * h->ev_warps + w) + 1]));
         h->t_ms[l] += t;
       }
-      h->t_launch[l] += h->lv[l].cluster >= 0 && h->prm.pd_schedule == 0
+      h->t_launch[l] += use_cluster(h, l)
                             ? (long long)h->ev_warps
                             : (long long)h->ev_warps * pd_launches(h->ev_iters, B);
       h->t_pxit[l] += (double)h->lv[l].W * h->lv[l].H * h->ev_warps * h->ev_iters;
@@ -935,6 +945,47 @@ extern "C" fs_status fs_timing_read(fs_handle* h, double* ms, long long* launche
     if (reset) { h->t_ms[l] = 0; h->t_launch[l] = 0; h->t_pxit[l] = 0; }
   }
   return FS_OK;
+}
+
+extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (iters < 1) return fail(FS_EINVAL, "iters must be >= 1");
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  cudaEvent_t e0, e1;
+  FS_CUDA(cudaEventCreate(&e0));
+  FS_CUDA(cudaEventCreate(&e1));
+  const int saved_block = h->prm.block_iters, saved_sched = h->prm.pd_schedule;
+  fs_status st = FS_OK;
+  for (int l = 0; l < h->L && st == FS_OK; ++l) {
+    HostLevel& L = h->lv[l];
+    L.tuned = -1;
+    float best = 3.4e38f;
+    int best_c = -1;
+    for (int cand = (L.cluster >= 0 ? 0 : 1); cand <= 8 && st == FS_OK; ++cand) {
+      h->prm.pd_schedule = cand == 0 ? 0 : 1;
+      h->prm.block_iters = cand == 0 ? saved_block : cand;
+      float t = 3.4e38f;
+      for (int rep = 0; rep < 4 && st == FS_OK; ++rep) {   // first run warms up
+        cudaError_t e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess && (st = run_pd(h, l, iters, h->stream)) != FS_OK) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { st = fail(FS_ECUDA, "fs_autotune: %s", cudaGetErrorString(e)); break; }
+        if (rep > 0 && ms < t) t = ms;
+      }
+      if (st == FS_OK && t < best) { best = t; best_c = cand; }
+    }
+    L.tuned = best_c;
+    if (choice) choice[l] = best_c;
+  }
+  h->prm.block_iters = saved_block;
+  h->prm.pd_schedule = saved_sched;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 extern "C" fs_status fs_stage_depth(fs_handle* h, float* d_disp, float* d_depth) {
