@@ -78,7 +78,11 @@ typedef struct {
  * pd_schedule: 0 = automatic (levels up to 128 x 128 run all iterations of
  * a warp in one launch of a thread-block cluster holding the whole level,
  * when the GPU can host that cluster; larger levels use temporal blocking),
- * 1 = temporal blocking on every level.  Both give identical results. */
+ * 1 = temporal blocking on every level.  Both give identical results.
+ * storage: 0 = FP32; 1 = FP16, 2 = BF16 storage of the images, the warped
+ * gradient and residual (I_u, rho0), the tensor T^1/2 and the dual field p,
+ * while the disparity (u, u_omega), the warp vector and every operation stay
+ * FP32 (values are rounded to nearest when stored). */
 typedef struct {
   float lambda;
   float huber_eps;
@@ -90,7 +94,8 @@ typedef struct {
   int block_iters;
   int use_graph;
   int pd_schedule;
-  int reserved[4];         /* must be 0 */
+  int storage;
+  int reserved[3];         /* must be 0 */
 } fs_params;
 
 typedef struct fs_handle fs_handle;

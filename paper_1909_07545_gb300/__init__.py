@@ -58,7 +58,8 @@ class FsParams(ctypes.Structure):
                 ("du_max", ctypes.c_float), ("beta", ctypes.c_float), ("eta", ctypes.c_float),
                 ("theta", ctypes.c_float), ("precond", ctypes.c_int),
                 ("block_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("pd_schedule", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("pd_schedule", ctypes.c_int), ("storage", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -115,11 +116,16 @@ def _check(status):
         raise FsError(status, _lib.fs_last_error().decode())
 
 
+STORAGE = {"f32": 0, "fp32": 0, "f16": 1, "fp16": 1, "bf16": 2}
+
+
 def default_params(**overrides) -> FsParams:
     lib = load_library()
     p = FsParams()
     _check(lib.fs_default_params(ctypes.byref(p)))
     for k, v in overrides.items():
+        if k == "storage" and isinstance(v, str):
+            v = STORAGE[v]
         setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
     return p
 

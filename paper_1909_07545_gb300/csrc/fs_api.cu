@@ -306,8 +306,8 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
     size_t bytes = (size_t)L.P * L.H * sizeof(float);
     FS_CUDA(cudaMemcpyAsync(A.u, Bs.u, bytes, cudaMemcpyDeviceToDevice, st));
     FS_CUDA(cudaMemcpyAsync(A.ubar, Bs.ubar, bytes, cudaMemcpyDeviceToDevice, st));
-    FS_CUDA(cudaMemcpyAsync(A.p1, Bs.p1, bytes, cudaMemcpyDeviceToDevice, st));
-    FS_CUDA(cudaMemcpyAsync(A.p2, Bs.p2, bytes, cudaMemcpyDeviceToDevice, st));
+    FS_CUDA(cudaMemcpyAsync(A.p1.p, Bs.p1.p, bytes, cudaMemcpyDeviceToDevice, st));
+    FS_CUDA(cudaMemcpyAsync(A.p2.p, Bs.p2.p, bytes, cudaMemcpyDeviceToDevice, st));
   }
   return FS_OK;
 }
@@ -381,9 +381,10 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
                         int warps, int iters, float* disp, float* depth, cudaStream_t st) {
   fs_status s;
   HostLevel& L0 = h->lv[0];
-  k_copy_in<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(I0, L0.v.I0, L0.W, L0.H, L0.P);
-  FS_LAUNCHED("k_copy_in");
-  k_prerotate<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(I1, h->cfield, L0.v.I1, L0.W, L0.H, L0.P);
+  k_copy_in_s<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(I0, L0.v.I0, L0.v.st, L0.W, L0.H, L0.P);
+  FS_LAUNCHED("k_copy_in_s");
+  k_prerotate<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(I1, h->cfield, L0.v.I1, L0.v.st, L0.W, L0.H,
+                                                     L0.P);
   FS_LAUNCHED("k_prerotate");
   int top = h->L - 1;
   if (init) {   // warm start: the finest level only, from the given disparity
@@ -491,7 +492,8 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     p = *prm;
     if (!(p.lambda > 0) || !(p.huber_eps >= 0) || !(p.du_max > 0) || !(p.beta >= 0) ||
         !(p.eta > 0) || !(p.theta >= 0 && p.theta <= 1) || p.block_iters < 0 ||
-        p.block_iters > 8 || p.pd_schedule < 0 || p.pd_schedule > 1)
+        p.block_iters > 8 || p.pd_schedule < 0 || p.pd_schedule > 1 || p.storage < 0 ||
+        p.storage > 2)
       return fail(FS_EINVAL, "parameter out of range");
   } else {
     fs_default_params(&p);
@@ -544,10 +546,13 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     size_t plane8 = align_up((size_t)L.P * L.H, 256);
     LevelView& v = L.v;
     v.W = L.W; v.H = L.H; v.P = L.P;
+    v.st = p.storage;
     v.mask = (const uint8_t*)cur; cur += plane8;
-    float** fl[] = {&v.I0, &v.I1, &v.sx, &v.sy, &v.tau, &v.sig, &v.u, &v.ubar, &v.uw,
-                    &v.p1, &v.p2, &v.Iu, &v.rho0, &v.u_alt, &v.ubar_alt, &v.p1_alt, &v.p2_alt};
+    float** fl[] = {&v.tau, &v.sig, &v.u, &v.ubar, &v.uw, &v.u_alt, &v.ubar_alt};
     for (float** f : fl) { *f = (float*)cur; cur += plane; }
+    SPlane* sp[] = {&v.I0, &v.I1, &v.sx, &v.sy, &v.p1, &v.p2, &v.Iu, &v.rho0, &v.p1_alt,
+                    &v.p2_alt};
+    for (SPlane* f : sp) { f->p = cur; cur += plane; }
     float2** f2[] = {&v.gamma, &v.w, &v.g};
     for (float2** f : f2) { *f = (float2*)cur; cur += 2 * plane; }
   }
@@ -810,26 +815,30 @@ extern "C" fs_status fs_batch_destroy(fs_batch* b) {
 
 // ------------------------------------------------------------------ stages
 
-static fs_status buffer_planes(fs_handle* h, int level, int buffer, float** base, int* planes,
-                               int* stride) {
+// Where a buffer lives: FP32 planes (kind 0), interleaved float2 (kind 1) or
+// planes in the level's storage (kind 2).
+struct BufLoc {
+  int kind = 0, planes = 1;
+  float* f[2] = {nullptr, nullptr};
+  SPlane s[2] = {{nullptr}, {nullptr}};
+};
+
+static fs_status buffer_loc(fs_handle* h, int level, int buffer, BufLoc& b) {
   LevelView& v = h->lv[level].v;
-  size_t plane = align_up((size_t)v.P * v.H * sizeof(float), 256) / sizeof(float);
-  *stride = 1;
   switch (buffer) {
-    case FS_BUF_I0: *base = v.I0; *planes = 1; break;
-    case FS_BUF_I1: *base = v.I1; *planes = 1; break;
-    case FS_BUF_GAMMA: *base = (float*)v.gamma; *planes = 2; *stride = 2; break;
-    case FS_BUF_U: *base = v.u; *planes = 1; break;
-    case FS_BUF_UBAR: *base = v.ubar; *planes = 1; break;
-    case FS_BUF_UW: *base = v.uw; *planes = 1; break;
-    case FS_BUF_P: *base = v.p1; *planes = 2; break;
-    case FS_BUF_W: *base = (float*)v.w; *planes = 2; *stride = 2; break;
-    case FS_BUF_IU: *base = v.Iu; *planes = 1; break;
-    case FS_BUF_RHO0: *base = v.rho0; *planes = 1; break;
-    case FS_BUF_G: *base = (float*)v.g; *planes = 2; *stride = 2; break;
+    case FS_BUF_I0: b.kind = 2; b.s[0] = v.I0; break;
+    case FS_BUF_I1: b.kind = 2; b.s[0] = v.I1; break;
+    case FS_BUF_GAMMA: b.kind = 1; b.planes = 2; b.f[0] = (float*)v.gamma; break;
+    case FS_BUF_U: b.f[0] = v.u; break;
+    case FS_BUF_UBAR: b.f[0] = v.ubar; break;
+    case FS_BUF_UW: b.f[0] = v.uw; break;
+    case FS_BUF_P: b.kind = 2; b.planes = 2; b.s[0] = v.p1; b.s[1] = v.p2; break;
+    case FS_BUF_W: b.kind = 1; b.planes = 2; b.f[0] = (float*)v.w; break;
+    case FS_BUF_IU: b.kind = 2; b.s[0] = v.Iu; break;
+    case FS_BUF_RHO0: b.kind = 2; b.s[0] = v.rho0; break;
+    case FS_BUF_G: b.kind = 1; b.planes = 2; b.f[0] = (float*)v.g; break;
     default: return fail(FS_EINVAL, "buffer %d cannot be accessed this way", buffer);
   }
-  (void)plane;
   return FS_OK;
 }
 
@@ -857,12 +866,15 @@ extern "C" fs_status fs_buffer_read(fs_handle* h, int level, int buffer, float* 
     FS_LAUNCHED("k_pack");
     return FS_OK;
   }
-  float* base;
-  int planes, stride;
-  if ((s = buffer_planes(h, level, buffer, &base, &planes, &stride)) != FS_OK) return s;
-  for (int c = 0; c < planes; ++c) {
-    const float* src = stride == 2 ? base + c : (c == 0 ? base : L.v.p2);
-    k_pack<<<grid2(L.W, L.H), kBlock2, 0, st>>>(src, stride, d_out + c * n, L.W, L.H, L.P);
+  BufLoc b;
+  if ((s = buffer_loc(h, level, buffer, b)) != FS_OK) return s;
+  for (int c = 0; c < b.planes; ++c) {
+    if (b.kind == 2)
+      k_pack_s<<<grid2(L.W, L.H), kBlock2, 0, st>>>(b.s[c], L.v.st, d_out + c * n, L.W, L.H, L.P);
+    else
+      k_pack<<<grid2(L.W, L.H), kBlock2, 0, st>>>(b.kind == 1 ? b.f[0] + c : b.f[c],
+                                                  b.kind == 1 ? 2 : 1, d_out + c * n, L.W,
+                                                  L.H, L.P);
     FS_LAUNCHED("k_pack");
   }
   return FS_OK;
@@ -877,12 +889,15 @@ extern "C" fs_status fs_buffer_write(fs_handle* h, int level, int buffer, const 
     return fail(FS_EINVAL, "buffer %d is derived and read-only", buffer);
   HostLevel& L = h->lv[level];
   size_t n = (size_t)L.W * L.H;
-  float* base;
-  int planes, stride;
-  if ((s = buffer_planes(h, level, buffer, &base, &planes, &stride)) != FS_OK) return s;
-  for (int c = 0; c < planes; ++c) {
-    float* dst = stride == 2 ? base + c : (c == 0 ? base : L.v.p2);
-    k_unpack<<<grid2(L.W, L.H), kBlock2, 0, h->stream>>>(d_in + c * n, dst, stride, L.W, L.H, L.P);
+  BufLoc b;
+  if ((s = buffer_loc(h, level, buffer, b)) != FS_OK) return s;
+  for (int c = 0; c < b.planes; ++c) {
+    if (b.kind == 2)
+      k_unpack_s<<<grid2(L.W, L.H), kBlock2, 0, h->stream>>>(d_in + c * n, b.s[c], L.v.st, L.W,
+                                                             L.H, L.P);
+    else
+      k_unpack<<<grid2(L.W, L.H), kBlock2, 0, h->stream>>>(
+          d_in + c * n, b.kind == 1 ? b.f[0] + c : b.f[c], b.kind == 1 ? 2 : 1, L.W, L.H, L.P);
     FS_LAUNCHED("k_unpack");
   }
   return FS_OK;
@@ -900,7 +915,8 @@ extern "C" fs_status fs_stage_prerotate(fs_handle* h, const float* d_I1) {
   if ((s = check_handle(h)) != FS_OK) return s;
   if (!d_I1) return fail(FS_EINVAL, "null input");
   HostLevel& L0 = h->lv[0];
-  k_prerotate<<<grid2(L0.W, L0.H), kBlock2, 0, h->stream>>>(d_I1, h->cfield, L0.v.I1, L0.W, L0.H, L0.P);
+  k_prerotate<<<grid2(L0.W, L0.H), kBlock2, 0, h->stream>>>(d_I1, h->cfield, L0.v.I1, L0.v.st,
+                                                             L0.W, L0.H, L0.P);
   FS_LAUNCHED("k_prerotate");
   return FS_OK;
 }

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace fs {
@@ -202,24 +204,62 @@ __device__ __forceinline__ float2 sample_bicubic2(const float2* __restrict__ f, 
   return make_float2(sx, sy);
 }
 
+// ---------------------------------------------------------------- storage
+
+// Storage of the images, warped gradients, tensor and dual fields: FP32,
+// or FP16 / BF16 with all arithmetic still in FP32 (values are converted on
+// load and rounded to nearest on store).
+enum Storage { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+
+// A plane of one of those fields, element type given by the level's storage.
+struct SPlane {
+  void* p;
+  __device__ __forceinline__ float ld(size_t i, int s) const {
+    if (s == ST_F16) return __half2float(__ldg((const __half*)p + i));
+    if (s == ST_BF16) return __bfloat162float(__ldg((const __nv_bfloat16*)p + i));
+    return __ldg((const float*)p + i);
+  }
+  __device__ __forceinline__ void st(size_t i, float v, int s) const {
+    if (s == ST_F16) ((__half*)p)[i] = __float2half_rn(v);
+    else if (s == ST_BF16) ((__nv_bfloat16*)p)[i] = __float2bfloat16_rn(v);
+    else ((float*)p)[i] = v;
+  }
+};
+
+// Bilinear sample of a stored plane at (x + dx, y + dy), clamped.
+__device__ __forceinline__ float sample_bilinear(const SPlane& img, int s, int W, int H, int P,
+                                                 int x, float dx, int y, float dy) {
+  Tap tx = tap_linear(x, dx, W), ty = tap_linear(y, dy, H);
+  const size_t r0 = (size_t)ty.i0 * P, r1 = (size_t)ty.i1 * P;
+  float v00 = img.ld(r0 + tx.i0, s), v01 = img.ld(r0 + tx.i1, s);
+  float v10 = img.ld(r1 + tx.i0, s), v11 = img.ld(r1 + tx.i1, s);
+  float top = fmaf(tx.a, v01 - v00, v00);
+  float bot = fmaf(tx.a, v11 - v10, v10);
+  return fmaf(ty.a, bot - top, top);
+}
+
 // ---------------------------------------------------------------- levels
 
-// Device view of one pyramid level (pitch P floats per row).
+// Device view of one pyramid level (pitch P elements per row).
 struct LevelView {
   int W, H, P;
+  int st;                // Storage of the SPlane fields
   const uint8_t* mask;
-  float *I0, *I1;
+  SPlane I0, I1;
   float2* gamma;
-  float *sx, *sy;        // T^1/2 = I - s s^T, s = sqrt(1 - e) n  (Eq. 12)
+  SPlane sx, sy;         // T^1/2 = I - s s^T, s = sqrt(1 - e) n  (Eq. 12)
   float *tau, *sig;      // primal / dual step sizes
-  float *u, *ubar, *uw, *p1, *p2, *Iu, *rho0;
+  float *u, *ubar, *uw;
+  SPlane p1, p2, Iu, rho0;
   float2 *w, *g;
-  float *u_alt, *ubar_alt, *p1_alt, *p2_alt;   // ping-pong copies for k_pd
+  float *u_alt, *ubar_alt;     // ping-pong copies for k_pd
+  SPlane p1_alt, p2_alt;
 };
 
 // Primal-dual state planes of one buffer set.
 struct PDState {
-  float *u, *ubar, *p1, *p2;
+  float *u, *ubar;
+  SPlane p1, p2;
 };
 
 struct PDParams {

@@ -10,7 +10,12 @@ enum PDClusterVariant { PD_CLUSTER_16 = 0, PD_CLUSTER_32 = 1 };
 
 __global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView L);
 __global__ void k_prerotate(const float* __restrict__ I1, const float2* __restrict__ field,
-                            float* __restrict__ out, int W, int H, int P);
+                            SPlane out, int st, int W, int H, int P);
+__global__ void k_copy_in_s(const float* __restrict__ src, SPlane dst, int st, int W, int H,
+                            int P);
+__global__ void k_pack_s(SPlane src, int st, float* __restrict__ dst, int W, int H, int P);
+__global__ void k_unpack_s(const float* __restrict__ src, SPlane dst, int st, int W, int H,
+                           int P);
 __global__ void k_copy_in(const float* __restrict__ src, float* __restrict__ dst, int W, int H,
                           int P);
 __global__ void k_downsample(LevelView F, LevelView C);

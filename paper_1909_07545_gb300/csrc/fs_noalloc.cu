@@ -112,22 +112,23 @@ extern "C" fs_status fs_pd_iterate_noalloc(const float* d_I0, const unsigned cha
   float* f = (float*)base;
   LevelView L{};
   L.W = W; L.H = H; L.P = W;
-  L.I0 = const_cast<float*>(d_I0);
-  L.Iu = const_cast<float*>(d_Iu);
-  L.rho0 = const_cast<float*>(d_rho0);
+  L.st = ST_F32;
+  L.I0.p = const_cast<float*>(d_I0);
+  L.Iu.p = const_cast<float*>(d_Iu);
+  L.rho0.p = const_cast<float*>(d_rho0);
   L.uw = const_cast<float*>(d_uw);
   L.u = d_u;
-  L.p1 = d_p;
-  L.p2 = d_p + n;
+  L.p1.p = d_p;
+  L.p2.p = d_p + n;
   L.ubar = f + 0 * n;
-  L.sx = f + 1 * n;
-  L.sy = f + 2 * n;
+  L.sx.p = f + 1 * n;
+  L.sy.p = f + 2 * n;
   L.tau = f + 3 * n;
   L.sig = f + 4 * n;
   L.u_alt = f + 5 * n;
   L.ubar_alt = f + 6 * n;
-  L.p1_alt = f + 7 * n;
-  L.p2_alt = f + 8 * n;
+  L.p1_alt.p = f + 7 * n;
+  L.p2_alt.p = f + 8 * n;
   uint8_t* bits = (uint8_t*)(f + kFloatPlanes * n);
   L.mask = bits;
 
@@ -164,8 +165,10 @@ extern "C" fs_status fs_pd_iterate_noalloc(const float* d_I0, const unsigned cha
   if (e == cudaSuccess && nl % 2 == 1) {
     const size_t bytes = n * sizeof(float);
     e = cudaMemcpyAsync(A.u, Bs.u, bytes, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(A.p1, Bs.p1, bytes, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(A.p2, Bs.p2, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(A.p1.p, Bs.p1.p, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(A.p2.p, Bs.p2.p, bytes, cudaMemcpyDeviceToDevice, st);
   }
   if (e != cudaSuccess) {
     snprintf(msg, sizeof(msg), "fs_pd_iterate_noalloc: %s", cudaGetErrorString(e));

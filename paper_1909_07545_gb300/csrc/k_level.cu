@@ -30,18 +30,28 @@ __global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView
 // The calibration field c(x) (Sec. IV-A) is built once per pose on the host
 // in FP64 (fs_api.cu): an FP32 field carries ~1e-7 relative round-off in
 // the projections, ~3e-5 px at 1000 px, which the warping then amplifies.
-// I1'(x) = I1(x + c(x)), bilinear; I1 dense (pitch W), output pitch P.
+// I1'(x) = I1(x + c(x)), bilinear; I1 dense FP32 (pitch W), output pitch P
+// in the level's storage.
 __global__ void k_prerotate(const float* __restrict__ I1, const float2* __restrict__ field,
-                            float* __restrict__ out, int W, int H, int P) {
+                            SPlane out, int st, int W, int H, int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= W || y >= H) return;
   size_t i = (size_t)y * P + x;
   float2 c = field[i];
-  out[i] = sample_bilinear(I1, W, H, W, x, c.x, y, c.y);
+  out.st(i, sample_bilinear(I1, W, H, W, x, c.x, y, c.y), st);
 }
 
-// Dense (pitch W) -> pitched copy, used for I0 and warm-start input.
+// Dense FP32 (pitch W) -> pitched plane in the level's storage (I0).
+__global__ void k_copy_in_s(const float* __restrict__ src, SPlane dst, int st, int W, int H,
+                            int P) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  dst.st((size_t)y * P + x, src[(size_t)y * W + x], st);
+}
+
+// Dense (pitch W) -> pitched FP32 copy, used for the warm-start input.
 __global__ void k_copy_in(const float* __restrict__ src, float* __restrict__ dst, int W, int H,
                           int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -66,15 +76,15 @@ __global__ void k_downsample(LevelView F, LevelView C) {
       int x = 2 * X + i, y = 2 * Y + j;
       if (x < F.W && y < F.H) {
         size_t k = (size_t)y * F.P + x;
-        float v0 = F.I0[k], v1 = F.I1[k];
+        float v0 = F.I0.ld(k, F.st), v1 = F.I1.ld(k, F.st);
         a0 += v0; a1 += v1; ++nall;
         if (F.mask[k] & MASK_IN) { s0 += v0; s1 += v1; ++nin; }
       }
     }
   }
   size_t o = (size_t)Y * C.P + X;
-  if (nin > 0) { C.I0[o] = s0 / (float)nin; C.I1[o] = s1 / (float)nin; }
-  else { C.I0[o] = a0 / (float)nall; C.I1[o] = a1 / (float)nall; }
+  if (nin > 0) { C.I0.st(o, s0 / (float)nin, C.st); C.I1.st(o, s1 / (float)nin, C.st); }
+  else { C.I0.st(o, a0 / (float)nall, C.st); C.I1.st(o, a1 / (float)nall, C.st); }
 }
 
 // u, w of level C (coarse) -> level F (fine): bilinear over coarse in-mask
@@ -114,7 +124,7 @@ __global__ void k_upsample(LevelView C, LevelView F) {
   }
   F.u[o] = u; F.ubar[o] = u; F.uw[o] = u;
   F.w[o] = make_float2(wx, wy);
-  F.p1[o] = 0.f; F.p2[o] = 0.f;
+  F.p1.st(o, 0.f, F.st); F.p2.st(o, 0.f, F.st);
 }
 
 // Warm start at the finest level from a disparity already in L.u: w is
@@ -145,7 +155,7 @@ __global__ void k_warm_start(LevelView L, float du_max) {
   }
   L.u[i] = d; L.ubar[i] = d; L.uw[i] = d;
   L.w[i] = w;
-  L.p1[i] = 0.f; L.p2[i] = 0.f;
+  L.p1.st(i, 0.f, L.st); L.p2.st(i, 0.f, L.st);
 }
 
 // Zero state at the coarsest level (Algorithm 1: u_0 = 0, w_0 = 0).
@@ -155,7 +165,7 @@ __global__ void k_zero_state(LevelView L) {
   if (x >= L.W || y >= L.H) return;
   size_t o = (size_t)y * L.P + x;
   L.u[o] = 0.f; L.ubar[o] = 0.f; L.uw[o] = 0.f;
-  L.p1[o] = 0.f; L.p2[o] = 0.f;
+  L.p1.st(o, 0.f, L.st); L.p2.st(o, 0.f, L.st);
   L.w[o] = make_float2(0.f, 0.f);
 }
 
@@ -173,18 +183,19 @@ __device__ __forceinline__ TensorAt tensor_at(const LevelView& L, int x, int y, 
   TensorAt t;
   size_t i = (size_t)y * L.P + x;
   if (!(L.mask[i] & MASK_IN)) { t.sx = t.sy = 0.f; t.aa = 1.f; t.bb = 0.f; t.cc = 1.f; return t; }
-  float c = L.I0[i];
+  auto I0 = [&](size_t k) { return L.I0.ld(k, L.st); };
+  float c = I0(i);
   bool r = x + 1 < L.W && (L.mask[i + 1] & MASK_IN);
   bool l = x > 0 && (L.mask[i - 1] & MASK_IN);
   bool d = y + 1 < L.H && (L.mask[i + L.P] & MASK_IN);
   bool u = y > 0 && (L.mask[i - L.P] & MASK_IN);
   float gx = 0.f, gy = 0.f;
-  if (r && l) gx = 0.5f * (L.I0[i + 1] - L.I0[i - 1]);
-  else if (r) gx = L.I0[i + 1] - c;
-  else if (l) gx = c - L.I0[i - 1];
-  if (d && u) gy = 0.5f * (L.I0[i + L.P] - L.I0[i - L.P]);
-  else if (d) gy = L.I0[i + L.P] - c;
-  else if (u) gy = c - L.I0[i - L.P];
+  if (r && l) gx = 0.5f * (I0(i + 1) - I0(i - 1));
+  else if (r) gx = I0(i + 1) - c;
+  else if (l) gx = c - I0(i - 1);
+  if (d && u) gy = 0.5f * (I0(i + L.P) - I0(i - L.P));
+  else if (d) gy = I0(i + L.P) - c;
+  else if (u) gy = c - I0(i - L.P);
   float mag = sqrtf(gx * gx + gy * gy);
   if (mag < 1e-12f) { t.sx = t.sy = 0.f; t.aa = 1.f; t.bb = 0.f; t.cc = 1.f; return t; }
   float nx = gx / mag, ny = gy / mag;
@@ -210,8 +221,8 @@ __global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
   size_t i = (size_t)y * L.P + x;
   uint8_t m = L.mask[i];
   TensorAt t = tensor_at(L, x, y, beta, eta);
-  L.sx[i] = t.sx;
-  L.sy[i] = t.sy;
+  L.sx.st(i, t.sx, L.st);
+  L.sy.st(i, t.sy, L.st);
   if (!precond) {
     const float s = 0.35355339059327373f;   // 1/sqrt(8)
     L.tau[i] = (m & MASK_IN) ? s : 0.f;       // tau = 0 holds u outside the mask
@@ -251,13 +262,13 @@ __global__ void k_warp(LevelView L) {
     float2 gr = sample_bicubic2(L.gamma, L.W, L.H, L.P, x, w.x, y, w.y);
     float n = sqrtf(gr.x * gr.x + gr.y * gr.y);
     if (n >= 1e-6f) g = make_float2(gr.x / n, gr.y / n);
-    float I1w = sample_bilinear(L.I1, L.W, L.H, L.P, x, w.x, y, w.y);
-    float I1g = sample_bilinear(L.I1, L.W, L.H, L.P, x, w.x + g.x, y, w.y + g.y);
+    float I1w = sample_bilinear(L.I1, L.st, L.W, L.H, L.P, x, w.x, y, w.y);
+    float I1g = sample_bilinear(L.I1, L.st, L.W, L.H, L.P, x, w.x + g.x, y, w.y + g.y);
     Iu = I1g - I1w;
-    rho0 = I1w - L.I0[i];
+    rho0 = I1w - L.I0.ld(i, L.st);
   }
-  L.Iu[i] = Iu;
-  L.rho0[i] = rho0;
+  L.Iu.st(i, Iu, L.st);
+  L.rho0.st(i, rho0, L.st);
   L.g[i] = g;
   float u = L.u[i];
   L.ubar[i] = u;
@@ -328,6 +339,22 @@ __global__ void k_unpack(const float* __restrict__ src, float* __restrict__ dst,
   dst[((size_t)y * P + x) * stride] = src[(size_t)y * W + x];
 }
 
+// Stored plane <-> dense FP32 (buffer access to the storage-typed fields).
+__global__ void k_pack_s(SPlane src, int st, float* __restrict__ dst, int W, int H, int P) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  dst[(size_t)y * W + x] = src.ld((size_t)y * P + x, st);
+}
+
+__global__ void k_unpack_s(const float* __restrict__ src, SPlane dst, int st, int W, int H,
+                           int P) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  dst.st((size_t)y * P + x, src[(size_t)y * W + x], st);
+}
+
 __global__ void k_mask_to_float(const uint8_t* __restrict__ m, float* __restrict__ dst, int W,
                                 int H, int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -342,7 +369,7 @@ __global__ void k_tensor_abc(LevelView L, float* __restrict__ dst) {
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
   size_t i = (size_t)y * L.P + x, o = (size_t)y * L.W + x, n = (size_t)L.W * L.H;
-  float sx = L.sx[i], sy = L.sy[i];
+  float sx = L.sx.ld(i, L.st), sy = L.sy.ld(i, L.st);
   dst[o] = 1.f - sx * sx;
   dst[n + o] = -sx * sy;
   dst[2 * n + o] = 1.f - sy * sy;

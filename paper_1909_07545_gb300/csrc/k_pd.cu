@@ -80,8 +80,8 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
       const size_t i = (size_t)gy * L.P + gx;
       u[r] = in.u[i];
       ub[r] = in.ubar[i];
-      p1[r] = in.p1[i];
-      p2[r] = in.p2[i];
+      p1[r] = in.p1.ld(i, L.st);
+      p2[r] = in.p2.ld(i, L.st);
     } else {
       u[r] = ub[r] = p1[r] = p2[r] = 0.f;
     }
@@ -126,8 +126,8 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
     const size_t i = (size_t)gy * L.P + gx;
     out.u[i] = u[r];
     out.ubar[i] = ub[r];
-    out.p1[i] = p1[r];
-    out.p2[i] = p2[r];
+    out.p1.st(i, p1[r], L.st);
+    out.p2.st(i, p2[r], L.st);
   }
 }
 
@@ -176,8 +176,8 @@ k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
       const size_t i = (size_t)gy * L.P + gx;
       u[r] = L.u[i];
       ub[r] = L.ubar[i];
-      p1[r] = L.p1[i];
-      p2[r] = L.p2[i];
+      p1[r] = L.p1.ld(i, L.st);
+      p2[r] = L.p2.ld(i, L.st);
       px_load(L, i, pp.lam, pp.eps, c[r]);
       mb |= (unsigned)L.mask[i] << (3 * r);
     } else {
@@ -228,8 +228,8 @@ k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
     const size_t i = (size_t)gy * L.P + gx;
     L.u[i] = u[r];
     L.ubar[i] = ub[r];
-    L.p1[i] = p1[r];
-    L.p2[i] = p2[r];
+    L.p1.st(i, p1[r], L.st);
+    L.p2.st(i, p2[r], L.st);
   }
 }
 

@@ -29,15 +29,15 @@ struct PxConst {
 
 __device__ __forceinline__ void px_load(const LevelView& L, size_t i, float lam, float eps,
                                         PxConst& c) {
-  c.sx = L.sx[i];
-  c.sy = L.sy[i];
+  c.sx = L.sx.ld(i, L.st);
+  c.sy = L.sy.ld(i, L.st);
   const float sg = L.sig[i];
   c.dinv = __fdiv_rn(1.f, fmaf(sg, eps, 1.f));
   c.sd = __fmul_rn(sg, c.dinv);
   c.tau = L.tau[i];
-  c.Iu = L.Iu[i];
+  c.Iu = L.Iu.ld(i, L.st);
   c.step = fabsf(__fmul_rn(__fmul_rn(c.tau, lam), c.Iu));
-  c.rho0 = L.rho0[i];
+  c.rho0 = L.rho0.ld(i, L.st);
   c.uw = L.uw[i];
   c.inv = c.Iu != 0.f ? __fdiv_rn(1.f, c.Iu) : 0.f;
 }
