@@ -213,7 +213,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip fs_autotune (default schedule per level)")
-    ap.add_argument("--batch", type=int, default=8,
+    ap.add_argument("--batch", type=int, default=4,
                     help="pairs per fs_batch for the batched-throughput figure (<= 1 skips)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -309,42 +309,53 @@ def main():
         pd_launches = sum(n for _, n, _ in per_level) // max(args.steps, 1)
         s.close()
 
-        # batched throughput: args.batch independent 1024^2 handles solved
-        # concurrently through one fs_batch graph (same pair on every handle)
-        batched = None
+        # variants of the same frame: 16-bit storage, and batches of
+        # independent handles solved concurrently through one fs_batch graph
+        def timed(run, n):
+            for _ in range(args.warmup):
+                run()
+            stream.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(n)]
+            for i in range(n):
+                flush.fill_(float(i))
+                evs[i][0].record(stream)
+                run()
+                evs[i][1].record(stream)
+            stream.synchronize()
+            ms, = reduce_max([float(sum(a.elapsed_time(b) for a, b in evs))], dist, "cuda")
+            return ms / n
+
+        def make(storage):
+            x = Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, L, stream=stream,
+                       lam=pair["lam"], huber_eps=pair["eps"], use_graph=1, storage=storage)
+            if args.autotune:
+                x.autotune(iters)
+            return x
+
+        variants = {}
+        vsteps = max(3, min(args.steps, 10))
+        for storage in ("f16", "bf16"):
+            x = make(storage)
+            ms = timed(lambda: x.solve(I0, I1, warps, iters, disp=disp, depth=depth), vsteps)
+            variants[storage] = {"value": job_rate(world, 1, ms), "unit": "frames/s",
+                                 "ms_per_frame": ms}
+            x.close()
         if args.batch > 1:
             from paper_1909_07545_gb300 import Batch
-            sols = [Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, L,
-                           stream=stream, lam=pair["lam"], huber_eps=pair["eps"])
-                    for _ in range(args.batch)]
-            if args.autotune:
+            for storage in ("f32", "f16"):
+                sols = [make(storage) for _ in range(args.batch)]
+                bt = Batch(sols, stream=stream)
+                outs_d = [torch.empty((H, W), device="cuda") for _ in sols]
+                outs_z = [torch.empty((H, W), device="cuda") for _ in sols]
+                ms = timed(lambda: bt.solve([I0] * len(sols), [I1] * len(sols), warps, iters,
+                                            disps=outs_d, depths=outs_z), vsteps)
+                variants[f"batched_{storage}"] = {
+                    "value": job_rate(world, len(sols), ms), "unit": "frames/s",
+                    "pairs_per_batch": len(sols), "ms_per_batch": ms}
+                bt.close()
                 for x in sols:
-                    x.autotune(iters)
-            bt = Batch(sols, stream=stream)
-            outs_d = [torch.empty((H, W), device="cuda") for _ in sols]
-            outs_z = [torch.empty((H, W), device="cuda") for _ in sols]
-            bstep = lambda: bt.solve([I0] * len(sols), [I1] * len(sols), warps, iters,
-                                     disps=outs_d, depths=outs_z)
-            for _ in range(args.warmup):
-                bstep()
-            stream.synchronize()
-            bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(args.steps)]
-            for i in range(args.steps):
-                flush.fill_(float(i))
-                bev[i][0].record(stream)
-                bstep()
-                bev[i][1].record(stream)
-            stream.synchronize()
-            bms = np.array([a.elapsed_time(b) for a, b in bev])
-            btot, = reduce_max([float(bms.sum())], dist, "cuda")
-            batched = {"pairs_per_batch": len(sols),
-                       "value": job_rate(world, args.steps * len(sols), btot),
-                       "unit": "frames/s", "ms_per_batch": btot / args.steps,
-                       "note": "independent handles, one fs_batch graph per step"}
-            bt.close()
-            for x in sols:
-                x.close()
+                    x.close()
 
     if rank != 0:
         if dist:
@@ -390,7 +401,7 @@ def main():
         "clocks": clk,
         "wall_s": t_wall,
     }
-    line["batched"] = batched
+    line["variants"] = variants
     line["e2e"] = {"value": world / e2e_s, "unit": "frames/s",
                    "h2d_bytes_per_step": 2 * W * H * 4, "d2h_bytes_per_step": 2 * W * H * 4}
     if not args.no_cpu_baseline:

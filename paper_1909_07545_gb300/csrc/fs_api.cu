@@ -38,6 +38,13 @@ fs_status fail(fs_status s, const char* fmt, ...) {
       return fail(FS_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));      \
   } while (0)
 
+#define FS_LAUNCH(name, call)                                                     \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(FS_ECUDA, "launch of %s failed: %s", name, cudaGetErrorString(e_)); \
+  } while (0)
+
 #define FS_LAUNCHED(name)                                                         \
   do {                                                                            \
     cudaError_t e_ = cudaGetLastError();                                          \
@@ -317,21 +324,17 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
   switch (stage) {
     case FS_STAGE_DOWNSAMPLE:
       if (l + 1 >= h->L) return fail(FS_EINVAL, "downsample: level %d has no coarser level", l);
-      k_downsample<<<grid2(h->lv[l + 1].W, h->lv[l + 1].H), kBlock2, 0, st>>>(L.v, h->lv[l + 1].v);
-      FS_LAUNCHED("k_downsample");
+      FS_LAUNCH("k_downsample", launch_downsample(L.v, h->lv[l + 1].v, st));
       return FS_OK;
     case FS_STAGE_TENSOR:
-      k_tensor<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, h->prm.beta, h->prm.eta, h->prm.precond);
-      FS_LAUNCHED("k_tensor");
+      FS_LAUNCH("k_tensor", launch_tensor(L.v, h->prm.beta, h->prm.eta, h->prm.precond, st));
       return FS_OK;
     case FS_STAGE_UPSAMPLE:
       if (l + 1 >= h->L) return fail(FS_EINVAL, "upsample: level %d has no coarser level", l);
-      k_upsample<<<grid2(L.W, L.H), kBlock2, 0, st>>>(h->lv[l + 1].v, L.v);
-      FS_LAUNCHED("k_upsample");
+      FS_LAUNCH("k_upsample", launch_upsample(h->lv[l + 1].v, L.v, st));
       return FS_OK;
     case FS_STAGE_WARP:
-      k_warp<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v);
-      FS_LAUNCHED("k_warp");
+      FS_LAUNCH("k_warp", launch_warp(L.v, st));
       return FS_OK;
     case FS_STAGE_PD:
       if (count < 1) return fail(FS_EINVAL, "pd: count must be >= 1");
@@ -341,8 +344,7 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
       FS_LAUNCHED("k_clip");
       return FS_OK;
     case FS_STAGE_WARM:
-      k_warm_start<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, h->prm.du_max);
-      FS_LAUNCHED("k_warm_start");
+      FS_LAUNCH("k_warm_start", launch_warm_start(L.v, h->prm.du_max, st));
       return FS_OK;
     case FS_STAGE_TRAJECTORY: {
       double n = std::sqrt(h->tp[0] * h->tp[0] + h->tp[1] * h->tp[1] + h->tp[2] * h->tp[2]);
@@ -381,11 +383,8 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
                         int warps, int iters, float* disp, float* depth, cudaStream_t st) {
   fs_status s;
   HostLevel& L0 = h->lv[0];
-  k_copy_in_s<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(I0, L0.v.I0, L0.v.st, L0.W, L0.H, L0.P);
-  FS_LAUNCHED("k_copy_in_s");
-  k_prerotate<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(I1, h->cfield, L0.v.I1, L0.v.st, L0.W, L0.H,
-                                                     L0.P);
-  FS_LAUNCHED("k_prerotate");
+  FS_LAUNCH("k_copy_in_s", launch_copy_in_I0(I0, L0.v, st));
+  FS_LAUNCH("k_prerotate", launch_prerotate(I1, h->cfield, L0.v, st));
   int top = h->L - 1;
   if (init) {   // warm start: the finest level only, from the given disparity
     k_copy_in<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(init, L0.v.u, L0.W, L0.H, L0.P);
@@ -413,8 +412,7 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
     HostLevel& L = h->lv[l];
     if ((s = run_stage(h, l, FS_STAGE_TENSOR, 0, st)) != FS_OK) return s;
     if (l == top) {
-      k_zero_state<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v);
-      FS_LAUNCHED("k_zero_state");
+      FS_LAUNCH("k_zero_state", launch_zero_state(L.v, st));
     } else if ((s = run_stage(h, l, FS_STAGE_UPSAMPLE, 0, st)) != FS_OK) {
       return s;
     }
@@ -856,8 +854,7 @@ extern "C" fs_status fs_buffer_read(fs_handle* h, int level, int buffer, float* 
     return FS_OK;
   }
   if (buffer == FS_BUF_TENSOR) {
-    k_tensor_abc<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, d_out);
-    FS_LAUNCHED("k_tensor_abc");
+    FS_LAUNCH("k_tensor_abc", launch_tensor_abc(L.v, d_out, st));
     return FS_OK;
   }
   if (buffer == FS_BUF_STEPS) {
@@ -869,12 +866,13 @@ extern "C" fs_status fs_buffer_read(fs_handle* h, int level, int buffer, float* 
   BufLoc b;
   if ((s = buffer_loc(h, level, buffer, b)) != FS_OK) return s;
   for (int c = 0; c < b.planes; ++c) {
-    if (b.kind == 2)
-      k_pack_s<<<grid2(L.W, L.H), kBlock2, 0, st>>>(b.s[c], L.v.st, d_out + c * n, L.W, L.H, L.P);
-    else
-      k_pack<<<grid2(L.W, L.H), kBlock2, 0, st>>>(b.kind == 1 ? b.f[0] + c : b.f[c],
-                                                  b.kind == 1 ? 2 : 1, d_out + c * n, L.W,
-                                                  L.H, L.P);
+    if (b.kind == 2) {
+      FS_LAUNCH("k_pack_s", launch_pack_s(b.s[c], L.v.st, d_out + c * n, L.W, L.H, L.P, st));
+      continue;
+    }
+    k_pack<<<grid2(L.W, L.H), kBlock2, 0, st>>>(b.kind == 1 ? b.f[0] + c : b.f[c],
+                                                b.kind == 1 ? 2 : 1, d_out + c * n, L.W, L.H,
+                                                L.P);
     FS_LAUNCHED("k_pack");
   }
   return FS_OK;
@@ -892,12 +890,13 @@ extern "C" fs_status fs_buffer_write(fs_handle* h, int level, int buffer, const 
   BufLoc b;
   if ((s = buffer_loc(h, level, buffer, b)) != FS_OK) return s;
   for (int c = 0; c < b.planes; ++c) {
-    if (b.kind == 2)
-      k_unpack_s<<<grid2(L.W, L.H), kBlock2, 0, h->stream>>>(d_in + c * n, b.s[c], L.v.st, L.W,
-                                                             L.H, L.P);
-    else
-      k_unpack<<<grid2(L.W, L.H), kBlock2, 0, h->stream>>>(
-          d_in + c * n, b.kind == 1 ? b.f[0] + c : b.f[c], b.kind == 1 ? 2 : 1, L.W, L.H, L.P);
+    if (b.kind == 2) {
+      FS_LAUNCH("k_unpack_s",
+                launch_unpack_s(d_in + c * n, b.s[c], L.v.st, L.W, L.H, L.P, h->stream));
+      continue;
+    }
+    k_unpack<<<grid2(L.W, L.H), kBlock2, 0, h->stream>>>(
+        d_in + c * n, b.kind == 1 ? b.f[0] + c : b.f[c], b.kind == 1 ? 2 : 1, L.W, L.H, L.P);
     FS_LAUNCHED("k_unpack");
   }
   return FS_OK;
@@ -915,9 +914,7 @@ extern "C" fs_status fs_stage_prerotate(fs_handle* h, const float* d_I1) {
   if ((s = check_handle(h)) != FS_OK) return s;
   if (!d_I1) return fail(FS_EINVAL, "null input");
   HostLevel& L0 = h->lv[0];
-  k_prerotate<<<grid2(L0.W, L0.H), kBlock2, 0, h->stream>>>(d_I1, h->cfield, L0.v.I1, L0.v.st,
-                                                             L0.W, L0.H, L0.P);
-  FS_LAUNCHED("k_prerotate");
+  FS_LAUNCH("k_prerotate", launch_prerotate(d_I1, h->cfield, L0.v, h->stream));
   return FS_OK;
 }
 

@@ -211,28 +211,34 @@ __device__ __forceinline__ float2 sample_bicubic2(const float2* __restrict__ f, 
 // load and rounded to nearest on store).
 enum Storage { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
 
-// A plane of one of those fields, element type given by the level's storage.
+// A plane of one of those fields; its element type is the level's storage,
+// fixed at compile time in every kernel that touches it (sld / sst).
 struct SPlane {
   void* p;
-  __device__ __forceinline__ float ld(size_t i, int s) const {
-    if (s == ST_F16) return __half2float(__ldg((const __half*)p + i));
-    if (s == ST_BF16) return __bfloat162float(__ldg((const __nv_bfloat16*)p + i));
-    return __ldg((const float*)p + i);
-  }
-  __device__ __forceinline__ void st(size_t i, float v, int s) const {
-    if (s == ST_F16) ((__half*)p)[i] = __float2half_rn(v);
-    else if (s == ST_BF16) ((__nv_bfloat16*)p)[i] = __float2bfloat16_rn(v);
-    else ((float*)p)[i] = v;
-  }
 };
 
+template <int S>
+__device__ __forceinline__ float sld(const SPlane& pl, size_t i) {
+  if constexpr (S == ST_F16) return __half2float(__ldg((const __half*)pl.p + i));
+  else if constexpr (S == ST_BF16) return __bfloat162float(__ldg((const __nv_bfloat16*)pl.p + i));
+  else return __ldg((const float*)pl.p + i);
+}
+
+template <int S>
+__device__ __forceinline__ void sst(const SPlane& pl, size_t i, float v) {
+  if constexpr (S == ST_F16) ((__half*)pl.p)[i] = __float2half_rn(v);
+  else if constexpr (S == ST_BF16) ((__nv_bfloat16*)pl.p)[i] = __float2bfloat16_rn(v);
+  else ((float*)pl.p)[i] = v;
+}
+
 // Bilinear sample of a stored plane at (x + dx, y + dy), clamped.
-__device__ __forceinline__ float sample_bilinear(const SPlane& img, int s, int W, int H, int P,
-                                                 int x, float dx, int y, float dy) {
+template <int S>
+__device__ __forceinline__ float sample_bilinear_s(const SPlane& img, int W, int H, int P, int x,
+                                                   float dx, int y, float dy) {
   Tap tx = tap_linear(x, dx, W), ty = tap_linear(y, dy, H);
   const size_t r0 = (size_t)ty.i0 * P, r1 = (size_t)ty.i1 * P;
-  float v00 = img.ld(r0 + tx.i0, s), v01 = img.ld(r0 + tx.i1, s);
-  float v10 = img.ld(r1 + tx.i0, s), v11 = img.ld(r1 + tx.i1, s);
+  float v00 = sld<S>(img, r0 + tx.i0), v01 = sld<S>(img, r0 + tx.i1);
+  float v10 = sld<S>(img, r1 + tx.i0), v11 = sld<S>(img, r1 + tx.i1);
   float top = fmaf(tx.a, v01 - v00, v00);
   float bot = fmaf(tx.a, v11 - v10, v10);
   return fmaf(ty.a, bot - top, top);

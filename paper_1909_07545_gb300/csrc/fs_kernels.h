@@ -9,21 +9,8 @@ enum PDVariant { PD_TILE_64 = 0, PD_TILE_32 = 1 };
 enum PDClusterVariant { PD_CLUSTER_16 = 0, PD_CLUSTER_32 = 1 };
 
 __global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView L);
-__global__ void k_prerotate(const float* __restrict__ I1, const float2* __restrict__ field,
-                            SPlane out, int st, int W, int H, int P);
-__global__ void k_copy_in_s(const float* __restrict__ src, SPlane dst, int st, int W, int H,
-                            int P);
-__global__ void k_pack_s(SPlane src, int st, float* __restrict__ dst, int W, int H, int P);
-__global__ void k_unpack_s(const float* __restrict__ src, SPlane dst, int st, int W, int H,
-                           int P);
 __global__ void k_copy_in(const float* __restrict__ src, float* __restrict__ dst, int W, int H,
                           int P);
-__global__ void k_downsample(LevelView F, LevelView C);
-__global__ void k_upsample(LevelView C, LevelView F);
-__global__ void k_zero_state(LevelView L);
-__global__ void k_warm_start(LevelView L, float du_max);
-__global__ void k_tensor(LevelView L, float beta, float eta, int precond);
-__global__ void k_warp(LevelView L);
 __global__ void k_clip(LevelView L, float du_max);
 __global__ void k_depth(LevelView L, DevCam cam, float Cx, float Cy, float Cz,
                         float* __restrict__ disp, float* __restrict__ depth);
@@ -33,7 +20,24 @@ __global__ void k_unpack(const float* __restrict__ src, float* __restrict__ dst,
                          int W, int H, int P);
 __global__ void k_mask_to_float(const uint8_t* __restrict__ m, float* __restrict__ dst, int W,
                                 int H, int P);
-__global__ void k_tensor_abc(LevelView L, float* __restrict__ dst);
+
+// Storage-typed kernels, launched through these (the level's storage picks
+// the instantiation).
+cudaError_t launch_prerotate(const float* I1, const float2* field, const LevelView& L0,
+                             cudaStream_t st);
+cudaError_t launch_copy_in_I0(const float* I0, const LevelView& L0, cudaStream_t st);
+cudaError_t launch_downsample(const LevelView& F, const LevelView& C, cudaStream_t st);
+cudaError_t launch_upsample(const LevelView& C, const LevelView& F, cudaStream_t st);
+cudaError_t launch_zero_state(const LevelView& L, cudaStream_t st);
+cudaError_t launch_warm_start(const LevelView& L, float du_max, cudaStream_t st);
+cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond,
+                          cudaStream_t st);
+cudaError_t launch_warp(const LevelView& L, cudaStream_t st);
+cudaError_t launch_tensor_abc(const LevelView& L, float* dst, cudaStream_t st);
+cudaError_t launch_pack_s(const SPlane& src, int storage, float* dst, int W, int H, int P,
+                          cudaStream_t st);
+cudaError_t launch_unpack_s(const float* src, const SPlane& dst, int storage, int W, int H,
+                            int P, cudaStream_t st);
 
 // Primal-dual iterations: n <= B iterations with halo B, tile variant
 // `variant`, state read from `in` and written to `out` (distinct buffers).

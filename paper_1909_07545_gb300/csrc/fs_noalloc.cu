@@ -136,8 +136,8 @@ extern "C" fs_status fs_pd_iterate_noalloc(const float* d_I0, const unsigned cha
   // contents left by an earlier call never reach this one
   dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
   k_mask_bits<<<grd, blk, 0, st>>>(d_mask, bits, W, H);
-  k_tensor<<<grd, blk, 0, st>>>(L, p.beta, p.eta, p.precond);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_tensor(L, p.beta, p.eta, p.precond, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(L.ubar, d_u, n * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) {

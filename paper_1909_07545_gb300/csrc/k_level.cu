@@ -32,23 +32,24 @@ __global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView
 // the projections, ~3e-5 px at 1000 px, which the warping then amplifies.
 // I1'(x) = I1(x + c(x)), bilinear; I1 dense FP32 (pitch W), output pitch P
 // in the level's storage.
+template <int S>
 __global__ void k_prerotate(const float* __restrict__ I1, const float2* __restrict__ field,
-                            SPlane out, int st, int W, int H, int P) {
+                            SPlane out, int W, int H, int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= W || y >= H) return;
   size_t i = (size_t)y * P + x;
   float2 c = field[i];
-  out.st(i, sample_bilinear(I1, W, H, W, x, c.x, y, c.y), st);
+  sst<S>(out, i, sample_bilinear(I1, W, H, W, x, c.x, y, c.y));
 }
 
 // Dense FP32 (pitch W) -> pitched plane in the level's storage (I0).
-__global__ void k_copy_in_s(const float* __restrict__ src, SPlane dst, int st, int W, int H,
-                            int P) {
+template <int S>
+__global__ void k_copy_in_s(const float* __restrict__ src, SPlane dst, int W, int H, int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= W || y >= H) return;
-  dst.st((size_t)y * P + x, src[(size_t)y * W + x], st);
+  sst<S>(dst, (size_t)y * P + x, src[(size_t)y * W + x]);
 }
 
 // Dense (pitch W) -> pitched FP32 copy, used for the warm-start input.
@@ -63,6 +64,7 @@ __global__ void k_copy_in(const float* __restrict__ src, float* __restrict__ dst
 // ------------------------------------------------------------ pyramid
 // 2x2 box mean over the children inside the finer mask (all existing
 // children when none is inside), for I0 and I1 together (Sec. IV-B).
+template <int S>
 __global__ void k_downsample(LevelView F, LevelView C) {
   int X = blockIdx.x * blockDim.x + threadIdx.x;
   int Y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -76,20 +78,21 @@ __global__ void k_downsample(LevelView F, LevelView C) {
       int x = 2 * X + i, y = 2 * Y + j;
       if (x < F.W && y < F.H) {
         size_t k = (size_t)y * F.P + x;
-        float v0 = F.I0.ld(k, F.st), v1 = F.I1.ld(k, F.st);
+        float v0 = sld<S>(F.I0, k), v1 = sld<S>(F.I1, k);
         a0 += v0; a1 += v1; ++nall;
         if (F.mask[k] & MASK_IN) { s0 += v0; s1 += v1; ++nin; }
       }
     }
   }
   size_t o = (size_t)Y * C.P + X;
-  if (nin > 0) { C.I0.st(o, s0 / (float)nin, C.st); C.I1.st(o, s1 / (float)nin, C.st); }
-  else { C.I0.st(o, a0 / (float)nall, C.st); C.I1.st(o, a1 / (float)nall, C.st); }
+  if (nin > 0) { sst<S>(C.I0, o, s0 / (float)nin); sst<S>(C.I1, o, s1 / (float)nin); }
+  else { sst<S>(C.I0, o, a0 / (float)nall); sst<S>(C.I1, o, a1 / (float)nall); }
 }
 
 // u, w of level C (coarse) -> level F (fine): bilinear over coarse in-mask
 // samples with renormalised weights, values x2, 0 outside the fine mask.
 // Also sets ubar = u_w = u and p = 0 on the fine level.
+template <int S>
 __global__ void k_upsample(LevelView C, LevelView F) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -124,7 +127,7 @@ __global__ void k_upsample(LevelView C, LevelView F) {
   }
   F.u[o] = u; F.ubar[o] = u; F.uw[o] = u;
   F.w[o] = make_float2(wx, wy);
-  F.p1.st(o, 0.f, F.st); F.p2.st(o, 0.f, F.st);
+  sst<S>(F.p1, o, 0.f); sst<S>(F.p2, o, 0.f);
 }
 
 // Warm start at the finest level from a disparity already in L.u: w is
@@ -133,6 +136,7 @@ __global__ void k_upsample(LevelView C, LevelView F) {
 // current point; ubar = u_w = u, p = 0.  Non-finite disparities count as 0
 // and n is capped at kMaxWarmSteps.
 constexpr int kMaxWarmSteps = 16384;
+template <int S>
 __global__ void k_warm_start(LevelView L, float du_max) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -155,17 +159,18 @@ __global__ void k_warm_start(LevelView L, float du_max) {
   }
   L.u[i] = d; L.ubar[i] = d; L.uw[i] = d;
   L.w[i] = w;
-  L.p1.st(i, 0.f, L.st); L.p2.st(i, 0.f, L.st);
+  sst<S>(L.p1, i, 0.f); sst<S>(L.p2, i, 0.f);
 }
 
 // Zero state at the coarsest level (Algorithm 1: u_0 = 0, w_0 = 0).
+template <int S>
 __global__ void k_zero_state(LevelView L) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
   size_t o = (size_t)y * L.P + x;
   L.u[o] = 0.f; L.ubar[o] = 0.f; L.uw[o] = 0.f;
-  L.p1.st(o, 0.f, L.st); L.p2.st(o, 0.f, L.st);
+  sst<S>(L.p1, o, 0.f); sst<S>(L.p2, o, 0.f);
   L.w[o] = make_float2(0.f, 0.f);
 }
 
@@ -178,12 +183,13 @@ struct TensorAt {
 // T^1/2 = e n n^T + n_perp n_perp^T = I - (1 - e) n n^T  (Eq. 12) with
 // e = exp(-beta |grad I0|^eta), grad I0 by central differences on the mask
 // (one-sided at its edge, 0 where both neighbours leave it).
+template <int S>
 __device__ __forceinline__ TensorAt tensor_at(const LevelView& L, int x, int y, float beta,
                                               float eta) {
   TensorAt t;
   size_t i = (size_t)y * L.P + x;
   if (!(L.mask[i] & MASK_IN)) { t.sx = t.sy = 0.f; t.aa = 1.f; t.bb = 0.f; t.cc = 1.f; return t; }
-  auto I0 = [&](size_t k) { return L.I0.ld(k, L.st); };
+  auto I0 = [&](size_t k) { return sld<S>(L.I0, k); };
   float c = I0(i);
   bool r = x + 1 < L.W && (L.mask[i + 1] & MASK_IN);
   bool l = x > 0 && (L.mask[i - 1] & MASK_IN);
@@ -214,15 +220,16 @@ __device__ __forceinline__ TensorAt tensor_at(const LevelView& L, int x, int y, 
 //   sigma(x) = 1 / max(2(|a| m1 + |b| m2), 2(|b| m1 + |c| m2))
 //   tau(x)   = 1 / ((|a|+|b|) m1 + (|b|+|c|) m2 at x,
 //                   + (|a|+|b|) m1 at x - e1, + (|b|+|c|) m2 at x - e2)
+template <int S>
 __global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
   size_t i = (size_t)y * L.P + x;
   uint8_t m = L.mask[i];
-  TensorAt t = tensor_at(L, x, y, beta, eta);
-  L.sx.st(i, t.sx, L.st);
-  L.sy.st(i, t.sy, L.st);
+  TensorAt t = tensor_at<S>(L, x, y, beta, eta);
+  sst<S>(L.sx, i, t.sx);
+  sst<S>(L.sy, i, t.sy);
   if (!precond) {
     const float s = 0.35355339059327373f;   // 1/sqrt(8)
     L.tau[i] = (m & MASK_IN) ? s : 0.f;       // tau = 0 holds u outside the mask
@@ -236,11 +243,11 @@ __global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
   L.sig[i] = r > 0.f ? 1.f / r : 0.f;
   float col = (t.aa + t.bb) * m1 + (t.bb + t.cc) * m2;
   if (x > 0 && (L.mask[i - 1] & MASK_GX)) {
-    TensorAt tl = tensor_at(L, x - 1, y, beta, eta);
+    TensorAt tl = tensor_at<S>(L, x - 1, y, beta, eta);
     col += tl.aa + tl.bb;
   }
   if (y > 0 && (L.mask[i - L.P] & MASK_GY)) {
-    TensorAt tu = tensor_at(L, x, y - 1, beta, eta);
+    TensorAt tu = tensor_at<S>(L, x, y - 1, beta, eta);
     col += tu.bb + tu.cc;
   }
   L.tau[i] = (col > 0.f && (m & MASK_IN)) ? 1.f / col : 0.f;
@@ -250,6 +257,7 @@ __global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
 // g = bicubic gamma'(x + w) renormalised (0 if |g| < 1e-6); I1w = I1(x + w);
 // I_u = I1(x + w + g) - I1w (Eq. 5); rho0 = I1w - I0 (Eq. 3, 9).  Starts a
 // warp: ubar = u_w = u.
+template <int S>
 __global__ void k_warp(LevelView L) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -262,13 +270,13 @@ __global__ void k_warp(LevelView L) {
     float2 gr = sample_bicubic2(L.gamma, L.W, L.H, L.P, x, w.x, y, w.y);
     float n = sqrtf(gr.x * gr.x + gr.y * gr.y);
     if (n >= 1e-6f) g = make_float2(gr.x / n, gr.y / n);
-    float I1w = sample_bilinear(L.I1, L.st, L.W, L.H, L.P, x, w.x, y, w.y);
-    float I1g = sample_bilinear(L.I1, L.st, L.W, L.H, L.P, x, w.x + g.x, y, w.y + g.y);
+    float I1w = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x, y, w.y);
+    float I1g = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x + g.x, y, w.y + g.y);
     Iu = I1g - I1w;
-    rho0 = I1w - L.I0.ld(i, L.st);
+    rho0 = I1w - sld<S>(L.I0, i);
   }
-  L.Iu.st(i, Iu, L.st);
-  L.rho0.st(i, rho0, L.st);
+  sst<S>(L.Iu, i, Iu);
+  sst<S>(L.rho0, i, rho0);
   L.g[i] = g;
   float u = L.u[i];
   L.ubar[i] = u;
@@ -340,19 +348,20 @@ __global__ void k_unpack(const float* __restrict__ src, float* __restrict__ dst,
 }
 
 // Stored plane <-> dense FP32 (buffer access to the storage-typed fields).
-__global__ void k_pack_s(SPlane src, int st, float* __restrict__ dst, int W, int H, int P) {
+template <int S>
+__global__ void k_pack_s(SPlane src, float* __restrict__ dst, int W, int H, int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= W || y >= H) return;
-  dst[(size_t)y * W + x] = src.ld((size_t)y * P + x, st);
+  dst[(size_t)y * W + x] = sld<S>(src, (size_t)y * P + x);
 }
 
-__global__ void k_unpack_s(const float* __restrict__ src, SPlane dst, int st, int W, int H,
-                           int P) {
+template <int S>
+__global__ void k_unpack_s(const float* __restrict__ src, SPlane dst, int W, int H, int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= W || y >= H) return;
-  dst.st((size_t)y * P + x, src[(size_t)y * W + x], st);
+  sst<S>(dst, (size_t)y * P + x, src[(size_t)y * W + x]);
 }
 
 __global__ void k_mask_to_float(const uint8_t* __restrict__ m, float* __restrict__ dst, int W,
@@ -364,15 +373,73 @@ __global__ void k_mask_to_float(const uint8_t* __restrict__ m, float* __restrict
 }
 
 // T^1/2 entries a, b, c from s: a = 1 - sx^2, b = -sx sy, c = 1 - sy^2.
+template <int S>
 __global__ void k_tensor_abc(LevelView L, float* __restrict__ dst) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
   size_t i = (size_t)y * L.P + x, o = (size_t)y * L.W + x, n = (size_t)L.W * L.H;
-  float sx = L.sx.ld(i, L.st), sy = L.sy.ld(i, L.st);
+  float sx = sld<S>(L.sx, i), sy = sld<S>(L.sy, i);
   dst[o] = 1.f - sx * sx;
   dst[n + o] = -sx * sy;
   dst[2 * n + o] = 1.f - sy * sy;
+}
+
+// ---------------------------------------------------------------- launchers
+// Host launch of the storage-typed kernels: the level's storage picks the
+// compiled instantiation.
+namespace {
+dim3 grid_of(int W, int H) { return dim3((W + 31) / 32, (H + 7) / 8); }
+const dim3 kBlk(32, 8);
+}  // namespace
+
+#define FS_STORAGE_SWITCH(st, CALL)                           \
+  switch (st) {                                               \
+    case ST_F16: { constexpr int S = ST_F16; CALL; } break;   \
+    case ST_BF16: { constexpr int S = ST_BF16; CALL; } break; \
+    default: { constexpr int S = ST_F32; CALL; } break;       \
+  }                                                           \
+  return cudaGetLastError();
+
+cudaError_t launch_prerotate(const float* I1, const float2* field, const LevelView& L0,
+                             cudaStream_t st) {
+  FS_STORAGE_SWITCH(L0.st, (k_prerotate<S><<<grid_of(L0.W, L0.H), kBlk, 0, st>>>(
+                               I1, field, L0.I1, L0.W, L0.H, L0.P)))
+}
+cudaError_t launch_copy_in_I0(const float* I0, const LevelView& L0, cudaStream_t st) {
+  FS_STORAGE_SWITCH(L0.st, (k_copy_in_s<S><<<grid_of(L0.W, L0.H), kBlk, 0, st>>>(
+                               I0, L0.I0, L0.W, L0.H, L0.P)))
+}
+cudaError_t launch_downsample(const LevelView& F, const LevelView& C, cudaStream_t st) {
+  FS_STORAGE_SWITCH(F.st, (k_downsample<S><<<grid_of(C.W, C.H), kBlk, 0, st>>>(F, C)))
+}
+cudaError_t launch_upsample(const LevelView& C, const LevelView& F, cudaStream_t st) {
+  FS_STORAGE_SWITCH(F.st, (k_upsample<S><<<grid_of(F.W, F.H), kBlk, 0, st>>>(C, F)))
+}
+cudaError_t launch_zero_state(const LevelView& L, cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_zero_state<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L)))
+}
+cudaError_t launch_warm_start(const LevelView& L, float du_max, cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_warm_start<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, du_max)))
+}
+cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond,
+                          cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_tensor<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, beta, eta,
+                                                                          precond)))
+}
+cudaError_t launch_warp(const LevelView& L, cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_warp<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L)))
+}
+cudaError_t launch_tensor_abc(const LevelView& L, float* dst, cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_tensor_abc<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, dst)))
+}
+cudaError_t launch_pack_s(const SPlane& src, int storage, float* dst, int W, int H, int P,
+                          cudaStream_t st) {
+  FS_STORAGE_SWITCH(storage, (k_pack_s<S><<<grid_of(W, H), kBlk, 0, st>>>(src, dst, W, H, P)))
+}
+cudaError_t launch_unpack_s(const float* src, const SPlane& dst, int storage, int W, int H,
+                            int P, cudaStream_t st) {
+  FS_STORAGE_SWITCH(storage, (k_unpack_s<S><<<grid_of(W, H), kBlk, 0, st>>>(src, dst, W, H, P)))
 }
 
 }  // namespace fs

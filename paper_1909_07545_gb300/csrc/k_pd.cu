@@ -33,7 +33,7 @@ namespace cg = cooperative_groups;
 
 namespace fs {
 
-template <int FW, int NY, int R>
+template <int FW, int NY, int R, int S>
 __global__ void __launch_bounds__(FW * NY, 1)
 k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int chained) {
   constexpr int FH = NY * R;
@@ -64,7 +64,7 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
     const int gy = oy + ty * R + r;
     if (col_in && gy >= 0 && gy < L.H) {
       const size_t i = (size_t)gy * L.P + gx;
-      px_load(L, i, pp.lam, pp.eps, c[r]);
+      px_load<S>(L, i, pp.lam, pp.eps, c[r]);
       mb |= (unsigned)L.mask[i] << (3 * r);
     } else {
       px_zero(c[r]);
@@ -80,8 +80,8 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
       const size_t i = (size_t)gy * L.P + gx;
       u[r] = in.u[i];
       ub[r] = in.ubar[i];
-      p1[r] = in.p1.ld(i, L.st);
-      p2[r] = in.p2.ld(i, L.st);
+      p1[r] = sld<S>(in.p1, i);
+      p2[r] = sld<S>(in.p2, i);
     } else {
       u[r] = ub[r] = p1[r] = p2[r] = 0.f;
     }
@@ -126,12 +126,12 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
     const size_t i = (size_t)gy * L.P + gx;
     out.u[i] = u[r];
     out.ubar[i] = ub[r];
-    out.p1.st(i, p1[r], L.st);
-    out.p2.st(i, p2[r], L.st);
+    sst<S>(out.p1, i, p1[r]);
+    sst<S>(out.p2, i, p2[r]);
   }
 }
 
-template <int TW, int NY, int R>
+template <int TW, int NY, int R, int S>
 __global__ void __launch_bounds__(TW * NY, 1)
 k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
   constexpr int TH = NY * R;
@@ -176,9 +176,9 @@ k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
       const size_t i = (size_t)gy * L.P + gx;
       u[r] = L.u[i];
       ub[r] = L.ubar[i];
-      p1[r] = L.p1.ld(i, L.st);
-      p2[r] = L.p2.ld(i, L.st);
-      px_load(L, i, pp.lam, pp.eps, c[r]);
+      p1[r] = sld<S>(L.p1, i);
+      p2[r] = sld<S>(L.p2, i);
+      px_load<S>(L, i, pp.lam, pp.eps, c[r]);
       mb |= (unsigned)L.mask[i] << (3 * r);
     } else {
       u[r] = ub[r] = p1[r] = p2[r] = 0.f;
@@ -228,12 +228,12 @@ k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
     const size_t i = (size_t)gy * L.P + gx;
     L.u[i] = u[r];
     L.ubar[i] = ub[r];
-    L.p1.st(i, p1[r], L.st);
-    L.p2.st(i, p2[r], L.st);
+    sst<S>(L.p1, i, p1[r]);
+    sst<S>(L.p2, i, p2[r]);
   }
 }
 
-template <int FW, int NY, int R>
+template <int FW, int NY, int R, int S>
 static cudaError_t launch_pd_t(const LevelView& L, const PDState& in, const PDState& out,
                                const PDParams& pp, int B, int n, bool chained,
                                cudaStream_t st) {
@@ -248,15 +248,26 @@ static cudaError_t launch_pd_t(const LevelView& L, const PDState& in, const PDSt
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k_pd<FW, NY, R>, L, in, out, pp, B, n, chained ? 1 : 0);
+  return cudaLaunchKernelEx(&cfg, k_pd<FW, NY, R, S>, L, in, out, pp, B, n, chained ? 1 : 0);
+}
+
+template <int S>
+static cudaError_t launch_pd_s(int variant, const LevelView& L, const PDState& in,
+                               const PDState& out, const PDParams& pp, int B, int n,
+                               cudaStream_t st, bool chained) {
+  switch (variant) {
+    case PD_TILE_64: return launch_pd_t<64, 8, 8, S>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_32: return launch_pd_t<32, 8, 4, S>(L, in, out, pp, B, n, chained, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_pd(int variant, const LevelView& L, const PDState& in, const PDState& out,
                       const PDParams& pp, int B, int n, cudaStream_t st, bool chained) {
-  switch (variant) {
-    case PD_TILE_64: return launch_pd_t<64, 8, 8>(L, in, out, pp, B, n, chained, st);
-    case PD_TILE_32: return launch_pd_t<32, 8, 4>(L, in, out, pp, B, n, chained, st);
-    default: return cudaErrorInvalidValue;
+  switch (L.st) {
+    case ST_F16: return launch_pd_s<ST_F16>(variant, L, in, out, pp, B, n, st, chained);
+    case ST_BF16: return launch_pd_s<ST_BF16>(variant, L, in, out, pp, B, n, st, chained);
+    default: return launch_pd_s<ST_F32>(variant, L, in, out, pp, B, n, st, chained);
   }
 }
 
@@ -290,11 +301,11 @@ static cudaLaunchConfig_t cluster_config(unsigned cx, unsigned cy, cudaStream_t 
 // True when a cluster of the tiles covering W x H can be resident (cluster
 // sizes above 8 need the non-portable opt-in; the occupancy query says
 // whether a GPC has room for it).
-template <int TW, int NY, int R>
-static bool cluster_fits_t(int W, int H) {
+template <int TW, int NY, int R, int S>
+static bool cluster_fits_s(int W, int H) {
   unsigned cx, cy;
   if (!cluster_dims<TW, NY, R>(W, H, cx, cy)) return false;
-  if (cudaFuncSetAttribute(k_pd_cluster<TW, NY, R>,
+  if (cudaFuncSetAttribute(k_pd_cluster<TW, NY, R, S>,
                            cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -302,21 +313,38 @@ static bool cluster_fits_t(int W, int H) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = cluster_config<TW, NY, R>(cx, cy, nullptr, attr);
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_pd_cluster<TW, NY, R>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, k_pd_cluster<TW, NY, R, S>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   return n >= 1;
 }
 
+// every storage instantiation must fit (a handle picks one at creation)
 template <int TW, int NY, int R>
-static cudaError_t launch_cluster_t(const LevelView& L, const PDParams& pp, int n,
+static bool cluster_fits_t(int W, int H) {
+  return cluster_fits_s<TW, NY, R, ST_F32>(W, H) && cluster_fits_s<TW, NY, R, ST_F16>(W, H) &&
+         cluster_fits_s<TW, NY, R, ST_BF16>(W, H);
+}
+
+template <int TW, int NY, int R, int S>
+static cudaError_t launch_cluster_s(const LevelView& L, const PDParams& pp, int n,
                                     cudaStream_t st) {
   unsigned cx, cy;
   if (!cluster_dims<TW, NY, R>(L.W, L.H, cx, cy) || n < 1) return cudaErrorInvalidValue;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = cluster_config<TW, NY, R>(cx, cy, st, attr);
-  return cudaLaunchKernelEx(&cfg, k_pd_cluster<TW, NY, R>, L, pp, n);
+  return cudaLaunchKernelEx(&cfg, k_pd_cluster<TW, NY, R, S>, L, pp, n);
+}
+
+template <int TW, int NY, int R>
+static cudaError_t launch_cluster_t(const LevelView& L, const PDParams& pp, int n,
+                                    cudaStream_t st) {
+  switch (L.st) {
+    case ST_F16: return launch_cluster_s<TW, NY, R, ST_F16>(L, pp, n, st);
+    case ST_BF16: return launch_cluster_s<TW, NY, R, ST_BF16>(L, pp, n, st);
+    default: return launch_cluster_s<TW, NY, R, ST_F32>(L, pp, n, st);
+  }
 }
 
 int pd_cluster_variant(int W, int H) {

@@ -27,17 +27,18 @@ struct PxConst {
   float Iu, rho0, uw, inv;   // linearisation, 1 / I_u (0 when I_u = 0)
 };
 
+template <int S>
 __device__ __forceinline__ void px_load(const LevelView& L, size_t i, float lam, float eps,
                                         PxConst& c) {
-  c.sx = L.sx.ld(i, L.st);
-  c.sy = L.sy.ld(i, L.st);
+  c.sx = sld<S>(L.sx, i);
+  c.sy = sld<S>(L.sy, i);
   const float sg = L.sig[i];
   c.dinv = __fdiv_rn(1.f, fmaf(sg, eps, 1.f));
   c.sd = __fmul_rn(sg, c.dinv);
   c.tau = L.tau[i];
-  c.Iu = L.Iu.ld(i, L.st);
+  c.Iu = sld<S>(L.Iu, i);
   c.step = fabsf(__fmul_rn(__fmul_rn(c.tau, lam), c.Iu));
-  c.rho0 = L.rho0.ld(i, L.st);
+  c.rho0 = sld<S>(L.rho0, i);
   c.uw = L.uw[i];
   c.inv = c.Iu != 0.f ? __fdiv_rn(1.f, c.Iu) : 0.f;
 }
