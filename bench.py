@@ -337,9 +337,20 @@ def main():
         vsteps = max(3, min(args.steps, 10))
         for storage in ("f16", "bf16"):
             x = make(storage)
-            ms = timed(lambda: x.solve(I0, I1, warps, iters, disp=disp, depth=depth), vsteps)
+            run = lambda: x.solve(I0, I1, warps, iters, disp=disp, depth=depth)
+            ms = timed(run, vsteps)
+            x.timing_enable(True)
+            run()
+            stream.synchronize()
+            x.timing_read(reset=True)
+            for i in range(vsteps):
+                flush.fill_(float(i))
+                run()
+                x.timing_read(reset=False)
+            lv = x.timing_read(reset=True)
             variants[storage] = {"value": job_rate(world, 1, ms), "unit": "frames/s",
-                                 "ms_per_frame": ms}
+                                 "ms_per_frame": ms,
+                                 "pd_per_level_ms": [m / vsteps for m, _, _ in lv]}
             x.close()
         if args.batch > 1:
             from paper_1909_07545_gb300 import Batch
@@ -348,11 +359,14 @@ def main():
                 bt = Batch(sols, stream=stream)
                 outs_d = [torch.empty((H, W), device="cuda") for _ in sols]
                 outs_z = [torch.empty((H, W), device="cuda") for _ in sols]
-                ms = timed(lambda: bt.solve([I0] * len(sols), [I1] * len(sols), warps, iters,
-                                            disps=outs_d, depths=outs_z), vsteps)
-                variants[f"batched_{storage}"] = {
-                    "value": job_rate(world, len(sols), ms), "unit": "frames/s",
-                    "pairs_per_batch": len(sols), "ms_per_batch": ms}
+                # k: pairs allowed on their finest level at once (0 = no bound)
+                for k in (0, 1, 2):
+                    bt.set_finest_limit(k)
+                    ms = timed(lambda: bt.solve([I0] * len(sols), [I1] * len(sols), warps,
+                                                iters, disps=outs_d, depths=outs_z), vsteps)
+                    variants[f"batched_{storage}_finest{k}"] = {
+                        "value": job_rate(world, len(sols), ms), "unit": "frames/s",
+                        "pairs_per_batch": len(sols), "finest_limit": k, "ms_per_batch": ms}
                 bt.close()
                 for x in sols:
                     x.close()

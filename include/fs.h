@@ -177,6 +177,18 @@ fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0, const float* con
                          const float* const* d_init, int warps, int iters,
                          float* const* d_disp, float* const* d_depth);
 
+/* Bound how many of the batch's pairs run their finest level at the same
+ * time: pair i starts its finest level (tensor, upsample, warps) only after
+ * pair i - k has finished its own; coarser levels of all pairs still
+ * overlap freely.  The finest level's working set (about 60 B per pixel in
+ * FP32 storage) is what decides whether concurrent pairs still fit the L2
+ * cache, so k = 1 or 2 keeps a 1024x1024 batch L2-resident while its coarse
+ * levels, which are latency-bound, run side by side.  k = 0 (the default)
+ * sets no bound.  Results are unchanged (each pair's work and order are the
+ * same); only the schedule differs.  Takes effect at the next
+ * fs_batch_solve, which captures a new graph.  FS_EINVAL for k < 0. */
+fs_status fs_batch_set_finest_limit(fs_batch* b, int k);
+
 /* Free the batch (its streams, events and graph; not the handles). */
 fs_status fs_batch_destroy(fs_batch* b);
 

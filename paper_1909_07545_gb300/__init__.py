@@ -34,7 +34,8 @@ EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_trajectory_field", "fs_solve", "fs_solve_host", "fs_destroy", "fs_last_error",
             "fs_buffer_read", "fs_buffer_write", "fs_run_stage", "fs_stage_prerotate",
             "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc",
-            "fs_batch_create", "fs_batch_solve", "fs_batch_destroy", "fs_autotune"]
+            "fs_batch_create", "fs_batch_solve", "fs_batch_set_finest_limit",
+            "fs_batch_destroy", "fs_autotune"]
 
 
 class FsError(RuntimeError):
@@ -98,6 +99,7 @@ def load_library():
         "fs_batch_create": [ctypes.POINTER(_P), i, _P, ctypes.POINTER(_P)],
         "fs_batch_solve": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), i, i,
                            ctypes.POINTER(_P), ctypes.POINTER(_P)],
+        "fs_batch_set_finest_limit": [_P, i],
         "fs_batch_destroy": [_P],
         "fs_autotune": [_P, i, _P],
     }
@@ -299,7 +301,7 @@ class Solver:
 class Batch:
     """fs_batch: one concurrent solve over several Solvers (one pair each)."""
 
-    def __init__(self, solvers, stream=None):
+    def __init__(self, solvers, stream=None, finest_limit=0):
         import torch
         self.lib = load_library()
         self.torch = torch
@@ -312,6 +314,12 @@ class Batch:
         _check(self.lib.fs_batch_create(hs, len(self.solvers), _P(stream.cuda_stream),
                                         ctypes.byref(b)))
         self.b = b
+        if finest_limit:
+            self.set_finest_limit(finest_limit)
+
+    def set_finest_limit(self, k):
+        """At most k pairs on their finest level at once (0: no bound)."""
+        _check(self.lib.fs_batch_set_finest_limit(self.b, int(k)))
 
     def solve(self, I0s, I1s, warps, iters, inits=None, disps=None, depths=None):
         """Device tensors per pair; returns lists of (disparity, depth) tensors."""

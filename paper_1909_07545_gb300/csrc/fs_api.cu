@@ -379,14 +379,19 @@ cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
 }
 
 // The whole method for one pair on stream st (Algorithm 1 in the pyramid).
+// finest_wait / finest_done (may be null): a dependency taken before the
+// finest level's work starts and an event recorded once it has ended, which a
+// batch uses to bound how many pairs occupy their finest level at once.
 fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const float* init,
-                        int warps, int iters, float* disp, float* depth, cudaStream_t st) {
+                        int warps, int iters, float* disp, float* depth, cudaStream_t st,
+                        cudaEvent_t finest_wait = nullptr, cudaEvent_t finest_done = nullptr) {
   fs_status s;
   HostLevel& L0 = h->lv[0];
   FS_LAUNCH("k_copy_in_s", launch_copy_in_I0(I0, L0.v, st));
   FS_LAUNCH("k_prerotate", launch_prerotate(I1, h->cfield, L0.v, st));
   int top = h->L - 1;
   if (init) {   // warm start: the finest level only, from the given disparity
+    if (finest_wait) FS_CUDA(cudaStreamWaitEvent(st, finest_wait, 0));
     k_copy_in<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(init, L0.v.u, L0.W, L0.H, L0.P);
     FS_LAUNCHED("k_copy_in");
     if ((s = run_stage(h, 0, FS_STAGE_WARM, 0, st)) != FS_OK) return s;
@@ -404,12 +409,14 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
       h->ev_levels = 1;
       h->ev_pending = true;
     }
+    if (finest_done) FS_CUDA(cudaEventRecord(finest_done, st));
     return enqueue_depth(h, disp, depth, st);
   }
   for (int l = 0; l < top; ++l)
     if ((s = run_stage(h, l, FS_STAGE_DOWNSAMPLE, 0, st)) != FS_OK) return s;
   for (int l = top; l >= 0; --l) {
     HostLevel& L = h->lv[l];
+    if (l == 0 && finest_wait) FS_CUDA(cudaStreamWaitEvent(st, finest_wait, 0));
     if ((s = run_stage(h, l, FS_STAGE_TENSOR, 0, st)) != FS_OK) return s;
     if (l == top) {
       FS_LAUNCH("k_zero_state", launch_zero_state(L.v, st));
@@ -430,6 +437,7 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
     h->ev_levels = h->L;
     h->ev_pending = true;
   }
+  if (finest_done) FS_CUDA(cudaEventRecord(finest_done, st));
   return enqueue_depth(h, disp, depth, st);
 }
 
@@ -690,6 +698,8 @@ struct fs_batch {
   cudaStream_t origin = nullptr;          // capture origin
   std::vector<cudaStream_t> lanes;        // one per pair
   std::vector<cudaEvent_t> joins;
+  std::vector<cudaEvent_t> finest;        // pair i's finest level has ended
+  int finest_limit = 0;                   // pairs on their finest level at once (0: all)
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void*> key;
@@ -699,6 +709,7 @@ struct fs_batch {
 static void batch_free(fs_batch* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->finest) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   for (cudaStream_t s : b->lanes) cudaStreamDestroy(s);
   if (b->origin) cudaStreamDestroy(b->origin);
@@ -730,6 +741,9 @@ extern "C" fs_status fs_batch_create(fs_handle* const* handles, int n, void* cud
     e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
     if (e != cudaSuccess) break;
     b->joins.push_back(j);
+    e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    b->finest.push_back(j);
   }
   if (e != cudaSuccess) {
     batch_free(b);
@@ -770,8 +784,12 @@ extern "C" fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0,
     for (int i = 0; i < n && s == FS_OK && e == cudaSuccess; ++i) {
       e = cudaStreamWaitEvent(b->lanes[i], b->fork, 0);
       if (e != cudaSuccess) break;
+      // pair i enters its finest level once pair i - k has left its own
+      const int k = b->finest_limit;
+      cudaEvent_t wait = (k > 0 && i >= k) ? b->finest[i - k] : nullptr;
+      cudaEvent_t done = k > 0 ? b->finest[i] : nullptr;
       s = enqueue_solve(b->h[i], d_I0[i], d_I1[i], d_init ? d_init[i] : nullptr, warps, iters,
-                        d_disp[i], d_depth[i], b->lanes[i]);
+                        d_disp[i], d_depth[i], b->lanes[i], wait, done);
       if (s != FS_OK) break;
       e = cudaEventRecord(b->joins[i], b->lanes[i]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->joins[i], 0);
@@ -801,6 +819,18 @@ extern "C" fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0,
       h->ev_pending = true;
     }
   }
+  return FS_OK;
+}
+
+extern "C" fs_status fs_batch_set_finest_limit(fs_batch* b, int k) {
+  if (!b) return fail(FS_EINVAL, "null batch");
+  if (k < 0) return fail(FS_EINVAL, "finest-level limit must be >= 0");
+  if (k != b->finest_limit && b->gexec) {   // the cached schedule no longer applies
+    cudaStreamSynchronize(b->stream);
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  b->finest_limit = k;
   return FS_OK;
 }
 

@@ -153,11 +153,16 @@ def test_batch_results_equal_lone_solves(small):
         s.close()
     solvers = [make_solver(p) for p in pairs]
     batch = fsb.Batch(solvers)
-    for rep in range(2):                     # capture, then replay
-        ds, zs = batch.solve([p["I0"] for p in pairs], [p["I1"] for p in pairs], 3, 25)
-        for (d, z), (ad, az) in zip(zip(ds, zs), alone):
-            assert np.array_equal(np64(d), ad)
-            assert np.array_equal(np64(z), az, equal_nan=True)
+    # no bound, then one and two pairs at a time on the finest level
+    for limit in (0, 1, 2):
+        batch.set_finest_limit(limit)
+        for rep in range(2):                 # capture, then replay
+            ds, zs = batch.solve([p["I0"] for p in pairs], [p["I1"] for p in pairs], 3, 25)
+            for (d, z), (ad, az) in zip(zip(ds, zs), alone):
+                assert np.array_equal(np64(d), ad)
+                assert np.array_equal(np64(z), az, equal_nan=True)
+    with pytest.raises(fsb.FsError):
+        batch.set_finest_limit(-1)
     batch.close()
     for s in solvers:
         s.close()
