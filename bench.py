@@ -154,6 +154,122 @@ def cpu_baseline(pair, target_s=15.0):
     return n * W * H / dt, n, dt
 
 
+def serve_leg(seed, seconds, rate, inflight, n_rigs=16, n_frames=3):
+    """Serving: Poisson arrivals from n_rigs moving rigs (sizes drawn from
+    640 / 1024 / 1280 px, each its own seeded Kannala-Brandt calibration,
+    relative pose and scene) through one fs_server; each rig's frames
+    warm-start from its previous disparity (3 warps x 50 iterations on the
+    finest level; a rig's first frame is a cold 10 x 100 solve over its
+    pyramid).  Each rig renders n_frames consecutive frames of its path,
+    replayed forwards and backwards (0, 1, 2, 1, 0, ...) so the motion stays
+    smooth.  Returns the open-loop figures at the offered rate and the
+    saturated throughput (every rig's queue kept full)."""
+    import queue
+
+    import torch
+
+    import synth
+    from paper_1909_07545_gb300 import Server
+    rng = np.random.default_rng(1000 + seed)
+    sizes = [int(v) for v in rng.choice([640, 1024, 1280], size=n_rigs)]
+    t0 = time.perf_counter()
+    rigs = [synth.rig_sequence(10000 * (seed + 1) + i, W, W, n_frames=n_frames)
+            for i, W in enumerate(sizes)]
+    render_s = time.perf_counter() - t0
+    srv = Server(budget_bytes=40 << 30, max_inflight=inflight, warps=3, iters=50,
+                 cold_warps=10, cold_iters=100)
+    ids = []
+    frames = []
+    outs = []
+    ring = 4                           # result buffers per rig
+    for q, W in zip(rigs, sizes):
+        ids.append(srv.add_rig(q["cam0"], q["cam1"], q["R"], q["t"], W, W, q["levels"],
+                               lam=q["lam"], huber_eps=q["eps"]))
+        frames.append([(torch.from_numpy(np.float32(a)).pin_memory(),
+                        torch.from_numpy(np.float32(b)).pin_memory()) for a, b, _ in q["frames"]])
+        outs.append([(torch.empty((W, W)).pin_memory(), torch.empty((W, W)).pin_memory())
+                     for _ in range(ring)])
+    cycle = list(range(n_frames)) + list(range(n_frames - 2, 0, -1))
+    pos = [0] * n_rigs
+    free = [queue.Queue() for _ in range(n_rigs)]
+    for r in range(n_rigs):
+        for k in range(ring):
+            free[r].put(k)
+
+    def submit(r):
+        slot = free[r].get()
+        I0, I1 = frames[r][cycle[pos[r] % len(cycle)]]
+        pos[r] += 1
+        d, z = outs[r][slot]
+        return srv.submit(ids[r], I0, I1, d, z), r, slot
+
+    done_q = queue.Queue()
+
+    def waiter():
+        while True:
+            item = done_q.get()
+            if item is None:
+                return
+            req, r, slot = item
+            srv.wait(req)
+            free[r].put(slot)
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    # warm-up: every rig's cold first frame, then two warm frames each
+    for _ in range(3):
+        for r in range(n_rigs):
+            done_q.put(submit(r))
+    srv.drain()
+    srv.stats(reset=True)
+
+    # open loop at the offered rate
+    arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds * 1.2) + 16))
+    arr = arr[arr < seconds]
+    which = rng.integers(0, n_rigs, size=len(arr))
+    start = time.perf_counter()
+    stalls = 0
+    for ta, r in zip(arr, which):
+        now = time.perf_counter() - start
+        if ta > now:
+            time.sleep(ta - now)
+        if free[int(r)].empty():
+            stalls += 1
+        done_q.put(submit(int(r)))
+    srv.drain()
+    open_loop = srv.stats(reset=True)
+
+    # saturated: keep every rig's ring full for a fixed number of requests
+    n_sat = 8 * n_rigs
+    t1 = time.perf_counter()
+    for i in range(n_sat):
+        done_q.put(submit(i % n_rigs))
+    srv.drain()
+    sat = srv.stats(reset=True)
+    sat_wall = time.perf_counter() - t1
+    done_q.put(None)
+    th.join()
+    srv.close()
+    px = {W: W * W for W in set(sizes)}
+    mean_px = float(np.mean([px[W] for W in sizes]))
+    return {
+        "workload": f"{n_rigs} rigs (sizes {sorted(set(sizes))}: "
+                    f"{[sizes.count(v) for v in sorted(set(sizes))]}), Kannala-Brandt 190 deg, "
+                    f"warm start 3x50 on the finest level, FP32",
+        "offered_per_s": rate, "seconds": seconds, "max_inflight": inflight,
+        "requests": int(open_loop["completed"]), "failed": int(open_loop["failed"]),
+        "frames_per_s": open_loop["frames_per_s"], "p50_ms": open_loop["p50_ms"],
+        "p99_ms": open_loop["p99_ms"], "max_ms": open_loop["max_ms"],
+        "mean_ms": open_loop["mean_ms"], "submit_stalls": stalls,
+        "cold": int(open_loop["cold"]), "evictions": int(open_loop["evictions"]),
+        "resident_gb": open_loop["resident_bytes"] / 1e9,
+        "saturated_frames_per_s": sat["frames_per_s"], "saturated_requests": n_sat,
+        "saturated_wall_s": sat_wall,
+        "gpix_iter_s_at_offered": open_loop["frames_per_s"] * mean_px * 150 / 1e9,
+        "render_s": render_s,
+    }
+
+
 def run_reference(args, pair, rank):
     """--impl reference: the FP64 oracle on the host cores, per step a bounded
     sample of the frame (primal-dual iterations of the finest level)."""
@@ -215,6 +331,10 @@ def main():
                     help="skip fs_autotune (default schedule per level)")
     ap.add_argument("--batch", type=int, default=4,
                     help="pairs per fs_batch for the batched-throughput figure (<= 1 skips)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the open-loop serving run (0 skips serving)")
+    ap.add_argument("--serve-rate", type=float, default=600.0, help="offered requests/s")
+    ap.add_argument("--serve-inflight", type=int, default=8)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -371,6 +491,17 @@ def main():
                 for x in sols:
                     x.close()
 
+    serving = None
+    if args.serve_seconds > 0:
+        serving = serve_leg(replica_seed(args.seed, rank), args.serve_seconds, args.serve_rate,
+                            args.serve_inflight)
+        if dist:
+            fps_sum = torch.tensor([serving["frames_per_s"]], dtype=torch.float64, device="cuda")
+            dist.all_reduce(fps_sum)
+            p99, = reduce_max([serving["p99_ms"]], dist, "cuda")
+            serving["frames_per_s_all_ranks"] = float(fps_sum.item())
+            serving["p99_ms_max_over_ranks"] = p99
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -416,6 +547,8 @@ def main():
         "wall_s": t_wall,
     }
     line["variants"] = variants
+    if serving is not None:
+        line["serving"] = serving
     line["e2e"] = {"value": world / e2e_s, "unit": "frames/s",
                    "h2d_bytes_per_step": 2 * W * H * 4, "d2h_bytes_per_step": 2 * W * H * 4}
     if not args.no_cpu_baseline:

@@ -117,6 +117,14 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H,
                     int levels, const fs_params* prm, void* cuda_stream,
                     fs_handle** out);
 
+/* Device bytes fs_create would allocate for a handle of this size, level
+ * count and storage (prm NULL = defaults), without allocating: the pyramid's
+ * planes (FP32 state, the 16-bit-capable planes in the storage type, float2
+ * fields, mask bytes) and the calibration field.  fs_solve_host adds 5
+ * planes of W x H floats on its first call.  FS_EINVAL for sizes or levels
+ * fs_create rejects. */
+fs_status fs_state_bytes(int W, int H, int levels, const fs_params* prm, size_t* out);
+
 /* Replace the pose; recomputes the calibration and trajectory fields. */
 fs_status fs_set_pose(fs_handle* h, const fs_pose* pose);
 

@@ -35,7 +35,10 @@ EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_buffer_read", "fs_buffer_write", "fs_run_stage", "fs_stage_prerotate",
             "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc",
             "fs_batch_create", "fs_batch_solve", "fs_batch_set_finest_limit",
-            "fs_batch_destroy", "fs_autotune"]
+            "fs_batch_destroy", "fs_autotune", "fs_state_bytes",
+            "fs_server_default_config", "fs_server_create", "fs_server_add_rig",
+            "fs_server_submit", "fs_server_wait", "fs_server_drain", "fs_server_stats_read",
+            "fs_server_evict_all", "fs_server_destroy"]
 
 
 class FsError(RuntimeError):
@@ -61,6 +64,22 @@ class FsParams(ctypes.Structure):
                 ("block_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("pd_schedule", ctypes.c_int), ("storage", ctypes.c_int),
                 ("reserved", ctypes.c_int * 3)]
+
+
+class FsServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("warps", ctypes.c_int), ("iters", ctypes.c_int),
+                ("cold_warps", ctypes.c_int), ("cold_iters", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class FsServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("cold", ctypes.c_longlong),
+                ("evictions", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("frames_per_s", ctypes.c_double),
+                ("resident_bytes", ctypes.c_size_t), ("peak_resident_bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -102,6 +121,17 @@ def load_library():
         "fs_batch_set_finest_limit": [_P, i],
         "fs_batch_destroy": [_P],
         "fs_autotune": [_P, i, _P],
+        "fs_state_bytes": [i, i, i, ctypes.POINTER(FsParams), ctypes.POINTER(ctypes.c_size_t)],
+        "fs_server_default_config": [ctypes.POINTER(FsServerConfig)],
+        "fs_server_create": [ctypes.POINTER(FsServerConfig), ctypes.POINTER(_P)],
+        "fs_server_add_rig": [_P, ctypes.POINTER(FsCalib), ctypes.POINTER(FsPose), i, i, i,
+                              ctypes.POINTER(FsParams), ctypes.POINTER(i)],
+        "fs_server_submit": [_P, i, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_longlong)],
+        "fs_server_wait": [_P, ctypes.c_longlong, d, ctypes.POINTER(d)],
+        "fs_server_drain": [_P, d],
+        "fs_server_stats_read": [_P, ctypes.POINTER(FsServerStats), i],
+        "fs_server_evict_all": [_P],
+        "fs_server_destroy": [_P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -343,6 +373,121 @@ class Batch:
         if getattr(self, "b", None):
             _check(self.lib.fs_batch_destroy(self.b))
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def state_bytes(W, H, levels, **params) -> int:
+    """Device bytes fs_create allocates for a handle (fs_state_bytes); no GPU needed."""
+    lib = load_library()
+    out = ctypes.c_size_t()
+    _check(lib.fs_state_bytes(int(W), int(H), int(levels), ctypes.byref(default_params(**params)),
+                              ctypes.byref(out)))
+    return out.value
+
+
+class Server:
+    """fs_server: continuous-batching request server over many rigs.
+
+    Each rig keeps its pyramid state and last disparity resident on the
+    device; a rig's first frame is solved cold (cold_warps x cold_iters per
+    level), later frames warm-start from its previous disparity on the
+    finest level (warps x iters).  Requests of different rigs overlap on the
+    GPU; admission is bounded by max_inflight and the device-memory budget.
+    Inputs and outputs are host arrays (pinned torch tensors let the copies
+    run asynchronously); they are kept referenced until the request is waited
+    for.
+    """
+
+    def __init__(self, budget_bytes=0, max_inflight=8, warps=3, iters=50, cold_warps=10,
+                 cold_iters=100):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        torch.cuda.init()
+        self.lib = load_library()
+        self.torch = torch
+        cfg = FsServerConfig()
+        _check(self.lib.fs_server_default_config(ctypes.byref(cfg)))
+        cfg.hbm_budget = int(budget_bytes)
+        cfg.max_inflight = int(max_inflight)
+        cfg.warps, cfg.iters = int(warps), int(iters)
+        cfg.cold_warps, cfg.cold_iters = int(cold_warps), int(cold_iters)
+        s = _P()
+        _check(self.lib.fs_server_create(ctypes.byref(cfg), ctypes.byref(s)))
+        self.s = s
+        self.sizes = []
+        self._held = {}
+
+    def add_rig(self, cam0, cam1, R, t, W, H, levels, params=None, **kw) -> int:
+        if params is None:
+            params = default_params(**kw)
+        cams = (FsCalib * 2)(_calib(cam0), _calib(cam1))
+        rid = ctypes.c_int()
+        _check(self.lib.fs_server_add_rig(self.s, cams, ctypes.byref(_pose(R, t)), int(W), int(H),
+                                          int(levels), ctypes.byref(params), ctypes.byref(rid)))
+        self.sizes.append((int(H), int(W)))
+        return rid.value
+
+    def _host(self, a, shape, out=False):
+        torch = self.torch
+        if isinstance(a, torch.Tensor):
+            if a.device.type != "cpu" or a.dtype != torch.float32 or not a.is_contiguous():
+                raise ValueError("server buffers must be contiguous float32 CPU tensors")
+            t = a
+        else:
+            if out:
+                if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and
+                        a.flags["C_CONTIGUOUS"]):
+                    raise ValueError("output arrays must be C-contiguous float32")
+                t = torch.from_numpy(a)
+            else:
+                t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+        if tuple(t.shape) != shape:
+            raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+        return t
+
+    def submit(self, rig, I0, I1, disp=None, depth=None) -> int:
+        """Queue a pair (host arrays, H x W); returns the request id."""
+        shape = self.sizes[rig]
+        bufs = [self._host(I0, shape), self._host(I1, shape),
+                None if disp is None else self._host(disp, shape, out=True),
+                None if depth is None else self._host(depth, shape, out=True)]
+        rid = ctypes.c_longlong()
+        _check(self.lib.fs_server_submit(self.s, int(rig), *[_ptr(b) for b in bufs],
+                                         ctypes.byref(rid)))
+        self._held[rid.value] = bufs
+        return rid.value
+
+    def wait(self, req, timeout=-1.0) -> float:
+        """Block until the request is done; returns its latency in ms."""
+        lat = ctypes.c_double()
+        st = self.lib.fs_server_wait(self.s, int(req), float(timeout), ctypes.byref(lat))
+        if st != -5:                      # FS_ETIMEOUT keeps the request known
+            self._held.pop(int(req), None)
+        _check(st)
+        return lat.value
+
+    def drain(self, timeout=-1.0):
+        _check(self.lib.fs_server_drain(self.s, float(timeout)))
+
+    def stats(self, reset=False) -> dict:
+        st = FsServerStats()
+        _check(self.lib.fs_server_stats_read(self.s, ctypes.byref(st), int(bool(reset))))
+        return {k: getattr(st, k) for k, _ in FsServerStats._fields_}
+
+    def evict_all(self):
+        _check(self.lib.fs_server_evict_all(self.s))
+
+    def close(self):
+        if getattr(self, "s", None):
+            _check(self.lib.fs_server_destroy(self.s))
+            self.s = None
+            self._held.clear()
 
     def __del__(self):
         try:

@@ -311,10 +311,11 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
   }
   if (nl % 2 == 1) {   // a single launch: bring the state back to the primary set
     size_t bytes = (size_t)L.P * L.H * sizeof(float);
+    size_t sbytes = (size_t)L.P * L.H * storage_size(L.v.st);
     FS_CUDA(cudaMemcpyAsync(A.u, Bs.u, bytes, cudaMemcpyDeviceToDevice, st));
     FS_CUDA(cudaMemcpyAsync(A.ubar, Bs.ubar, bytes, cudaMemcpyDeviceToDevice, st));
-    FS_CUDA(cudaMemcpyAsync(A.p1.p, Bs.p1.p, bytes, cudaMemcpyDeviceToDevice, st));
-    FS_CUDA(cudaMemcpyAsync(A.p2.p, Bs.p2.p, bytes, cudaMemcpyDeviceToDevice, st));
+    FS_CUDA(cudaMemcpyAsync(A.p1.p, Bs.p1.p, sbytes, cudaMemcpyDeviceToDevice, st));
+    FS_CUDA(cudaMemcpyAsync(A.p2.p, Bs.p2.p, sbytes, cudaMemcpyDeviceToDevice, st));
   }
   return FS_OK;
 }
@@ -458,6 +459,17 @@ fs_status check_handle(const fs_handle* h) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Device bytes of one level: the mask byte plane, 7 FP32 planes (tau,
+// sigma, u, ubar, u_w and the ping-pong u, ubar), 10 planes in the storage
+// type (I0, I1, s_x, s_y, p1, p2, I_u, rho0 and the ping-pong p1, p2) and 3
+// float2 planes (gamma, w, g); every plane starts on a 256-byte boundary.
+size_t level_bytes(int P, int H, int storage) {
+  size_t plane = align_up((size_t)P * H * sizeof(float), 256);
+  size_t splane = align_up((size_t)P * H * storage_size(storage), 256);
+  size_t plane8 = align_up((size_t)P * H, 256);
+  return plane8 + 7 * plane + 10 * splane + 3 * 2 * plane;
+}
+
 }  // namespace
 
 extern "C" {
@@ -479,10 +491,12 @@ fs_status fs_default_params(fs_params* out) {
   return FS_OK;
 }
 
-fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, int levels,
-                    const fs_params* prm, void* cuda_stream, fs_handle** out) {
-  if (!out) return fail(FS_EINVAL, "null output handle pointer");
-  *out = nullptr;
+}  // extern "C"
+
+// The argument checks of fs_create, without allocating (also used by the
+// server to reject a rig when it is registered).
+fs_status fs_internal_validate(const fs_calib cam[2], const fs_pose* pose, int W, int H,
+                               int levels, const fs_params* prm) {
   if (!cam || !pose) return fail(FS_EINVAL, "null calibration or pose");
   if (levels < 1 || levels > kMaxLevels) return fail(FS_EINVAL, "levels must be in [1, %d]", kMaxLevels);
   if (W < 4 || H < 4 || W > 32768 || H > 32768) return fail(FS_EINVAL, "bad image size %dx%d", W, H);
@@ -493,17 +507,28 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     double v = i < 9 ? pose->R[i] : pose->t[i - 9];
     if (!std::isfinite(v)) return fail(FS_EINVAL, "pose has a non-finite entry");
   }
-  fs_params p;
   if (prm) {
-    p = *prm;
+    const fs_params& p = *prm;
     if (!(p.lambda > 0) || !(p.huber_eps >= 0) || !(p.du_max > 0) || !(p.beta >= 0) ||
         !(p.eta > 0) || !(p.theta >= 0 && p.theta <= 1) || p.block_iters < 0 ||
         p.block_iters > 8 || p.pd_schedule < 0 || p.pd_schedule > 1 || p.storage < 0 ||
         p.storage > 2)
       return fail(FS_EINVAL, "parameter out of range");
-  } else {
-    fs_default_params(&p);
   }
+  size_t bytes = 0;
+  return fs_state_bytes(W, H, levels, prm, &bytes);   // level sizes
+}
+
+extern "C" {
+
+fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, int levels,
+                    const fs_params* prm, void* cuda_stream, fs_handle** out) {
+  if (!out) return fail(FS_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  fs_status s;
+  if ((s = fs_internal_validate(cam, pose, W, H, levels, prm)) != FS_OK) return s;
+  fs_params p;
+  if (prm) p = *prm; else fs_default_params(&p);
 
   fs_handle* h = new (std::nothrow) fs_handle();
   if (!h) return fail(FS_ENOMEM, "host allocation failed");
@@ -532,9 +557,7 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     L.fy = cam[0].fy * sc;
     L.cx = (cam[0].cx + 0.5) * sc - 0.5;
     L.cy = (cam[0].cy + 0.5) * sc - 0.5;
-    size_t plane = align_up((size_t)L.P * L.H * sizeof(float), 256);
-    size_t plane8 = align_up((size_t)L.P * L.H, 256);
-    bytes += plane8 + 17 * plane + 3 * 2 * plane;
+    bytes += level_bytes(L.P, L.H, p.storage);
     int cv = pd_cluster_variant(L.W, L.H);
     L.cluster = (cv >= 0 && pd_cluster_fits(cv, L.W, L.H)) ? cv : -1;
   }
@@ -549,6 +572,7 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
   for (int l = 0; l < levels; ++l) {
     HostLevel& L = h->lv[l];
     size_t plane = align_up((size_t)L.P * L.H * sizeof(float), 256);
+    size_t splane = align_up((size_t)L.P * L.H * storage_size(p.storage), 256);
     size_t plane8 = align_up((size_t)L.P * L.H, 256);
     LevelView& v = L.v;
     v.W = L.W; v.H = L.H; v.P = L.P;
@@ -558,7 +582,7 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     for (float** f : fl) { *f = (float*)cur; cur += plane; }
     SPlane* sp[] = {&v.I0, &v.I1, &v.sx, &v.sy, &v.p1, &v.p2, &v.Iu, &v.rho0, &v.p1_alt,
                     &v.p2_alt};
-    for (SPlane* f : sp) { f->p = cur; cur += plane; }
+    for (SPlane* f : sp) { f->p = cur; cur += splane; }
     float2** f2[] = {&v.gamma, &v.w, &v.g};
     for (float2** f : f2) { *f = (float2*)cur; cur += 2 * plane; }
   }
@@ -583,6 +607,25 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     return fail(FS_ECUDA, "fs_create: %s", cudaGetErrorString(e));
   }
   *out = h;
+  return FS_OK;
+}
+
+fs_status fs_state_bytes(int W, int H, int levels, const fs_params* prm, size_t* out) {
+  if (!out) return fail(FS_EINVAL, "null output");
+  if (levels < 1 || levels > kMaxLevels) return fail(FS_EINVAL, "levels must be in [1, %d]", kMaxLevels);
+  if (W < 4 || H < 4 || W > 32768 || H > 32768) return fail(FS_EINVAL, "bad image size %dx%d", W, H);
+  const int storage = prm ? prm->storage : 0;
+  if (storage < 0 || storage > 2) return fail(FS_EINVAL, "parameter out of range");
+  size_t bytes = 0;
+  int lw = W, lh = H;
+  for (int l = 0; l < levels; ++l) {
+    if (l > 0) { lw = (lw + 1) / 2; lh = (lh + 1) / 2; }
+    if (lw < 4 || lh < 4)
+      return fail(FS_EINVAL, "level %d would be %dx%d (< 4x4): too many levels", l, lw, lh);
+    bytes += level_bytes((int)align_up((size_t)lw, 32), lh, storage);
+  }
+  bytes += align_up(align_up((size_t)W, 32) * H * sizeof(float2), 256);
+  *out = bytes;
   return FS_OK;
 }
 

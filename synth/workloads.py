@@ -101,3 +101,54 @@ def fronto_plane(seed=0, model="equidistant", W=192, H=192, f=None, depth=2.0,
               supersample, 0.0, rng)
     p.update(levels=4, warps=8, iters=60, lam=50.0, eps=0.01, name=f"plane_{model}")
     return p
+
+
+def _smooth_path(rng, n_axes, max_rate, fmin=0.05, fmax=0.3):
+    """A function of time: per axis a sum of 3 sinusoids of low frequency,
+    amplitudes scaled so that the rate of change (the norm over the axes)
+    never exceeds max_rate."""
+    f = rng.uniform(fmin, fmax, size=(n_axes, 3))
+    ph = rng.uniform(0.0, 2 * math.pi, size=(n_axes, 3))
+    # |d/dt sum a_j sin(2 pi f_j t + ph_j)| <= sum a_j 2 pi f_j  (per axis)
+    a = max_rate / (3 * 2 * math.pi * f * math.sqrt(n_axes))
+
+    def at(t):
+        return (a * np.sin(2 * math.pi * f * t + ph)).sum(axis=1)
+    return at
+
+
+def rig_sequence(seed=0, W=640, H=640, n_frames=3, rate_hz=37.5, supersample=1, noise=0.01,
+                 levels=None, n_objects=20):
+    """A moving stereo rig: one seeded Kannala-Brandt calibration (f = 320 px
+    at 1024, 190 deg), a fixed relative pose (0.12 m baseline along x plus a
+    rotation <= 2 deg) and a fixed scene of planes and spheres at 0.5-20 m.
+    The rig's camera 0 follows a smooth path (position and rotation vector
+    each a sum of 3 low-frequency sinusoids per axis; speed <= 0.5 m/s,
+    rotation-vector rate <= 5 deg/s); frame k is rendered at time k / rate_hz.
+
+    Returns dict(cam0, cam1, R, t, levels, frames=[(I0, I1, gt_range), ...]).
+    R, t (X1 = R X0 + t) are the rig's, identical for every frame."""
+    rng = np.random.default_rng(seed)
+    f = 320.0 * W / 1024.0
+    half = math.radians(190.0) / 2.0
+    cam = _cam("kb", W, H, f, 190.0, draw_kb(rng, half))
+    R = rotation(rng.normal(size=3), math.radians(rng.uniform(0.0, 2.0)))
+    C1 = np.array([0.12, 0.0, 0.0])
+    scene = make_scene(rng, n_objects, (0.5, 20.0), 20.0, f, kinds=("plane", "sphere"))
+    pos = _smooth_path(rng, 3, 0.5)
+    rot = _smooth_path(rng, 3, math.radians(5.0))
+    frames = []
+    for k in range(n_frames):
+        tk = k / rate_hz
+        o = pos(tk)
+        rv = rot(tk)
+        ang = float(np.linalg.norm(rv))
+        R0 = rotation(rv, ang) if ang > 0 else np.eye(3)      # world -> camera 0
+        I0, gt = render(scene, cam, R0, o, W, H, supersample, noise, rng)
+        # camera 1: X1 = R X0 + t, so world -> camera 1 is R R0 and its
+        # centre is o + R0^T C1
+        I1, _ = render(scene, cam, R @ R0, o + R0.T @ C1, W, H, supersample, noise, rng)
+        frames.append((I0, I1, gt))
+    return dict(cam0=cam, cam1=dict(cam), R=R, t=-R @ C1, frames=frames,
+                levels=levels or auto_levels(W), lam=50.0, eps=0.01,
+                name=f"rig_kb_{W}")

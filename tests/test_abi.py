@@ -83,3 +83,42 @@ def test_host_side_validation(lib):
     assert lib.fs_batch_destroy(None) == 0
     assert lib.fs_destroy(None) == 0
     assert lib.fs_create(None, None, 64, 64, 1, None, None, ctypes.byref(h)) == -1
+
+
+def test_state_bytes_counts_the_level_planes(lib):
+    # mask bytes + 7 FP32 planes + 10 storage-typed planes + 3 float2 planes
+    # per level (pitch = width rounded up to 32, planes on 256-byte
+    # boundaries), plus the full-resolution calibration field
+    up = lambda v, a: (v + a - 1) // a * a
+
+    def expect(W, H, L, esize):
+        total, w, h = 0, W, H
+        for l in range(L):
+            if l:
+                w, h = (w + 1) // 2, (h + 1) // 2
+            P = up(w, 32)
+            total += up(P * h, 256) + 7 * up(4 * P * h, 256) + 10 * up(esize * P * h, 256) \
+                + 6 * up(4 * P * h, 256)
+        return total + up(up(W, 32) * H * 8, 256)
+    for W, H, L in [(64, 64, 2), (203, 157, 3), (1024, 1024, 5)]:
+        assert fsb.state_bytes(W, H, L) == expect(W, H, L, 4)
+        assert fsb.state_bytes(W, H, L, storage="f16") == expect(W, H, L, 2)
+        assert fsb.state_bytes(W, H, L, storage="bf16") < fsb.state_bytes(W, H, L)
+    with pytest.raises(fsb.FsError):
+        fsb.state_bytes(64, 64, 6)
+
+
+def test_server_config_validation(lib):
+    cfg = fsb.FsServerConfig()
+    assert lib.fs_server_default_config(ctypes.byref(cfg)) == 0
+    assert cfg.hbm_budget == 40 << 30 and cfg.max_inflight == 8
+    assert (cfg.warps, cfg.iters, cfg.cold_warps, cfg.cold_iters) == (3, 50, 10, 100)
+    s = ctypes.c_void_p()
+    bad = fsb.FsServerConfig(cfg.hbm_budget, 0, 3, 50, 10, 100)
+    assert lib.fs_server_create(ctypes.byref(bad), ctypes.byref(s)) == -1
+    bad = fsb.FsServerConfig(cfg.hbm_budget, 2, 0, 50, 10, 100)
+    assert lib.fs_server_create(ctypes.byref(bad), ctypes.byref(s)) == -1
+    assert lib.fs_server_create(ctypes.byref(cfg), None) == -1
+    assert lib.fs_server_drain(None, 0.0) == -1
+    assert lib.fs_server_stats_read(None, None, 0) == -1
+    assert lib.fs_server_destroy(None) == 0
