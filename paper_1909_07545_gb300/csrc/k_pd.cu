@@ -57,36 +57,47 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
   float u[R], ub[R], p1[R], p2[R];
   PxConst c[R];
   unsigned mb = 0;
-  // per-warp constants first: written by earlier kernels, not by the
-  // preceding launch of this chain
+  // Addresses clamped into the level and a validity flag per row: every
+  // load below is unconditional, so all of a thread's loads are in flight
+  // at once instead of one row's after another's.
+  const int gxc = min(max(gx, 0), L.W - 1);
+  unsigned idx[R];            // < 2^31: levels are at most 32768 x 32768
+  bool ok[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int gy = oy + ty * R + r;
-    if (col_in && gy >= 0 && gy < L.H) {
-      const size_t i = (size_t)gy * L.P + gx;
-      px_load<S>(L, i, pp.lam, pp.eps, c[r]);
-      mb |= (unsigned)L.mask[i] << (3 * r);
-    } else {
-      px_zero(c[r]);
+    ok[r] = col_in && gy >= 0 && gy < L.H;
+    idx[r] = (unsigned)(min(max(gy, 0), L.H - 1) * L.P + gxc);
+  }
+  // per-warp constants first: written by earlier kernels, not by the
+  // preceding launch of this chain
+  {
+    PxRaw raw[R];
+    unsigned char m8[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      px_fetch<S>(L, idx[r], ok[r], raw[r]);
+      m8[r] = ok[r] ? L.mask[idx[r]] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      px_make(raw[r], pp.lam, pp.eps, c[r]);
+      mb |= (unsigned)m8[r] << (3 * r);
     }
   }
   // the state is the preceding launch's output
   if (chained) cudaGridDependencySynchronize();
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const int fy = ty * R + r;
-    const int gy = oy + fy;
-    if (col_in && gy >= 0 && gy < L.H) {
-      const size_t i = (size_t)gy * L.P + gx;
-      u[r] = in.u[i];
-      ub[r] = in.ubar[i];
-      p1[r] = sld<S>(in.p1, i);
-      p2[r] = sld<S>(in.p2, i);
-    } else {
-      u[r] = ub[r] = p1[r] = p2[r] = 0.f;
-    }
-    s_ub[fy][tx] = ub[r];
+    const float a = in.u[idx[r]], b = in.ubar[idx[r]];
+    const float q1 = sld<S>(in.p1, idx[r]), q2 = sld<S>(in.p2, idx[r]);
+    u[r] = ok[r] ? a : 0.f;
+    ub[r] = ok[r] ? b : 0.f;
+    p1[r] = ok[r] ? q1 : 0.f;
+    p2[r] = ok[r] ? q2 : 0.f;
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) s_ub[ty * R + r][tx] = ub[r];
   __syncthreads();
 
   const int txr = min(tx + 1, FW - 1);
@@ -168,22 +179,39 @@ k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
   float u[R], ub[R], p1[R], p2[R];
   PxConst c[R];
   unsigned mb = 0;
+  // clamped addresses and unconditional loads, as in k_pd
+  const int gxc = min(gx, L.W - 1);
+  unsigned idx[R];            // < 2^31: levels are at most 32768 x 32768
+  bool ok[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gy = oy + ty * R + r;
+    ok[r] = col_in && gy < L.H;
+    idx[r] = (unsigned)(min(gy, L.H - 1) * L.P + gxc);
+  }
+  {
+    PxRaw raw[R];
+    unsigned char m8[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float a = L.u[idx[r]], b = L.ubar[idx[r]];
+      const float q1 = sld<S>(L.p1, idx[r]), q2 = sld<S>(L.p2, idx[r]);
+      u[r] = ok[r] ? a : 0.f;
+      ub[r] = ok[r] ? b : 0.f;
+      p1[r] = ok[r] ? q1 : 0.f;
+      p2[r] = ok[r] ? q2 : 0.f;
+      px_fetch<S>(L, idx[r], ok[r], raw[r]);
+      m8[r] = ok[r] ? L.mask[idx[r]] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      px_make(raw[r], pp.lam, pp.eps, c[r]);
+      mb |= (unsigned)m8[r] << (3 * r);
+    }
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int fy = ty * R + r;
-    const int gy = oy + fy;
-    if (col_in && gy < L.H) {
-      const size_t i = (size_t)gy * L.P + gx;
-      u[r] = L.u[i];
-      ub[r] = L.ubar[i];
-      p1[r] = sld<S>(L.p1, i);
-      p2[r] = sld<S>(L.p2, i);
-      px_load<S>(L, i, pp.lam, pp.eps, c[r]);
-      mb |= (unsigned)L.mask[i] << (3 * r);
-    } else {
-      u[r] = ub[r] = p1[r] = p2[r] = 0.f;
-      px_zero(c[r]);
-    }
     s_ub[fy * SU + tx] = ub[r];
     if (tx == 0 && to_left_ub) to_left_ub[fy * SU + TW] = ub[r];
     if (fy == 0 && to_up_ub) to_up_ub[TH * SU + tx] = ub[r];

@@ -24,29 +24,54 @@ struct PxConst {
   float sx, sy;      // T^1/2 = I - s s^T
   float dinv, sd;    // 1 / (1 + sigma eps), sigma / (1 + sigma eps)
   float tau, step;   // tau, |tau lam I_u|
-  float Iu, rho0, uw, inv;   // linearisation, 1 / I_u (0 when I_u = 0)
+  float c0;          // u_w - rho0 / I_u (0 when I_u = 0)
 };
+
+// The per-pixel inputs of a warp as stored, fetched with no use in between
+// so that a thread's loads for all its rows are in flight together.
+struct PxRaw {
+  float sx, sy, sig, tau, Iu, rho0, uw;
+};
+
+// Fetch from plane index i; v = false (a pixel outside the level) gives the
+// inputs of a pixel that never moves (all 0).  i must be a valid index even
+// when v is false (callers clamp it), so the loads need no branch.
+template <int S>
+__device__ __forceinline__ void px_fetch(const LevelView& L, size_t i, bool v, PxRaw& r) {
+  r.sx = sld<S>(L.sx, i);
+  r.sy = sld<S>(L.sy, i);
+  r.sig = L.sig[i];
+  r.tau = L.tau[i];
+  r.Iu = sld<S>(L.Iu, i);
+  r.rho0 = sld<S>(L.rho0, i);
+  r.uw = L.uw[i];
+  if (!v) r.sx = r.sy = r.sig = r.tau = r.Iu = r.rho0 = r.uw = 0.f;
+}
+
+// Per-pixel constants from the fetched inputs (all-zero inputs give the
+// constants of px_zero).
+__device__ __forceinline__ void px_make(const PxRaw& r, float lam, float eps, PxConst& c) {
+  c.sx = r.sx;
+  c.sy = r.sy;
+  c.dinv = __fdiv_rn(1.f, fmaf(r.sig, eps, 1.f));
+  c.sd = __fmul_rn(r.sig, c.dinv);
+  c.tau = r.tau;
+  c.step = fabsf(__fmul_rn(__fmul_rn(c.tau, lam), r.Iu));
+  c.c0 = r.Iu != 0.f ? __fsub_rn(r.uw, __fdiv_rn(r.rho0, r.Iu)) : 0.f;
+}
 
 template <int S>
 __device__ __forceinline__ void px_load(const LevelView& L, size_t i, float lam, float eps,
                                         PxConst& c) {
-  c.sx = sld<S>(L.sx, i);
-  c.sy = sld<S>(L.sy, i);
-  const float sg = L.sig[i];
-  c.dinv = __fdiv_rn(1.f, fmaf(sg, eps, 1.f));
-  c.sd = __fmul_rn(sg, c.dinv);
-  c.tau = L.tau[i];
-  c.Iu = sld<S>(L.Iu, i);
-  c.step = fabsf(__fmul_rn(__fmul_rn(c.tau, lam), c.Iu));
-  c.rho0 = sld<S>(L.rho0, i);
-  c.uw = L.uw[i];
-  c.inv = c.Iu != 0.f ? __fdiv_rn(1.f, c.Iu) : 0.f;
+  PxRaw r;
+  px_fetch<S>(L, i, true, r);
+  px_make(r, lam, eps, c);
 }
 
 __device__ __forceinline__ void px_zero(PxConst& c) {
   c.sx = c.sy = 0.f;
   c.dinv = 1.f;
-  c.sd = c.tau = c.step = c.Iu = c.rho0 = c.uw = c.inv = 0.f;
+  c.sd = c.tau = c.step = c.c0 = 0.f;
 }
 
 // Dual ascent at one pixel: ub, right = ubar(x + e1), below = ubar(x + e2).
@@ -87,9 +112,7 @@ __device__ __forceinline__ float px_relax(float un, float u, float theta) {
 // Returns the new u (unchanged where tau = 0, i.e. outside the mask).
 __device__ __forceinline__ float px_primal(float u, float dv, const PxConst& c) {
   const float uh = fmaf(c.tau, dv, u);
-  // rho0 + I_u (uh - u_w): the small increment keeps its precision
-  const float rb = fmaf(c.Iu, __fsub_rn(uh, c.uw), c.rho0);
-  const float du = fminf(fmaxf(__fmul_rn(-rb, c.inv), -c.step), c.step);
+  const float du = fminf(fmaxf(__fsub_rn(c.c0, uh), -c.step), c.step);
   return __fadd_rn(uh, du);
 }
 
