@@ -154,13 +154,14 @@ def cpu_baseline(pair, target_s=15.0):
     return n * W * H / dt, n, dt
 
 
-def serve_leg(seed, seconds, rate, inflight, n_rigs=16, n_frames=3):
+def serve_leg(seed, seconds, rate, inflight, warm_mode=1, n_rigs=16, n_frames=3):
     """Serving: Poisson arrivals from n_rigs moving rigs (sizes drawn from
     640 / 1024 / 1280 px, each its own seeded Kannala-Brandt calibration,
     relative pose and scene) through one fs_server; each rig's frames
-    warm-start from its previous disparity (3 warps x 50 iterations on the
-    finest level; a rig's first frame is a cold 10 x 100 solve over its
-    pyramid).  Each rig renders n_frames consecutive frames of its path,
+    warm-start from its previous result (3 warps x 50 iterations on the
+    finest level, continuing from the last u and w for warm_mode 1, from
+    the last disparity for 0; a rig's first frame is a cold 10 x 100 solve
+    over its pyramid).  Each rig renders n_frames consecutive frames of its path,
     replayed forwards and backwards (0, 1, 2, 1, 0, ...) so the motion stays
     smooth.  Returns the open-loop figures at the offered rate and the
     saturated throughput (every rig's queue kept full)."""
@@ -177,7 +178,7 @@ def serve_leg(seed, seconds, rate, inflight, n_rigs=16, n_frames=3):
             for i, W in enumerate(sizes)]
     render_s = time.perf_counter() - t0
     srv = Server(budget_bytes=40 << 30, max_inflight=inflight, warps=3, iters=50,
-                 cold_warps=10, cold_iters=100)
+                 cold_warps=10, cold_iters=100, warm_mode=warm_mode)
     ids = []
     frames = []
     outs = []
@@ -255,7 +256,9 @@ def serve_leg(seed, seconds, rate, inflight, n_rigs=16, n_frames=3):
     return {
         "workload": f"{n_rigs} rigs (sizes {sorted(set(sizes))}: "
                     f"{[sizes.count(v) for v in sorted(set(sizes))]}), Kannala-Brandt 190 deg, "
-                    f"warm start 3x50 on the finest level, FP32",
+                    f"warm start 3x50 on the finest level "
+                    f"({'from the last u and w' if warm_mode == 1 else 'from the last disparity'}), "
+                    f"FP32",
         "offered_per_s": rate, "seconds": seconds, "max_inflight": inflight,
         "requests": int(open_loop["completed"]), "failed": int(open_loop["failed"]),
         "frames_per_s": open_loop["frames_per_s"], "p50_ms": open_loop["p50_ms"],
@@ -335,6 +338,7 @@ def main():
                     help="length of the open-loop serving run (0 skips serving)")
     ap.add_argument("--serve-rate", type=float, default=600.0, help="offered requests/s")
     ap.add_argument("--serve-inflight", type=int, default=8)
+    ap.add_argument("--serve-warm-mode", type=int, default=1, choices=[0, 1])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -494,7 +498,7 @@ def main():
     serving = None
     if args.serve_seconds > 0:
         serving = serve_leg(replica_seed(args.seed, rank), args.serve_seconds, args.serve_rate,
-                            args.serve_inflight)
+                            args.serve_inflight, args.serve_warm_mode)
         if dist:
             fps_sum = torch.tensor([serving["frames_per_s"]], dtype=torch.float64, device="cuda")
             dist.all_reduce(fps_sum)

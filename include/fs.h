@@ -147,6 +147,18 @@ fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1,
                    const float* d_init, int warps, int iters,
                    float* d_disp, float* d_depth);
 
+/* Warm start of the next frame of a video stream from the handle's own last
+ * result, with no disparity round trip: the finest level's u and its 2-D
+ * correspondence field w, as the last fs_solve / fs_solve_continue of this
+ * handle left them, initialise the finest level (u_w = ubar = u, p = 0) and
+ * `warps` x `iters` run there, as for a d_init warm start, but w is taken
+ * as it was instead of being rebuilt from the disparity along gamma'.
+ * FS_EINVAL if the handle holds no result (no solve yet, or fs_autotune /
+ * fs_run_stage has run since).  fs_buffer_write of level 0's U and W (in
+ * fs_stages.h) replaces the state it continues from. */
+fs_status fs_solve_continue(fs_handle* h, const float* d_I0, const float* d_I1, int warps,
+                            int iters, float* d_disp, float* d_depth);
+
 /* fs_solve from HOST buffers: copies the inputs to the device, solves,
  * copies the outputs back and synchronises the handle's stream before
  * returning.  Host buffers may be pageable or pinned (pinned is faster). */

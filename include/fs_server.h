@@ -60,7 +60,13 @@ typedef struct {
   int warps, iters;      /* warm-started request: warps x iterations on the
                             finest level */
   int cold_warps, cold_iters;   /* cold request: per pyramid level */
-  int reserved[4];       /* zero */
+  int warm_mode;         /* how a warm request starts from the rig's last
+                            result: 1 = its finest-level u and w as they are
+                            (fs_solve_continue); 0 = its disparity, w rebuilt
+                            along gamma' (fs_solve with d_init) */
+  int autotune;          /* 1: fs_autotune each rig's schedule (for `iters`)
+                            when its state is made resident */
+  int reserved[2];       /* zero */
 } fs_server_config;
 
 typedef struct {
@@ -75,11 +81,13 @@ typedef struct {
   size_t peak_resident_bytes;
 } fs_server_stats;
 
-/* Defaults: 40 GiB budget, 8 in flight, 3 x 50 warm, 10 x 100 cold. */
+/* Defaults: 40 GiB budget, 8 in flight, 3 x 50 warm, 10 x 100 cold,
+ * warm_mode 1, autotune 1. */
 fs_status fs_server_default_config(fs_server_config* out);
 
 /* Create a server on the calling thread's current CUDA device.  cfg NULL =
- * defaults.  FS_EINVAL for max_inflight < 1 or warps / iters < 1;
+ * defaults.  FS_EINVAL for max_inflight < 1, warps / iters < 1 or a
+ * warm_mode other than 0 / 1;
  * FS_ECUDA if no device is usable. */
 fs_status fs_server_create(const fs_server_config* cfg, fs_server** out);
 

@@ -82,7 +82,7 @@ def warm_start_w(d, gamma, M, du_max):
 
 
 def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params(),
-          on_iter=None, keep_levels=False, level_hook=None, d_init=None):
+          on_iter=None, keep_levels=False, level_hook=None, d_init=None, w_init=None):
     """Full method on one pair; returns disparity (px), range (m), w and more.
 
     level_hook(level, I0_l, I1_l) -> (I0_l, I1_l), when given, may replace
@@ -91,6 +91,8 @@ def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params()
 
     d_init, when given, warm-starts from that full-resolution disparity:
     u = d_init, w rebuilt by warm_start_w, and only the finest level runs.
+    w_init (H, W, 2), given with d_init, is a video stream's continuation:
+    w is taken as given (the previous frame's w) instead of being rebuilt.
     """
     cam0 = calib_from_dict(cam0)
     cam1 = calib_from_dict(cam1)
@@ -121,7 +123,10 @@ def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params()
         M = masks[0]
         gamma0 = trajectory_field(calibs[0], tp, W, H, M)
         u = np.where(M, np.asarray(d_init, dtype=np.float64), 0.0)
-        w = np.where(M[..., None], warm_start_w(u, gamma0, M, prm.du_max), 0.0)
+        if w_init is None:
+            w = np.where(M[..., None], warm_start_w(u, gamma0, M, prm.du_max), 0.0)
+        else:
+            w = np.where(M[..., None], np.asarray(w_init, dtype=np.float64), 0.0)
         first = 0
     for l in range(first, -1, -1):
         Wl, Hl = sizes[l]

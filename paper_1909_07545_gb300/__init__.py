@@ -31,7 +31,8 @@ STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ENOMEM", -3: "FS_ECUDA", -4: "FS_
 
 # every entry point declared in include/*.h
 EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
-            "fs_trajectory_field", "fs_solve", "fs_solve_host", "fs_destroy", "fs_last_error",
+            "fs_trajectory_field", "fs_solve", "fs_solve_continue", "fs_solve_host", "fs_destroy",
+            "fs_last_error",
             "fs_buffer_read", "fs_buffer_write", "fs_run_stage", "fs_stage_prerotate",
             "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc",
             "fs_batch_create", "fs_batch_solve", "fs_batch_set_finest_limit",
@@ -70,7 +71,8 @@ class FsServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
                 ("warps", ctypes.c_int), ("iters", ctypes.c_int),
                 ("cold_warps", ctypes.c_int), ("cold_iters", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("warm_mode", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class FsServerStats(ctypes.Structure):
@@ -104,6 +106,7 @@ def load_library():
         "fs_level_size": [_P, i, ctypes.POINTER(i), ctypes.POINTER(i)],
         "fs_trajectory_field": [_P, i, _P],
         "fs_solve": [_P, _P, _P, _P, i, i, _P, _P],
+        "fs_solve_continue": [_P, _P, _P, i, i, _P, _P],
         "fs_solve_host": [_P, _P, _P, _P, i, i, _P, _P],
         "fs_destroy": [_P],
         "fs_buffer_read": [_P, i, i, _P],
@@ -233,6 +236,20 @@ class Solver:
         _check(self.lib.fs_solve(self.h, _ptr(I0), _ptr(I1), _ptr(init), int(warps), int(iters),
                                  _ptr(disp), _ptr(depth)))
         self._keep = (I0, I1, init)
+        return disp, depth
+
+    def solve_continue(self, I0, I1, warps, iters, disp=None, depth=None):
+        """fs_solve_continue: warm start from this handle's own last u and w."""
+        torch = self.torch
+        I0 = self._dev(I0)
+        I1 = self._dev(I1)
+        if disp is None:
+            disp = torch.empty((self.H, self.W), device="cuda", dtype=torch.float32)
+        if depth is None:
+            depth = torch.empty((self.H, self.W), device="cuda", dtype=torch.float32)
+        _check(self.lib.fs_solve_continue(self.h, _ptr(I0), _ptr(I1), int(warps), int(iters),
+                                          _ptr(disp), _ptr(depth)))
+        self._keep = (I0, I1)
         return disp, depth
 
     def solve_host(self, I0, I1, warps, iters, init=None, disp=None, depth=None):
@@ -393,10 +410,11 @@ def state_bytes(W, H, levels, **params) -> int:
 class Server:
     """fs_server: continuous-batching request server over many rigs.
 
-    Each rig keeps its pyramid state and last disparity resident on the
+    Each rig keeps its pyramid state and last result resident on the
     device; a rig's first frame is solved cold (cold_warps x cold_iters per
-    level), later frames warm-start from its previous disparity on the
-    finest level (warps x iters).  Requests of different rigs overlap on the
+    level), later frames warm-start from its previous result on the finest
+    level (warps x iters): warm_mode 1 continues from the finest level's u
+    and w, warm_mode 0 restarts from the disparity (w rebuilt along gamma').  Requests of different rigs overlap on the
     GPU; admission is bounded by max_inflight and the device-memory budget.
     Inputs and outputs are host arrays (pinned torch tensors let the copies
     run asynchronously); they are kept referenced until the request is waited
@@ -404,7 +422,7 @@ class Server:
     """
 
     def __init__(self, budget_bytes=0, max_inflight=8, warps=3, iters=50, cold_warps=10,
-                 cold_iters=100):
+                 cold_iters=100, warm_mode=1, autotune=1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -417,6 +435,8 @@ class Server:
         cfg.max_inflight = int(max_inflight)
         cfg.warps, cfg.iters = int(warps), int(iters)
         cfg.cold_warps, cfg.cold_iters = int(cold_warps), int(cold_iters)
+        cfg.warm_mode = int(warm_mode)
+        cfg.autotune = int(autotune)
         s = _P()
         _check(self.lib.fs_server_create(ctypes.byref(cfg), ctypes.byref(s)))
         self.s = s

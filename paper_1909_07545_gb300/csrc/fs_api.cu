@@ -183,6 +183,8 @@ struct fs_handle {
   double t_ms[kMaxLevels] = {};
   long long t_launch[kMaxLevels] = {};
   double t_pxit[kMaxLevels] = {};
+  // the finest level's u and w hold the result of the last solve
+  bool has_state = false;
 };
 
 namespace {
@@ -383,19 +385,25 @@ cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
 // finest_wait / finest_done (may be null): a dependency taken before the
 // finest level's work starts and an event recorded once it has ended, which a
 // batch uses to bound how many pairs occupy their finest level at once.
+// cont: warm start from the finest level's own u and w (fs_solve_continue).
 fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const float* init,
                         int warps, int iters, float* disp, float* depth, cudaStream_t st,
-                        cudaEvent_t finest_wait = nullptr, cudaEvent_t finest_done = nullptr) {
+                        cudaEvent_t finest_wait = nullptr, cudaEvent_t finest_done = nullptr,
+                        bool cont = false) {
   fs_status s;
   HostLevel& L0 = h->lv[0];
   FS_LAUNCH("k_copy_in_s", launch_copy_in_I0(I0, L0.v, st));
   FS_LAUNCH("k_prerotate", launch_prerotate(I1, h->cfield, L0.v, st));
   int top = h->L - 1;
-  if (init) {   // warm start: the finest level only, from the given disparity
+  if (init || cont) {   // warm start: the finest level only
     if (finest_wait) FS_CUDA(cudaStreamWaitEvent(st, finest_wait, 0));
-    k_copy_in<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(init, L0.v.u, L0.W, L0.H, L0.P);
-    FS_LAUNCHED("k_copy_in");
-    if ((s = run_stage(h, 0, FS_STAGE_WARM, 0, st)) != FS_OK) return s;
+    if (cont) {          // from the level's own last u and w
+      FS_LAUNCH("k_continue", launch_continue(L0.v, st));
+    } else {             // from the given disparity, w rebuilt along gamma'
+      k_copy_in<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(init, L0.v.u, L0.W, L0.H, L0.P);
+      FS_LAUNCHED("k_copy_in");
+      if ((s = run_stage(h, 0, FS_STAGE_WARM, 0, st)) != FS_OK) return s;
+    }
     if ((s = run_stage(h, 0, FS_STAGE_TENSOR, 0, st)) != FS_OK) return s;
     for (int w = 0; w < warps; ++w) {
       if ((s = run_stage(h, 0, FS_STAGE_WARP, 0, st)) != FS_OK) return s;
@@ -659,23 +667,37 @@ fs_status fs_trajectory_field(fs_handle* h, int level, float* d_out) {
   return fs_buffer_read(h, level, FS_BUF_GAMMA, d_out);
 }
 
-fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1, const float* d_init,
-                   int warps, int iters, float* d_disp, float* d_depth) {
+}  // extern "C"
+
+// fs_solve and fs_solve_continue: direct launches, or a CUDA graph captured
+// once per set of buffers and replayed.
+static fs_status solve_impl(fs_handle* h, const float* d_I0, const float* d_I1,
+                            const float* d_init, bool cont, int warps, int iters, float* d_disp,
+                            float* d_depth) {
   fs_status s;
   if ((s = check_handle(h)) != FS_OK) return s;
   if (!d_I0 || !d_I1) return fail(FS_EINVAL, "null input image");
   if (warps < 1 || iters < 1) return fail(FS_EINVAL, "warps and iters must be >= 1");
+  if (cont && !h->has_state) return fail(FS_EINVAL, "fs_solve_continue: the handle holds no result");
   if (h->timing && (s = prepare_timing(h, warps)) != FS_OK) return s;
-  if (!h->prm.use_graph) return enqueue_solve(h, d_I0, d_I1, d_init, warps, iters, d_disp, d_depth, h->stream);
+  if (!h->prm.use_graph) {
+    h->has_state = false;
+    s = enqueue_solve(h, d_I0, d_I1, d_init, warps, iters, d_disp, d_depth, h->stream, nullptr,
+                      nullptr, cont);
+    h->has_state = s == FS_OK;
+    return s;
+  }
 
-  const void* key[7] = {d_I0, d_I1, d_init, d_disp, d_depth, nullptr, nullptr};
+  const void* key[7] = {d_I0, d_I1, d_init, d_disp, d_depth, cont ? (const void*)1 : nullptr,
+                        nullptr};
   bool hit = h->gexec && warps == h->gwarps && iters == h->giters &&
              memcmp(key, h->gkey, sizeof(key)) == 0;
   if (!hit) {
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     if (!h->cap_stream) FS_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     FS_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    s = enqueue_solve(h, d_I0, d_I1, d_init, warps, iters, d_disp, d_depth, h->cap_stream);
+    s = enqueue_solve(h, d_I0, d_I1, d_init, warps, iters, d_disp, d_depth, h->cap_stream,
+                      nullptr, nullptr, cont);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (s != FS_OK) { if (g) cudaGraphDestroy(g); return s; }
@@ -687,14 +709,28 @@ fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1, const flo
     h->gwarps = warps;
     h->giters = iters;
   }
+  h->has_state = false;
   FS_CUDA(cudaGraphLaunch(h->gexec, h->stream));
+  h->has_state = true;
   if (h->timing) {              // the replay re-records the captured events
     h->ev_warps = warps;
     h->ev_iters = iters;
-    h->ev_levels = d_init ? 1 : h->L;
+    h->ev_levels = (d_init || cont) ? 1 : h->L;
     h->ev_pending = true;
   }
   return FS_OK;
+}
+
+extern "C" {
+
+fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1, const float* d_init,
+                   int warps, int iters, float* d_disp, float* d_depth) {
+  return solve_impl(h, d_I0, d_I1, d_init, false, warps, iters, d_disp, d_depth);
+}
+
+fs_status fs_solve_continue(fs_handle* h, const float* d_I0, const float* d_I1, int warps,
+                            int iters, float* d_disp, float* d_depth) {
+  return solve_impl(h, d_I0, d_I1, nullptr, true, warps, iters, d_disp, d_depth);
 }
 
 fs_status fs_solve_host(fs_handle* h, const float* h_I0, const float* h_I1, const float* h_init,
@@ -855,6 +891,7 @@ extern "C" fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0,
   FS_CUDA(cudaGraphLaunch(b->gexec, b->stream));
   for (int i = 0; i < n; ++i) {
     fs_handle* h = b->h[i];
+    h->has_state = true;
     if (h->timing) {
       h->ev_warps = warps;
       h->ev_iters = iters;
@@ -979,6 +1016,7 @@ extern "C" fs_status fs_run_stage(fs_handle* h, int level, int stage, int count)
   fs_status s;
   if ((s = check_handle(h)) != FS_OK) return s;
   if (level < 0 || level >= h->L) return fail(FS_EINVAL, "level %d out of range", level);
+  h->has_state = false;
   return run_stage(h, level, stage, count, h->stream);
 }
 
@@ -1038,6 +1076,7 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
   if ((s = check_handle(h)) != FS_OK) return s;
   if (iters < 1) return fail(FS_EINVAL, "iters must be >= 1");
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  h->has_state = false;   // the trial runs overwrite every level's state
   cudaEvent_t e0, e1;
   FS_CUDA(cudaEventCreate(&e0));
   FS_CUDA(cudaEventCreate(&e1));

@@ -30,6 +30,7 @@ cudaError_t launch_downsample(const LevelView& F, const LevelView& C, cudaStream
 cudaError_t launch_upsample(const LevelView& C, const LevelView& F, cudaStream_t st);
 cudaError_t launch_zero_state(const LevelView& L, cudaStream_t st);
 cudaError_t launch_warm_start(const LevelView& L, float du_max, cudaStream_t st);
+cudaError_t launch_continue(const LevelView& L, cudaStream_t st);
 cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond,
                           cudaStream_t st);
 cudaError_t launch_warp(const LevelView& L, cudaStream_t st);

@@ -29,6 +29,7 @@
 
 #include "fs.h"
 #include "fs_server.h"
+#include "fs_stages.h"
 
 extern fs_status fs_internal_set_error(fs_status s, const char* msg);
 extern fs_status fs_internal_validate(const fs_calib cam[2], const fs_pose* pose, int W, int H,
@@ -175,6 +176,14 @@ fs_status make_resident(fs_server* s, Rig* rg, std::string* msg) {
     *msg = std::string("rig plane allocation failed: ") + cudaGetErrorString(e);
     return FS_ENOMEM;
   }
+  if (s->cfg.autotune && (st = fs_autotune(rg->h, s->cfg.iters, nullptr)) != FS_OK) {
+    *msg = fs_last_error();
+    fs_destroy(rg->h);
+    cudaFree(rg->planes);
+    rg->h = nullptr;
+    rg->planes = nullptr;
+    return st;
+  }
   return FS_OK;
 }
 
@@ -192,11 +201,16 @@ fs_status enqueue_request(fs_server* s, Rig* rg, Request* r, bool cold_start, st
     *msg = std::string("input copy failed: ") + cudaGetErrorString(e);
     return FS_ECUDA;
   }
-  // a warm start reads the previous disparity from dD and writes the new one
-  // over it (the library copies d_init in before anything writes d_disp)
-  fs_status st_solve =
-      cold_start ? fs_solve(rg->h, dI0, dI1, nullptr, s->cfg.cold_warps, s->cfg.cold_iters, dD, dZ)
-                 : fs_solve(rg->h, dI0, dI1, dD, s->cfg.warps, s->cfg.iters, dD, dZ);
+  // a warm start from the disparity reads the previous one from dD and
+  // writes the new one over it (the library copies d_init in before anything
+  // writes d_disp); a continued one reads the handle's own u and w
+  fs_status st_solve;
+  if (cold_start)
+    st_solve = fs_solve(rg->h, dI0, dI1, nullptr, s->cfg.cold_warps, s->cfg.cold_iters, dD, dZ);
+  else if (s->cfg.warm_mode == 1)
+    st_solve = fs_solve_continue(rg->h, dI0, dI1, s->cfg.warps, s->cfg.iters, dD, dZ);
+  else
+    st_solve = fs_solve(rg->h, dI0, dI1, dD, s->cfg.warps, s->cfg.iters, dD, dZ);
   if (st_solve != FS_OK) {
     *msg = fs_last_error();
     return st_solve;
@@ -322,6 +336,8 @@ fs_status fs_server_default_config(fs_server_config* out) {
   out->iters = 50;
   out->cold_warps = 10;
   out->cold_iters = 100;
+  out->warm_mode = 1;
+  out->autotune = 1;
   return FS_OK;
 }
 
@@ -338,6 +354,7 @@ fs_status fs_server_create(const fs_server_config* cfg, fs_server** out) {
   if (c.max_inflight < 1) return set_error(FS_EINVAL, "max_inflight must be >= 1");
   if (c.warps < 1 || c.iters < 1 || c.cold_warps < 1 || c.cold_iters < 1)
     return set_error(FS_EINVAL, "warps and iters must be >= 1");
+  if (c.warm_mode != 0 && c.warm_mode != 1) return set_error(FS_EINVAL, "warm_mode must be 0 or 1");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(FS_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));

@@ -162,6 +162,24 @@ __global__ void k_warm_start(LevelView L, float du_max) {
   sst<S>(L.p1, i, 0.f); sst<S>(L.p2, i, 0.f);
 }
 
+// Warm start at the finest level from its own last u and w (a video
+// stream's next frame): ubar = u_w = u, p = 0, w kept.  Non-finite
+// disparities count as 0 (with w = 0).
+template <int S>
+__global__ void k_continue(LevelView L) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t i = (size_t)y * L.P + x;
+  float d = L.u[i];
+  if (!(L.mask[i] & MASK_IN) || !isfinite(d)) {
+    d = 0.f;
+    L.w[i] = make_float2(0.f, 0.f);
+  }
+  L.u[i] = d; L.ubar[i] = d; L.uw[i] = d;
+  sst<S>(L.p1, i, 0.f); sst<S>(L.p2, i, 0.f);
+}
+
 // Zero state at the coarsest level (Algorithm 1: u_0 = 0, w_0 = 0).
 template <int S>
 __global__ void k_zero_state(LevelView L) {
@@ -421,6 +439,9 @@ cudaError_t launch_zero_state(const LevelView& L, cudaStream_t st) {
 }
 cudaError_t launch_warm_start(const LevelView& L, float du_max, cudaStream_t st) {
   FS_STORAGE_SWITCH(L.st, (k_warm_start<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, du_max)))
+}
+cudaError_t launch_continue(const LevelView& L, cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_continue<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L)))
 }
 cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond,
                           cudaStream_t st) {

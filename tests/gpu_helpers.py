@@ -70,14 +70,15 @@ def ragged_pair(seed=0, W=203, H=157):
 
 
 def oracle_solve(pair, levels=None, warps=None, iters=None, level_hook=None, on_iter=None,
-                 d_init=None, **prm):
+                 d_init=None, w_init=None, **prm):
     return oracle.solve(pair["I0"], pair["I1"], pair["cam0"], pair["cam1"], pair["R"],
                         pair["t"], levels or pair["levels"], warps or pair["warps"],
                         iters or pair["iters"], oracle_params(pair, **prm),
-                        level_hook=level_hook, on_iter=on_iter, d_init=d_init)
+                        level_hook=level_hook, on_iter=on_iter, d_init=d_init, w_init=w_init)
 
 
-def oracle_sensitivity(pair, ref, levels=None, warps=None, iters=None, d_init=None, **prm):
+def oracle_sensitivity(pair, ref, levels=None, warps=None, iters=None, d_init=None, w_init=None,
+                       **prm):
     """How far the FP64 oracle's own disparity moves under perturbations of
     the size FP32 arithmetic makes: (1) its pyramid images (and pre-rotated
     I1) rounded to float32, (2) its primal-dual state (u, ubar, p) rounded to
@@ -87,19 +88,19 @@ def oracle_sensitivity(pair, ref, levels=None, warps=None, iters=None, d_init=No
     f32 = lambda a: np.float32(a).astype(np.float64)
     a = oracle_solve(pair, levels, warps, iters,
                      level_hook=lambda l, i0, i1: (f32(i0), f32(i1)), d_init=d_init,
-                     **prm)["disp"]
+                     w_init=w_init, **prm)["disp"]
 
     def round_state(level, om, k, st, lv):
         for key in ("u", "ubar", "p1", "p2"):
             st[key] = f32(st[key])
     c = oracle_solve(pair, levels, warps, iters, on_iter=round_state, d_init=d_init,
-                     **prm)["disp"]
+                     w_init=w_init, **prm)["disp"]
     rng = np.random.default_rng(12345)
     noisy = dict(pair)
     rel = 2.0 ** -22
     noisy["I0"] = pair["I0"] * (1 + rel * rng.normal(size=pair["I0"].shape))
     noisy["I1"] = pair["I1"] * (1 + rel * rng.normal(size=pair["I1"].shape))
-    b = oracle_solve(noisy, levels, warps, iters, d_init=d_init, **prm)["disp"]
+    b = oracle_solve(noisy, levels, warps, iters, d_init=d_init, w_init=w_init, **prm)["disp"]
     return np.maximum(np.maximum(np.abs(a - ref["disp"]), np.abs(b - ref["disp"])),
                       np.abs(c - ref["disp"]))
 

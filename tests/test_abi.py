@@ -113,11 +113,15 @@ def test_server_config_validation(lib):
     assert lib.fs_server_default_config(ctypes.byref(cfg)) == 0
     assert cfg.hbm_budget == 40 << 30 and cfg.max_inflight == 8
     assert (cfg.warps, cfg.iters, cfg.cold_warps, cfg.cold_iters) == (3, 50, 10, 100)
+    assert cfg.warm_mode == 1 and cfg.autotune == 1
     s = ctypes.c_void_p()
     bad = fsb.FsServerConfig(cfg.hbm_budget, 0, 3, 50, 10, 100)
     assert lib.fs_server_create(ctypes.byref(bad), ctypes.byref(s)) == -1
     bad = fsb.FsServerConfig(cfg.hbm_budget, 2, 0, 50, 10, 100)
     assert lib.fs_server_create(ctypes.byref(bad), ctypes.byref(s)) == -1
+    bad = fsb.FsServerConfig(cfg.hbm_budget, 2, 3, 50, 10, 100, 2)
+    assert lib.fs_server_create(ctypes.byref(bad), ctypes.byref(s)) == -1
+    assert "warm_mode" in lib.fs_last_error().decode()
     assert lib.fs_server_create(ctypes.byref(cfg), None) == -1
     assert lib.fs_server_drain(None, 0.0) == -1
     assert lib.fs_server_stats_read(None, None, 0) == -1

@@ -64,9 +64,10 @@ def _pinned(a):
     return torch.from_numpy(a).pin_memory()
 
 
-def _lone_chain(q, cold_every=False, **prm):
+def _lone_chain(q, cold_every=False, warm_mode=1, **prm):
     """The same frames through one fs_handle: cold first frame, then warm
-    starts from the previous disparity (or every frame cold)."""
+    starts from the previous result (fs_solve_continue for warm_mode 1, the
+    previous disparity as d_init for 0), or every frame cold."""
     import paper_1909_07545_gb300 as fsb
     H, W = q["frames"][0][0].shape
     s = fsb.Solver(q["cam0"], q["cam1"], q["R"], q["t"], W, H, q["levels"], lam=q["lam"],
@@ -75,6 +76,8 @@ def _lone_chain(q, cold_every=False, **prm):
     for I0, I1, _ in q["frames"]:
         if prev is None or cold_every:
             d, z = s.solve(I0, I1, *COLD)
+        elif warm_mode == 1:
+            d, z = s.solve_continue(I0, I1, *WARM)
         else:
             d, z = s.solve(I0, I1, *WARM, init=prev)
         prev = d.clone()
@@ -83,8 +86,9 @@ def _lone_chain(q, cold_every=False, **prm):
     return res
 
 
-def test_served_in_a_mix_equals_served_alone_and_lone_handle(rigs):
-    srv = _server(max_inflight=3)
+@pytest.mark.parametrize("warm_mode", [1, 0])
+def test_served_in_a_mix_equals_served_alone_and_lone_handle(rigs, warm_mode):
+    srv = _server(max_inflight=3, warm_mode=warm_mode)
     ids = [_add(srv, q) for q in rigs]
     outs = {}
     reqs = []
@@ -101,9 +105,9 @@ def test_served_in_a_mix_equals_served_alone_and_lone_handle(rigs):
     srv.close()
 
     for r, q in zip(ids, rigs):
-        alone = _server(max_inflight=1)
+        alone = _server(max_inflight=1, warm_mode=warm_mode)
         a = _add(alone, q)
-        chain = _lone_chain(q)
+        chain = _lone_chain(q, warm_mode=warm_mode)
         for k in range(3):
             d, z = _outs(q)
             I0, I1, _ = q["frames"][k]

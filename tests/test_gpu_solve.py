@@ -23,10 +23,11 @@ def _built():
     build.build()
 
 
-def _oracle(pair, levels=None, warps=None, iters=None, d_init=None, **prm):
+def _oracle(pair, levels=None, warps=None, iters=None, d_init=None, w_init=None, **prm):
     return oracle.solve(pair["I0"], pair["I1"], pair["cam0"], pair["cam1"], pair["R"],
                         pair["t"], levels or pair["levels"], warps or pair["warps"],
-                        iters or pair["iters"], oracle_params(pair, **prm), d_init=d_init)
+                        iters or pair["iters"], oracle_params(pair, **prm), d_init=d_init,
+                        w_init=w_init)
 
 
 def _compare(pair, ref, disp, depth, sens):
@@ -135,6 +136,30 @@ def test_warm_start_matches_oracle(small):
     _compare(small, ref, disp, depth, sens)
     # the rebuilt warp vector itself, before any iteration
     s.solve(small["I0"], small["I1"], 1, 1, init=d0)
+    s.close()
+
+
+def test_continue_matches_oracle(small):
+    # continuation of a video stream: the finest level's u and w (here the
+    # oracle's cold result, rounded to float32, written into the handle) are
+    # taken as they are; finest level only
+    import paper_1909_07545_gb300 as fsb
+    s = make_solver(small)
+    with pytest.raises(fsb.FsError):          # nothing to continue from yet
+        s.solve_continue(small["I0"], small["I1"], 1, 1)
+    cold = _oracle(small, warps=2, iters=20)
+    d0 = np.float32(cold["disp"]).astype(np.float64)
+    w0 = np.float32(cold["w"]).astype(np.float64)
+    ref = _oracle(small, warps=3, iters=30, d_init=d0, w_init=w0)
+    sens = oracle_sensitivity(small, ref, warps=3, iters=30, d_init=d0, w_init=w0)
+    s.solve(small["I0"], small["I1"], 1, 2)   # any result, then replaced
+    s.write(0, "U", d0)
+    s.write(0, "W", np.moveaxis(w0, -1, 0))
+    disp, depth = s.solve_continue(small["I0"], small["I1"], 3, 30)
+    _compare(small, ref, disp, depth, sens)
+    s.autotune(iters=4)                       # overwrites the state
+    with pytest.raises(fsb.FsError):
+        s.solve_continue(small["I0"], small["I1"], 1, 1)
     s.close()
 
 

@@ -86,3 +86,21 @@ def test_warm_start_walks_the_trajectory_field():
     sel = nd.binary_erosion(Mc, iterations=12)
     assert np.abs(coarse - fine)[sel].max() < 0.05
     assert np.abs(np.linalg.norm(fine, axis=-1)[sel] - 4.0).max() < 0.05
+
+
+def test_continuation_with_the_rebuilt_field_is_the_disparity_warm_start():
+    # w_init = the field warm_start_w would rebuild from d_init gives the
+    # d_init-only warm start exactly; a different w_init changes the result
+    p = synth.plain_small(4, W=64, H=64)
+    prm = oracle.Params(lam=p["lam"], eps=p["eps"])
+    args = (p["I0"], p["I1"], p["cam0"], p["cam1"], p["R"], p["t"], 2)
+    r0 = oracle.solve(*args, 2, 10, prm)
+    cam = oracle.calib_from_dict(p["cam0"])
+    M = oracle.fov_mask(cam, 64, 64)
+    g = oracle.trajectory_field(cam, oracle.virtual_translation(p["R"], p["t"]), 64, 64, M)
+    w0 = oracle.warm_start_w(np.where(M, r0["disp"], 0.0), g, M, prm.du_max)
+    a = oracle.solve(*args, 1, 8, prm, d_init=r0["disp"])
+    b = oracle.solve(*args, 1, 8, prm, d_init=r0["disp"], w_init=w0)
+    assert np.array_equal(a["disp"], b["disp"]) and np.array_equal(a["w"], b["w"])
+    c = oracle.solve(*args, 1, 8, prm, d_init=r0["disp"], w_init=r0["w"] + 0.5)
+    assert np.abs(c["disp"] - a["disp"])[M].max() > 1e-3
