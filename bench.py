@@ -29,6 +29,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "frames/s & p99 latency, 1024² fisheye pair; primal-dual Gpix-iter/s vs plain"
 PD_BYTES_PER_PX_ITER = 52.0   # unblocked FP32 traffic of one pixel-iteration (9 reads + 4 writes)
+# DRAM bytes (read + write) of one level-0 k_pd launch of this workload at 7
+# iterations per launch, from one ncu capture of the current kernel (cold L2;
+# the command and figures are in profiles/k_pd_level0_kb1024.md)
+PD_L0_DRAM_BYTES_PER_LAUNCH = 47.6e6
+PD_L0_PROFILED_DEPTH = 7
 
 
 def workload_pair(name, seed):
@@ -516,6 +521,9 @@ def main():
     fps = job_rate(world, args.steps, total_ms)
     ms0, n0, px0 = per_level[0]
     achieved = PD_BYTES_PER_PX_ITER * px0 / (ms0 / 1000.0) / 1e9
+    # the profiled traffic applies while level 0 runs at the profiled depth
+    l0_depth = tuned[0] if tuned else None
+    traffic = PD_L0_DRAM_BYTES_PER_LAUNCH if l0_depth == PD_L0_PROFILED_DEPTH else None
     peaks, src = measured_peaks()
     peak = float(peaks["hbm_gbs"])
     pd_ms = sum(m for m, _, _ in per_level) / args.steps
@@ -542,8 +550,11 @@ def main():
         "pd": {"ms_per_frame": pd_ms, "share_of_step": pd_ms / ms_per_step,
                "per_level_ms": [m / args.steps for m, _, _ in per_level]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_pd level 0 (1024x1024)",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_note": "DRAM bytes per level-0 launch, ncu, cold L2",
+                     "kernel": f"k_pd level 0 (1024x1024), blocking depth {l0_depth}",
+                     "launches_per_frame": n0 // max(args.steps, 1),
+                     "algorithmic_bytes_per_launch": PD_BYTES_PER_PX_ITER * px0 / max(n0, 1),
                      "peak_source": f"{src} hbm_gbs",
                      "algorithmic_bytes_per_px_iter": PD_BYTES_PER_PX_ITER},
         "gpu_launches": int(args.steps * (pd_launches + per_frame_other)),

@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--iters", type=int, default=100)
     ap.add_argument("--block-iters", type=int, default=0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="fs_autotune the per-level schedule first (as bench.py does)")
     args = ap.parse_args()
     sys.path.insert(0, os.getcwd())
     import torch
@@ -40,6 +42,9 @@ def main():
     H, W = pair["I0"].shape
     s = Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, pair["levels"],
                lam=pair["lam"], huber_eps=pair["eps"], block_iters=args.block_iters)
+    if args.autotune:
+        print("autotuned schedule per level (0 = cluster, else blocking depth):",
+              s.autotune(pair["iters"]))
     I0 = torch.as_tensor(np.float32(pair["I0"]), device="cuda")
     I1 = torch.as_tensor(np.float32(pair["I1"]), device="cuda")
     if args.mode == "frame":
