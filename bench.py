@@ -278,6 +278,65 @@ def serve_leg(seed, seconds, rate, inflight, warm_mode=1, n_rigs=16, n_frames=3)
     }
 
 
+def uneven_batch_leg(seed, stream, steps, warmup, storage="f16", per_size=16,
+                     sizes=(512, 800, 1024, 1280)):
+    """Batching: per_size pairs of each size, every pair its own seeded
+    Kannala-Brandt calibration, relative pose and scene (the 1024 generator
+    scaled), 4-6 pyramid levels (level count: coarsest level >= 40 px),
+    10 warps x 100 iterations, 16-bit storage, each handle autotuned, all
+    pairs in one fs_batch graph.  Returns frames/s per finest-level bound."""
+    import torch
+
+    import synth
+    from paper_1909_07545_gb300 import Batch, Solver
+    t0 = time.perf_counter()
+    pairs = []
+    for j, W in enumerate(sizes):
+        for i in range(per_size):
+            pairs.append(synth.plain_kb(100000 * (seed + 1) + 1000 * j + i, W=W, H=W,
+                                        supersample=1, levels=synth.auto_levels(W)))
+    render_s = time.perf_counter() - t0
+    sols, I0s, I1s = [], [], []
+    for p in pairs:
+        W = p["I0"].shape[1]
+        x = Solver(p["cam0"], p["cam1"], p["R"], p["t"], W, W, p["levels"], stream=stream,
+                   lam=p["lam"], huber_eps=p["eps"], use_graph=1, storage=storage)
+        x.autotune(p["iters"])
+        sols.append(x)
+        I0s.append(torch.as_tensor(np.float32(p["I0"]), device="cuda"))
+        I1s.append(torch.as_tensor(np.float32(p["I1"]), device="cuda"))
+    bt = Batch(sols, stream=stream)
+    outs_d = [torch.empty_like(a) for a in I0s]
+    outs_z = [torch.empty_like(a) for a in I0s]
+    res = {}
+    for k in (0, 1, 2, 4):
+        bt.set_finest_limit(k)
+        run = lambda: bt.solve(I0s, I1s, 10, 100, disps=outs_d, depths=outs_z)
+        for _ in range(warmup):
+            run()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            run()
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[f"finest{k}"] = {"frames_per_s": len(pairs) * 1000.0 / ms, "ms_per_batch": ms}
+    bt.close()
+    for x in sols:
+        x.close()
+    px_iter = sum(sum(level_pixels(p["I0"].shape[1], p["I0"].shape[0], p["levels"])) * 1000
+                  for p in pairs)
+    best = max(r["frames_per_s"] for r in res.values())
+    return {"workload": f"{len(pairs)} pairs, {per_size} each of {list(sizes)} px, "
+                        f"Kannala-Brandt 190 deg, own calibration and pose each, "
+                        f"4-6 levels x 10 warps x 100 iterations, {storage} storage, one graph",
+            "by_finest_limit": res, "best_frames_per_s": best,
+            "gpix_iter_s_best": px_iter * best / len(pairs) / 1e9, "render_s": render_s}
+
+
 def run_reference(args, pair, rank):
     """--impl reference: the FP64 oracle on the host cores, per step a bounded
     sample of the frame (primal-dual iterations of the finest level)."""
@@ -344,6 +403,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=600.0, help="offered requests/s")
     ap.add_argument("--serve-inflight", type=int, default=8)
     ap.add_argument("--serve-warm-mode", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--uneven-batch", action="store_true",
+                    help="also time 64 pairs of 512/800/1024/1280 px in one batch graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -429,7 +490,7 @@ def main():
         hD = torch.empty((H, W), dtype=torch.float32).pin_memory()
         hZ = torch.empty((H, W), dtype=torch.float32).pin_memory()
         s.solve_host(hI0, hI1, warps, iters, disp=hD, depth=hZ)
-        e2e_steps = max(3, min(args.steps, 10))
+        e2e_steps = max(10, min(args.steps, 20))
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             s.solve_host(hI0, hI1, warps, iters, disp=hD, depth=hZ)
@@ -500,6 +561,10 @@ def main():
                 for x in sols:
                     x.close()
 
+    uneven = None
+    if args.uneven_batch:
+        uneven = uneven_batch_leg(replica_seed(args.seed, rank), stream, 3, 3)
+
     serving = None
     if args.serve_seconds > 0:
         serving = serve_leg(replica_seed(args.seed, rank), args.serve_seconds, args.serve_rate,
@@ -564,6 +629,8 @@ def main():
     line["variants"] = variants
     if serving is not None:
         line["serving"] = serving
+    if uneven is not None:
+        line["uneven_batch"] = uneven
     line["e2e"] = {"value": world / e2e_s, "unit": "frames/s",
                    "h2d_bytes_per_step": 2 * W * H * 4, "d2h_bytes_per_step": 2 * W * H * 4}
     if not args.no_cpu_baseline:

@@ -63,12 +63,17 @@ def kb_is_monotone(k, half_angle, samples=10000):
 
 # ---------------------------------------------------------------- scene ---
 
-def _texture_params(rng, fmax):
+def _texture_params(rng, fmax, octaves=6):
+    """16 plane waves with frequencies log-uniform over `octaves` octaves
+    below fmax (cycles per metre) and amplitudes falling as f^-1/2, so that
+    every pyramid level sees texture (natural images have amplitude spectra
+    falling with frequency; a texture with only fine detail is pure aliasing
+    on the coarse levels)."""
     n = 16
     dirs = rng.normal(size=(n, 3))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
-    freq = rng.uniform(0.15, 1.0, size=n) * fmax          # cycles per metre
-    amp = rng.uniform(0.5, 1.0, size=n) / np.sqrt(np.arange(1, n + 1))
+    freq = fmax * 2.0 ** (-octaves * rng.uniform(0.0, 1.0, size=n))   # cycles per metre
+    amp = rng.uniform(0.5, 1.0, size=n) * np.sqrt(fmax / freq)
     phase = rng.uniform(0.0, 2.0 * np.pi, size=n)
     base = rng.uniform(0.35, 0.65)
     return dict(k=dirs * freq[:, None], amp=amp, phase=phase, base=base)

@@ -152,3 +152,57 @@ def rig_sequence(seed=0, W=640, H=640, n_frames=3, rate_hz=37.5, supersample=1, 
     return dict(cam0=cam, cam1=dict(cam), R=R, t=-R @ C1, frames=frames,
                 levels=levels or auto_levels(W), lam=50.0, eps=0.01,
                 name=f"rig_kb_{W}")
+
+
+def _project(cam, X):
+    """Pixel position of camera-frame points X (..., 3) through the lens."""
+    from .render import lens_radius
+    x, y, z = X[..., 0], X[..., 1], X[..., 2]
+    th = np.arctan2(np.hypot(x, y), z)
+    phi = np.arctan2(y, x)
+    r = lens_radius(cam, th)
+    return np.stack([cam["fx"] * r * np.cos(phi) + cam["cx"],
+                     cam["fy"] * r * np.sin(phi) + cam["cy"]], -1)
+
+
+def gt_disparity(pair, steps=64):
+    """Ground-truth disparity of a rendered pair: the arc length, in pixels,
+    of the path a camera-0 pixel's true 3-D point X traces in the image of a
+    camera with camera 0's orientation and lens as that camera's centre moves
+    from camera 0's to camera 1's (the point X - s C1, s from 0 to 1; C1 the
+    camera-1 centre in camera-0 coordinates).  This is the distance along the
+    epipolar curve to the true correspondence after the orientation of camera
+    1 is undone.  Polyline of `steps` segments.  Returns (d_gt, valid): valid
+    where the pixel sees a finite point inside the lens FOV that stays in
+    front of the moving camera and inside its FOV."""
+    from .render import lens_rays
+    cam = pair["cam0"]
+    H, W = pair["I0"].shape
+    py, px = np.mgrid[0:H, 0:W].astype(np.float64)
+    rays, valid = lens_rays(cam, px, py)
+    rng = pair["gt_range"]
+    valid = valid & np.isfinite(rng)
+    X = rays * np.where(valid, rng, 1.0)[..., None]
+    R = np.asarray(pair["R"], dtype=np.float64)
+    C1 = -R.T @ np.asarray(pair["t"], dtype=np.float64)
+    half = math.radians(cam["fov_deg"]) / 2.0
+    prev = _project(cam, X)
+    arc = np.zeros((H, W))
+    for k in range(1, steps + 1):
+        P = X - (k / steps) * C1
+        th = np.arctan2(np.hypot(P[..., 0], P[..., 1]), P[..., 2])
+        valid &= th <= half
+        cur = _project(cam, P)
+        arc += np.linalg.norm(cur - prev, axis=-1)
+        prev = cur
+    return np.where(valid, arc, np.nan), valid
+
+
+def disparity_errors(d, d_gt, valid):
+    """End-point error statistics against ground truth over `valid`: mean,
+    median, and the fractions of erroneous pixels above 1, 3 and 5 px (the
+    error measure of the paper's Sec. V, tau > 1 and tau > 5 px)."""
+    e = np.abs(np.asarray(d, dtype=np.float64) - d_gt)[valid]
+    return dict(epe_mean=float(e.mean()), epe_median=float(np.median(e)),
+                tau1=float((e > 1.0).mean()), tau3=float((e > 3.0).mean()),
+                tau5=float((e > 5.0).mean()), n=int(valid.sum()))
