@@ -497,6 +497,16 @@ def main():
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         e2e_s, = reduce_max([e2e_s], dist, "cuda")
         pd_launches = sum(n for _, n, _ in per_level) // max(args.steps, 1)
+
+        # a per-frame pose change: fs_set_pose recomputes the calibration field
+        # (FP64 on host threads from the cached rays) and the trajectory fields
+        s.set_pose(pair["R"], pair["t"])
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            s.set_pose(pair["R"], pair["t"])
+        stream.synchronize()
+        set_pose_ms = (time.perf_counter() - t0) / 5 * 1000.0
         s.close()
 
         # variants of the same frame: 16-bit storage, and batches of
@@ -627,6 +637,7 @@ def main():
         "wall_s": t_wall,
     }
     line["variants"] = variants
+    line["set_pose_ms"] = set_pose_ms
     if serving is not None:
         line["serving"] = serving
     if uneven is not None:

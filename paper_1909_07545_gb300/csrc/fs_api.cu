@@ -164,6 +164,8 @@ struct fs_handle {
   cudaStream_t cap_stream = nullptr;
   HostLevel lv[kMaxLevels];
   std::vector<uint8_t> mask0;            // host copy of the level-0 mask bits
+  std::vector<double> rays0;             // pi_0^-1(x) of every level-0 pixel (3 per pixel;
+                                         // pose-independent, kept for fs_set_pose)
   float2* cfield = nullptr;
   double tp[3] = {0, 0, 0};
   void* arena = nullptr;
@@ -221,16 +223,22 @@ fs_status build_fields(fs_handle* h) {
   if (!(n > 0) || !std::isfinite(n))
     return fail(FS_EINVAL, "pose: translation must be non-zero and finite");
   // calibration field c(x) = pi_1(R X) - pi_0(X), X = pi_0^-1(x), t = 0
-  // (Sec. IV-A), in FP64 on host threads; FP32 only for storage
+  // (Sec. IV-A), in FP64 on host threads; FP32 only for storage.  The rays
+  // X depend only on camera 0, so a pose change (fs_set_pose) rotates and
+  // projects the cached rays instead of inverting the lens again.
   HostLevel& L0 = h->lv[0];
-  std::vector<float2> field((size_t)L0.P * L0.H, make_float2(0.f, 0.f));
+  const size_t np = (size_t)L0.P * L0.H;
+  const bool have_rays = h->rays0.size() == 3 * np;
+  if (!have_rays) h->rays0.assign(3 * np, 0.0);
+  std::vector<float2> field(np, make_float2(0.f, 0.f));
   auto rows = [&](int y0, int y1) {
     for (int y = y0; y < y1; ++y)
       for (int x = 0; x < L0.W; ++x) {
         size_t i = (size_t)y * L0.P + x;
         if (!(h->mask0[i] & MASK_IN)) continue;
-        double X[3], X1[3], p0[2], p1[2];
-        unproject_d(h->cam[0], x, y, X);
+        double* X = &h->rays0[3 * i];
+        if (!have_rays) unproject_d(h->cam[0], x, y, X);
+        double X1[3], p0[2], p1[2];
         project_d(h->cam[0], X, p0);
         for (int r = 0; r < 3; ++r) X1[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2];
         project_d(h->cam[1], X1, p1);
@@ -238,7 +246,7 @@ fs_status build_fields(fs_handle* h) {
       }
   };
   unsigned nt = std::thread::hardware_concurrency();
-  nt = nt == 0 ? 1 : (nt > 16 ? 16 : nt);
+  nt = nt == 0 ? 1 : (nt > 32 ? 32 : nt);
   std::vector<std::thread> pool;
   int chunk = (L0.H + (int)nt - 1) / (int)nt;
   for (unsigned k = 0; k < nt; ++k) {

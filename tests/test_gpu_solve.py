@@ -203,3 +203,25 @@ def test_autotuned_schedule_gives_identical_results(small):
     assert np.array_equal(np64(d0), np64(d1))
     s0.close()
     s1.close()
+
+
+def test_set_pose_equals_a_handle_created_with_that_pose():
+    # a per-frame pose change recomputes the calibration field (Sec. IV-A) and
+    # the trajectory fields (Sec. III-B) in place; the result is the same as
+    # a handle created with the new pose, also through a captured graph
+    p = ragged_pair(3)
+    R, t = p["R"], p["t"]
+    s1 = make_solver(p, use_graph=1)
+    s1.set_pose(np.eye(3), np.array([-0.08, 0.0, 0.01]))
+    s1.solve(p["I0"], p["I1"], 2, 10)              # captures a graph with that pose
+    s1.set_pose(R, t)
+    s2 = make_solver(p, use_graph=1)
+    for l in range(p["levels"]):
+        assert np.array_equal(np64(s1.trajectory_field(l)), np64(s2.trajectory_field(l)))
+    d1, z1 = s1.solve(p["I0"], p["I1"], 2, 10)
+    d2, z2 = s2.solve(p["I0"], p["I1"], 2, 10)
+    assert np.array_equal(np64(s1.read(0, "I1")), np64(s2.read(0, "I1")))
+    assert np.array_equal(np64(d1), np64(d2))
+    assert np.array_equal(np64(z1), np64(z2), equal_nan=True)
+    s1.close()
+    s2.close()
