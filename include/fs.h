@@ -46,18 +46,27 @@ typedef enum {
 
 /* Radially symmetric camera models, pixel = c + f * r(theta) * (X, Y)/|(X, Y)|
  * with theta the angle off the optical axis (Sec. III-B allows any model
- * with a defined projection; Kannala-Brandt is one the paper cites). */
+ * with a defined projection and cites the unified, enhanced unified and
+ * Kannala-Brandt models; Sec. III-D notes the closed-form unprojections of
+ * the first two).  With s = sin(theta), c = cos(theta):
+ *   unified (xi = k[0]):              r = s / (c + xi)
+ *   enhanced unified (alpha = k[0], beta = k[1]):
+ *                                     r = s / (alpha sqrt(beta s^2 + c^2) + (1 - alpha) c)
+ * i.e. the usual forms m = (X, Y) / (Z + xi |X|) and
+ * m = (X, Y) / (alpha sqrt(beta (X^2 + Y^2) + Z^2) + (1 - alpha) Z). */
 typedef enum {
   FS_PINHOLE = 0,          /* r = tan(theta)                                  */
   FS_EQUIDISTANT = 1,      /* r = theta                                       */
-  FS_KANNALA_BRANDT = 2    /* r = theta + k1 t^3 + k2 t^5 + k3 t^7 + k4 t^9   */
+  FS_KANNALA_BRANDT = 2,   /* r = theta + k1 t^3 + k2 t^5 + k3 t^7 + k4 t^9   */
+  FS_UNIFIED = 3,          /* r = s / (c + xi),  xi = k[0] >= 0              */
+  FS_ENHANCED_UNIFIED = 4  /* alpha = k[0] in [0, 1), beta = k[1] > 0         */
 } fs_model;
 
 typedef struct {
   int model;               /* fs_model                                        */
   double fx, fy;           /* focal lengths, pixels                           */
   double cx, cy;           /* principal point, pixels                         */
-  double k[4];             /* Kannala-Brandt k1..k4 (ignored otherwise)       */
+  double k[4];             /* model parameters (see fs_model; unused = 0)     */
   double fov_deg;          /* full field of view; the mask keeps theta <= fov/2 */
 } fs_calib;
 

@@ -3,13 +3,17 @@
 Test infrastructure only (see ``oracle/__init__``).
 
 The method only needs *some* projection function pi (Sec. III-B: any model
-works as long as pi is defined; Kannala-Brandt is cited there) and its inverse
-for triangulation (Sec. III-D, last paragraph: Kannala-Brandt needs a
-non-linear solve).  Three radially symmetric models are written out:
+works as long as pi is defined; the unified, enhanced unified and
+Kannala-Brandt models are cited there) and its inverse for triangulation
+(Sec. III-D, last paragraph).  Five radially symmetric models are written
+out, with s = sin(theta), c = cos(theta):
 
-  pinhole         r(theta) = tan(theta)
-  equidistant     r(theta) = theta
-  Kannala-Brandt  r(theta) = theta + k1 theta^3 + k2 theta^5 + k3 theta^7 + k4 theta^9
+  pinhole           r(theta) = tan(theta)
+  equidistant       r(theta) = theta
+  Kannala-Brandt    r(theta) = theta + k1 theta^3 + k2 theta^5 + k3 theta^7 + k4 theta^9
+  unified           r(theta) = s / (c + xi)                      (xi = k[0])
+  enhanced unified  r(theta) = s / (alpha sqrt(beta s^2 + c^2) + (1 - alpha) c)
+                                                     (alpha = k[0], beta = k[1])
 
 with pixel = (fx * r * X/rho + cx, fy * r * Y/rho + cy), rho = |(X, Y)|,
 theta = atan2(rho, Z).  Pixel centres sit on integer coordinates.
@@ -24,9 +28,11 @@ from dataclasses import dataclass
 
 import numpy as np
 
-PINHOLE, EQUIDISTANT, KANNALA_BRANDT = 0, 1, 2
+PINHOLE, EQUIDISTANT, KANNALA_BRANDT, UNIFIED, ENHANCED_UNIFIED = 0, 1, 2, 3, 4
 _MODEL_NAMES = {"pinhole": PINHOLE, "equidistant": EQUIDISTANT,
-                "kb": KANNALA_BRANDT, "kannala_brandt": KANNALA_BRANDT}
+                "kb": KANNALA_BRANDT, "kannala_brandt": KANNALA_BRANDT,
+                "ucm": UNIFIED, "unified": UNIFIED,
+                "eucm": ENHANCED_UNIFIED, "enhanced_unified": ENHANCED_UNIFIED}
 
 
 @dataclass(frozen=True)
@@ -63,6 +69,12 @@ def radial(calib: Calib, theta):
         return np.tan(theta)
     if calib.model == EQUIDISTANT:
         return theta
+    if calib.model == UNIFIED:
+        return np.sin(theta) / (np.cos(theta) + calib.k[0])
+    if calib.model == ENHANCED_UNIFIED:
+        alpha, beta = calib.k[0], calib.k[1]
+        s, c = np.sin(theta), np.cos(theta)
+        return s / (alpha * np.sqrt(beta * s * s + c * c) + (1.0 - alpha) * c)
     k1, k2, k3, k4 = calib.k
     t2 = theta * theta
     return theta * (1.0 + t2 * (k1 + t2 * (k2 + t2 * (k3 + t2 * k4))))

@@ -18,7 +18,8 @@ __all__ = ["Solver", "Batch", "FsError", "load_library", "default_params", "BUF"
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfs.so")
 
-MODELS = {"pinhole": 0, "equidistant": 1, "kb": 2, "kannala_brandt": 2}
+MODELS = {"pinhole": 0, "equidistant": 1, "kb": 2, "kannala_brandt": 2, "ucm": 3, "unified": 3,
+          "eucm": 4, "enhanced_unified": 4}
 
 BUF = dict(I0=0, I1=1, MASK=2, GAMMA=3, TENSOR=4, STEPS=5, U=6, UBAR=7, UW=8, P=9, W=10,
            IU=11, RHO0=12, G=13)

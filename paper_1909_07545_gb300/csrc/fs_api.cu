@@ -62,9 +62,18 @@ struct HostLevel {
   LevelView v{};
 };
 
+// Denominator of the enhanced unified model, alpha sqrt(beta s^2 + c^2) +
+// (1 - alpha) c (the unified model is alpha = xi / (1 + xi), beta = 1 up
+// to the scale 1 + xi; both are written out).
+double eucm_den(const fs_calib& c, double s, double cs) {
+  return c.k[0] * std::sqrt(c.k[1] * s * s + cs * cs) + (1.0 - c.k[0]) * cs;
+}
+
 double radial(const fs_calib& c, double th) {
   if (c.model == FS_PINHOLE) return std::tan(th);
   if (c.model == FS_EQUIDISTANT) return th;
+  if (c.model == FS_UNIFIED) return std::sin(th) / (std::cos(th) + c.k[0]);
+  if (c.model == FS_ENHANCED_UNIFIED) return std::sin(th) / eucm_den(c, std::sin(th), std::cos(th));
   double t2 = th * th;
   return th * (1.0 + t2 * (c.k[0] + t2 * (c.k[1] + t2 * (c.k[2] + t2 * c.k[3]))));
 }
@@ -81,20 +90,28 @@ DevCam dev_cam(const fs_calib& c, double fx, double fy, double cx, double cy) {
 }
 
 fs_status check_calib(const fs_calib& c, int which) {
-  if (c.model < FS_PINHOLE || c.model > FS_KANNALA_BRANDT)
+  if (c.model < FS_PINHOLE || c.model > FS_ENHANCED_UNIFIED)
     return fail(FS_EINVAL, "camera %d: unknown model %d", which, c.model);
+  if (c.model == FS_UNIFIED && !(c.k[0] >= 0 && std::isfinite(c.k[0])))
+    return fail(FS_ECALIB, "camera %d: unified model needs xi >= 0", which);
+  if (c.model == FS_ENHANCED_UNIFIED && !(c.k[0] >= 0 && c.k[0] < 1 && c.k[1] > 0 &&
+                                          std::isfinite(c.k[1])))
+    return fail(FS_ECALIB, "camera %d: enhanced unified model needs 0 <= alpha < 1, beta > 0",
+                which);
   if (!(c.fx > 0) || !(c.fy > 0) || !std::isfinite(c.cx) || !std::isfinite(c.cy))
     return fail(FS_ECALIB, "camera %d: focal lengths must be > 0, centre finite", which);
   if (!(c.fov_deg > 0 && c.fov_deg < 360))
     return fail(FS_ECALIB, "camera %d: fov_deg must be in (0, 360)", which);
   if (c.model == FS_PINHOLE && !(c.fov_deg < 180))
     return fail(FS_ECALIB, "camera %d: a pinhole fov must be < 180 degrees", which);
-  if (c.model == FS_KANNALA_BRANDT) {
-    // r(theta) must increase on [0, fov/2] (10^4 samples)
+  if (c.model >= FS_KANNALA_BRANDT) {
+    // r(theta) must be finite and increase on [0, fov/2] (10^4 samples);
+    // for the unified models this also keeps the denominator positive
     double tm = c.fov_deg * M_PI / 360.0, prev = 0.0;
     for (int i = 1; i < 10000; ++i) {
       double r = radial(c, tm * i / 9999.0);
-      if (!(r > prev)) return fail(FS_ECALIB, "camera %d: r(theta) not increasing", which);
+      if (!(r > prev) || !std::isfinite(r))
+        return fail(FS_ECALIB, "camera %d: r(theta) not increasing", which);
       prev = r;
     }
   }
@@ -104,6 +121,16 @@ fs_status check_calib(const fs_calib& c, int which) {
 double radial_d(const fs_calib& c, double th) {
   if (c.model == FS_PINHOLE) { double cs = std::cos(th); return 1.0 / (cs * cs); }
   if (c.model == FS_EQUIDISTANT) return 1.0;
+  if (c.model == FS_UNIFIED) {
+    double cs = std::cos(th), d = cs + c.k[0];
+    return (1.0 + c.k[0] * cs) / (d * d);
+  }
+  if (c.model == FS_ENHANCED_UNIFIED) {
+    double s = std::sin(th), cs = std::cos(th), q = std::sqrt(c.k[1] * s * s + cs * cs);
+    double D = eucm_den(c, s, cs);
+    double dD = c.k[0] * s * cs * (c.k[1] - 1.0) / q - (1.0 - c.k[0]) * s;
+    return (cs * D - s * dD) / (D * D);
+  }
   double t2 = th * th;
   return 1.0 + t2 * (3 * c.k[0] + t2 * (5 * c.k[1] + t2 * (7 * c.k[2] + t2 * 9 * c.k[3])));
 }
@@ -113,6 +140,17 @@ double radial_d(const fs_calib& c, double th) {
 double theta_of(const fs_calib& c, double rn) {
   if (c.model == FS_EQUIDISTANT) return rn;
   if (c.model == FS_PINHOLE) return std::atan(rn);
+  if (c.model == FS_UNIFIED) {       // closed form (Sec. III-D)
+    double xi = c.k[0], r2 = rn * rn;
+    double eta = (xi + std::sqrt(std::max(1.0 + (1.0 - xi * xi) * r2, 0.0))) / (1.0 + r2);
+    return std::atan2(eta * rn, eta - xi);
+  }
+  if (c.model == FS_ENHANCED_UNIFIED) {
+    double a = c.k[0], b = c.k[1], r2 = rn * rn;
+    double mz = (1.0 - b * a * a * r2) /
+                (a * std::sqrt(std::max(1.0 - (2.0 * a - 1.0) * b * r2, 0.0)) + 1.0 - a);
+    return std::atan2(rn, mz);
+  }
   double lo = 0.0, hi = c.fov_deg * M_PI / 360.0;
   for (int i = 0; i < 24; ++i) {
     double mid = 0.5 * (lo + hi);

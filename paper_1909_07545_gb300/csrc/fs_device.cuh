@@ -17,7 +17,8 @@ constexpr uint8_t MASK_IN = 1, MASK_GX = 2, MASK_GY = 4;
 
 // Radially symmetric camera, pixel = c + f * r(theta) * (X, Y)/|(X, Y)|.
 struct DevCam {
-  int model;            // 0 pinhole, 1 equidistant, 2 Kannala-Brandt
+  int model;            // 0 pinhole, 1 equidistant, 2 Kannala-Brandt, 3 unified
+                        // (k1 = xi), 4 enhanced unified (k1 = alpha, k2 = beta)
   float fx, fy, cx, cy;
   float k1, k2, k3, k4;
   float theta_max;      // FOV half-angle (radians)
@@ -27,6 +28,11 @@ struct DevCam {
 __host__ __device__ __forceinline__ float cam_r(const DevCam& c, float th) {
   if (c.model == 0) return tanf(th);
   if (c.model == 1) return th;
+  if (c.model == 3) return sinf(th) / (cosf(th) + c.k1);
+  if (c.model == 4) {
+    float s = sinf(th), cs = cosf(th);
+    return s / (c.k1 * sqrtf(c.k2 * s * s + cs * cs) + (1.f - c.k1) * cs);
+  }
   float t2 = th * th;
   return th * (1.f + t2 * (c.k1 + t2 * (c.k2 + t2 * (c.k3 + t2 * c.k4))));
 }
@@ -35,19 +41,46 @@ __host__ __device__ __forceinline__ float cam_r(const DevCam& c, float th) {
 __host__ __device__ __forceinline__ float cam_dr(const DevCam& c, float th) {
   if (c.model == 0) { float cs = cosf(th); return 1.f / (cs * cs); }
   if (c.model == 1) return 1.f;
+  if (c.model == 3) {
+    float cs = cosf(th), d = cs + c.k1;
+    return (1.f + c.k1 * cs) / (d * d);
+  }
+  if (c.model == 4) {
+    float s = sinf(th), cs = cosf(th), q = sqrtf(c.k2 * s * s + cs * cs);
+    float D = c.k1 * q + (1.f - c.k1) * cs;
+    float dD = c.k1 * s * cs * (c.k2 - 1.f) / q - (1.f - c.k1) * s;
+    return (cs * D - s * dD) / (D * D);
+  }
   float t2 = th * th;
   return 1.f + t2 * (3.f * c.k1 + t2 * (5.f * c.k2 + t2 * (7.f * c.k3 + t2 * 9.f * c.k4)));
 }
 
-// theta with r(theta) = rn on [0, theta_max]: closed form for pinhole and
-// equidistant.  For Kannala-Brandt, whose r(theta) can bend strongly near the
-// FOV edge, 10 bisection steps first narrow [0, theta_max] to a bracket of
-// width theta_max / 1024, then 8 Newton steps converge inside it (a step
-// that leaves the bracket is replaced by its midpoint).  r must increase on
-// the interval (checked at handle creation).
+// theta with r(theta) = rn on [0, theta_max].  Pinhole and equidistant:
+// closed form.  Unified models: closed form (Sec. III-D), clamped to
+// theta_max for radii beyond the FOV circle, as the bracketed solve below
+// is.  Kannala-Brandt, whose r(theta) can bend strongly near the FOV edge:
+// 10 bisection steps first narrow [0, theta_max] to a bracket of width
+// theta_max / 1024, then 8 Newton steps converge inside it (a step that
+// leaves the bracket is replaced by its midpoint).  r must increase on the
+// interval (checked at handle creation).
 __device__ __forceinline__ float cam_theta(const DevCam& c, float rn) {
   if (c.model == 1) return rn;
   if (c.model == 0) return atanf(rn);
+  if (c.model == 3) {
+    // closed form: the ray is (eta m, eta - xi), eta = (xi + sqrt(1 + (1 - xi^2)
+    // r^2)) / (1 + r^2)
+    float r2 = rn * rn;
+    float eta = (c.k1 + sqrtf(fmaxf(1.f + (1.f - c.k1 * c.k1) * r2, 0.f))) / (1.f + r2);
+    return fminf(atan2f(eta * rn, eta - c.k1), c.theta_max);
+  }
+  if (c.model == 4) {
+    // closed form: the ray is (m, m_z), m_z = (1 - beta alpha^2 r^2) /
+    // (alpha sqrt(1 - (2 alpha - 1) beta r^2) + 1 - alpha)
+    float r2 = rn * rn, a = c.k1, b = c.k2;
+    float mz = (1.f - b * a * a * r2) /
+               (a * sqrtf(fmaxf(1.f - (2.f * a - 1.f) * b * r2, 0.f)) + 1.f - a);
+    return fminf(atan2f(rn, mz), c.theta_max);
+  }
   float lo = 0.f, hi = c.theta_max;
 #pragma unroll 1
   for (int i = 0; i < 10; ++i) {

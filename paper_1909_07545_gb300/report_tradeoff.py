@@ -1,0 +1,82 @@
+"""Accuracy against ground truth and time per frame as functions of the warp
+count N and the increment limit du_max (the trade-offs of the paper's
+Sec. IV-C and V-A: Fig. 4, time linear in N while the error falls; Fig. 6,
+a smaller du_max needs more warps but tracks the epipolar curve better).
+
+    python -m paper_1909_07545_gb300.report_tradeoff [--size 800] [--levels 5]
+        [--iters 10] [--out report.json]
+
+Run from the repository root (it uses the ``synth`` scene generator).  The
+scene is the 180-degree equidistant generator (3 textured planes at 1-5 m,
+0.1 m baseline) at the given size; every solve is one CUDA graph replay timed
+with CUDA events (mean of 3 after one untimed solve).  Errors are over the
+FOV mask where the ground truth is defined: mean and median end-point error
+and the fractions of pixels off by more than 1 and 5 px.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--size", type=int, default=800)
+    ap.add_argument("--levels", type=int, default=5)
+    ap.add_argument("--iters", type=int, default=10)
+    ap.add_argument("--warps", default="1,2,5,10,15,20")
+    ap.add_argument("--du-max", default="0.1,0.2,0.5,1.0")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    sys.path.insert(0, os.getcwd())
+    import torch
+
+    import synth
+    from paper_1909_07545_gb300 import Solver
+
+    W = args.size
+    p = synth.plain_small(args.seed, W=W, H=W)
+    g, valid = synth.gt_disparity(p)
+    I0 = torch.as_tensor(np.float32(p["I0"]), device="cuda")
+    I1 = torch.as_tensor(np.float32(p["I1"]), device="cuda")
+    rows = []
+    for dm in [float(v) for v in args.du_max.split(",")]:
+        s = Solver(p["cam0"], p["cam1"], p["R"], p["t"], W, W, args.levels, lam=p["lam"],
+                   huber_eps=p["eps"], du_max=dm, use_graph=1)
+        s.autotune(args.iters)
+        mask = s.read(0, "MASK").cpu().numpy() > 0.5
+        v = valid & mask
+        d = torch.empty((W, W), device="cuda")
+        z = torch.empty((W, W), device="cuda")
+        for n in [int(v) for v in args.warps.split(",")]:
+            s.solve(I0, I1, n, args.iters, disp=d, depth=z)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                s.solve(I0, I1, n, args.iters, disp=d, depth=z)
+            e1.record()
+            torch.cuda.synchronize()
+            err = synth.disparity_errors(d.double().cpu().numpy(), g, v)
+            rows.append(dict(du_max=dm, warps=n, ms=e0.elapsed_time(e1) / 3, **err))
+            print(json.dumps(rows[-1]), flush=True)
+        s.close()
+    print(f"\n{W}x{W}, {args.levels} levels, {args.iters} iterations per warp")
+    print("| du_max | N | ms/frame | EPE mean | EPE median | tau>1 | tau>5 |")
+    print("|---:|---:|---:|---:|---:|---:|---:|")
+    for r in rows:
+        print(f"| {r['du_max']} | {r['warps']} | {r['ms']:.2f} | {r['epe_mean']:.3f} | "
+              f"{r['epe_median']:.3f} | {100 * r['tau1']:.1f} % | {100 * r['tau5']:.1f} % |")
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(dict(size=W, levels=args.levels, iters=args.iters, rows=rows), f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -29,6 +29,12 @@ def lens_radius(cam, theta):
         return np.tan(theta)
     if m == "equidistant":
         return np.asarray(theta, dtype=np.float64)
+    if m in ("ucm", "unified"):                  # m = (X, Y) / (Z + xi |X|)
+        return np.sin(theta) / (np.cos(theta) + cam["k"][0])
+    if m in ("eucm", "enhanced_unified"):        # alpha, beta
+        a, b = cam["k"][0], cam["k"][1]
+        s, c = np.sin(theta), np.cos(theta)
+        return s / (a * np.sqrt(b * s * s + c * c) + (1.0 - a) * c)
     k1, k2, k3, k4 = cam["k"]
     t2 = theta * theta
     return theta + k1 * theta * t2 + k2 * theta * t2 ** 2 + k3 * theta * t2 ** 3 \

@@ -151,3 +151,32 @@ def disparity_parity(d_gpu, ref, sens):
     ok = (report["mean"] <= MEAN_TOL and report["q998"] <= MAX_TOL
           and n_gpu <= 2 * n_probe + 10 and report["max"] <= max(MAX_TOL, 2 * report["probe_max"]))
     return ok, report
+
+
+def unified_cam(model, W, H, fov_deg=190.0, xi=0.85, alpha=0.6, beta=1.15):
+    """A unified (xi) or enhanced unified (alpha, beta) calibration whose FOV
+    circle nearly fills a W x H image."""
+    from synth.render import lens_radius
+    k = [xi, 0.0, 0.0, 0.0] if model == "ucm" else [alpha, beta, 0.0, 0.0]
+    cam = dict(model=model, fx=1.0, fy=1.0, cx=(W - 1) / 2.0, cy=(H - 1) / 2.0, k=k,
+               fov_deg=fov_deg)
+    f = 0.47 * min(W, H) / float(lens_radius(cam, np.radians(fov_deg) / 2.0))
+    cam["fx"] = cam["fy"] = f
+    return cam
+
+
+def unified_pair(seed=0, W=192, H=176, model0="ucm", model1="ucm"):
+    """A rendered pair with unified / enhanced unified lenses (camera 1 may
+    use the other model), a rotated second camera and a 0.1 m baseline."""
+    import math
+    from synth.render import make_scene, render, rotation
+    rng = np.random.default_rng(seed)
+    cam0 = unified_cam(model0, W, H)
+    cam1 = unified_cam(model1, W, H)
+    scene = make_scene(rng, 6, (1.0, 5.0), 8.0, cam0["fx"], kinds=("plane", "sphere"))
+    R = rotation([0.2, 1.0, -0.3], math.radians(1.2))
+    C1 = np.array([0.1, -0.005, 0.01])
+    I0, gt = render(scene, cam0, np.eye(3), np.zeros(3), W, H, 2)
+    I1, _ = render(scene, cam1, R, C1, W, H, 2)
+    return f32pair(dict(I0=I0, I1=I1, cam0=cam0, cam1=cam1, R=R, t=-R @ C1, gt_range=gt,
+                        levels=3, warps=3, iters=25, lam=50.0, eps=0.01))

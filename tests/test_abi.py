@@ -70,6 +70,14 @@ def test_host_side_validation(lib):
     neg = dict(EQ, fx=-1.0)
     st, _ = _create([EQ, neg])
     assert st == -4
+    # unified: xi >= 0; enhanced unified: 0 <= alpha < 1, beta > 0, and r
+    # increasing over the FOV (alpha = 0.95, beta = 1 folds back before 95 deg)
+    for bad in (dict(EQ, model="ucm", k=[-0.2, 0, 0, 0]),
+                dict(EQ, model="eucm", k=[1.0, 1.0, 0, 0]),
+                dict(EQ, model="eucm", k=[0.5, 0.0, 0, 0]),
+                dict(EQ, model="eucm", k=[0.95, 1.0, 0, 0], fov_deg=190.0)):
+        st, msg = _create([bad, EQ])
+        assert st == -4, (bad, msg)
     prm = fsb.default_params(block_iters=9)
     st, msg = _create([EQ, EQ], prm=prm)
     assert st == -1 and "parameter" in msg

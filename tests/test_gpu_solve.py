@@ -66,6 +66,21 @@ def test_plain_small_256_matches_oracle(small, small_ref):
     s.close()
 
 
+@pytest.mark.parametrize("models", [("ucm", "ucm"), ("eucm", "ucm")])
+def test_unified_model_pairs_match_oracle(models):
+    # the unified and enhanced unified lenses (Sec. III-B, III-D), camera 1
+    # possibly of the other model (the calibration field then also carries
+    # the difference of the lenses, Sec. IV-A)
+    from gpu_helpers import unified_pair
+    p = unified_pair(11, model0=models[0], model1=models[1])
+    ref = _oracle(p)
+    sens = oracle_sensitivity(p, ref)
+    s = make_solver(p)
+    disp, depth = s.solve(p["I0"], p["I1"], p["warps"], p["iters"])
+    _compare(p, ref, disp, depth, sens)
+    s.close()
+
+
 @pytest.mark.parametrize("block", [1, 5, 8])
 def test_schedules_and_block_depths_are_identical(small, block):
     s1 = make_solver(small, block_iters=block, pd_schedule=1)

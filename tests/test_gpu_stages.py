@@ -12,7 +12,7 @@ import pytest
 import oracle
 import synth
 from gpu_helpers import (f32pair, gpu_level_data, level_calibs, make_solver, np64,
-                         oracle_params, ragged_pair)
+                         oracle_params, ragged_pair, unified_pair)
 
 pytestmark = pytest.mark.gpu
 
@@ -45,9 +45,16 @@ def _kb_rig(seed=0, W=1024):
     return dict(I0=z, I1=z, cam0=cam, cam1=dict(cam), R=R, t=t, levels=5, lam=50.0, eps=0.01)
 
 
-@pytest.mark.parametrize("which", ["small", "ragged", "kb"])
-def test_masks_bit_exact_and_trajectory_field(which, small, ragged):
-    pair = {"small": small, "ragged": ragged, "kb": None}[which] or _kb_rig()
+@pytest.fixture(scope="module")
+def unified():
+    return {m: unified_pair(5, model0=m, model1="eucm" if m == "ucm" else "ucm")
+            for m in ("ucm", "eucm")}
+
+
+@pytest.mark.parametrize("which", ["small", "ragged", "kb", "ucm", "eucm"])
+def test_masks_bit_exact_and_trajectory_field(which, small, ragged, unified):
+    pair = {"small": small, "ragged": ragged, "kb": None}.get(which, unified.get(which)) \
+        or _kb_rig()
     s = make_solver(pair)
     sizes, cals, masks = level_calibs(pair, pair["levels"])
     tp = oracle.virtual_translation(pair["R"], pair["t"])
@@ -73,8 +80,11 @@ def test_masks_bit_exact_and_trajectory_field(which, small, ragged):
     s.close()
 
 
-def test_prerotation(ragged):
-    pair = ragged
+@pytest.mark.parametrize("which", ["ragged", "ucm", "eucm"])
+def test_prerotation(which, ragged, unified):
+    # for "ucm" / "eucm" camera 1 uses the other unified model, so the
+    # calibration field also carries the difference of the lenses (Sec. IV-A)
+    pair = ragged if which == "ragged" else unified[which]
     s = make_solver(pair)
     s.prerotate(pair["I1"])
     got = np64(s.read(0, "I1"))
@@ -286,8 +296,9 @@ def test_upsample(small, ragged):
         s.close()
 
 
-def test_depth_triangulation(ragged):
-    pair = ragged
+@pytest.mark.parametrize("which", ["ragged", "ucm", "eucm"])
+def test_depth_triangulation(which, ragged, unified):
+    pair = ragged if which == "ragged" else unified[which]
     s = make_solver(pair)
     cam = oracle.calib_from_dict(pair["cam0"])
     H, W = pair["I0"].shape

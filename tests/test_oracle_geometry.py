@@ -5,7 +5,8 @@ import math
 import numpy as np
 import pytest
 
-from oracle.camera import Calib, EQUIDISTANT, KANNALA_BRANDT, PINHOLE, project, unproject
+from oracle.camera import (Calib, ENHANCED_UNIFIED, EQUIDISTANT, KANNALA_BRANDT, PINHOLE,
+                           UNIFIED, project, unproject)
 from oracle.geometry import (calibration_field, prerotate, trajectory_field,
                              trajectory_vector, triangulate_range, virtual_translation)
 from oracle.pyramid import fov_mask
@@ -13,6 +14,8 @@ from oracle.pyramid import fov_mask
 EQ = Calib(EQUIDISTANT, 80.0, 80.0, 127.5, 127.5, fov_deg=180.0)
 KB = Calib(KANNALA_BRANDT, 320.0, 320.0, 511.5, 511.5, (0.03, -0.01, 0.004, 0.001), 190.0)
 PH = Calib(PINHOLE, 90.0, 90.0, 63.5, 63.5, fov_deg=100.0)
+UCM = Calib(UNIFIED, 150.0, 150.0, 255.5, 255.5, (0.85, 0, 0, 0), 190.0)
+EUCM = Calib(ENHANCED_UNIFIED, 160.0, 160.0, 255.5, 255.5, (0.6, 1.15, 0, 0), 190.0)
 
 
 def _grid(cam, W, H):
@@ -75,7 +78,7 @@ def test_invariance_to_translation_scale_and_depth(cam, W):
     assert np.abs(g1 - g3).max() < 1e-5
 
 
-@pytest.mark.parametrize("cam", [EQ, KB])
+@pytest.mark.parametrize("cam", [EQ, KB, UCM, EUCM])
 def test_field_is_tangent_to_traced_epipolar_curves(cam):
     # brute force: project the 3-D points Z r0 + t' for Z from far to near and
     # check that the field at each projected point is tangent to that curve
