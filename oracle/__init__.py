@@ -17,6 +17,7 @@ geometry     trajectory field (Sec. III-B, Eq. 6-7), calibration field and
 pyramid      levels, circular FOV mask, down/up-sampling (Sec. IV-B)
 variational  tensor (Eq. 12), masked gradient/divergence, preconditioning,
              primal-dual step (Eq. 11, 13), linearisation (Eq. 3, 5), energy
+tgv          the TGV-L1 energy of Eq. 10 and its primal-dual step (Eq. 11)
 solve        Algorithm 1 driven coarse-to-fine (Algorithm 1, Sec. IV)
 
 Pinning status (what fixes each function independently of itself) is listed
@@ -35,6 +36,7 @@ from .variational import (Params, grad_masks, grad, div, tensor_sqrt, preconditi
                           dual_step, shrink, primal_step, pd_iteration,
                           warp_linearize, clip_update, energy)
 from .solve import solve, solve_level_warps, warm_start_w
+from .tgv import div_q, grad_v, tgv_energy, tgv_iteration, tgv_steps
 
 __all__ = [
     "Calib", "calib_from_dict", "project", "unproject", "radial", "fov_radius",
@@ -45,4 +47,5 @@ __all__ = [
     "Params", "grad_masks", "grad", "div", "tensor_sqrt", "precondition",
     "dual_step", "shrink", "primal_step", "pd_iteration", "warp_linearize",
     "clip_update", "energy", "solve", "solve_level_warps", "warm_start_w",
+    "grad_v", "div_q", "tgv_steps", "tgv_iteration", "tgv_energy",
 ]

@@ -29,6 +29,7 @@ from .geometry import (calibration_field, prerotate, trajectory_field,
                        triangulate_range, virtual_translation)
 from .pyramid import downsample_fast, fov_mask, level_sizes, scaled_calib, upsample
 from .interp import bicubic
+from .tgv import tgv_iteration, tgv_steps
 from .variational import (Params, clip_update, grad_masks, pd_iteration,
                           precondition, tensor_sqrt, warp_linearize)
 
@@ -37,25 +38,47 @@ def level_data(I0l, M, prm: Params):
     a, b, c = tensor_sqrt(I0l, M, prm.beta, prm.eta)
     m1, m2 = grad_masks(M)
     tau, sig1, sig2 = precondition(a, b, c, M, m1, m2, prm.precond)
-    return dict(a=a, b=b, c=c, m1=m1, m2=m2, M=M, tau=tau, sig1=sig1, sig2=sig2)
+    lv = dict(a=a, b=b, c=c, m1=m1, m2=m2, M=M, tau=tau, sig1=sig1, sig2=sig2)
+    if prm.regularizer == "tgv":
+        lv["tau_u"], lv["tau_v"], lv["sig_p"], lv["sig_q"] = tgv_steps(a, b, c, M, m1, m2,
+                                                                        prm.precond)
+    return lv
+
+
+TGV_STATE = ("v1", "v2", "q11", "q12", "q21", "q22")
+
+
+def tgv_zero_state(shape):
+    """v and q of a new level: 0 (like p, Sec. III-C state across levels)."""
+    return {k: np.zeros(shape) for k in TGV_STATE}
 
 
 def solve_level_warps(I0l, I1l, gamma, lv, u, w, p1, p2, warps, iters,
-                      prm: Params, on_iter=None, level=0):
-    """Run `warps` warps of `iters` primal-dual iterations on one level."""
+                      prm: Params, on_iter=None, level=0, tgv=None):
+    """Run `warps` warps of `iters` primal-dual iterations on one level.
+
+    tgv: for the TGV-L1 energy, the dict of v and q (TGV_STATE), carried
+    across the warps like p and updated in place."""
     M = lv["M"]
     for om in range(warps):
         Iu, rho0, g = warp_linearize(I0l, I1l, w, gamma, M)
         st = dict(u=u.copy(), ubar=u.copy(), p1=p1, p2=p2, Iu=Iu, rho0=rho0,
                   u_w=u.copy())
+        if tgv is not None:
+            st.update(tgv, vb1=tgv["v1"].copy(), vb2=tgv["v2"].copy())
         if on_iter is not None:
             on_iter(level, om, -1, st, lv)
         for k in range(iters):
-            pd_iteration(st, lv, prm)
+            if tgv is not None:
+                tgv_iteration(st, lv, prm)
+            else:
+                pd_iteration(st, lv, prm)
             if on_iter is not None:
                 on_iter(level, om, k, st, lv)
         u, w = clip_update(st["u"], st["u_w"], w, g, prm.du_max, M)
         p1, p2 = st["p1"], st["p2"]
+        if tgv is not None:
+            tgv.update({k: st[k] for k in TGV_STATE})
     return u, w, p1, p2
 
 
@@ -141,8 +164,9 @@ def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params()
             w = upsample(w, masks[l + 1], Wl, Hl, M)
         p1 = np.zeros((Hl, Wl))
         p2 = np.zeros((Hl, Wl))
+        tgv = tgv_zero_state((Hl, Wl)) if prm.regularizer == "tgv" else None
         u, w, p1, p2 = solve_level_warps(pyr0[l], pyr1[l], gamma, lv, u, w, p1, p2,
-                                         warps, iters, prm, on_iter, l)
+                                         warps, iters, prm, on_iter, l, tgv)
         if keep_levels:
             per_level.append(dict(level=l, u=u.copy(), w=w.copy(), gamma=gamma,
                                   I0=pyr0[l], I1=pyr1[l], **lv))

@@ -52,6 +52,9 @@ class Params:
     eta: float = 0.85        # Sec. IV-C, Eq. 12
     theta: float = 1.0       # over-relaxation (Chambolle-Pock Algorithm 1)
     precond: bool = True     # diagonal preconditioning (Pock-Chambolle 2011)
+    regularizer: str = "huber_tv"   # or "tgv": the TGV-L1 energy of Eq. 10
+    alpha0: float = 17.0     # Sec. IV-C, TGV second-order weight
+    alpha1: float = 1.2      # Sec. IV-C, TGV first-order weight
 
 
 def grad_masks(M):
