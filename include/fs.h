@@ -91,7 +91,15 @@ typedef struct {
  * storage: 0 = FP32; 1 = FP16, 2 = BF16 storage of the images, the warped
  * gradient and residual (I_u, rho0), the tensor T^1/2 and the dual field p,
  * while the disparity (u, u_omega), the warp vector and every operation stay
- * FP32 (values are rounded to nearest when stored). */
+ * FP32 (values are rounded to nearest when stored).
+ * regularizer: FS_REG_HUBER_TV (0) = lambda |rho| + h_eps(T^1/2 grad u), the
+ * first-order member of Eq. 10; FS_REG_TGV (1) = the paper's tensor-guided
+ * TGV-L1 energy of Eq. 10, lambda |rho| + alpha1 |T^1/2 grad u - v| +
+ * alpha0 |grad v| (alpha0 = 17, alpha1 = 1.2 in Sec. IV-C; huber_eps,
+ * block_iters and pd_schedule do not apply), solved by the primal-dual
+ * steps of Eq. 11 with diagonal preconditioning; FP32 storage only. */
+#define FS_REG_HUBER_TV 0
+#define FS_REG_TGV 1
 typedef struct {
   float lambda;
   float huber_eps;
@@ -104,7 +112,8 @@ typedef struct {
   int use_graph;
   int pd_schedule;
   int storage;
-  int reserved[3];         /* must be 0 */
+  int regularizer;         /* FS_REG_HUBER_TV or FS_REG_TGV                   */
+  float alpha0, alpha1;    /* TGV weights (regularizer = FS_REG_TGV)          */
 } fs_params;
 
 typedef struct fs_handle fs_handle;

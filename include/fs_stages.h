@@ -32,7 +32,10 @@ typedef enum {
   FS_BUF_W = 10,      /* 2: warp vector w (Eq. 9)                             */
   FS_BUF_IU = 11,     /* 1: I_u, variation of I1 along gamma' (Eq. 5)         */
   FS_BUF_RHO0 = 12,   /* 1: I1(x + w) - I0(x)                                 */
-  FS_BUF_G = 13       /* 2: gamma' at x + w, renormalised (bicubic)           */
+  FS_BUF_G = 13,      /* 2: gamma' at x + w, renormalised (bicubic)           */
+  FS_BUF_V = 14,      /* 2: TGV auxiliary field v (Eq. 10; TGV handles only)  */
+  FS_BUF_VBAR = 15,   /* 2: over-relaxed v (Eq. 11; TGV handles only)         */
+  FS_BUF_Q = 16       /* 4: TGV dual q, rows dv1 (x, y) then dv2 (x, y)       */
 } fs_buffer;
 
 typedef enum {

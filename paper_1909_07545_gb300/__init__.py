@@ -22,9 +22,10 @@ MODELS = {"pinhole": 0, "equidistant": 1, "kb": 2, "kannala_brandt": 2, "ucm": 3
           "eucm": 4, "enhanced_unified": 4}
 
 BUF = dict(I0=0, I1=1, MASK=2, GAMMA=3, TENSOR=4, STEPS=5, U=6, UBAR=7, UW=8, P=9, W=10,
-           IU=11, RHO0=12, G=13)
+           IU=11, RHO0=12, G=13, V=14, VBAR=15, Q=16)
 BUF_PLANES = {0: 1, 1: 1, 2: 1, 3: 2, 4: 3, 5: 2, 6: 1, 7: 1, 8: 1, 9: 2, 10: 2, 11: 1, 12: 1,
-              13: 2}
+              13: 2, 14: 2, 15: 2, 16: 4}
+REGULARIZER = {"huber_tv": 0, "tgv": 1}
 STAGE = dict(DOWNSAMPLE=0, TENSOR=1, UPSAMPLE=2, WARP=3, PD=4, CLIP=5, TRAJECTORY=6, WARM=7)
 
 STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ENOMEM", -3: "FS_ECUDA", -4: "FS_ECALIB",
@@ -65,7 +66,8 @@ class FsParams(ctypes.Structure):
                 ("theta", ctypes.c_float), ("precond", ctypes.c_int),
                 ("block_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("pd_schedule", ctypes.c_int), ("storage", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("regularizer", ctypes.c_int), ("alpha0", ctypes.c_float),
+                ("alpha1", ctypes.c_float)]
 
 
 class FsServerConfig(ctypes.Structure):
@@ -162,6 +164,8 @@ def default_params(**overrides) -> FsParams:
     for k, v in overrides.items():
         if k == "storage" and isinstance(v, str):
             v = STORAGE[v]
+        if k == "regularizer" and isinstance(v, str):
+            v = REGULARIZER[v]
         setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
     return p
 

@@ -337,6 +337,11 @@ int pd_launches(int iters, int B) {
 fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
   HostLevel& L = h->lv[l];
   PDParams pp{h->prm.lambda, h->prm.huber_eps, h->prm.theta};
+  if (h->prm.regularizer == FS_REG_TGV) {
+    FS_LAUNCH("k_tgv", launch_tgv_iterations(L.v, pp, h->prm.alpha0, h->prm.alpha1,
+                                             h->prm.precond, iters, st));
+    return FS_OK;
+  }
   if (use_cluster(h, l)) {
     cudaError_t e = launch_pd_cluster(L.cluster, L.v, pp, iters, st);
     if (e != cudaSuccess)
@@ -381,9 +386,12 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
     case FS_STAGE_UPSAMPLE:
       if (l + 1 >= h->L) return fail(FS_EINVAL, "upsample: level %d has no coarser level", l);
       FS_LAUNCH("k_upsample", launch_upsample(h->lv[l + 1].v, L.v, st));
+      if (h->prm.regularizer == FS_REG_TGV) FS_LAUNCH("k_tgv_reset", launch_tgv_reset(L.v, st));
       return FS_OK;
     case FS_STAGE_WARP:
       FS_LAUNCH("k_warp", launch_warp(L.v, st));
+      if (h->prm.regularizer == FS_REG_TGV)
+        FS_LAUNCH("k_tgv_warp_start", launch_tgv_warp_start(L.v, st));
       return FS_OK;
     case FS_STAGE_PD:
       if (count < 1) return fail(FS_EINVAL, "pd: count must be >= 1");
@@ -394,6 +402,7 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
       return FS_OK;
     case FS_STAGE_WARM:
       FS_LAUNCH("k_warm_start", launch_warm_start(L.v, h->prm.du_max, st));
+      if (h->prm.regularizer == FS_REG_TGV) FS_LAUNCH("k_tgv_reset", launch_tgv_reset(L.v, st));
       return FS_OK;
     case FS_STAGE_TRAJECTORY: {
       double n = std::sqrt(h->tp[0] * h->tp[0] + h->tp[1] * h->tp[1] + h->tp[2] * h->tp[2]);
@@ -445,6 +454,7 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
     if (finest_wait) FS_CUDA(cudaStreamWaitEvent(st, finest_wait, 0));
     if (cont) {          // from the level's own last u and w
       FS_LAUNCH("k_continue", launch_continue(L0.v, st));
+      if (h->prm.regularizer == FS_REG_TGV) FS_LAUNCH("k_tgv_reset", launch_tgv_reset(L0.v, st));
     } else {             // from the given disparity, w rebuilt along gamma'
       k_copy_in<<<grid2(L0.W, L0.H), kBlock2, 0, st>>>(init, L0.v.u, L0.W, L0.H, L0.P);
       FS_LAUNCHED("k_copy_in");
@@ -475,6 +485,7 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
     if ((s = run_stage(h, l, FS_STAGE_TENSOR, 0, st)) != FS_OK) return s;
     if (l == top) {
       FS_LAUNCH("k_zero_state", launch_zero_state(L.v, st));
+      if (h->prm.regularizer == FS_REG_TGV) FS_LAUNCH("k_tgv_reset", launch_tgv_reset(L.v, st));
     } else if ((s = run_stage(h, l, FS_STAGE_UPSAMPLE, 0, st)) != FS_OK) {
       return s;
     }
@@ -517,11 +528,12 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // sigma, u, ubar, u_w and the ping-pong u, ubar), 10 planes in the storage
 // type (I0, I1, s_x, s_y, p1, p2, I_u, rho0 and the ping-pong p1, p2) and 3
 // float2 planes (gamma, w, g); every plane starts on a 256-byte boundary.
-size_t level_bytes(int P, int H, int storage) {
+size_t level_bytes(int P, int H, int storage, int regularizer) {
   size_t plane = align_up((size_t)P * H * sizeof(float), 256);
   size_t splane = align_up((size_t)P * H * storage_size(storage), 256);
   size_t plane8 = align_up((size_t)P * H, 256);
-  return plane8 + 7 * plane + 10 * splane + 3 * 2 * plane;
+  size_t tgv = regularizer == FS_REG_TGV ? 8 * plane : 0;   // v, vbar, q
+  return plane8 + 7 * plane + 10 * splane + 3 * 2 * plane + tgv;
 }
 
 }  // namespace
@@ -542,6 +554,9 @@ fs_status fs_default_params(fs_params* out) {
   out->precond = 1;
   out->block_iters = 0;
   out->use_graph = 0;
+  out->regularizer = FS_REG_HUBER_TV;
+  out->alpha0 = 17.f;
+  out->alpha1 = 1.2f;
   return FS_OK;
 }
 
@@ -566,8 +581,12 @@ fs_status fs_internal_validate(const fs_calib cam[2], const fs_pose* pose, int W
     if (!(p.lambda > 0) || !(p.huber_eps >= 0) || !(p.du_max > 0) || !(p.beta >= 0) ||
         !(p.eta > 0) || !(p.theta >= 0 && p.theta <= 1) || p.block_iters < 0 ||
         p.block_iters > 8 || p.pd_schedule < 0 || p.pd_schedule > 1 || p.storage < 0 ||
-        p.storage > 2)
+        p.storage > 2 || p.regularizer < 0 || p.regularizer > 1)
       return fail(FS_EINVAL, "parameter out of range");
+    if (p.regularizer == FS_REG_TGV &&
+        (!(p.alpha0 >= 0) || !(p.alpha1 > 0) || !std::isfinite(p.alpha0) ||
+         !std::isfinite(p.alpha1) || p.storage != 0))
+      return fail(FS_EINVAL, "TGV needs alpha0 >= 0, alpha1 > 0 and FP32 storage");
   }
   size_t bytes = 0;
   return fs_state_bytes(W, H, levels, prm, &bytes);   // level sizes
@@ -611,7 +630,7 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     L.fy = cam[0].fy * sc;
     L.cx = (cam[0].cx + 0.5) * sc - 0.5;
     L.cy = (cam[0].cy + 0.5) * sc - 0.5;
-    bytes += level_bytes(L.P, L.H, p.storage);
+    bytes += level_bytes(L.P, L.H, p.storage, p.regularizer);
     int cv = pd_cluster_variant(L.W, L.H);
     L.cluster = (cv >= 0 && pd_cluster_fits(cv, L.W, L.H)) ? cv : -1;
   }
@@ -639,6 +658,10 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     for (SPlane* f : sp) { f->p = cur; cur += splane; }
     float2** f2[] = {&v.gamma, &v.w, &v.g};
     for (float2** f : f2) { *f = (float2*)cur; cur += 2 * plane; }
+    if (p.regularizer == FS_REG_TGV) {
+      float** ft[] = {&v.v1, &v.v2, &v.vb1, &v.vb2, &v.q11, &v.q12, &v.q21, &v.q22};
+      for (float** f : ft) { *f = (float*)cur; cur += plane; }
+    }
   }
   h->cfield = (float2*)cur;
   e = cudaMemsetAsync(h->arena, 0, bytes, h->stream);
@@ -669,14 +692,16 @@ fs_status fs_state_bytes(int W, int H, int levels, const fs_params* prm, size_t*
   if (levels < 1 || levels > kMaxLevels) return fail(FS_EINVAL, "levels must be in [1, %d]", kMaxLevels);
   if (W < 4 || H < 4 || W > 32768 || H > 32768) return fail(FS_EINVAL, "bad image size %dx%d", W, H);
   const int storage = prm ? prm->storage : 0;
-  if (storage < 0 || storage > 2) return fail(FS_EINVAL, "parameter out of range");
+  const int reg = prm ? prm->regularizer : 0;
+  if (storage < 0 || storage > 2 || reg < 0 || reg > 1)
+    return fail(FS_EINVAL, "parameter out of range");
   size_t bytes = 0;
   int lw = W, lh = H;
   for (int l = 0; l < levels; ++l) {
     if (l > 0) { lw = (lw + 1) / 2; lh = (lh + 1) / 2; }
     if (lw < 4 || lh < 4)
       return fail(FS_EINVAL, "level %d would be %dx%d (< 4x4): too many levels", l, lw, lh);
-    bytes += level_bytes((int)align_up((size_t)lw, 32), lh, storage);
+    bytes += level_bytes((int)align_up((size_t)lw, 32), lh, storage, reg);
   }
   bytes += align_up(align_up((size_t)W, 32) * H * sizeof(float2), 256);
   *out = bytes;
@@ -973,7 +998,7 @@ extern "C" fs_status fs_batch_destroy(fs_batch* b) {
 // planes in the level's storage (kind 2).
 struct BufLoc {
   int kind = 0, planes = 1;
-  float* f[2] = {nullptr, nullptr};
+  float* f[4] = {nullptr, nullptr, nullptr, nullptr};
   SPlane s[2] = {{nullptr}, {nullptr}};
 };
 
@@ -991,6 +1016,12 @@ static fs_status buffer_loc(fs_handle* h, int level, int buffer, BufLoc& b) {
     case FS_BUF_IU: b.kind = 2; b.s[0] = v.Iu; break;
     case FS_BUF_RHO0: b.kind = 2; b.s[0] = v.rho0; break;
     case FS_BUF_G: b.kind = 1; b.planes = 2; b.f[0] = (float*)v.g; break;
+    case FS_BUF_V: case FS_BUF_VBAR: case FS_BUF_Q:
+      if (!v.v1) return fail(FS_EINVAL, "buffer %d exists on TGV handles only", buffer);
+      if (buffer == FS_BUF_V) { b.planes = 2; b.f[0] = v.v1; b.f[1] = v.v2; }
+      else if (buffer == FS_BUF_VBAR) { b.planes = 2; b.f[0] = v.vb1; b.f[1] = v.vb2; }
+      else { b.planes = 4; b.f[0] = v.q11; b.f[1] = v.q12; b.f[2] = v.q21; b.f[3] = v.q22; }
+      break;
     default: return fail(FS_EINVAL, "buffer %d cannot be accessed this way", buffer);
   }
   return FS_OK;
@@ -1121,6 +1152,13 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
   fs_status s;
   if ((s = check_handle(h)) != FS_OK) return s;
   if (iters < 1) return fail(FS_EINVAL, "iters must be >= 1");
+  if (h->prm.regularizer == FS_REG_TGV) {   // one schedule only: nothing to choose
+    for (int l = 0; l < h->L; ++l) {
+      h->lv[l].tuned = -1;
+      if (choice) choice[l] = -1;
+    }
+    return FS_OK;
+  }
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   h->has_state = false;   // the trial runs overwrite every level's state
   cudaEvent_t e0, e1;

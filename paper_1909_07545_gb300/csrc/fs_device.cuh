@@ -294,7 +294,9 @@ struct LevelView {
   float *u, *ubar, *uw;
   SPlane p1, p2, Iu, rho0;
   float2 *w, *g;
-  float *u_alt, *ubar_alt;     // ping-pong copies for k_pd
+  float *u_alt, *ubar_alt;
+  // TGV-L1 (Eq. 10): v, vbar (2 planes each) and q (4), null otherwise
+  float *v1, *v2, *vb1, *vb2, *q11, *q12, *q21, *q22;     // ping-pong copies for k_pd
   SPlane p1_alt, p2_alt;
 };
 

@@ -31,6 +31,13 @@ cudaError_t launch_upsample(const LevelView& C, const LevelView& F, cudaStream_t
 cudaError_t launch_zero_state(const LevelView& L, cudaStream_t st);
 cudaError_t launch_warm_start(const LevelView& L, float du_max, cudaStream_t st);
 cudaError_t launch_continue(const LevelView& L, cudaStream_t st);
+
+// TGV-L1 (k_tgv.cu): n iterations of the dual then the primal launch; v,
+// vbar, q <- 0; vbar <- v at a warp's start.
+cudaError_t launch_tgv_iterations(const LevelView& L, const PDParams& pp, float alpha0,
+                                  float alpha1, int precond, int n, cudaStream_t st);
+cudaError_t launch_tgv_reset(const LevelView& L, cudaStream_t st);
+cudaError_t launch_tgv_warp_start(const LevelView& L, cudaStream_t st);
 cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond,
                           cudaStream_t st);
 cudaError_t launch_warp(const LevelView& L, cudaStream_t st);

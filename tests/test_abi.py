@@ -81,6 +81,12 @@ def test_host_side_validation(lib):
     prm = fsb.default_params(block_iters=9)
     st, msg = _create([EQ, EQ], prm=prm)
     assert st == -1 and "parameter" in msg
+    for bad in (dict(regularizer="tgv", storage="f16"), dict(regularizer="tgv", alpha1=0.0),
+                dict(regularizer="tgv", alpha0=-1.0), dict(regularizer=2)):
+        st, msg = _create([EQ, EQ], prm=fsb.default_params(**bad))
+        assert st == -1, bad
+    p = fsb.default_params()
+    assert p.regularizer == 0 and p.alpha0 == pytest.approx(17.0) and p.alpha1 == pytest.approx(1.2)
     h = ctypes.c_void_p()
     assert lib.fs_solve(None, None, None, None, 1, 1, None, None) == -1
     b = ctypes.c_void_p()
@@ -114,6 +120,10 @@ def test_state_bytes_counts_the_level_planes(lib):
         assert fsb.state_bytes(W, H, L, storage="bf16") < fsb.state_bytes(W, H, L)
     with pytest.raises(fsb.FsError):
         fsb.state_bytes(64, 64, 6)
+    # TGV-L1 adds v, vbar (2 planes each) and q (4) per level
+    extra = sum(8 * up(4 * up((64 + (1 << l) - 1) >> l, 32) * ((64 + (1 << l) - 1) >> l), 256)
+                for l in range(2))
+    assert fsb.state_bytes(64, 64, 2, regularizer="tgv") == expect(64, 64, 2, 4) + extra
 
 
 def test_server_config_validation(lib):

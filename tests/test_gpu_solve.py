@@ -81,6 +81,18 @@ def test_unified_model_pairs_match_oracle(models):
     s.close()
 
 
+def test_tgv_solve_matches_oracle(small):
+    # the paper's own regulariser, TGV-L1 (Eq. 10-11), through the whole
+    # method: 3 levels x 3 warps x 30 iterations
+    ref = _oracle(small, warps=3, iters=30, regularizer="tgv")
+    sens = oracle_sensitivity(small, ref, warps=3, iters=30, regularizer="tgv")
+    s = make_solver(small, regularizer="tgv", use_graph=1)
+    assert s.autotune(8) == [-1] * small["levels"]     # one schedule: nothing to tune
+    disp, depth = s.solve(small["I0"], small["I1"], 3, 30)
+    _compare(small, ref, disp, depth, sens)
+    s.close()
+
+
 @pytest.mark.parametrize("block", [1, 5, 8])
 def test_schedules_and_block_depths_are_identical(small, block):
     s1 = make_solver(small, block_iters=block, pd_schedule=1)

@@ -233,6 +233,57 @@ def test_pd_iterations_match_oracle(sched, block, small, ragged):
         s.close()
 
 
+@pytest.mark.parametrize("precond", [1, 0])
+def test_tgv_iterations_match_oracle(precond, small, ragged):
+    # the TGV-L1 primal-dual steps (Eq. 10-11) on loaded state, against the
+    # oracle's tgv_iteration with the GPU's own tensor and tau
+    for pair in (small, ragged):
+        rng = np.random.default_rng(31)
+        u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
+        H, W = pair["I0"].shape
+        v = rng.uniform(-0.3, 0.3, (2, H, W))
+        q = rng.uniform(-2.0, 2.0, (4, H, W))
+        s = make_solver(pair, regularizer="tgv", precond=precond)
+        u = _load_pd(s, pair, u, uw, p, Iu, rho0)
+        lv = gpu_level_data(s, 0)
+        M = lv["M"]
+        v = np.where(M, v, 0.0)
+        q = np.where(M, q, 0.0)
+        s.write(0, "V", v)
+        s.write(0, "VBAR", v)
+        s.write(0, "Q", q)
+        f32 = lambda a: np.float32(a).astype(np.float64)
+        _, tv, _, sq = oracle.tgv_steps(lv["a"], lv["b"], lv["c"], M, lv["m1"], lv["m2"],
+                                        bool(precond))
+        sig = np64(s.read(0, "STEPS"))[1]
+        if precond:
+            lv.update(tau_u=lv["tau"], tau_v=tv, sig_q=sq,
+                      sig_p=np.where(M, np.where(sig > 0, sig / (1 + sig), 1.0), 0.0))
+        else:
+            c = np.where(M, 1.0 / np.sqrt(12.0), 0.0)
+            lv.update(tau_u=c, tau_v=c, sig_q=c, sig_p=c)
+        st = dict(u=f32(u), ubar=f32(u), p1=f32(p[0]), p2=f32(p[1]), Iu=f32(Iu),
+                  rho0=f32(rho0), u_w=f32(uw), v1=f32(v[0]), v2=f32(v[1]), vb1=f32(v[0]),
+                  vb2=f32(v[1]), q11=f32(q[0]), q12=f32(q[1]), q21=f32(q[2]), q22=f32(q[3]))
+        prm = oracle_params(pair, regularizer="tgv", precond=bool(precond))
+        done = 0
+        for n in (1, 5, 12):
+            s.stage(0, "PD", n)
+            for _ in range(n):
+                oracle.tgv_iteration(st, lv, prm)
+            done += n
+            tol = 4e-6 * done
+            assert np.abs(np64(s.read(0, "U")) - st["u"]).max() < tol, done
+            gp = np64(s.read(0, "P"))
+            assert np.abs(gp[0] - st["p1"]).max() < tol and np.abs(gp[1] - st["p2"]).max() < tol
+            gv = np64(s.read(0, "V"))
+            assert np.abs(gv[0] - st["v1"]).max() < tol and np.abs(gv[1] - st["v2"]).max() < tol
+            gq = np64(s.read(0, "Q"))
+            for k, name in enumerate(("q11", "q12", "q21", "q22")):
+                assert np.abs(gq[k] - st[name]).max() < 4 * tol, name
+        s.close()
+
+
 @pytest.mark.parametrize("which", ["small", "ragged"])
 def test_pd_schedules_are_bit_exact(which, small, ragged):
     # the whole-level cluster schedule and temporal blocking at every depth
