@@ -604,6 +604,7 @@ def main():
     ms0, n0, px0 = per_level[0]
     achieved = PD_BYTES_PER_PX_ITER * px0 / (ms0 / 1000.0) / 1e9
     # the profiled traffic applies while level 0 runs at the profiled depth
+    # (on 64-wide tiles)
     l0_depth = tuned[0] if tuned else None
     traffic = PD_L0_DRAM_BYTES_PER_LAUNCH if l0_depth == PD_L0_PROFILED_DEPTH else None
     peaks, src = measured_peaks()
@@ -621,7 +622,9 @@ def main():
                    "iters": iters, "camera": "kannala_brandt f=320 fov=190",
                    "l2": "flushed between steps (256 MB write)",
                    "pd_schedule_per_level": (
-                       ["cluster" if c == 0 else f"blocking x{c}" for c in tuned]
+                       ["cluster" if c == 0 else
+                        f"blocking x{c} (64-wide tiles)" if c <= 8 else
+                        f"blocking x{c - 8} (32-wide tiles)" for c in tuned]
                        if tuned else "default (cluster <= 128 px, blocking 6 / 8 above)"),
                    "autotuned": bool(tuned), "graph": True,
                    "parallelism": f"replicas x{world}"},

@@ -83,10 +83,12 @@ fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
  * iterations (best of 3 after a warm-up, CUDA events on the handle's
  * stream) of each candidate -- the whole-level cluster schedule where the
  * level fits one cluster, and temporal blocking with 1..8 iterations per
- * launch -- and keeps the fastest for later solves when block_iters = 0 and
- * pd_schedule = 0.  choice (may be NULL) receives per level 0 = cluster or
- * the depth 1..8.  Overwrites the levels' state; synchronises the stream.
- * All candidates give identical results. */
+ * launch on 64-wide or on 32-wide tiles -- and keeps the fastest for later
+ * solves when block_iters = 0 and pd_schedule = 0.  choice (may be NULL)
+ * receives per level 0 = cluster, 1..8 = that depth on 64-wide tiles,
+ * 9..16 = depth (choice - 8) on 32-wide tiles, -1 = nothing to choose (TGV
+ * handles).  Overwrites the levels' state; synchronises the stream.  All
+ * candidates give identical results. */
 fs_status fs_autotune(fs_handle* h, int iters, int* choice);
 
 #ifdef __cplusplus

@@ -316,7 +316,8 @@ class Solver:
 
     def autotune(self, iters=20):
         """Pick the primal-dual schedule per level by timing (fs_autotune).
-        Returns per level 0 = cluster or the temporal-blocking depth."""
+        Returns per level 0 = cluster, 1..8 = temporal-blocking depth on
+        64-wide tiles, 9..16 = depth (value - 8) on 32-wide tiles."""
         out = (ctypes.c_int * 8)()
         _check(self.lib.fs_autotune(self.h, int(iters), out))
         return [out[l] for l in range(self.levels)]

@@ -59,6 +59,7 @@ struct HostLevel {
   double fx = 0, fy = 0, cx = 0, cy = 0;   // level calibration (camera 0)
   int cluster = -1;                         // whole-level cluster variant, -1 if none
   int tuned = -1;                           // autotuned choice: 0 cluster, 1..8 depth, -1 none
+  int tuned_variant = -1;                   // autotuned tile variant, -1: by size
   LevelView v{};
 };
 
@@ -349,7 +350,9 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
     return FS_OK;
   }
   int B = pd_block(h, l);
-  int variant = (L.W >= 128 && L.H >= 128) ? PD_TILE_64 : PD_TILE_32;
+  int variant = L.tuned_variant >= 0 && h->prm.block_iters <= 0
+                    ? L.tuned_variant
+                    : ((L.W >= 128 && L.H >= 128) ? PD_TILE_64 : PD_TILE_32);
   PDState A{L.v.u, L.v.ubar, L.v.p1, L.v.p2};
   PDState Bs{L.v.u_alt, L.v.ubar_alt, L.v.p1_alt, L.v.p2_alt};
   int nl = pd_launches(iters, B);
@@ -1169,11 +1172,16 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
   for (int l = 0; l < h->L && st == FS_OK; ++l) {
     HostLevel& L = h->lv[l];
     L.tuned = -1;
+    L.tuned_variant = -1;
     float best = 3.4e38f;
     int best_c = -1;
-    for (int cand = (L.cluster >= 0 ? 0 : 1); cand <= 8 && st == FS_OK; ++cand) {
+    // candidates: 0 = cluster; 1..8 = depth with 64-wide tiles; 9..16 =
+    // depth 1..8 with 32-wide tiles
+    for (int cand = (L.cluster >= 0 ? 0 : 1); cand <= 16 && st == FS_OK; ++cand) {
       h->prm.pd_schedule = cand == 0 ? 0 : 1;
-      h->prm.block_iters = cand == 0 ? saved_block : cand;
+      h->prm.block_iters = saved_block;
+      L.tuned = cand == 0 ? 0 : 1 + (cand - 1) % 8;
+      L.tuned_variant = cand == 0 ? -1 : (cand <= 8 ? PD_TILE_64 : PD_TILE_32);
       float t = 3.4e38f;
       for (int rep = 0; rep < 4 && st == FS_OK; ++rep) {   // first run warms up
         cudaError_t e = cudaEventRecord(e0, h->stream);
@@ -1187,7 +1195,8 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
       }
       if (st == FS_OK && t < best) { best = t; best_c = cand; }
     }
-    L.tuned = best_c;
+    L.tuned = best_c <= 0 ? best_c : 1 + (best_c - 1) % 8;
+    L.tuned_variant = best_c <= 0 ? -1 : (best_c <= 8 ? PD_TILE_64 : PD_TILE_32);
     if (choice) choice[l] = best_c;
   }
   h->prm.block_iters = saved_block;
