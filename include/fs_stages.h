@@ -91,6 +91,12 @@ fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
  * candidates give identical results. */
 fs_status fs_autotune(fs_handle* h, int iters, int* choice);
 
+/* Set the per-level schedule directly, in fs_autotune's encoding (one entry
+ * per level; -1 = the library default for that level), e.g. to reuse a
+ * tuning measured earlier.  FS_EINVAL for a value out of range or a cluster
+ * choice (0) on a level that does not fit one cluster. */
+fs_status fs_set_schedule(fs_handle* h, const int* choice);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1206,6 +1206,26 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
   return st;
 }
 
+extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (!choice) return fail(FS_EINVAL, "null schedule");
+  for (int l = 0; l < h->L; ++l) {
+    int c = choice[l];
+    if (c < -1 || c > 16) return fail(FS_EINVAL, "level %d: schedule %d out of range", l, c);
+    if (c == 0 && h->lv[l].cluster < 0)
+      return fail(FS_EINVAL, "level %d does not fit one thread-block cluster", l);
+  }
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  for (int l = 0; l < h->L; ++l) {
+    int c = choice[l];
+    HostLevel& L = h->lv[l];
+    L.tuned = c <= 0 ? c : 1 + (c - 1) % 8;
+    L.tuned_variant = c <= 0 ? -1 : (c <= 8 ? PD_TILE_64 : PD_TILE_32);
+  }
+  return FS_OK;
+}
+
 extern "C" fs_status fs_stage_depth(fs_handle* h, float* d_disp, float* d_depth) {
   fs_status s;
   if ((s = check_handle(h)) != FS_OK) return s;

@@ -6,8 +6,10 @@ primal-dual iterations of one level, on a seeded synthetic workload.
 
 Run from the repository root (it uses the ``synth`` scene generator).  No
 CUDA graph is used, so every kernel is a separate launch a profiler can
-select.  Prints the launch order of one frame so that ``ncu -s`` offsets
-can be computed.
+select.  In frame mode one untimed frame runs first (after the autotuner,
+with --autotune) and the profiled frames are bracketed by
+cudaProfilerStart / Stop, so ``ncu --profile-from-start off`` captures
+exactly those frames.
 """
 from __future__ import annotations
 
@@ -28,8 +30,13 @@ def main():
     ap.add_argument("--iters", type=int, default=100)
     ap.add_argument("--block-iters", type=int, default=0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--regularizer", default="huber_tv", choices=["huber_tv", "tgv"])
     ap.add_argument("--autotune", action="store_true",
                     help="fs_autotune the per-level schedule first (as bench.py does)")
+    ap.add_argument("--schedule", default=None,
+                    help="per-level schedule in fs_autotune's encoding, e.g. 7,8,15,16,16 "
+                         "(the choice bench.py reports; timing-based tuning under a "
+                         "profiler would see the profiler's overheads)")
     args = ap.parse_args()
     sys.path.insert(0, os.getcwd())
     import torch
@@ -41,22 +48,26 @@ def main():
         else synth.plain_small(args.seed)
     H, W = pair["I0"].shape
     s = Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, pair["levels"],
-               lam=pair["lam"], huber_eps=pair["eps"], block_iters=args.block_iters)
+               lam=pair["lam"], huber_eps=pair["eps"], block_iters=args.block_iters,
+               regularizer=args.regularizer)
     if args.autotune:
         print("autotuned schedule per level (0 = cluster, else blocking depth):",
               s.autotune(pair["iters"]))
+    if args.schedule:
+        s.set_schedule([int(v) for v in args.schedule.split(",")])
     I0 = torch.as_tensor(np.float32(pair["I0"]), device="cuda")
     I1 = torch.as_tensor(np.float32(pair["I1"]), device="cuda")
     if args.mode == "frame":
         L, warps, iters = pair["levels"], pair["warps"], pair["iters"]
+        s.solve(I0, I1, warps, iters)          # warm-up frame, outside the profiled range
+        torch.cuda.synchronize()
+        # with ncu --profile-from-start off only these frames are captured
+        torch.cuda.profiler.start()
         for _ in range(args.frames):
             s.solve(I0, I1, warps, iters)
         torch.cuda.synchronize()
-        B = args.block_iters or 4
-        n = (iters + B - 1) // B
-        n += n % 2
-        print(f"frame: {L} levels x {warps} warps x {n} k_pd launches; k_pd launches per "
-              f"level {warps * n}, before level 0: {(L - 1) * warps * n}")
+        torch.cuda.profiler.stop()
+        print(f"frame: {L} levels x {warps} warps x {iters} iterations, {args.frames} frame(s)")
     else:
         # state of a realistic warp at the chosen level, then the PD stage alone
         s.solve(I0, I1, 1, 10)

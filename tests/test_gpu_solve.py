@@ -252,3 +252,21 @@ def test_set_pose_equals_a_handle_created_with_that_pose():
     assert np.array_equal(np64(z1), np64(z2), equal_nan=True)
     s1.close()
     s2.close()
+
+
+def test_set_schedule_reproduces_a_tuned_schedule(small):
+    import paper_1909_07545_gb300 as fsb
+    s1 = make_solver(small)
+    choice = s1.autotune(iters=6)
+    s2 = make_solver(small)
+    s2.set_schedule(choice)
+    d1, _ = s1.solve(small["I0"], small["I1"], 2, 11)
+    d2, _ = s2.solve(small["I0"], small["I1"], 2, 11)
+    assert np.array_equal(np64(d1), np64(d2))
+    s2.set_schedule([9, 16, 1])                # every level on an explicit schedule
+    d3, _ = s2.solve(small["I0"], small["I1"], 2, 11)
+    assert np.array_equal(np64(d1), np64(d3))
+    with pytest.raises(fsb.FsError):
+        s2.set_schedule([17, -1, -1])
+    s1.close()
+    s2.close()
