@@ -555,9 +555,11 @@ def main():
         # the paper's own regulariser, TGV-L1 (Eq. 10-11): same frame, FP32
         x = Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, L, stream=stream,
                    lam=pair["lam"], huber_eps=pair["eps"], use_graph=1, regularizer="tgv")
+        tgv_sched = x.autotune(iters) if args.autotune else None
         ms = timed(lambda: x.solve(I0, I1, warps, iters, disp=disp, depth=depth), vsteps)
         variants["tgv_f32"] = {"value": job_rate(world, 1, ms), "unit": "frames/s",
-                               "ms_per_frame": ms}
+                               "ms_per_frame": ms,
+                               "schedule_per_level": tgv_sched or "default (blocking 4)"}
         x.close()
         if args.batch > 1:
             from paper_1909_07545_gb300 import Batch

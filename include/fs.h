@@ -95,9 +95,10 @@ typedef struct {
  * regularizer: FS_REG_HUBER_TV (0) = lambda |rho| + h_eps(T^1/2 grad u), the
  * first-order member of Eq. 10; FS_REG_TGV (1) = the paper's tensor-guided
  * TGV-L1 energy of Eq. 10, lambda |rho| + alpha1 |T^1/2 grad u - v| +
- * alpha0 |grad v| (alpha0 = 17, alpha1 = 1.2 in Sec. IV-C; huber_eps,
- * block_iters and pd_schedule do not apply), solved by the primal-dual
- * steps of Eq. 11 with diagonal preconditioning; FP32 storage only. */
+ * alpha0 |grad v| (alpha0 = 17, alpha1 = 1.2 in Sec. IV-C; huber_eps and
+ * pd_schedule do not apply; block_iters is the temporal-blocking depth, 0 =
+ * tuned or 4), solved by the primal-dual steps of Eq. 11 with diagonal
+ * preconditioning; FP32 storage only. */
 #define FS_REG_HUBER_TV 0
 #define FS_REG_TGV 1
 typedef struct {

@@ -86,9 +86,10 @@ fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
  * launch on 64-wide or on 32-wide tiles -- and keeps the fastest for later
  * solves when block_iters = 0 and pd_schedule = 0.  choice (may be NULL)
  * receives per level 0 = cluster, 1..8 = that depth on 64-wide tiles,
- * 9..16 = depth (choice - 8) on 32-wide tiles, -1 = nothing to choose (TGV
- * handles).  Overwrites the levels' state; synchronises the stream.  All
- * candidates give identical results. */
+ * 9..16 = depth (choice - 8) on 32-wide tiles.  On TGV handles the
+ * candidates are 0 = a dual and a primal launch per iteration and 1..8 =
+ * temporal-blocking depth.  Overwrites the levels' state; synchronises the
+ * stream.  All candidates give identical results. */
 fs_status fs_autotune(fs_handle* h, int iters, int* choice);
 
 /* Set the per-level schedule directly, in fs_autotune's encoding (one entry

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "fs.h"
+#include "pd_tgv_math.cuh"
 #include "fs_stages.h"
 #include "fs_kernels.h"
 
@@ -339,8 +340,10 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
   HostLevel& L = h->lv[l];
   PDParams pp{h->prm.lambda, h->prm.huber_eps, h->prm.theta};
   if (h->prm.regularizer == FS_REG_TGV) {
-    FS_LAUNCH("k_tgv", launch_tgv_iterations(L.v, pp, h->prm.alpha0, h->prm.alpha1,
-                                             h->prm.precond, iters, st));
+    TgvParams tp{h->prm.lambda, h->prm.theta, h->prm.alpha0, h->prm.alpha1, h->prm.precond};
+    // block_iters when set, else the tuned depth, else 4 (0 = launch per step)
+    int B = h->prm.block_iters > 0 ? h->prm.block_iters : (L.tuned >= 0 ? L.tuned : 4);
+    FS_LAUNCH("k_tgv", launch_tgv_iterations(L.v, tp, B, iters, st));
     return FS_OK;
   }
   if (use_cluster(h, l)) {
@@ -535,7 +538,8 @@ size_t level_bytes(int P, int H, int storage, int regularizer) {
   size_t plane = align_up((size_t)P * H * sizeof(float), 256);
   size_t splane = align_up((size_t)P * H * storage_size(storage), 256);
   size_t plane8 = align_up((size_t)P * H, 256);
-  size_t tgv = regularizer == FS_REG_TGV ? 8 * plane : 0;   // v, vbar, q
+  // v, vbar, q and the alternate set of the 12 TGV state planes
+  size_t tgv = regularizer == FS_REG_TGV ? 20 * plane : 0;
   return plane8 + 7 * plane + 10 * splane + 3 * 2 * plane + tgv;
 }
 
@@ -664,6 +668,7 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     if (p.regularizer == FS_REG_TGV) {
       float** ft[] = {&v.v1, &v.v2, &v.vb1, &v.vb2, &v.q11, &v.q12, &v.q21, &v.q22};
       for (float** f : ft) { *f = (float*)cur; cur += plane; }
+      for (int j = 0; j < 12; ++j) { v.tgv_alt[j] = (float*)cur; cur += plane; }
     }
   }
   h->cfield = (float2*)cur;
@@ -1155,13 +1160,6 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
   fs_status s;
   if ((s = check_handle(h)) != FS_OK) return s;
   if (iters < 1) return fail(FS_EINVAL, "iters must be >= 1");
-  if (h->prm.regularizer == FS_REG_TGV) {   // one schedule only: nothing to choose
-    for (int l = 0; l < h->L; ++l) {
-      h->lv[l].tuned = -1;
-      if (choice) choice[l] = -1;
-    }
-    return FS_OK;
-  }
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   h->has_state = false;   // the trial runs overwrite every level's state
   cudaEvent_t e0, e1;
@@ -1176,12 +1174,15 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
     float best = 3.4e38f;
     int best_c = -1;
     // candidates: 0 = cluster; 1..8 = depth with 64-wide tiles; 9..16 =
-    // depth 1..8 with 32-wide tiles
-    for (int cand = (L.cluster >= 0 ? 0 : 1); cand <= 16 && st == FS_OK; ++cand) {
+    // depth 1..8 with 32-wide tiles.  TGV: 0 = a launch per step, 1..8 =
+    // blocking depth.
+    const bool tgv = h->prm.regularizer == FS_REG_TGV;
+    const int first = tgv ? 0 : (L.cluster >= 0 ? 0 : 1), last = tgv ? 8 : 16;
+    for (int cand = first; cand <= last && st == FS_OK; ++cand) {
       h->prm.pd_schedule = cand == 0 ? 0 : 1;
       h->prm.block_iters = saved_block;
-      L.tuned = cand == 0 ? 0 : 1 + (cand - 1) % 8;
-      L.tuned_variant = cand == 0 ? -1 : (cand <= 8 ? PD_TILE_64 : PD_TILE_32);
+      L.tuned = (cand == 0 || tgv) ? cand : 1 + (cand - 1) % 8;
+      L.tuned_variant = (cand == 0 || tgv) ? -1 : (cand <= 8 ? PD_TILE_64 : PD_TILE_32);
       float t = 3.4e38f;
       for (int rep = 0; rep < 4 && st == FS_OK; ++rep) {   // first run warms up
         cudaError_t e = cudaEventRecord(e0, h->stream);
@@ -1195,8 +1196,8 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
       }
       if (st == FS_OK && t < best) { best = t; best_c = cand; }
     }
-    L.tuned = best_c <= 0 ? best_c : 1 + (best_c - 1) % 8;
-    L.tuned_variant = best_c <= 0 ? -1 : (best_c <= 8 ? PD_TILE_64 : PD_TILE_32);
+    L.tuned = (best_c <= 0 || tgv) ? best_c : 1 + (best_c - 1) % 8;
+    L.tuned_variant = (best_c <= 0 || tgv) ? -1 : (best_c <= 8 ? PD_TILE_64 : PD_TILE_32);
     if (choice) choice[l] = best_c;
   }
   h->prm.block_iters = saved_block;
@@ -1210,18 +1211,20 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
   fs_status s;
   if ((s = check_handle(h)) != FS_OK) return s;
   if (!choice) return fail(FS_EINVAL, "null schedule");
+  const bool tgv = h->prm.regularizer == FS_REG_TGV;
   for (int l = 0; l < h->L; ++l) {
     int c = choice[l];
-    if (c < -1 || c > 16) return fail(FS_EINVAL, "level %d: schedule %d out of range", l, c);
-    if (c == 0 && h->lv[l].cluster < 0)
+    if (c < -1 || c > (tgv ? 8 : 16))
+      return fail(FS_EINVAL, "level %d: schedule %d out of range", l, c);
+    if (c == 0 && !tgv && h->lv[l].cluster < 0)
       return fail(FS_EINVAL, "level %d does not fit one thread-block cluster", l);
   }
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   for (int l = 0; l < h->L; ++l) {
     int c = choice[l];
     HostLevel& L = h->lv[l];
-    L.tuned = c <= 0 ? c : 1 + (c - 1) % 8;
-    L.tuned_variant = c <= 0 ? -1 : (c <= 8 ? PD_TILE_64 : PD_TILE_32);
+    L.tuned = (c <= 0 || tgv) ? c : 1 + (c - 1) % 8;
+    L.tuned_variant = (c <= 0 || tgv) ? -1 : (c <= 8 ? PD_TILE_64 : PD_TILE_32);
   }
   return FS_OK;
 }

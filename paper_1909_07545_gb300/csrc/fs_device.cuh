@@ -295,8 +295,11 @@ struct LevelView {
   SPlane p1, p2, Iu, rho0;
   float2 *w, *g;
   float *u_alt, *ubar_alt;
-  // TGV-L1 (Eq. 10): v, vbar (2 planes each) and q (4), null otherwise
-  float *v1, *v2, *vb1, *vb2, *q11, *q12, *q21, *q22;     // ping-pong copies for k_pd
+  // TGV-L1 (Eq. 10): v, vbar (2 planes each) and q (4), null otherwise,
+  // and an alternate set of the 12 state planes (u, ubar, v1, v2, vb1, vb2,
+  // p1, p2, q11, q12, q21, q22) for the temporally blocked kernel
+  float *v1, *v2, *vb1, *vb2, *q11, *q12, *q21, *q22;
+  float* tgv_alt[12];     // ping-pong copies for k_pd
   SPlane p1_alt, p2_alt;
 };
 

@@ -32,10 +32,12 @@ cudaError_t launch_zero_state(const LevelView& L, cudaStream_t st);
 cudaError_t launch_warm_start(const LevelView& L, float du_max, cudaStream_t st);
 cudaError_t launch_continue(const LevelView& L, cudaStream_t st);
 
-// TGV-L1 (k_tgv.cu): n iterations of the dual then the primal launch; v,
-// vbar, q <- 0; vbar <- v at a warp's start.
-cudaError_t launch_tgv_iterations(const LevelView& L, const PDParams& pp, float alpha0,
-                                  float alpha1, int precond, int n, cudaStream_t st);
+// TGV-L1 (k_tgv.cu): n iterations, with B = 0 as a dual and a primal launch
+// each, else temporally blocked with at most B (1..8) per launch (identical
+// results); v, vbar, q <- 0; vbar <- v at a warp's start.
+struct TgvParams;
+cudaError_t launch_tgv_iterations(const LevelView& L, const TgvParams& tp, int B, int n,
+                                  cudaStream_t st);
 cudaError_t launch_tgv_reset(const LevelView& L, cudaStream_t st);
 cudaError_t launch_tgv_warp_start(const LevelView& L, cudaStream_t st);
 cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond,

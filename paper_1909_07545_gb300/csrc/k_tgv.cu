@@ -3,130 +3,248 @@
 //
 //   E(u, v) = lam |rho_bar(u)| + alpha1 |T^1/2 grad u - v| + alpha0 |grad v|
 //
-// with v a vector field and grad v its 2 x 2 Jacobian.  One iteration is two
-// launches over the level, the dual ascent then the primal descent; every
-// pixel reads its own and its right / lower (dual) or left / upper (primal)
-// neighbours, so the two launches need no other synchronisation:
-//
-//   p    <- Pi_alpha1(p + sigma_p (T^1/2 grad ubar - vbar))
-//   q    <- Pi_alpha0(q + sigma_q grad vbar)
-//   u    <- shrink(u + tau_u div(T^1/2 p))                    (Eq. 13)
-//   v    <- v + tau_v (p + div q)
-//   ubar <- u' + theta (u' - u),   vbar <- v' + theta (v' - v)
-//
-// Pi_r projects a pixel's vector onto the ball of radius r (Euclidean for p,
-// Frobenius for q): the consistent saddle point of Eq. 10 (Eq. 11 prints the
-// weights inside unit-ball projections of the dual steps only).  Steps
-// (Pock-Chambolle 2011 diagonal preconditioning on the entrywise bound of
-// the block operator (T^1/2 grad u - v, grad v)): tau_u is the Huber-TV
-// tau; sigma_p = 1 / (max row sum of |T^1/2| |grad| + 1), which is
-// sigma / (1 + sigma) of the stored Huber-TV sigma; sigma_q = 1/2;
-// tau_v = 1 / (1 + the active forward differences touching the pixel); all 0
-// outside the FOV mask, where u, v, p and q stay put.  precond = 0 uses
-// 1/sqrt(12) for all four.
+// The per-pixel steps are in pd_tgv_math.cuh.  Two schedules compute them
+// with identical arithmetic:
+//   * launch per step: a dual launch then a primal launch per iteration,
+//     state in place (each pixel reads its right / lower neighbours in the
+//     dual and its left / upper ones in the primal, so the launch boundary is
+//     the only synchronisation needed);
+//   * temporal blocking (k_tgv_blocked): a CTA keeps a 32 x 32 footprint's
+//     whole state (u, ubar, v, vbar, p, q: 12 values per pixel) in registers
+//     for n <= B iterations, exchanging ubar, vbar and the masked products
+//     T^1/2 p and q with its neighbours through shared memory; the outer B
+//     pixels of the footprint are halo, recomputed by the neighbouring CTAs.
+//     State ping-pongs between the level's planes and an alternate set, and
+//     a warp runs an even number of launches so that it ends in the level's
+//     planes.
+// Steps (Pock-Chambolle 2011 diagonal preconditioning of the block operator
+// (T^1/2 grad u - v, grad v), in tgv_const): tau_u the Huber-TV tau; sigma_p
+// = 1 / (max row sum of |T^1/2| |grad| + 1) from the stored Huber-TV sigma;
+// sigma_q = 1/2; tau_v = 1 / (1 + the active differences touching the
+// pixel); all 0 off the FOV mask, where nothing moves.
 #include "fs_kernels.h"
+#include "pd_tgv_math.cuh"
 
 namespace fs {
 
 namespace {
 
-__device__ __forceinline__ float ball(float n2, float r) {
-  // scale that projects a vector of squared norm n2 onto the ball of radius r
-  return n2 > r * r ? r * rsqrtf(n2) : 1.f;
+__device__ __forceinline__ void load_const(const LevelView& L, size_t i, int x, int y,
+                                           const TgvParams& tp, TgvConst& c) {
+  const unsigned m = L.mask[i];
+  const unsigned ml = x > 0 ? L.mask[i - 1] : 0u;
+  const unsigned mu = y > 0 ? L.mask[i - L.P] : 0u;
+  tgv_const(m, ml, mu, sld<ST_F32>(L.sx, i), sld<ST_F32>(L.sy, i), L.sig[i], L.tau[i],
+            sld<ST_F32>(L.Iu, i), sld<ST_F32>(L.rho0, i), L.uw[i], tp, c);
 }
 
-// T^1/2 p at pixel k with its mask bits (the masked products of px_dual).
-__device__ __forceinline__ void t_half_p(const LevelView& L, size_t k, unsigned m, float& t1,
-                                         float& t2) {
+// t = T^1/2 p and the masked q of pixel k (what tgv_px_dual returns).
+__device__ __forceinline__ void masked_products(const LevelView& L, size_t k, unsigned m,
+                                                float& t1, float& t2, float& qx1, float& qx2,
+                                                float& qy1, float& qy2) {
   const float sx = sld<ST_F32>(L.sx, k), sy = sld<ST_F32>(L.sy, k);
   const float p1 = sld<ST_F32>(L.p1, k), p2 = sld<ST_F32>(L.p2, k);
   const float dp = fmaf(sx, p1, __fmul_rn(sy, p2));
-  t1 = (m & MASK_GX) ? fmaf(-sx, dp, p1) : 0.f;
-  t2 = (m & MASK_GY) ? fmaf(-sy, dp, p2) : 0.f;
+  const bool gx = m & MASK_GX, gy = m & MASK_GY;
+  t1 = gx ? fmaf(-sx, dp, p1) : 0.f;
+  t2 = gy ? fmaf(-sy, dp, p2) : 0.f;
+  qx1 = gx ? L.q11[k] : 0.f;
+  qx2 = gx ? L.q21[k] : 0.f;
+  qy1 = gy ? L.q12[k] : 0.f;
+  qy2 = gy ? L.q22[k] : 0.f;
 }
-
-constexpr float kScalarStep = 0.28867513459481287f;   // 1 / sqrt(12)
 
 }  // namespace
 
-__global__ void k_tgv_dual(LevelView L, float alpha0, float alpha1, int precond) {
+__global__ void k_tgv_dual(LevelView L, TgvParams tp) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
   const size_t i = (size_t)y * L.P + x;
   const unsigned m = L.mask[i];
   if (!(m & MASK_IN)) return;
+  TgvConst c;
+  load_const(L, i, x, y, tp, c);
   const bool gx = m & MASK_GX, gy = m & MASK_GY;
-  const float sg = L.sig[i];
-  const float sp = precond ? (sg > 0.f ? __fdiv_rn(sg, 1.f + sg) : 1.f) : kScalarStep;
-  const float sq = precond ? 0.5f : kScalarStep;
-  // p: T^1/2 grad ubar - vbar
-  const float ub = L.ubar[i];
-  const float g1 = gx ? __fsub_rn(L.ubar[i + 1], ub) : 0.f;
-  const float g2 = gy ? __fsub_rn(L.ubar[i + L.P], ub) : 0.f;
-  const float sx = sld<ST_F32>(L.sx, i), sy = sld<ST_F32>(L.sy, i);
-  const float d = fmaf(sx, g1, __fmul_rn(sy, g2));
-  const float vb1 = L.vb1[i], vb2 = L.vb2[i];
-  float p1 = fmaf(sp, __fsub_rn(fmaf(-sx, d, g1), vb1), sld<ST_F32>(L.p1, i));
-  float p2 = fmaf(sp, __fsub_rn(fmaf(-sy, d, g2), vb2), sld<ST_F32>(L.p2, i));
-  const float sp_ = ball(fmaf(p1, p1, __fmul_rn(p2, p2)), alpha1);
-  sst<ST_F32>(L.p1, i, __fmul_rn(p1, sp_));
-  sst<ST_F32>(L.p2, i, __fmul_rn(p2, sp_));
-  // q: grad vbar (Jacobian rows dv1, dv2)
-  const float j11 = gx ? __fsub_rn(L.vb1[i + 1], vb1) : 0.f;
-  const float j12 = gy ? __fsub_rn(L.vb1[i + L.P], vb1) : 0.f;
-  const float j21 = gx ? __fsub_rn(L.vb2[i + 1], vb2) : 0.f;
-  const float j22 = gy ? __fsub_rn(L.vb2[i + L.P], vb2) : 0.f;
-  float q11 = fmaf(sq, j11, L.q11[i]), q12 = fmaf(sq, j12, L.q12[i]);
-  float q21 = fmaf(sq, j21, L.q21[i]), q22 = fmaf(sq, j22, L.q22[i]);
-  const float n2 = fmaf(q11, q11, fmaf(q12, q12, fmaf(q21, q21, __fmul_rn(q22, q22))));
-  const float sc = alpha0 > 0.f ? ball(n2, alpha0) : 0.f;
-  L.q11[i] = __fmul_rn(q11, sc);
-  L.q12[i] = __fmul_rn(q12, sc);
-  L.q21[i] = __fmul_rn(q21, sc);
-  L.q22[i] = __fmul_rn(q22, sc);
+  const size_t r = gx ? i + 1 : i, b = gy ? i + L.P : i;   // unread when masked
+  float p1 = sld<ST_F32>(L.p1, i), p2 = sld<ST_F32>(L.p2, i);
+  float q11 = L.q11[i], q12 = L.q12[i], q21 = L.q21[i], q22 = L.q22[i];
+  float t1, t2, qx1, qx2, qy1, qy2;
+  tgv_px_dual(m, L.ubar[i], L.ubar[r], L.ubar[b], L.vb1[i], L.vb1[r], L.vb1[b], L.vb2[i],
+              L.vb2[r], L.vb2[b], c, tp, p1, p2, q11, q12, q21, q22, t1, t2, qx1, qx2, qy1,
+              qy2);
+  sst<ST_F32>(L.p1, i, p1);
+  sst<ST_F32>(L.p2, i, p2);
+  L.q11[i] = q11;
+  L.q12[i] = q12;
+  L.q21[i] = q21;
+  L.q22[i] = q22;
 }
 
-__global__ void k_tgv_primal(LevelView L, float lam, float theta, int precond) {
+__global__ void k_tgv_primal(LevelView L, TgvParams tp) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
   const size_t i = (size_t)y * L.P + x;
   const unsigned m = L.mask[i];
   if (!(m & MASK_IN)) return;
-  const unsigned ml = x > 0 ? L.mask[i - 1] : 0u;
-  const unsigned mu = y > 0 ? L.mask[i - L.P] : 0u;
-  // u: div(T^1/2 p), then the L1 resolvent (Eq. 13) in its clamp form
-  float t1, t2, tl1 = 0.f, tl2, tu1, tu2 = 0.f;
-  t_half_p(L, i, m, t1, t2);
-  if (x > 0) t_half_p(L, i - 1, ml, tl1, tl2);
-  if (y > 0) t_half_p(L, i - L.P, mu, tu1, tu2);
-  const float dv = __fadd_rn(__fsub_rn(t1, tl1), __fsub_rn(t2, tu2));
-  const float u = L.u[i];
-  const float tau = precond ? L.tau[i] : kScalarStep;
-  const float uh = fmaf(tau, dv, u);
-  const float Iu = sld<ST_F32>(L.Iu, i), rho0 = sld<ST_F32>(L.rho0, i);
-  const float step = fabsf(__fmul_rn(__fmul_rn(tau, lam), Iu));
-  const float c0 = Iu != 0.f ? __fsub_rn(L.uw[i], __fdiv_rn(rho0, Iu)) : 0.f;
-  const float un = __fadd_rn(uh, fminf(fmaxf(__fsub_rn(c0, uh), -step), step));
-  L.u[i] = un;
-  L.ubar[i] = fmaf(theta, __fsub_rn(un, u), un);
-  // v: p + div q
-  const bool gx = m & MASK_GX, gy = m & MASK_GY;
-  const bool glx = ml & MASK_GX, guy = mu & MASK_GY;
-  const float d1 = __fadd_rn(__fsub_rn(gx ? L.q11[i] : 0.f, glx ? L.q11[i - 1] : 0.f),
-                             __fsub_rn(gy ? L.q12[i] : 0.f, guy ? L.q12[i - L.P] : 0.f));
-  const float d2 = __fadd_rn(__fsub_rn(gx ? L.q21[i] : 0.f, glx ? L.q21[i - 1] : 0.f),
-                             __fsub_rn(gy ? L.q22[i] : 0.f, guy ? L.q22[i - L.P] : 0.f));
-  const int cnt = (int)gx + (int)glx + (int)gy + (int)guy;
-  const float tv = precond ? __fdiv_rn(1.f, (float)(1 + cnt)) : kScalarStep;
-  const float v1 = L.v1[i], v2 = L.v2[i];
-  const float v1n = fmaf(tv, __fadd_rn(sld<ST_F32>(L.p1, i), d1), v1);
-  const float v2n = fmaf(tv, __fadd_rn(sld<ST_F32>(L.p2, i), d2), v2);
-  L.v1[i] = v1n;
-  L.v2[i] = v2n;
-  L.vb1[i] = fmaf(theta, __fsub_rn(v1n, v1), v1n);
-  L.vb2[i] = fmaf(theta, __fsub_rn(v2n, v2), v2n);
+  TgvConst c;
+  load_const(L, i, x, y, tp, c);
+  float t1, t2, qx1, qx2, qy1, qy2;
+  float t1_l = 0.f, t2_l, qx1_l = 0.f, qx2_l = 0.f, qy1_l, qy2_l;
+  float t1_u, t2_u = 0.f, qx1_u, qx2_u, qy1_u = 0.f, qy2_u = 0.f;
+  masked_products(L, i, m, t1, t2, qx1, qx2, qy1, qy2);
+  if (x > 0) masked_products(L, i - 1, L.mask[i - 1], t1_l, t2_l, qx1_l, qx2_l, qy1_l, qy2_l);
+  if (y > 0)
+    masked_products(L, i - L.P, L.mask[i - L.P], t1_u, t2_u, qx1_u, qx2_u, qy1_u, qy2_u);
+  float u = L.u[i], ub, v1 = L.v1[i], v2 = L.v2[i], vb1, vb2;
+  tgv_px_primal(t1, t1_l, t2, t2_u, qx1, qx1_l, qy1, qy1_u, qx2, qx2_l, qy2, qy2_u,
+                sld<ST_F32>(L.p1, i), sld<ST_F32>(L.p2, i), c, tp.theta, u, ub, v1, v2, vb1,
+                vb2);
+  L.u[i] = u;
+  L.ubar[i] = ub;
+  L.v1[i] = v1;
+  L.v2[i] = v2;
+  L.vb1[i] = vb1;
+  L.vb2[i] = vb2;
+}
+
+// One set of the 12 state planes of a TGV level.
+struct TgvState {
+  float* s[12];   // u, ubar, v1, v2, vb1, vb2, p1, p2, q11, q12, q21, q22
+};
+
+template <int FW, int NY, int R>
+__global__ void __launch_bounds__(FW * NY, 2)
+k_tgv_blocked(LevelView L, TgvState in, TgvState out, TgvParams tp, int B, int n_iters,
+              int chained) {
+  constexpr int FH = NY * R;
+  // neighbours' values: ubar, vbar (read by the dual from the right / below)
+  // and t, masked q (read by the primal from the left / above)
+  __shared__ float s_ub[FH][FW], s_vb1[FH][FW], s_vb2[FH][FW];
+  __shared__ float s_t1[FH][FW], s_t2[FH][FW];
+  __shared__ float s_qx1[FH][FW], s_qx2[FH][FW], s_qy1[FH][FW], s_qy2[FH][FW];
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int IW = FW - 2 * B, IH = FH - 2 * B;
+  const int ox = (int)blockIdx.x * IW - B;
+  const int oy = (int)blockIdx.y * IH - B;
+  const int gx = ox + tx;
+  const bool col_in = gx >= 0 && gx < L.W;
+
+  if (chained) cudaTriggerProgrammaticLaunchCompletion();
+
+  // constants (written before the chain; unconditional loads from clamped
+  // addresses, rows off the level made inert)
+  const int gxc = min(max(gx, 0), L.W - 1);
+  unsigned idx[R];
+  bool ok[R];
+  TgvConst c[R];
+  unsigned mb = 0;
+  {
+    // every load first, from clamped addresses (the left / upper neighbour
+    // of column / row 0 is read as the pixel itself and its bits dropped),
+    // then the constants: a thread's loads are all in flight together
+    float sx[R], sy[R], sg[R], ta[R], iu[R], r0[R], uw[R];
+    unsigned m[R], ml[R], mu[R];
+    const unsigned dl = gxc > 0 ? 1u : 0u;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int gy = oy + ty * R + r;
+      ok[r] = col_in && gy >= 0 && gy < L.H;
+      const int gyc = min(max(gy, 0), L.H - 1);
+      idx[r] = (unsigned)(gyc * L.P + gxc);
+      const unsigned du = gyc > 0 ? (unsigned)L.P : 0u;
+      sx[r] = sld<ST_F32>(L.sx, idx[r]);
+      sy[r] = sld<ST_F32>(L.sy, idx[r]);
+      sg[r] = L.sig[idx[r]];
+      ta[r] = L.tau[idx[r]];
+      iu[r] = sld<ST_F32>(L.Iu, idx[r]);
+      r0[r] = sld<ST_F32>(L.rho0, idx[r]);
+      uw[r] = L.uw[idx[r]];
+      m[r] = L.mask[idx[r]];
+      ml[r] = L.mask[idx[r] - dl];
+      mu[r] = L.mask[idx[r] - du];
+      if (!dl) ml[r] = 0u;
+      if (!du) mu[r] = 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const unsigned mm = ok[r] ? m[r] : 0u;
+      tgv_const(mm, ml[r], mu[r], sx[r], sy[r], sg[r], ta[r], iu[r], r0[r], uw[r], tp, c[r]);
+      mb |= mm << (3 * r);
+    }
+  }
+  if (chained) cudaGridDependencySynchronize();
+  float u[R], ub[R], v1[R], v2[R], vb1[R], vb2[R], p1[R], p2[R], q11[R], q12[R], q21[R],
+      q22[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const unsigned k = idx[r];
+    float a[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) a[j] = in.s[j][k];
+    const float z = ok[r] ? 1.f : 0.f;   // off the level: inert zeros
+    u[r] = a[0] * z; ub[r] = a[1] * z; v1[r] = a[2] * z; v2[r] = a[3] * z;
+    vb1[r] = a[4] * z; vb2[r] = a[5] * z; p1[r] = a[6] * z; p2[r] = a[7] * z;
+    q11[r] = a[8] * z; q12[r] = a[9] * z; q21[r] = a[10] * z; q22[r] = a[11] * z;
+    const int fy = ty * R + r;
+    s_ub[fy][tx] = ub[r];
+    s_vb1[fy][tx] = vb1[r];
+    s_vb2[fy][tx] = vb2[r];
+  }
+  __syncthreads();
+
+  const int txr = min(tx + 1, FW - 1), txl = max(tx - 1, 0);
+  float t1[R], t2[R], qx1[R], qx2[R], qy1[R], qy2[R];
+#pragma unroll 1
+  for (int it = 0; it < n_iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int fy = ty * R + r;
+      const int fb = min(fy + 1, FH - 1);
+      const float ub_b = (r + 1 < R) ? ub[r + 1] : s_ub[fb][tx];
+      const float vb1_b = (r + 1 < R) ? vb1[r + 1] : s_vb1[fb][tx];
+      const float vb2_b = (r + 1 < R) ? vb2[r + 1] : s_vb2[fb][tx];
+      tgv_px_dual(mb >> (3 * r), ub[r], s_ub[fy][txr], ub_b, vb1[r], s_vb1[fy][txr], vb1_b,
+                  vb2[r], s_vb2[fy][txr], vb2_b, c[r], tp, p1[r], p2[r], q11[r], q12[r],
+                  q21[r], q22[r], t1[r], t2[r], qx1[r], qx2[r], qy1[r], qy2[r]);
+      s_t1[fy][tx] = t1[r];
+      s_t2[fy][tx] = t2[r];
+      s_qx1[fy][tx] = qx1[r];
+      s_qx2[fy][tx] = qx2[r];
+      s_qy1[fy][tx] = qy1[r];
+      s_qy2[fy][tx] = qy2[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int fy = ty * R + r;
+      const int fu = max(fy - 1, 0);
+      const float t2_u = r > 0 ? t2[r - 1] : s_t2[fu][tx];
+      const float qy1_u = r > 0 ? qy1[r - 1] : s_qy1[fu][tx];
+      const float qy2_u = r > 0 ? qy2[r - 1] : s_qy2[fu][tx];
+      tgv_px_primal(t1[r], s_t1[fy][txl], t2[r], t2_u, qx1[r], s_qx1[fy][txl], qy1[r], qy1_u,
+                    qx2[r], s_qx2[fy][txl], qy2[r], qy2_u, p1[r], p2[r], c[r], tp.theta,
+                    u[r], ub[r], v1[r], v2[r], vb1[r], vb2[r]);
+      s_ub[fy][tx] = ub[r];
+      s_vb1[fy][tx] = vb1[r];
+      s_vb2[fy][tx] = vb2[r];
+    }
+    __syncthreads();
+  }
+
+  if (!col_in || tx < B || tx >= FW - B) return;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int fy = ty * R + r;
+    if (fy < B || fy >= FH - B || !ok[r]) continue;
+    const unsigned k = idx[r];
+    const float a[12] = {u[r], ub[r], v1[r], v2[r], vb1[r], vb2[r], p1[r], p2[r],
+                         q11[r], q12[r], q21[r], q22[r]};
+#pragma unroll
+    for (int j = 0; j < 12; ++j) out.s[j][k] = a[j];
+  }
 }
 
 // v, vbar, q <- 0 on a new level (and before a warm start), like p.
@@ -150,15 +268,70 @@ __global__ void k_tgv_warp_start(LevelView L) {
 }
 
 namespace {
+
 dim3 tgrid(int W, int H) { return dim3((W + 31) / 32, (H + 7) / 8); }
+
+TgvState primary(const LevelView& L) {
+  return TgvState{{L.u, L.ubar, L.v1, L.v2, L.vb1, L.vb2, (float*)L.p1.p, (float*)L.p2.p,
+                   L.q11, L.q12, L.q21, L.q22}};
+}
+
+TgvState alternate(const LevelView& L) {
+  TgvState s;
+  for (int j = 0; j < 12; ++j) s.s[j] = L.tgv_alt[j];
+  return s;
+}
+
+constexpr int kTgvFW = 32, kTgvNY = 8, kTgvR = 4;
+
+cudaError_t launch_blocked(const LevelView& L, const TgvState& in, const TgvState& out,
+                           const TgvParams& tp, int B, int n, bool chained, cudaStream_t st) {
+  const int IW = kTgvFW - 2 * B, IH = kTgvNY * kTgvR - 2 * B;
+  if (IW <= 0 || IH <= 0 || n < 0 || n > B) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((L.W + IW - 1) / IW, (L.H + IH - 1) / IH, 1);
+  cfg.blockDim = dim3(kTgvFW, kTgvNY, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_tgv_blocked<kTgvFW, kTgvNY, kTgvR>, L, in, out, tp, B, n,
+                            chained ? 1 : 0);
+}
+
 }  // namespace
 
-cudaError_t launch_tgv_iterations(const LevelView& L, const PDParams& pp, float alpha0,
-                                  float alpha1, int precond, int n, cudaStream_t st) {
-  const dim3 g = tgrid(L.W, L.H), b(32, 8);
-  for (int k = 0; k < n; ++k) {
-    k_tgv_dual<<<g, b, 0, st>>>(L, alpha0, alpha1, precond);
-    k_tgv_primal<<<g, b, 0, st>>>(L, pp.lam, pp.theta, precond);
+cudaError_t launch_tgv_iterations(const LevelView& L, const TgvParams& tp, int B, int n,
+                                  cudaStream_t st) {
+  if (B <= 0) {                       // a dual and a primal launch per iteration
+    const dim3 g = tgrid(L.W, L.H), b(32, 8);
+    for (int k = 0; k < n; ++k) {
+      k_tgv_dual<<<g, b, 0, st>>>(L, tp);
+      k_tgv_primal<<<g, b, 0, st>>>(L, tp);
+    }
+    return cudaGetLastError();
+  }
+  // temporal blocking: at most B iterations per launch, an even number of
+  // launches (when n >= 2) so that the state ends in the level's planes
+  int nl = (n + B - 1) / B;
+  if (nl % 2 == 1 && n >= 2) ++nl;
+  const TgvState A = primary(L), Bs = alternate(L);
+  for (int k = 0, done = 0; k < nl; ++k) {
+    int m = (n - done) / (nl - k);
+    if ((n - done) % (nl - k)) ++m;
+    cudaError_t e = launch_blocked(L, (k % 2 == 0) ? A : Bs, (k % 2 == 0) ? Bs : A, tp, B, m,
+                                   k > 0, st);
+    if (e != cudaSuccess) return e;
+    done += m;
+  }
+  if (nl % 2 == 1) {                  // a single launch: copy the state back
+    const size_t bytes = (size_t)L.P * L.H * sizeof(float);
+    for (int j = 0; j < 12; ++j) {
+      cudaError_t e = cudaMemcpyAsync(A.s[j], Bs.s[j], bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaGetLastError();
 }

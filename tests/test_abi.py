@@ -120,8 +120,9 @@ def test_state_bytes_counts_the_level_planes(lib):
         assert fsb.state_bytes(W, H, L, storage="bf16") < fsb.state_bytes(W, H, L)
     with pytest.raises(fsb.FsError):
         fsb.state_bytes(64, 64, 6)
-    # TGV-L1 adds v, vbar (2 planes each) and q (4) per level
-    extra = sum(8 * up(4 * up((64 + (1 << l) - 1) >> l, 32) * ((64 + (1 << l) - 1) >> l), 256)
+    # TGV-L1 adds v, vbar (2 planes each), q (4) and an alternate set of
+    # the 12 state planes per level
+    extra = sum(20 * up(4 * up((64 + (1 << l) - 1) >> l, 32) * ((64 + (1 << l) - 1) >> l), 256)
                 for l in range(2))
     assert fsb.state_bytes(64, 64, 2, regularizer="tgv") == expect(64, 64, 2, 4) + extra
 

@@ -285,6 +285,33 @@ def test_tgv_iterations_match_oracle(precond, small, ragged):
 
 
 @pytest.mark.parametrize("which", ["small", "ragged"])
+def test_tgv_schedules_are_bit_exact(which, small, ragged):
+    # a dual and a primal launch per iteration, and temporal blocking at
+    # several depths, compute the same per-pixel arithmetic
+    pair = small if which == "small" else ragged
+    H, W = pair["I0"].shape
+    outs = []
+    for block in (0, 1, 3, 4, 8):
+        rng = np.random.default_rng(32)
+        u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
+        v = rng.uniform(-0.3, 0.3, (2, H, W))
+        q = rng.uniform(-2.0, 2.0, (4, H, W))
+        s = make_solver(pair, regularizer="tgv")
+        _load_pd(s, pair, u, uw, p, Iu, rho0)
+        M = np64(s.read(0, "MASK")) > 0.5
+        s.write(0, "V", np.where(M, v, 0.0))
+        s.write(0, "VBAR", np.where(M, v, 0.0))
+        s.write(0, "Q", np.where(M, q, 0.0))
+        s.set_schedule([block] + [-1] * (pair["levels"] - 1))
+        s.stage(0, "PD", 17)
+        outs.append([np64(s.read(0, b)) for b in ("U", "UBAR", "P", "V", "VBAR", "Q")])
+        s.close()
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("which", ["small", "ragged"])
 def test_pd_schedules_are_bit_exact(which, small, ragged):
     # the whole-level cluster schedule and temporal blocking at every depth
     # compute the same per-pixel arithmetic: results must be identical
