@@ -159,29 +159,35 @@ def cpu_baseline(pair, target_s=15.0):
     return n * W * H / dt, n, dt
 
 
-def serve_leg(seed, seconds, rate, inflight, warm_mode=1, n_rigs=16, n_frames=3):
-    """Serving: Poisson arrivals from n_rigs moving rigs (sizes drawn from
-    640 / 1024 / 1280 px, each its own seeded Kannala-Brandt calibration,
-    relative pose and scene) through one fs_server; each rig's frames
-    warm-start from its previous result (3 warps x 50 iterations on the
-    finest level, continuing from the last u and w for warm_mode 1, from
-    the last disparity for 0; a rig's first frame is a cold 10 x 100 solve
-    over its pyramid).  Each rig renders n_frames consecutive frames of its path,
-    replayed forwards and backwards (0, 1, 2, 1, 0, ...) so the motion stays
-    smooth.  Returns the open-loop figures at the offered rate and the
-    saturated throughput (every rig's queue kept full)."""
-    import queue
-
-    import torch
-
+def render_rigs(seed, n_rigs=16, n_frames=3):
+    """The serving workload's rigs: sizes drawn from 640 / 1024 / 1280 px,
+    each its own seeded Kannala-Brandt calibration, relative pose and scene,
+    n_frames consecutive frames of its smooth path."""
     import synth
-    from paper_1909_07545_gb300 import Server
     rng = np.random.default_rng(1000 + seed)
     sizes = [int(v) for v in rng.choice([640, 1024, 1280], size=n_rigs)]
     t0 = time.perf_counter()
     rigs = [synth.rig_sequence(10000 * (seed + 1) + i, W, W, n_frames=n_frames)
             for i, W in enumerate(sizes)]
-    render_s = time.perf_counter() - t0
+    return rigs, sizes, time.perf_counter() - t0
+
+
+def serve_leg(rigs, sizes, seed, seconds, rate, inflight, warm_mode=1, storage="f32"):
+    """Serving: Poisson arrivals from the rigs through one fs_server; each
+    rig's frames warm-start from its previous result (3 warps x 50
+    iterations on the finest level, continuing from the last u and w for
+    warm_mode 1, from the last disparity for 0; a rig's first frame is a
+    cold 10 x 100 solve over its pyramid).  Each rig's frames are replayed
+    forwards and backwards (0, 1, 2, 1, 0, ...) so the motion stays smooth.
+    Returns the open-loop figures at the offered rate and the saturated
+    throughput (every rig's queue kept full)."""
+    import queue
+
+    import torch
+
+    from paper_1909_07545_gb300 import Server
+    n_rigs, n_frames = len(rigs), len(rigs[0]["frames"])
+    rng = np.random.default_rng(2000 + seed)
     srv = Server(budget_bytes=40 << 30, max_inflight=inflight, warps=3, iters=50,
                  cold_warps=10, cold_iters=100, warm_mode=warm_mode)
     ids = []
@@ -190,7 +196,7 @@ def serve_leg(seed, seconds, rate, inflight, warm_mode=1, n_rigs=16, n_frames=3)
     ring = 4                           # result buffers per rig
     for q, W in zip(rigs, sizes):
         ids.append(srv.add_rig(q["cam0"], q["cam1"], q["R"], q["t"], W, W, q["levels"],
-                               lam=q["lam"], huber_eps=q["eps"]))
+                               lam=q["lam"], huber_eps=q["eps"], storage=storage))
         frames.append([(torch.from_numpy(np.float32(a)).pin_memory(),
                         torch.from_numpy(np.float32(b)).pin_memory()) for a, b, _ in q["frames"]])
         outs.append([(torch.empty((W, W)).pin_memory(), torch.empty((W, W)).pin_memory())
@@ -263,7 +269,7 @@ def serve_leg(seed, seconds, rate, inflight, warm_mode=1, n_rigs=16, n_frames=3)
                     f"{[sizes.count(v) for v in sorted(set(sizes))]}), Kannala-Brandt 190 deg, "
                     f"warm start 3x50 on the finest level "
                     f"({'from the last u and w' if warm_mode == 1 else 'from the last disparity'}), "
-                    f"FP32",
+                    f"{storage} storage",
         "offered_per_s": rate, "seconds": seconds, "max_inflight": inflight,
         "requests": int(open_loop["completed"]), "failed": int(open_loop["failed"]),
         "frames_per_s": open_loop["frames_per_s"], "p50_ms": open_loop["p50_ms"],
@@ -274,7 +280,6 @@ def serve_leg(seed, seconds, rate, inflight, warm_mode=1, n_rigs=16, n_frames=3)
         "saturated_frames_per_s": sat["frames_per_s"], "saturated_requests": n_sat,
         "saturated_wall_s": sat_wall,
         "gpix_iter_s_at_offered": open_loop["frames_per_s"] * mean_px * 150 / 1e9,
-        "render_s": render_s,
     }
 
 
@@ -584,10 +589,16 @@ def main():
     if args.uneven_batch:
         uneven = uneven_batch_leg(replica_seed(args.seed, rank), stream, 3, 3)
 
-    serving = None
+    serving = serving_f16 = None
     if args.serve_seconds > 0:
-        serving = serve_leg(replica_seed(args.seed, rank), args.serve_seconds, args.serve_rate,
-                            args.serve_inflight, args.serve_warm_mode)
+        rigs, sizes, render_s = render_rigs(replica_seed(args.seed, rank))
+        serving = serve_leg(rigs, sizes, replica_seed(args.seed, rank), args.serve_seconds,
+                            args.serve_rate, args.serve_inflight, args.serve_warm_mode)
+        serving["render_s"] = render_s
+        # the same requests with FP16 storage (FP32 arithmetic)
+        serving_f16 = serve_leg(rigs, sizes, replica_seed(args.seed, rank), args.serve_seconds,
+                                args.serve_rate, args.serve_inflight, args.serve_warm_mode,
+                                storage="f16")
         if dist:
             fps_sum = torch.tensor([serving["frames_per_s"]], dtype=torch.float64, device="cuda")
             dist.all_reduce(fps_sum)
@@ -652,6 +663,9 @@ def main():
     line["set_pose_ms"] = set_pose_ms
     if serving is not None:
         line["serving"] = serving
+        line["serving_f16"] = {k: serving_f16[k] for k in
+                               ("workload", "frames_per_s", "p50_ms", "p99_ms", "max_ms",
+                                "saturated_frames_per_s", "requests", "failed")}
     if uneven is not None:
         line["uneven_batch"] = uneven
     line["e2e"] = {"value": world / e2e_s, "unit": "frames/s",
