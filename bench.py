@@ -66,7 +66,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -441,6 +441,8 @@ def main():
                    lam=pair["lam"], huber_eps=pair["eps"], use_graph=1,
                    block_iters=args.block_iters)
         tuned = s.autotune(iters) if args.autotune else None
+        # pixels inside each level's FOV mask (the pixels the method moves)
+        mask_px = [int((s.read(l, "MASK") > 0.5).sum().item()) for l in range(L)]
         I0 = torch.as_tensor(np.float32(pair["I0"]), device="cuda")
         I1 = torch.as_tensor(np.float32(pair["I1"]), device="cuda")
         disp = torch.empty((H, W), device="cuda")
@@ -645,6 +647,7 @@ def main():
                        "p99": float(np.percentile(step_ms, 99)),
                        "max": float(step_ms.max())},
         "gpix_iter_s": pxit_frame * fps / world / 1e9 * world,
+        "gpix_iter_s_in_mask": sum(mask_px) * warps * iters * fps / 1e9,
         "pd": {"ms_per_frame": pd_ms, "share_of_step": pd_ms / ms_per_step,
                "per_level_ms": [m / args.steps for m, _, _ in per_level]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -67,6 +67,15 @@ fs_status fs_stage_prerotate(fs_handle* h, const float* d_I1);
  * may be NULL. */
 fs_status fs_stage_depth(fs_handle* h, float* d_disp, float* d_depth);
 
+/* The linearised energy of the current state of `level` (Eq. 10 with the
+ * data term of Eq. 3, 5, the handle's regulariser), reduced on the GPU
+ * (warp shuffles, FP64 accumulation): out[0] = total, out[1] = data term
+ * lam sum_M |rho0 + I_u (u - u_w)|, out[2] = regulariser (Huber-TV:
+ * sum h_eps(T^1/2 grad u); TGV: alpha1 sum_M |T^1/2 grad u - v| + alpha0
+ * sum |grad v|), out[3] = the L1 residual sum_M |rho0 + I_u (u - u_w)|.
+ * Host output; synchronises the handle's stream. */
+fs_status fs_energy(fs_handle* h, int level, double out[4]);
+
 /* Kernel timing with CUDA events on the handle's stream.  While enabled,
  * every fs_solve records an event pair around the primal-dual launches of
  * each (level, warp); fs_timing_read synchronises the stream, folds the

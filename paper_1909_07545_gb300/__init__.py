@@ -38,7 +38,7 @@ EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_buffer_read", "fs_buffer_write", "fs_run_stage", "fs_stage_prerotate",
             "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc",
             "fs_batch_create", "fs_batch_solve", "fs_batch_set_finest_limit",
-            "fs_batch_destroy", "fs_autotune", "fs_set_schedule", "fs_state_bytes",
+            "fs_batch_destroy", "fs_autotune", "fs_set_schedule", "fs_energy", "fs_state_bytes",
             "fs_server_default_config", "fs_server_create", "fs_server_add_rig",
             "fs_server_submit", "fs_server_wait", "fs_server_drain", "fs_server_stats_read",
             "fs_server_evict_all", "fs_server_destroy"]
@@ -128,6 +128,7 @@ def load_library():
         "fs_batch_destroy": [_P],
         "fs_autotune": [_P, i, _P],
         "fs_set_schedule": [_P, _P],
+        "fs_energy": [_P, i, ctypes.POINTER(d)],
         "fs_state_bytes": [i, i, i, ctypes.POINTER(FsParams), ctypes.POINTER(ctypes.c_size_t)],
         "fs_server_default_config": [ctypes.POINTER(FsServerConfig)],
         "fs_server_create": [ctypes.POINTER(FsServerConfig), ctypes.POINTER(_P)],
@@ -322,6 +323,12 @@ class Solver:
         out = (ctypes.c_int * 8)()
         _check(self.lib.fs_autotune(self.h, int(iters), out))
         return [out[l] for l in range(self.levels)]
+
+    def energy(self, level=0):
+        """fs_energy: (total, data, regulariser, L1 residual) of a level's state."""
+        out = (ctypes.c_double * 4)()
+        _check(self.lib.fs_energy(self.h, int(level), out))
+        return tuple(out)
 
     def set_schedule(self, choice):
         """Set the per-level schedule in autotune()'s encoding (-1 = default)."""

@@ -227,6 +227,7 @@ struct fs_handle {
   double t_pxit[kMaxLevels] = {};
   // the finest level's u and w hold the result of the last solve
   bool has_state = false;
+  double* eacc = nullptr;                // fs_energy's 3 device accumulators
 };
 
 namespace {
@@ -843,6 +844,7 @@ fs_status fs_destroy(fs_handle* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->stage) cudaFree(h->stage);
+  if (h->eacc) cudaFree(h->eacc);
   if (h->arena) cudaFree(h->arena);
   delete h;
   return FS_OK;
@@ -1205,6 +1207,30 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
+}
+
+extern "C" fs_status fs_energy(fs_handle* h, int level, double out[4]) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (level < 0 || level >= h->L) return fail(FS_EINVAL, "level %d out of range", level);
+  if (!out) return fail(FS_EINVAL, "null output");
+  if (!h->eacc) {
+    cudaError_t e = cudaMalloc(&h->eacc, 3 * sizeof(double));
+    if (e != cudaSuccess) { h->eacc = nullptr; return fail(FS_ENOMEM, "energy accumulator: %s", cudaGetErrorString(e)); }
+  }
+  double acc[3];
+  FS_CUDA(cudaMemsetAsync(h->eacc, 0, sizeof(acc), h->stream));
+  const bool tgv = h->prm.regularizer == FS_REG_TGV;
+  FS_LAUNCH("k_energy", launch_energy(h->lv[level].v, h->prm.lambda, tgv ? 0.f : h->prm.huber_eps,
+                                      tgv ? 1 : 0, h->prm.alpha0, h->prm.alpha1, h->eacc,
+                                      h->stream));
+  FS_CUDA(cudaMemcpyAsync(acc, h->eacc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+  FS_CUDA(cudaStreamSynchronize(h->stream));
+  out[0] = acc[0] + acc[1];
+  out[1] = acc[0];
+  out[2] = acc[1];
+  out[3] = acc[2];
+  return FS_OK;
 }
 
 extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {

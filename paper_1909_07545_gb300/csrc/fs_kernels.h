@@ -39,6 +39,10 @@ struct TgvParams;
 cudaError_t launch_tgv_iterations(const LevelView& L, const TgvParams& tp, int B, int n,
                                   cudaStream_t st);
 cudaError_t launch_tgv_reset(const LevelView& L, cudaStream_t st);
+// Energy terms of a level summed into acc[0..2] (data, regulariser, L1
+// residual); acc must be zeroed first (k_energy.cu).
+cudaError_t launch_energy(const LevelView& L, float lam, float eps, int tgv, float alpha0,
+                          float alpha1, double* acc, cudaStream_t st);
 cudaError_t launch_tgv_warp_start(const LevelView& L, cudaStream_t st);
 cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond,
                           cudaStream_t st);

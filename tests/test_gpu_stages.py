@@ -311,6 +311,53 @@ def test_tgv_schedules_are_bit_exact(which, small, ragged):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("reg", ["huber_tv", "tgv"])
+def test_energy_reduction_matches_oracle(reg, small, ragged):
+    # fs_energy (warp-shuffle reduction on the GPU) against the oracle's
+    # energy of the same state, with the GPU's own tensor
+    for pair in (small, ragged):
+        rng = np.random.default_rng(41)
+        u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
+        H, W = pair["I0"].shape
+        s = make_solver(pair, regularizer=reg)
+        u = _load_pd(s, pair, u, uw, p, Iu, rho0)
+        lv = gpu_level_data(s, 0)
+        M = lv["M"]
+        f32 = lambda a: np.float32(a).astype(np.float64)
+        args = (f32(u), f32(uw), f32(Iu), f32(rho0), lv["a"], lv["b"], lv["c"], lv["m1"],
+                lv["m2"], M)
+        prm = oracle_params(pair, regularizer=reg)
+        if reg == "tgv":
+            v = np.where(M, rng.uniform(-0.3, 0.3, (2, H, W)), 0.0)
+            s.write(0, "V", v)
+            ref = oracle.tgv_energy(args[0], f32(v[0]), f32(v[1]), *args[1:], prm.lam,
+                                    prm.alpha0, prm.alpha1)
+        else:
+            ref = oracle.energy(*args, prm.lam, prm.eps)
+        total, data, regu, resid = s.energy(0)
+        assert abs(total - ref) <= 2e-5 * ref, (reg, total, ref)
+        assert abs(data - prm.lam * resid) <= 1e-6 * max(1.0, data)   # per-pixel FP32 products
+        s.close()
+
+
+def test_energy_descends_on_the_gpu(small):
+    # the GPU's iterations settle on a lower energy: with scalar steps the
+    # energy ends well below its start and stops rising once the iterates
+    # settle (Chambolle-Pock is not a descent method step by step)
+    rng = np.random.default_rng(42)
+    u, uw, p, Iu, rho0 = _pd_inputs(small, rng)
+    s = make_solver(small, precond=0)
+    _load_pd(s, small, u, uw, p * 0.0, Iu, rho0)
+    E = [s.energy(0)[0]]
+    for _ in range(60):
+        s.stage(0, "PD", 10)
+        E.append(s.energy(0)[0])
+    E = np.array(E)
+    assert E[-1] < 0.8 * E[0]
+    assert np.all(np.diff(E[30:]) <= 1e-5 * E[0])
+    s.close()
+
+
 @pytest.mark.parametrize("which", ["small", "ragged"])
 def test_pd_schedules_are_bit_exact(which, small, ragged):
     # the whole-level cluster schedule and temporal blocking at every depth
