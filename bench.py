@@ -638,8 +638,9 @@ def main():
                    "l2": "flushed between steps (256 MB write)",
                    "pd_schedule_per_level": (
                        ["cluster" if c == 0 else
-                        f"blocking x{c} (64-wide tiles)" if c <= 8 else
-                        f"blocking x{c - 8} (32-wide tiles)" for c in tuned]
+                        f"blocking x{c} (64x64 footprints)" if c <= 8 else
+                        f"blocking x{c - 8} (32x32 footprints)" if c <= 16 else
+                        f"blocking x{c - 16} (64x32 footprints)" for c in tuned]
                        if tuned else "default (cluster <= 128 px, blocking 6 / 8 above)"),
                    "autotuned": bool(tuned), "graph": True,
                    "parallelism": f"replicas x{world}"},

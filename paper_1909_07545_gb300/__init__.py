@@ -319,7 +319,8 @@ class Solver:
     def autotune(self, iters=20):
         """Pick the primal-dual schedule per level by timing (fs_autotune).
         Returns per level 0 = cluster, 1..8 = temporal-blocking depth on
-        64-wide tiles, 9..16 = depth (value - 8) on 32-wide tiles."""
+        64x64 footprints, 9..16 = depth (value - 8) on 32x32 footprints,
+        17..24 = depth (value - 16) on 64x32 footprints."""
         out = (ctypes.c_int * 8)()
         _check(self.lib.fs_autotune(self.h, int(iters), out))
         return [out[l] for l in range(self.levels)]

@@ -319,6 +319,15 @@ int pd_block(const fs_handle* h, int l) {
   return b > 8 ? 8 : b;
 }
 
+// A schedule choice of fs_autotune / fs_set_schedule: 0 = cluster (Huber-TV)
+// or a launch per step (TGV); 1..8, 9..16, 17..24 = blocking depth on 64 x 64,
+// 32 x 32, 64 x 32 footprints (TGV: 1..8 = depth); -1 = none.
+void decode_choice(int c, bool tgv, int& depth, int& variant) {
+  if (c <= 0 || tgv) { depth = c; variant = -1; return; }
+  depth = 1 + (c - 1) % 8;
+  variant = c <= 8 ? PD_TILE_64 : (c <= 16 ? PD_TILE_32 : PD_TILE_64x32);
+}
+
 // Whether level l runs the whole-level cluster schedule.
 bool use_cluster(const fs_handle* h, int l) {
   const HostLevel& L = h->lv[l];
@@ -1179,12 +1188,11 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
     // depth 1..8 with 32-wide tiles.  TGV: 0 = a launch per step, 1..8 =
     // blocking depth.
     const bool tgv = h->prm.regularizer == FS_REG_TGV;
-    const int first = tgv ? 0 : (L.cluster >= 0 ? 0 : 1), last = tgv ? 8 : 16;
+    const int first = tgv ? 0 : (L.cluster >= 0 ? 0 : 1), last = tgv ? 8 : 24;
     for (int cand = first; cand <= last && st == FS_OK; ++cand) {
       h->prm.pd_schedule = cand == 0 ? 0 : 1;
       h->prm.block_iters = saved_block;
-      L.tuned = (cand == 0 || tgv) ? cand : 1 + (cand - 1) % 8;
-      L.tuned_variant = (cand == 0 || tgv) ? -1 : (cand <= 8 ? PD_TILE_64 : PD_TILE_32);
+      decode_choice(cand, tgv, L.tuned, L.tuned_variant);
       float t = 3.4e38f;
       for (int rep = 0; rep < 4 && st == FS_OK; ++rep) {   // first run warms up
         cudaError_t e = cudaEventRecord(e0, h->stream);
@@ -1198,8 +1206,7 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
       }
       if (st == FS_OK && t < best) { best = t; best_c = cand; }
     }
-    L.tuned = (best_c <= 0 || tgv) ? best_c : 1 + (best_c - 1) % 8;
-    L.tuned_variant = (best_c <= 0 || tgv) ? -1 : (best_c <= 8 ? PD_TILE_64 : PD_TILE_32);
+    decode_choice(best_c, tgv, L.tuned, L.tuned_variant);
     if (choice) choice[l] = best_c;
   }
   h->prm.block_iters = saved_block;
@@ -1240,7 +1247,7 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
   const bool tgv = h->prm.regularizer == FS_REG_TGV;
   for (int l = 0; l < h->L; ++l) {
     int c = choice[l];
-    if (c < -1 || c > (tgv ? 8 : 16))
+    if (c < -1 || c > (tgv ? 8 : 24))
       return fail(FS_EINVAL, "level %d: schedule %d out of range", l, c);
     if (c == 0 && !tgv && h->lv[l].cluster < 0)
       return fail(FS_EINVAL, "level %d does not fit one thread-block cluster", l);
@@ -1249,8 +1256,7 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
   for (int l = 0; l < h->L; ++l) {
     int c = choice[l];
     HostLevel& L = h->lv[l];
-    L.tuned = (c <= 0 || tgv) ? c : 1 + (c - 1) % 8;
-    L.tuned_variant = (c <= 0 || tgv) ? -1 : (c <= 8 ? PD_TILE_64 : PD_TILE_32);
+    decode_choice(c, tgv, L.tuned, L.tuned_variant);
   }
   return FS_OK;
 }

@@ -34,7 +34,7 @@ namespace cg = cooperative_groups;
 namespace fs {
 
 template <int FW, int NY, int R, int S>
-__global__ void __launch_bounds__(FW * NY, 1)
+__global__ void __launch_bounds__(FW * NY, FW * NY >= 512 ? 1 : 2)
 k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int chained) {
   constexpr int FH = NY * R;
   __shared__ float s_ub[FH][FW];
@@ -286,6 +286,7 @@ static cudaError_t launch_pd_s(int variant, const LevelView& L, const PDState& i
   switch (variant) {
     case PD_TILE_64: return launch_pd_t<64, 8, 8, S>(L, in, out, pp, B, n, chained, st);
     case PD_TILE_32: return launch_pd_t<32, 8, 4, S>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_64x32: return launch_pd_t<64, 4, 8, S>(L, in, out, pp, B, n, chained, st);
     default: return cudaErrorInvalidValue;
   }
 }
