@@ -103,6 +103,9 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
   const int txr = min(tx + 1, FW - 1);
   const int txl = max(tx - 1, 0);
 
+  // a thread's own products stay in registers; shared memory carries t1 to
+  // the right-hand neighbour and the last row's t2 to the thread below
+  float t1r[R], t2r[R];
 #pragma unroll 1
   for (int it = 0; it < n_iters; ++it) {
 #pragma unroll
@@ -110,16 +113,18 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
       const int fy = ty * R + r;
       const float right = s_ub[fy][txr];
       const float below = (r + 1 < R) ? ub[r + 1] : s_ub[min(fy + 1, FH - 1)][tx];
-      float t1, t2;
-      px_dual(mb >> (3 * r), ub[r], right, below, c[r], p1[r], p2[r], t1, t2);
-      s_t1[fy][tx] = t1;
-      s_t2[fy][tx] = t2;
+      px_dual(mb >> (3 * r), ub[r], right, below, c[r], p1[r], p2[r], t1r[r], t2r[r]);
+      s_t1[fy][tx] = t1r[r];
+      if (r == R - 1) s_t2[fy][tx] = t2r[r];
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int fy = ty * R + r;
-      const float dv = px_div(s_t1[fy][tx], s_t1[fy][txl], s_t2[fy][tx], s_t2[max(fy - 1, 0)][tx]);
+      // the row above: this thread's previous row, or the last row of the
+      // thread above (the top row of the footprint is halo: its own value)
+      const float t2_up = r > 0 ? t2r[r - 1] : (ty > 0 ? s_t2[fy - 1][tx] : t2r[0]);
+      const float dv = px_div(t1r[r], s_t1[fy][txl], t2r[r], t2_up);
       const float un = px_primal(u[r], dv, c[r]);
       ub[r] = px_relax(un, u[r], theta);
       u[r] = un;
