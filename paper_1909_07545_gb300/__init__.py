@@ -1,10 +1,15 @@
 """GB300 non-rectified variational fisheye stereo (Roxas & Oishi) -- Python binding.
 
-Argument marshalling over the C ABI of ``libfs.so`` (``include/fs.h`` and
-``include/fs_stages.h``); every step of the method runs in the library's
-CUDA kernels.  PyTorch only supplies device memory and the CUDA stream.
-The library must have been built (``paper_1909_07545_gb300.build.build()``);
-without it, creating a solver raises instead of falling back to anything.
+Argument marshalling over the C ABI of ``libfs.so`` (``include/fs.h``,
+``include/fs_stages.h``, ``include/fs_server.h``); every step of the method
+runs in the library's CUDA kernels.  PyTorch only supplies device memory and
+the CUDA stream.  The library must have been built
+(``paper_1909_07545_gb300.build.build()``); without it, creating a solver
+raises instead of falling back to anything.
+
+    Solver   one rig: fs_create / fs_solve / fs_solve_continue / stages
+    Batch    many pairs in one CUDA graph (fs_batch_*)
+    Server   continuous-batching request server over many rigs (fs_server_*)
 """
 from __future__ import annotations
 
@@ -13,8 +18,8 @@ import os
 
 import numpy as np
 
-__all__ = ["Solver", "Batch", "FsError", "load_library", "default_params", "BUF", "STAGE",
-           "LIB_PATH", "EXPORTED"]
+__all__ = ["Solver", "Batch", "Server", "FsError", "load_library", "default_params",
+           "state_bytes", "BUF", "STAGE", "LIB_PATH", "EXPORTED"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfs.so")
 
