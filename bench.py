@@ -32,7 +32,7 @@ PD_BYTES_PER_PX_ITER = 52.0   # unblocked FP32 traffic of one pixel-iteration (9
 # DRAM bytes (read + write) of one level-0 k_pd launch of this workload at 7
 # iterations per launch, from one ncu capture of the current kernel (cold L2;
 # the command and figures are in profiles/k_pd_level0_kb1024.md)
-PD_L0_DRAM_BYTES_PER_LAUNCH = 47.6e6
+PD_L0_DRAM_BYTES_PER_LAUNCH = 47.5e6
 PD_L0_PROFILED_DEPTH = 7
 
 
