@@ -591,22 +591,18 @@ def main():
     if args.uneven_batch:
         uneven = uneven_batch_leg(replica_seed(args.seed, rank), stream, 3, 3)
 
+    # serving: one server on rank 0's GPU (the figures are per GPU; replicas
+    # would serve independent request streams)
     serving = serving_f16 = None
-    if args.serve_seconds > 0:
-        rigs, sizes, render_s = render_rigs(replica_seed(args.seed, rank))
-        serving = serve_leg(rigs, sizes, replica_seed(args.seed, rank), args.serve_seconds,
-                            args.serve_rate, args.serve_inflight, args.serve_warm_mode)
+    if args.serve_seconds > 0 and rank == 0:
+        rigs, sizes, render_s = render_rigs(args.seed)
+        serving = serve_leg(rigs, sizes, args.seed, args.serve_seconds, args.serve_rate,
+                            args.serve_inflight, args.serve_warm_mode)
         serving["render_s"] = render_s
+        serving["gpus"] = 1
         # the same requests with FP16 storage (FP32 arithmetic)
-        serving_f16 = serve_leg(rigs, sizes, replica_seed(args.seed, rank), args.serve_seconds,
-                                args.serve_rate, args.serve_inflight, args.serve_warm_mode,
-                                storage="f16")
-        if dist:
-            fps_sum = torch.tensor([serving["frames_per_s"]], dtype=torch.float64, device="cuda")
-            dist.all_reduce(fps_sum)
-            p99, = reduce_max([serving["p99_ms"]], dist, "cuda")
-            serving["frames_per_s_all_ranks"] = float(fps_sum.item())
-            serving["p99_ms_max_over_ranks"] = p99
+        serving_f16 = serve_leg(rigs, sizes, args.seed, args.serve_seconds, args.serve_rate,
+                                args.serve_inflight, args.serve_warm_mode, storage="f16")
 
     if rank != 0:
         if dist:
