@@ -55,7 +55,8 @@ typedef struct fs_server fs_server;
 typedef struct {
   size_t hbm_budget;     /* device bytes the rigs' resident state may hold in
                             total (fs_state_bytes of each handle plus 4 planes
-                            of W x H floats per rig); 0 = 40 GiB */
+                            of W x H floats per rig); 0 = 40 GiB; lowered at
+                            creation to the device's free memory less 1 GiB */
   int max_inflight;      /* requests on the GPU at once, >= 1 */
   int warps, iters;      /* warm-started request: warps x iterations on the
                             finest level */

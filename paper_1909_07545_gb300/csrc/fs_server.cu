@@ -358,6 +358,14 @@ fs_status fs_server_create(const fs_server_config* cfg, fs_server** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(FS_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  // never plan for more than the device has free now (less 1 GiB of headroom
+  // for the CUDA context, graphs and the callers' own buffers)
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+    const size_t headroom = (size_t)1 << 30;
+    const size_t avail = free_b > headroom ? free_b - headroom : 0;
+    if (c.hbm_budget > avail) c.hbm_budget = avail;
+  }
   fs_server* s = new (std::nothrow) fs_server();
   if (!s) return set_error(FS_ENOMEM, "host allocation failed");
   s->cfg = c;
