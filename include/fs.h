@@ -41,7 +41,8 @@ typedef enum {
   FS_ENOMEM = -2,    /* device allocation failed                             */
   FS_ECUDA = -3,     /* a CUDA call or kernel launch failed                  */
   FS_ECALIB = -4,    /* calibration rejected (e.g. non-monotone r(theta))    */
-  FS_ETIMEOUT = -5   /* a bounded device-side wait ran out                   */
+  FS_ETIMEOUT = -5,  /* a bounded wait ran out                               */
+  FS_ECANCELLED = -6 /* the request was cancelled before it ran (server)     */
 } fs_status;
 
 /* Radially symmetric camera models, pixel = c + f * r(theta) * (X, Y)/|(X, Y)|

@@ -76,6 +76,7 @@ typedef struct {
   long long failed;      /* of those, requests that failed */
   long long cold;        /* requests solved cold (first frame or after eviction) */
   long long evictions;   /* rig states freed to admit another rig */
+  long long cancelled;   /* requests cancelled before they ran */
   double p50_ms, p99_ms, max_ms, mean_ms;  /* latency of completed requests */
   double frames_per_s;   /* completed / (last completion - first submission) */
   size_t resident_bytes; /* device bytes of the resident rig states now */
@@ -113,6 +114,13 @@ fs_status fs_server_submit(fs_server* s, int rig, const float* h_I0, const float
  * forgets the request, and sets *latency_ms (may be NULL).  FS_ETIMEOUT if
  * it is still pending (it stays known); FS_EINVAL for an unknown id. */
 fs_status fs_server_wait(fs_server* s, long long req_id, double timeout_s, double* latency_ms);
+
+/* Cancel a request that is still queued: it will not run, and
+ * fs_server_wait returns FS_ECANCELLED for it.  FS_EINVAL for an unknown id
+ * or a request already on the GPU or done (it then completes normally).
+ * A cancelled warm request of a rig leaves that rig's state as it was, so
+ * the rig's next request continues from its last completed frame. */
+fs_status fs_server_cancel(fs_server* s, long long req_id);
 
 /* Wait until every submitted request has completed (timeout_s < 0: no
  * limit).  FS_ETIMEOUT if some are still pending. */

@@ -34,7 +34,7 @@ REGULARIZER = {"huber_tv": 0, "tgv": 1}
 STAGE = dict(DOWNSAMPLE=0, TENSOR=1, UPSAMPLE=2, WARP=3, PD=4, CLIP=5, TRAJECTORY=6, WARM=7)
 
 STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ENOMEM", -3: "FS_ECUDA", -4: "FS_ECALIB",
-          -5: "FS_ETIMEOUT"}
+          -5: "FS_ETIMEOUT", -6: "FS_ECANCELLED"}
 
 # every entry point declared in include/*.h
 EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
@@ -45,7 +45,8 @@ EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_batch_create", "fs_batch_solve", "fs_batch_set_finest_limit",
             "fs_batch_destroy", "fs_autotune", "fs_set_schedule", "fs_energy", "fs_state_bytes",
             "fs_server_default_config", "fs_server_create", "fs_server_add_rig",
-            "fs_server_submit", "fs_server_wait", "fs_server_drain", "fs_server_stats_read",
+            "fs_server_submit", "fs_server_wait", "fs_server_cancel", "fs_server_drain",
+            "fs_server_stats_read",
             "fs_server_evict_all", "fs_server_destroy"]
 
 
@@ -86,7 +87,8 @@ class FsServerConfig(ctypes.Structure):
 class FsServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
                 ("failed", ctypes.c_longlong), ("cold", ctypes.c_longlong),
-                ("evictions", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
+                ("evictions", ctypes.c_longlong), ("cancelled", ctypes.c_longlong),
+                ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("frames_per_s", ctypes.c_double),
                 ("resident_bytes", ctypes.c_size_t), ("peak_resident_bytes", ctypes.c_size_t)]
@@ -142,6 +144,7 @@ def load_library():
         "fs_server_submit": [_P, i, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_longlong)],
         "fs_server_wait": [_P, ctypes.c_longlong, d, ctypes.POINTER(d)],
         "fs_server_drain": [_P, d],
+        "fs_server_cancel": [_P, ctypes.c_longlong],
         "fs_server_stats_read": [_P, ctypes.POINTER(FsServerStats), i],
         "fs_server_evict_all": [_P],
         "fs_server_destroy": [_P],
@@ -516,6 +519,10 @@ class Server:
             self._held.pop(int(req), None)
         _check(st)
         return lat.value
+
+    def cancel(self, req):
+        """Cancel a request that is still queued (FsError if it already ran)."""
+        _check(self.lib.fs_server_cancel(self.s, int(req)))
 
     def drain(self, timeout=-1.0):
         _check(self.lib.fs_server_drain(self.s, float(timeout)))

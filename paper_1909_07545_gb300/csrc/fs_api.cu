@@ -11,6 +11,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fs.h"
 #include "pd_tgv_math.cuh"
 #include "fs_stages.h"
@@ -188,6 +190,14 @@ inline dim3 grid2(int W, int H) { return dim3((W + 31) / 32, (H + 7) / 8); }
 const dim3 kBlock2(32, 8);
 
 }  // namespace
+
+// Host-side NVTX range for profilers (a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Sets the thread's fs_last_error message for the other translation units.
 fs_status fs_internal_set_error(fs_status s, const char* msg) {
@@ -461,6 +471,7 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
                         int warps, int iters, float* disp, float* depth, cudaStream_t st,
                         cudaEvent_t finest_wait = nullptr, cudaEvent_t finest_done = nullptr,
                         bool cont = false) {
+  NvtxRange range(init || cont ? "fs warm solve" : "fs solve");
   fs_status s;
   HostLevel& L0 = h->lv[0];
   FS_LAUNCH("k_copy_in_s", launch_copy_in_I0(I0, L0.v, st));
@@ -496,6 +507,10 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
   for (int l = 0; l < top; ++l)
     if ((s = run_stage(h, l, FS_STAGE_DOWNSAMPLE, 0, st)) != FS_OK) return s;
   for (int l = top; l >= 0; --l) {
+    static const char* kLevelNames[] = {"fs level 0", "fs level 1", "fs level 2",
+                                        "fs level 3", "fs level 4", "fs level 5",
+                                        "fs level 6", "fs level 7"};
+    NvtxRange level_range(kLevelNames[l < 8 ? l : 7]);
     HostLevel& L = h->lv[l];
     if (l == 0 && finest_wait) FS_CUDA(cudaStreamWaitEvent(st, finest_wait, 0));
     if ((s = run_stage(h, l, FS_STAGE_TENSOR, 0, st)) != FS_OK) return s;

@@ -89,7 +89,7 @@ struct fs_server {
   std::thread worker;
   // statistics since the last reset
   std::vector<double> lat;
-  long long submitted = 0, completed = 0, failed = 0, cold = 0, evictions = 0;
+  long long submitted = 0, completed = 0, failed = 0, cold = 0, evictions = 0, cancelled = 0;
   bool have_first = false;
   Clock::time_point first_submit, last_done;
 };
@@ -466,6 +466,27 @@ fs_status fs_server_wait(fs_server* s, long long req_id, double timeout_s, doubl
   return FS_OK;
 }
 
+fs_status fs_server_cancel(fs_server* s, long long req_id) {
+  fs_status st;
+  if ((st = check_server(s)) != FS_OK) return st;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto kit = s->known.find(req_id);
+  if (kit == s->known.end()) return set_error(FS_EINVAL, "unknown request %lld", req_id);
+  auto it = std::find(s->pending.begin(), s->pending.end(), kit->second);
+  if (it == s->pending.end())
+    return set_error(FS_EINVAL, "request %lld is already on the GPU or done", req_id);
+  Request* r = *it;
+  s->pending.erase(it);
+  r->status = FS_ECANCELLED;
+  r->msg = "cancelled before it ran";
+  r->t_done = Clock::now();
+  r->done = true;
+  ++s->cancelled;
+  s->cv_done.notify_all();
+  s->cv_work.notify_one();
+  return FS_OK;
+}
+
 fs_status fs_server_drain(fs_server* s, double timeout_s) {
   fs_status st;
   if ((st = check_server(s)) != FS_OK) return st;
@@ -490,6 +511,7 @@ fs_status fs_server_stats_read(fs_server* s, fs_server_stats* out, int reset) {
   out->failed = s->failed;
   out->cold = s->cold;
   out->evictions = s->evictions;
+  out->cancelled = s->cancelled;
   out->resident_bytes = s->resident;
   out->peak_resident_bytes = s->peak;
   if (!s->lat.empty()) {
@@ -511,7 +533,7 @@ fs_status fs_server_stats_read(fs_server* s, fs_server_stats* out, int reset) {
   }
   if (reset) {
     s->lat.clear();
-    s->submitted = s->completed = s->failed = s->cold = s->evictions = 0;
+    s->submitted = s->completed = s->failed = s->cold = s->evictions = s->cancelled = 0;
     s->have_first = false;
     s->peak = s->resident;
   }

@@ -212,3 +212,35 @@ def test_served_16bit_chain_is_as_close_as_the_storage_allows(kind, rigs):
         print(rep)
         assert ge.mean() <= 3 * pe.mean(), rep
         assert np.quantile(ge, 0.99) <= 3 * np.quantile(pe, 0.99), rep
+
+
+def test_cancelled_request_does_not_run(rigs):
+    # a queued request can be cancelled; the rig's next request then
+    # continues from its last completed frame, as if the cancelled one had
+    # never been submitted
+    import paper_1909_07545_gb300 as fsb
+    q = rigs[0]
+    srv = _server(max_inflight=1)
+    r = _add(srv, q)
+    frames = [q["frames"][k] for k in (0, 1, 2, 0)]
+    outs = [_outs(q) for _ in frames]
+    ids = [srv.submit(r, _pinned(I0), _pinned(I1), d, z) for (I0, I1, _), (d, z) in
+           zip(frames, outs)]
+    srv.cancel(ids[2])                         # the rig is still busy with the first two
+    with pytest.raises(fsb.FsError):
+        srv.cancel(ids[2])                     # no longer queued
+    for k, x in enumerate(ids):
+        if k == 2:
+            with pytest.raises(fsb.FsError) as e:
+                srv.wait(x)
+            assert e.value.status == -6
+        else:
+            srv.wait(x)
+    st = srv.stats()
+    assert st["cancelled"] == 1 and st["completed"] == 3 and st["failed"] == 0
+    srv.close()
+    # the same frames without the cancelled one, through one handle
+    kept = dict(q, frames=[frames[0], frames[1], frames[3]])
+    chain = _lone_chain(kept)
+    for got, ref in zip([outs[0], outs[1], outs[3]], chain):
+        assert np.array_equal(got[0].numpy().astype(np.float64), ref[0])

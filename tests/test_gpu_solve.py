@@ -81,6 +81,20 @@ def test_unified_model_pairs_match_oracle(models):
     s.close()
 
 
+def test_tiny_odd_sized_pair_matches_oracle():
+    # 37 x 29: a single partial tile per level, ragged on both axes
+    p = f32pair(synth.plain_small(6, W=37, H=29))
+    ref = _oracle(p, levels=2, warps=3, iters=25)
+    sens = oracle_sensitivity(p, ref, levels=2, warps=3, iters=25)
+    s = make_solver(p, levels=2)
+    disp, depth = s.solve(p["I0"], p["I1"], 3, 25)
+    d = np64(disp)
+    assert np.all(d[~ref["mask"]] == 0.0)
+    ok, rep = disparity_parity(d, ref, sens)     # disparities here are below a pixel
+    assert ok, rep
+    s.close()
+
+
 def test_tgv_solve_matches_oracle(small):
     # the paper's own regulariser, TGV-L1 (Eq. 10-11), through the whole
     # method: 3 levels x 3 warps x 30 iterations
