@@ -336,6 +336,10 @@ __global__ void k_depth(LevelView L, DevCam cam, float Cx, float Cy, float Cz,
   if (!depth) return;
   if (!in) { depth[o] = __int_as_float(0x7fc00000); return; }
   float2 w = L.w[i];
+  if (w.x == 0.f && w.y == 0.f) {   // no displacement: the rays coincide, range +inf
+    depth[o] = __int_as_float(0x7f800000);
+    return;
+  }
   Ray r0 = cam_unproject(cam, (float)x, (float)y);
   Ray r1 = cam_unproject(cam, (float)x + w.x, (float)y + w.y);
   float nx = r0.y * r1.z - r0.z * r1.y;

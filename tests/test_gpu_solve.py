@@ -285,3 +285,45 @@ def test_set_schedule_reproduces_a_tuned_schedule(small):
         s2.set_schedule([25, -1, -1])
     s1.close()
     s2.close()
+
+
+def test_degenerate_constant_images_give_zero_disparity(small):
+    # no texture: I_u = 0 everywhere, the data term has no slope, so every
+    # step leaves u at 0 (and the range is +inf where the rays coincide)
+    p = dict(small, I0=np.full_like(small["I0"], 0.5), I1=np.full_like(small["I1"], 0.5))
+    s = make_solver(p)
+    disp, depth = s.solve(p["I0"], p["I1"], 2, 10)
+    d, z = np64(disp), np64(depth)
+    M = np64(s.read(0, "MASK")) > 0.5
+    assert np.all(d == 0.0)
+    assert np.all(np.isposinf(z[M])) and np.all(np.isnan(z[~M]))
+    s.close()
+
+
+def test_large_frame_properties():
+    # 4096 x 4096, 7 levels (beyond what the oracle can solve here): outputs
+    # finite inside the FOV, zero / NaN outside, and two schedules identical
+    import math
+    W = 4096
+    rng = np.random.default_rng(9)
+    yy, xx = np.mgrid[0:W, 0:W].astype(np.float32)
+    img = 0.5 + 0.2 * np.sin(xx / 17.0) * np.cos(yy / 23.0) + 0.05 * rng.random((W, W))
+    cam = dict(model="equidistant", fx=1280.0, fy=1280.0, cx=(W - 1) / 2, cy=(W - 1) / 2,
+               k=[0, 0, 0, 0], fov_deg=180.0)
+    pair = dict(I0=img, I1=np.roll(img, -3, axis=1), cam0=cam, cam1=dict(cam), R=np.eye(3),
+                t=np.array([-0.1, 0.0, 0.0]), levels=7, lam=50.0, eps=0.01)
+    outs = []
+    for sched in (None, [16] * 7):
+        s = make_solver(pair, use_graph=1)
+        if sched:
+            s.set_schedule(sched)
+        d, z = s.solve(pair["I0"], pair["I1"], 1, 6)
+        M = np64(s.read(0, "MASK")) > 0.5
+        outs.append((np64(d), np64(z)))
+        s.close()
+    d, z = outs[0]
+    assert np.all(np.isfinite(d[M])) and np.all(d[~M] == 0.0) and np.all(np.isnan(z[~M]))
+    assert np.abs(d[M]).max() < 0.2 * 1 * (2 ** 7 - 1) + 1e-3    # reach of 1 warp per level
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1], equal_nan=True)
+    assert math.isfinite(float(d[M].mean()))
