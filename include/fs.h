@@ -99,9 +99,17 @@ typedef struct {
  * alpha0 |grad v| (alpha0 = 17, alpha1 = 1.2 in Sec. IV-C; huber_eps and
  * pd_schedule do not apply; block_iters is the temporal-blocking depth, 0 =
  * tuned or 4), solved by the primal-dual steps of Eq. 11 with diagonal
- * preconditioning; FP32 storage only. */
+ * preconditioning; FP32 storage only.
+ * deriv: how I_u, the derivative of the warped I1 along the trajectory, is
+ * taken.  FS_DERIV_FORWARD (0) = I1(x + w + g) - I1(x + w), the difference of
+ * Eq. 7 (g the unit tangent gamma'); FS_DERIV_CENTRAL (1) = half of
+ * I1(x + w + g) - I1(x + w - g), exact on a quadratic image and free of the
+ * sample I1(x + w) that Eq. 7 shares with the residual rho0, whose noise
+ * otherwise biases every warp's step towards +u. */
 #define FS_REG_HUBER_TV 0
 #define FS_REG_TGV 1
+#define FS_DERIV_FORWARD 0
+#define FS_DERIV_CENTRAL 1
 typedef struct {
   float lambda;
   float huber_eps;
@@ -116,12 +124,14 @@ typedef struct {
   int storage;
   int regularizer;         /* FS_REG_HUBER_TV or FS_REG_TGV                   */
   float alpha0, alpha1;    /* TGV weights (regularizer = FS_REG_TGV)          */
+  int deriv;               /* FS_DERIV_FORWARD or FS_DERIV_CENTRAL            */
 } fs_params;
 
 typedef struct fs_handle fs_handle;
 
 /* Fill *out with the defaults (lambda 50, eps 0.01, du_max 0.2, beta 9,
- * eta 0.85, theta 1, precond 1, block_iters 0, use_graph 0). */
+ * eta 0.85, theta 1, precond 1, block_iters 0, use_graph 0, Huber-TV,
+ * alpha0 17, alpha1 1.2, deriv FS_DERIV_FORWARD). */
 fs_status fs_default_params(fs_params* out);
 
 /* Create the per-rig state for W x H pairs and `levels` pyramid levels

@@ -61,7 +61,7 @@ def solve_level_warps(I0l, I1l, gamma, lv, u, w, p1, p2, warps, iters,
     across the warps like p and updated in place."""
     M = lv["M"]
     for om in range(warps):
-        Iu, rho0, g = warp_linearize(I0l, I1l, w, gamma, M)
+        Iu, rho0, g = warp_linearize(I0l, I1l, w, gamma, M, prm.deriv)
         st = dict(u=u.copy(), ubar=u.copy(), p1=p1, p2=p2, Iu=Iu, rho0=rho0,
                   u_w=u.copy())
         if tgv is not None:

@@ -55,6 +55,8 @@ class Params:
     regularizer: str = "huber_tv"   # or "tgv": the TGV-L1 energy of Eq. 10
     alpha0: float = 17.0     # Sec. IV-C, TGV second-order weight
     alpha1: float = 1.2      # Sec. IV-C, TGV first-order weight
+    deriv: str = "forward"   # I_u: "forward" = Eq. 7; "central" = half the
+                             # difference of the samples at x + w +- g
 
 
 def grad_masks(M):
@@ -197,13 +199,21 @@ def pd_iteration(st, lv, prm: Params):
     return st
 
 
-def warp_linearize(I0, I1, w, gamma, M):
+def warp_linearize(I0, I1, w, gamma, M, deriv="forward"):
     """Warp I1 along w and linearise along the trajectory (Eq. 3, 5, 9).
 
     g = bicubic gamma'(x + w) renormalised (0 when |g| < 1e-6);
-    I1w = I1(x + w);  I_u = I1(x + w + g) - I1w;  rho0 = I1w - I0.
+    I1w = I1(x + w);  rho0 = I1w - I0;
+    I_u = I1(x + w + g) - I1w                        deriv "forward" (Eq. 7)
+    I_u = (I1(x + w + g) - I1(x + w - g)) / 2        deriv "central"
+    The forward difference of Eq. 7 shares the sample I1w with rho0, so
+    independent image noise of variance s^2 gives E[I_u rho0] a -s^2 term:
+    each warp's step is biased towards +u.  The central difference does not
+    contain I1w (no such term) and is exact on a quadratic image.
     Returns (Iu, rho0, g), all 0 outside the mask.
     """
+    if deriv not in ("forward", "central"):
+        raise ValueError(f"deriv must be 'forward' or 'central', not {deriv!r}")
     H, W = I0.shape
     py, px = np.mgrid[0:H, 0:W].astype(np.float64)
     xs = px + w[..., 0]
@@ -214,7 +224,11 @@ def warp_linearize(I0, I1, w, gamma, M):
     g = np.where(ok[..., None], graw / np.where(ok, n, 1.0)[..., None], 0.0)
     I1w = bilinear(I1, xs, ys)
     I1g = bilinear(I1, xs + g[..., 0], ys + g[..., 1])
-    Iu = np.where(M, I1g - I1w, 0.0)
+    if deriv == "forward":
+        Iu = I1g - I1w
+    else:
+        Iu = 0.5 * (I1g - bilinear(I1, xs - g[..., 0], ys - g[..., 1]))
+    Iu = np.where(M, Iu, 0.0)
     rho0 = np.where(M, I1w - I0, 0.0)
     return Iu, rho0, np.where(M[..., None], g, 0.0)
 

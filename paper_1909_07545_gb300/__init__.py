@@ -31,6 +31,7 @@ BUF = dict(I0=0, I1=1, MASK=2, GAMMA=3, TENSOR=4, STEPS=5, U=6, UBAR=7, UW=8, P=
 BUF_PLANES = {0: 1, 1: 1, 2: 1, 3: 2, 4: 3, 5: 2, 6: 1, 7: 1, 8: 1, 9: 2, 10: 2, 11: 1, 12: 1,
               13: 2, 14: 2, 15: 2, 16: 4}
 REGULARIZER = {"huber_tv": 0, "tgv": 1}
+DERIV = {"forward": 0, "central": 1}
 STAGE = dict(DOWNSAMPLE=0, TENSOR=1, UPSAMPLE=2, WARP=3, PD=4, CLIP=5, TRAJECTORY=6, WARM=7)
 
 STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ENOMEM", -3: "FS_ECUDA", -4: "FS_ECALIB",
@@ -73,7 +74,10 @@ class FsParams(ctypes.Structure):
                 ("block_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("pd_schedule", ctypes.c_int), ("storage", ctypes.c_int),
                 ("regularizer", ctypes.c_int), ("alpha0", ctypes.c_float),
-                ("alpha1", ctypes.c_float)]
+                ("alpha1", ctypes.c_float), ("deriv", ctypes.c_int)]
+
+
+_PARAM_FIELDS = {f[0] for f in FsParams._fields_}
 
 
 class FsServerConfig(ctypes.Structure):
@@ -176,7 +180,12 @@ def default_params(**overrides) -> FsParams:
             v = STORAGE[v]
         if k == "regularizer" and isinstance(v, str):
             v = REGULARIZER[v]
-        setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
+        if k == "deriv" and isinstance(v, str):
+            v = DERIV[v]
+        name = "lambda_" if k in ("lam", "lambda") else k
+        if name not in _PARAM_FIELDS:
+            raise TypeError(f"unknown solver parameter {k!r}")
+        setattr(p, name, v)
     return p
 
 

@@ -415,7 +415,7 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
       if (h->prm.regularizer == FS_REG_TGV) FS_LAUNCH("k_tgv_reset", launch_tgv_reset(L.v, st));
       return FS_OK;
     case FS_STAGE_WARP:
-      FS_LAUNCH("k_warp", launch_warp(L.v, st));
+      FS_LAUNCH("k_warp", launch_warp(L.v, h->prm.deriv == FS_DERIV_CENTRAL, st));
       if (h->prm.regularizer == FS_REG_TGV)
         FS_LAUNCH("k_tgv_warp_start", launch_tgv_warp_start(L.v, st));
       return FS_OK;
@@ -589,6 +589,7 @@ fs_status fs_default_params(fs_params* out) {
   out->regularizer = FS_REG_HUBER_TV;
   out->alpha0 = 17.f;
   out->alpha1 = 1.2f;
+  out->deriv = FS_DERIV_FORWARD;
   return FS_OK;
 }
 
@@ -613,7 +614,7 @@ fs_status fs_internal_validate(const fs_calib cam[2], const fs_pose* pose, int W
     if (!(p.lambda > 0) || !(p.huber_eps >= 0) || !(p.du_max > 0) || !(p.beta >= 0) ||
         !(p.eta > 0) || !(p.theta >= 0 && p.theta <= 1) || p.block_iters < 0 ||
         p.block_iters > 8 || p.pd_schedule < 0 || p.pd_schedule > 1 || p.storage < 0 ||
-        p.storage > 2 || p.regularizer < 0 || p.regularizer > 1)
+        p.storage > 2 || p.regularizer < 0 || p.regularizer > 1 || p.deriv < 0 || p.deriv > 1)
       return fail(FS_EINVAL, "parameter out of range");
     if (p.regularizer == FS_REG_TGV &&
         (!(p.alpha0 >= 0) || !(p.alpha1 > 0) || !std::isfinite(p.alpha0) ||

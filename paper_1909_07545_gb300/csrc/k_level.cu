@@ -273,10 +273,12 @@ __global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
 
 // ------------------------------------------------------------ warp + linearise
 // g = bicubic gamma'(x + w) renormalised (0 if |g| < 1e-6); I1w = I1(x + w);
-// I_u = I1(x + w + g) - I1w (Eq. 5); rho0 = I1w - I0 (Eq. 3, 9).  Starts a
-// warp: ubar = u_w = u.
+// rho0 = I1w - I0 (Eq. 3, 9); I_u = I1(x + w + g) - I1w (Eq. 5, 7), or with
+// `central` half the difference of the samples at x + w +- g (free of the
+// I1w noise that the forward difference shares with rho0).  Starts a warp:
+// ubar = u_w = u.
 template <int S>
-__global__ void k_warp(LevelView L) {
+__global__ void k_warp(LevelView L, int central) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
@@ -290,7 +292,12 @@ __global__ void k_warp(LevelView L) {
     if (n >= 1e-6f) g = make_float2(gr.x / n, gr.y / n);
     float I1w = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x, y, w.y);
     float I1g = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x + g.x, y, w.y + g.y);
-    Iu = I1g - I1w;
+    if (central) {
+      float I1m = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x - g.x, y, w.y - g.y);
+      Iu = 0.5f * (I1g - I1m);
+    } else {
+      Iu = I1g - I1w;
+    }
     rho0 = I1w - sld<S>(L.I0, i);
   }
   sst<S>(L.Iu, i, Iu);
@@ -452,8 +459,8 @@ cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond
   FS_STORAGE_SWITCH(L.st, (k_tensor<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, beta, eta,
                                                                           precond)))
 }
-cudaError_t launch_warp(const LevelView& L, cudaStream_t st) {
-  FS_STORAGE_SWITCH(L.st, (k_warp<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L)))
+cudaError_t launch_warp(const LevelView& L, int central, cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_warp<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, central)))
 }
 cudaError_t launch_tensor_abc(const LevelView& L, float* dst, cudaStream_t st) {
   FS_STORAGE_SWITCH(L.st, (k_tensor_abc<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, dst)))

@@ -82,11 +82,15 @@ def test_host_side_validation(lib):
     st, msg = _create([EQ, EQ], prm=prm)
     assert st == -1 and "parameter" in msg
     for bad in (dict(regularizer="tgv", storage="f16"), dict(regularizer="tgv", alpha1=0.0),
-                dict(regularizer="tgv", alpha0=-1.0), dict(regularizer=2)):
+                dict(regularizer="tgv", alpha0=-1.0), dict(regularizer=2), dict(deriv=2),
+                dict(deriv=-1)):
         st, msg = _create([EQ, EQ], prm=fsb.default_params(**bad))
         assert st == -1, bad
     p = fsb.default_params()
     assert p.regularizer == 0 and p.alpha0 == pytest.approx(17.0) and p.alpha1 == pytest.approx(1.2)
+    assert p.deriv == 0 and fsb.default_params(deriv="central").deriv == 1   # Eq. 7 by default
+    with pytest.raises(TypeError):
+        fsb.default_params(derivative="central")                   # no silent typo
     h = ctypes.c_void_p()
     assert lib.fs_solve(None, None, None, None, 1, 1, None, None) == -1
     b = ctypes.c_void_p()

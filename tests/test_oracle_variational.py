@@ -238,6 +238,54 @@ def test_warp_linearize_on_affine_image():
     assert np.all(Iu[~M] == 0) and np.all(rho0[~M] == 0)
 
 
+def test_warp_linearize_derivatives_on_quadratic_image():
+    # I1 = q x^2 along gamma' = e1: the derivative at x + w is 2 q (x + w).
+    # Bilinear sampling of a quadratic errs by q f (1 - f) at fraction f, the
+    # same at x + w +- 1, so the central difference is exact and the forward
+    # difference of Eq. 7 is off by the curvature term q (1 + 0 f).
+    H, W = 8, 24
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    qc = 0.003
+    I1 = qc * px * px
+    I0 = np.zeros((H, W))
+    gam = np.zeros((H, W, 2))
+    gam[..., 0] = 1.0
+    w = np.zeros((H, W, 2))
+    w[..., 0] = 0.3
+    M = np.zeros((H, W), bool)
+    M[1:7, 2:20] = True
+    exact = 2 * qc * (px + 0.3)
+    Iu_f, rho_f, _ = warp_linearize(I0, I1, w, gam, M, "forward")
+    Iu_c, rho_c, _ = warp_linearize(I0, I1, w, gam, M, "central")
+    assert np.allclose(Iu_c[M], exact[M], atol=1e-13)
+    assert np.allclose(Iu_f[M], exact[M] + qc, atol=1e-13)
+    assert np.array_equal(rho_f, rho_c)
+    with pytest.raises(ValueError):
+        warp_linearize(I0, I1, w, gam, M, "backward")
+
+
+def test_warp_linearize_noise_correlation():
+    # I1 white noise of variance s^2, I0 independent, w = 0: the forward
+    # difference shares I1(x) with rho0, so mean(I_u rho0) -> -s^2; the
+    # central difference holds no I1(x) and the mean -> 0 (standard error
+    # about s^2 sqrt(2) / sqrt(n))
+    rng = np.random.default_rng(11)
+    H, W = 256, 256
+    s = 0.1
+    I1 = rng.normal(0.0, s, (H, W))
+    I0 = rng.normal(0.0, s, (H, W))
+    gam = np.zeros((H, W, 2))
+    gam[..., 1] = 1.0
+    w = np.zeros((H, W, 2))
+    M = np.zeros((H, W), bool)
+    M[2:-2, 2:-2] = True
+    n = M.sum()
+    for deriv, want in (("forward", -s * s), ("central", 0.0)):
+        Iu, rho0, _ = warp_linearize(I0, I1, w, gam, M, deriv)
+        got = (Iu * rho0)[M].mean()
+        assert abs(got - want) < 5 * s * s * np.sqrt(2.0 / n), (deriv, got)
+
+
 def test_clip_update_cases():
     M = np.array([[True, True, True, False]])
     u = np.array([[0.5, -0.05, -1.0, 3.0]])
