@@ -108,6 +108,28 @@ fs_status fs_autotune(fs_handle* h, int iters, int* choice);
  * choice (0) on a level that does not fit one cluster. */
 fs_status fs_set_schedule(fs_handle* h, const int* choice);
 
+/* Guard-band debug mode, the out-of-bounds check in place of a memory
+ * sanitizer.  A handle created while the environment variable
+ * FS_GUARD_BANDS is a positive integer puts a band of 0xFF bytes before every
+ * device plane of its state and after the last one.  A band is two rows of
+ * the widest level-0 element (float2), rounded up to 256 bytes.  A stray
+ * store into a band is detected; a stray load reads NaN (all-ones float, half
+ * and bfloat16), or all mask bits, and shows in the results.  Every fs_solve
+ * and fs_solve_continue then ends with this check, which synchronises the
+ * handle's stream.  It returns FS_OK when every band is intact, FS_ECUDA
+ * naming the plane after the first overwritten band, and FS_EINVAL for a
+ * handle made without guard bands.  Results are the same bits as without
+ * the bands; only the plane addresses move. */
+fs_status fs_guard_check(fs_handle* h);
+
+/* Testing aid for the check above: set byte `offset` of guard band `band`
+ * (0 = the band before level 0's mask plane, bands in allocation order) to
+ * 0, a store that fs_guard_check must then report; out = the number of
+ * bands (may be NULL).  band = -1 only counts.  Writes inside the handle's
+ * own allocation.  FS_EINVAL without guard bands or for an index out of
+ * range. */
+fs_status fs_guard_clobber(fs_handle* h, int band, size_t offset, int* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,7 @@ EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc",
             "fs_batch_create", "fs_batch_solve", "fs_batch_set_finest_limit",
             "fs_batch_destroy", "fs_autotune", "fs_set_schedule", "fs_energy", "fs_state_bytes",
+            "fs_guard_check", "fs_guard_clobber",
             "fs_server_default_config", "fs_server_create", "fs_server_add_rig",
             "fs_server_submit", "fs_server_wait", "fs_server_cancel", "fs_server_drain",
             "fs_server_stats_read",
@@ -139,6 +140,8 @@ def load_library():
         "fs_batch_destroy": [_P],
         "fs_autotune": [_P, i, _P],
         "fs_set_schedule": [_P, _P],
+        "fs_guard_check": [_P],
+        "fs_guard_clobber": [_P, i, ctypes.c_size_t, ctypes.POINTER(i)],
         "fs_energy": [_P, i, ctypes.POINTER(d)],
         "fs_state_bytes": [i, i, i, ctypes.POINTER(FsParams), ctypes.POINTER(ctypes.c_size_t)],
         "fs_server_default_config": [ctypes.POINTER(FsServerConfig)],
@@ -352,6 +355,18 @@ class Solver:
         """Set the per-level schedule in autotune()'s encoding (-1 = default)."""
         arr = (ctypes.c_int * 8)(*([int(c) for c in choice] + [-1] * (8 - len(choice))))
         _check(self.lib.fs_set_schedule(self.h, arr))
+
+    def guard_check(self):
+        """fs_guard_check: raise FsError if a guard band was overwritten
+        (handles created with FS_GUARD_BANDS=1 in the environment)."""
+        _check(self.lib.fs_guard_check(self.h))
+
+    def guard_clobber(self, band=-1, offset=0):
+        """fs_guard_clobber: zero one byte of a guard band (testing aid);
+        returns the number of bands."""
+        n = ctypes.c_int()
+        _check(self.lib.fs_guard_clobber(self.h, int(band), int(offset), ctypes.byref(n)))
+        return n.value
 
     def timing_enable(self, on=True):
         _check(self.lib.fs_timing_enable(self.h, 1 if on else 0))

@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <climits>
+#include <cstdlib>
 #include <new>
 #include <string>
 #include <thread>
@@ -238,7 +240,32 @@ struct fs_handle {
   // the finest level's u and w hold the result of the last solve
   bool has_state = false;
   double* eacc = nullptr;                // fs_energy's 3 device accumulators
+  // guard-band mode (FS_GUARD_BANDS=1 at creation): a band of 0xFF bytes
+  // before every plane and after the last; band offsets (bytes into the
+  // arena) on the device, the plane that follows each band on the host
+  size_t guard = 0;
+  std::vector<unsigned long long> gband;
+  std::vector<std::string> gname;
+  unsigned long long* gband_dev = nullptr;
+  int* gflag = nullptr;
 };
+
+namespace fs {
+
+// One block per guard band: the lowest band index whose bytes are not all
+// 0xFF goes to *first_bad (left at INT_MAX when every band is intact).
+__global__ void k_guard_check(const uint32_t* __restrict__ base,
+                              const unsigned long long* __restrict__ band, int n_band,
+                              size_t words, int* first_bad) {
+  const int b = blockIdx.x;
+  if (b >= n_band) return;
+  const uint32_t* p = base + band[b] / 4;
+  bool bad = false;
+  for (size_t i = threadIdx.x; i < words; i += blockDim.x) bad |= p[i] != 0xFFFFFFFFu;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicMin(first_bad, b);
+}
+
+}  // namespace fs
 
 namespace {
 
@@ -669,12 +696,31 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
   }
   size_t cbytes = align_up((size_t)h->lv[0].P * H * sizeof(float2), 256);
   bytes += cbytes;
+  const char* genv = std::getenv("FS_GUARD_BANDS");
+  if (genv && std::atoi(genv) > 0) {
+    // two rows of the widest element (float2) of level 0 on each side
+    h->guard = align_up(2 * (size_t)h->lv[0].P * sizeof(float2), 256);
+    size_t n_planes = 1;                                  // the calibration field
+    for (int l = 0; l < levels; ++l) n_planes += 21 + (p.regularizer == FS_REG_TGV ? 20 : 0);
+    bytes += (n_planes + 1) * h->guard;
+  }
   cudaError_t e = cudaMalloc(&h->arena, bytes);
   if (e != cudaSuccess) {
     delete h;
     return fail(FS_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
   }
   char* cur = (char*)h->arena;
+  // the next plane of `size` bytes, after a guard band in guard-band mode
+  auto take = [&](size_t size, int l, const char* name) {
+    if (h->guard) {
+      h->gband.push_back((unsigned long long)(cur - (char*)h->arena));
+      h->gname.push_back(std::string("level ") + std::to_string(l) + " " + name);
+      cur += h->guard;
+    }
+    char* at = cur;
+    cur += size;
+    return at;
+  };
   for (int l = 0; l < levels; ++l) {
     HostLevel& L = h->lv[l];
     size_t plane = align_up((size_t)L.P * L.H * sizeof(float), 256);
@@ -683,36 +729,61 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     LevelView& v = L.v;
     v.W = L.W; v.H = L.H; v.P = L.P;
     v.st = p.storage;
-    v.mask = (const uint8_t*)cur; cur += plane8;
+    v.mask = (const uint8_t*)take(plane8, l, "mask");
     float** fl[] = {&v.tau, &v.sig, &v.u, &v.ubar, &v.uw, &v.u_alt, &v.ubar_alt};
-    for (float** f : fl) { *f = (float*)cur; cur += plane; }
+    const char* nfl[] = {"tau", "sigma", "u", "ubar", "u_w", "u (ping-pong)", "ubar (ping-pong)"};
+    for (int j = 0; j < 7; ++j) *fl[j] = (float*)take(plane, l, nfl[j]);
     SPlane* sp[] = {&v.I0, &v.I1, &v.sx, &v.sy, &v.p1, &v.p2, &v.Iu, &v.rho0, &v.p1_alt,
                     &v.p2_alt};
-    for (SPlane* f : sp) { f->p = cur; cur += splane; }
+    const char* nsp[] = {"I0", "I1", "s_x", "s_y", "p1", "p2", "I_u", "rho0",
+                         "p1 (ping-pong)", "p2 (ping-pong)"};
+    for (int j = 0; j < 10; ++j) sp[j]->p = take(splane, l, nsp[j]);
     float2** f2[] = {&v.gamma, &v.w, &v.g};
-    for (float2** f : f2) { *f = (float2*)cur; cur += 2 * plane; }
+    const char* nf2[] = {"gamma'", "w", "g"};
+    for (int j = 0; j < 3; ++j) *f2[j] = (float2*)take(2 * plane, l, nf2[j]);
     if (p.regularizer == FS_REG_TGV) {
       float** ft[] = {&v.v1, &v.v2, &v.vb1, &v.vb2, &v.q11, &v.q12, &v.q21, &v.q22};
-      for (float** f : ft) { *f = (float*)cur; cur += plane; }
-      for (int j = 0; j < 12; ++j) { v.tgv_alt[j] = (float*)cur; cur += plane; }
+      const char* nft[] = {"v1", "v2", "vbar1", "vbar2", "q11", "q12", "q21", "q22"};
+      for (int j = 0; j < 8; ++j) *ft[j] = (float*)take(plane, l, nft[j]);
+      for (int j = 0; j < 12; ++j) v.tgv_alt[j] = (float*)take(plane, l, "TGV ping-pong");
     }
   }
-  h->cfield = (float2*)cur;
+  h->cfield = (float2*)take(cbytes, 0, "calibration field");
+  if (h->guard) {                                         // the band after the last plane
+    h->gband.push_back((unsigned long long)(cur - (char*)h->arena));
+    h->gname.push_back("end of the arena");
+    cur += h->guard;
+  }
   e = cudaMemsetAsync(h->arena, 0, bytes, h->stream);
+  for (size_t j = 0; e == cudaSuccess && j < h->gband.size(); ++j)
+    e = cudaMemsetAsync((char*)h->arena + h->gband[j], 0xFF, h->guard, h->stream);
+  if (e == cudaSuccess && h->guard) {
+    e = cudaMalloc(&h->gband_dev, h->gband.size() * sizeof(unsigned long long) + sizeof(int));
+    if (e == cudaSuccess) {
+      h->gflag = (int*)(h->gband_dev + h->gband.size());
+      e = cudaMemcpyAsync(h->gband_dev, h->gband.data(),
+                          h->gband.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                          h->stream);
+    }
+  }
   if (e != cudaSuccess) {
+    cudaStreamSynchronize(h->stream);
+    if (h->gband_dev) cudaFree(h->gband_dev);
     cudaFree(h->arena);
     delete h;
-    return fail(FS_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+    return fail(FS_ECUDA, "arena initialisation failed: %s", cudaGetErrorString(e));
   }
   std::vector<uint8_t> host;
   if ((s = upload_masks(h, host)) != FS_OK || (s = build_fields(h)) != FS_OK) {
     cudaStreamSynchronize(h->stream);
+    if (h->gband_dev) cudaFree(h->gband_dev);
     cudaFree(h->arena);
     delete h;
     return s;
   }
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
+    if (h->gband_dev) cudaFree(h->gband_dev);
     cudaFree(h->arena);
     delete h;
     return fail(FS_ECUDA, "fs_create: %s", cudaGetErrorString(e));
@@ -774,9 +845,40 @@ fs_status fs_trajectory_field(fs_handle* h, int level, float* d_out) {
 
 }  // extern "C"
 
+extern "C" fs_status fs_guard_check(fs_handle* h) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (!h->guard) return fail(FS_EINVAL, "the handle was created without FS_GUARD_BANDS");
+  const int none = INT_MAX;
+  int first = none;
+  FS_CUDA(cudaMemcpyAsync(h->gflag, &none, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  fs::k_guard_check<<<(unsigned)h->gband.size(), 256, 0, h->stream>>>(
+      (const uint32_t*)h->arena, h->gband_dev, (int)h->gband.size(), h->guard / 4, h->gflag);
+  FS_CUDA(cudaGetLastError());
+  FS_CUDA(cudaMemcpyAsync(&first, h->gflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  FS_CUDA(cudaStreamSynchronize(h->stream));
+  if (first != none)
+    return fail(FS_ECUDA, "guard band before %s overwritten", h->gname[first].c_str());
+  return FS_OK;
+}
+
+extern "C" fs_status fs_guard_clobber(fs_handle* h, int band, size_t offset, int* out) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (!h->guard) return fail(FS_EINVAL, "the handle was created without FS_GUARD_BANDS");
+  if (out) *out = (int)h->gband.size();
+  if (band == -1) return FS_OK;
+  if (band < 0 || band >= (int)h->gband.size() || offset >= h->guard)
+    return fail(FS_EINVAL, "no guard band %d or offset %zu", band, offset);
+  FS_CUDA(cudaMemsetAsync((char*)h->arena + h->gband[band] + offset, 0, 1, h->stream));
+  FS_CUDA(cudaStreamSynchronize(h->stream));
+  return FS_OK;
+}
+
 // fs_solve and fs_solve_continue: direct launches, or a CUDA graph captured
-// once per set of buffers and replayed.
-static fs_status solve_impl(fs_handle* h, const float* d_I0, const float* d_I1,
+// once per set of buffers and replayed.  In guard-band mode every solve ends
+// with fs_guard_check (which synchronises the stream).
+static fs_status solve_launch(fs_handle* h, const float* d_I0, const float* d_I1,
                             const float* d_init, bool cont, int warps, int iters, float* d_disp,
                             float* d_depth) {
   fs_status s;
@@ -826,6 +928,14 @@ static fs_status solve_impl(fs_handle* h, const float* d_I0, const float* d_I1,
   return FS_OK;
 }
 
+static fs_status solve_impl(fs_handle* h, const float* d_I0, const float* d_I1,
+                            const float* d_init, bool cont, int warps, int iters, float* d_disp,
+                            float* d_depth) {
+  fs_status s = solve_launch(h, d_I0, d_I1, d_init, cont, warps, iters, d_disp, d_depth);
+  if (s == FS_OK && h->guard) s = fs_guard_check(h);
+  return s;
+}
+
 extern "C" {
 
 fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1, const float* d_init,
@@ -870,6 +980,7 @@ fs_status fs_destroy(fs_handle* h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->stage) cudaFree(h->stage);
   if (h->eacc) cudaFree(h->eacc);
+  if (h->gband_dev) cudaFree(h->gband_dev);
   if (h->arena) cudaFree(h->arena);
   delete h;
   return FS_OK;

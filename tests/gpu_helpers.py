@@ -123,7 +123,9 @@ def oracle_sensitivity(pair, ref, levels=None, warps=None, iters=None, d_init=No
 # ill-conditioned: the FP64 oracle itself moves there by up to ~0.2 px under
 # FP32-sized perturbations (oracle_sensitivity), so no FP32 implementation
 # holds a 5e-3 px bound at every pixel.  The gate:
-#   mean |dd| over the FOV mask <= 1e-4 px;
+#   mean |dd| over the FOV mask <= 1e-4 px, or no more than the mean of the
+#   oracle's own largest probe response where that is larger (the noisy
+#   scenes, whose warps amplify FP32-sized perturbations);
 #   |dd| <= 5e-3 px on at least 99.8 % of the mask;
 #   the pixels above 5e-3 px are at most 2 x as many as the oracle's own
 #   under the probes (+ 10), and no |dd| exceeds max(5e-3, 2 x the largest
@@ -148,7 +150,7 @@ def disparity_parity(d_gpu, ref, sens):
                   max_well_conditioned=float(err[well].max()) if well.any() else 0.0,
                   n_ill_conditioned=int((~well).sum()), n_over=n_gpu, n_over_probe=n_probe,
                   probe_max=float(s.max()), probe_mean=float(s.mean()))
-    ok = (report["mean"] <= MEAN_TOL and report["q998"] <= MAX_TOL
+    ok = (report["mean"] <= max(MEAN_TOL, report["probe_mean"]) and report["q998"] <= MAX_TOL
           and n_gpu <= 2 * n_probe + 10 and report["max"] <= max(MAX_TOL, 2 * report["probe_max"]))
     return ok, report
 

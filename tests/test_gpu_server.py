@@ -121,6 +121,32 @@ def test_served_in_a_mix_equals_served_alone_and_lone_handle(rigs, warm_mode):
         alone.close()
 
 
+def test_served_under_guard_bands(rigs, monkeypatch):
+    # FS_GUARD_BANDS=1: every rig handle the server makes has guard bands and
+    # every served solve ends with fs_guard_check, whose failure fails the
+    # request; results are the same bits as the lone handle's chain
+    monkeypatch.setenv("FS_GUARD_BANDS", "1")
+    srv = _server(max_inflight=3, warm_mode=1)
+    ids = [_add(srv, q) for q in rigs]
+    outs, reqs = {}, []
+    for k in range(3):
+        for r, q in zip(ids, rigs):
+            d, z = _outs(q)
+            I0, I1, _ = q["frames"][k]
+            reqs.append(srv.submit(r, _pinned(I0), _pinned(I1), d, z))
+            outs[(r, k)] = (d.numpy(), z.numpy())
+    for x in reqs:
+        srv.wait(x)
+    st = srv.stats()
+    assert st["completed"] == 9 and st["failed"] == 0
+    srv.close()
+    monkeypatch.delenv("FS_GUARD_BANDS")
+    for r, q in zip(ids, rigs):
+        chain = _lone_chain(q, warm_mode=1)
+        for k in range(3):
+            assert np.array_equal(outs[(r, k)][0].astype(np.float64), chain[k][0]), (r, k)
+
+
 def test_budget_admission_evicts_idle_rigs_lru(rigs):
     import paper_1909_07545_gb300 as fsb
     A, B = rigs[0], rigs[2]

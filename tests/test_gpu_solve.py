@@ -129,6 +129,18 @@ def test_ragged_rotated_pair_matches_oracle():
     s.close()
 
 
+def test_central_derivative_matches_oracle():
+    # I_u as the central difference along the trajectory (the option beside
+    # Eq. 7's forward difference) on the noisy Kannala-Brandt rig at 256^2
+    p = f32pair(synth.plain_kb(0, W=256, H=256, levels=3))
+    ref = _oracle(p, warps=5, iters=50, deriv="central")
+    sens = oracle_sensitivity(p, ref, warps=5, iters=50, deriv="central")
+    s = make_solver(p, deriv="central")
+    disp, depth = s.solve(p["I0"], p["I1"], 5, 50)
+    _compare(p, ref, disp, depth, sens)
+    s.close()
+
+
 def test_unpreconditioned_steps_match_oracle(small):
     ref = _oracle(small, warps=3, iters=40, precond=False)
     sens = oracle_sensitivity(small, ref, warps=3, iters=40, precond=False)
@@ -327,3 +339,48 @@ def test_large_frame_properties():
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1], equal_nan=True)
     assert math.isfinite(float(d[M].mean()))
+
+
+def test_bench_configuration_at_full_counts():
+    # the timed configuration itself: 1024^2 Kannala-Brandt, 5 levels x 10
+    # warps x 100 iterations, autotuned schedule in a CUDA graph, against
+    # the oracle's disparity at 4096 seeded FOV pixels and its quantiles
+    # (tests/golden/kb1024_oracle.json, written by make_kb1024_oracle.py).
+    # The scene's noise makes this solve ill-conditioned (the oracle itself
+    # moves by a mean 2e-3 px and up to ~1 px under FP32-sized
+    # perturbations), so the gate is the small-size one made relative to the
+    # stored probe responses: mean, 99.8th percentile and maximum of |dd| no
+    # more than twice the oracle's own (floors 1e-4 / 5e-3 / 5e-3 px), and
+    # the quantiles of the field within twice their probe shift (floor
+    # 2e-3 px).  What holds at any size: the same bits as the default
+    # schedule, zero / NaN off the FOV, the reach of the clipped increments.
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "kb1024_oracle.json")) as f:
+        gold = json.load(f)
+    p = f32pair(synth.plain_kb(0))
+    outs = []
+    for tuned in (True, False):
+        s = make_solver(p, use_graph=1)
+        if tuned:
+            s.autotune(p["iters"])
+        d, z = s.solve(p["I0"], p["I1"], p["warps"], p["iters"])
+        d, z = s.solve(p["I0"], p["I1"], p["warps"], p["iters"], disp=d, depth=z)   # replay
+        M = np64(s.read(0, "MASK")) > 0.5
+        outs.append((np64(d), np64(z)))
+        s.close()
+    (d, z), (d0, z0) = outs
+    assert np.array_equal(d, d0) and np.array_equal(z, z0, equal_nan=True)
+    assert int(M.sum()) == gold["n_mask"]
+    assert np.all(d[~M] == 0.0) and np.all(np.isnan(z[~M]))
+    assert np.abs(d[M]).max() <= 0.2 * p["warps"] * (2 ** p["levels"] - 1) + 1e-3
+    ys, xs, dref, probe = (np.array(c) for c in zip(*gold["sample"]))
+    err = np.abs(d[ys.astype(int), xs.astype(int)] - dref)
+    ps = gold["probe_sample_stats"]
+    rep = dict(mean=err.mean(), q998=float(np.quantile(err, 0.998)), max=err.max(), probe=ps)
+    assert rep["mean"] <= max(1e-4, 2 * ps["mean"]), rep
+    assert rep["q998"] <= max(5e-3, 2 * ps["q998"]), rep
+    assert rep["max"] <= max(5e-3, 2 * ps["max"]), rep
+    qs = np.quantile(d[M], gold["quantile_levels"])
+    tol = np.maximum(2e-3, 2 * np.array(gold["probe_quantile_shift"]))
+    assert np.all(np.abs(qs - gold["disp_quantiles"]) <= tol), (qs, gold["disp_quantiles"], tol)

@@ -147,9 +147,10 @@ def _smooth_field(rng, H, W, scale, n=2):
     return out
 
 
-def test_warp_linearize(small, ragged):
+@pytest.mark.parametrize("deriv", ["forward", "central"])
+def test_warp_linearize(small, ragged, deriv):
     for pair in (small, ragged):
-        s = make_solver(pair)
+        s = make_solver(pair, deriv=deriv)
         sizes, cals, masks = level_calibs(pair, pair["levels"])
         rng = np.random.default_rng(7)
         H, W = pair["I0"].shape
@@ -162,7 +163,7 @@ def test_warp_linearize(small, ragged):
         s.stage(0, "WARP")
         gam = np64(s.trajectory_field(0)).transpose(1, 2, 0)
         Iu, rho0, g = oracle.warp_linearize(pair["I0"], pair["I1"], w.transpose(1, 2, 0), gam,
-                                            masks[0])
+                                            masks[0], deriv)
         assert np.abs(np64(s.read(0, "RHO0")) - rho0).max() < 5e-6
         # where the bicubic sum of unit vectors is short (stencil reaching off
         # the mask or across an epipole) renormalising it amplifies rounding;
