@@ -29,11 +29,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "frames/s & p99 latency, 1024² fisheye pair; primal-dual Gpix-iter/s vs plain"
 PD_BYTES_PER_PX_ITER = 52.0   # unblocked FP32 traffic of one pixel-iteration (9 reads + 4 writes)
-# DRAM bytes (read + write) of one level-0 k_pd launch of this workload at 7
-# iterations per launch, from one ncu capture of the current kernel (cold L2;
-# the command and figures are in profiles/k_pd_level0_kb1024.md)
-PD_L0_DRAM_BYTES_PER_LAUNCH = 47.5e6
-PD_L0_PROFILED_DEPTH = 7
+# DRAM bytes (read + write) of one level-0 k_pd launch of this workload on
+# 64 x 64 footprints of 1024 threads at 7 iterations per launch (schedule
+# choice 31), from one ncu capture of the current kernel (cold L2; the
+# command and figures are in profiles/k_pd_level0_kb1024.md)
+PD_L0_DRAM_BYTES_PER_LAUNCH = 47.7e6
+PD_L0_PROFILED_CHOICE = 31
+FOOTPRINTS = ["64x64 footprints, 512 threads", "32x32 footprints", "64x32 footprints",
+              "64x64 footprints, 1024 threads"]
+
+
+def schedule_label(c):
+    """fs_autotune's per-level choice in words (0 = cluster; 1..32 = depth
+    1..8 on each of the four footprints)."""
+    if c == 0:
+        return "cluster"
+    return f"blocking x{(c - 1) % 8 + 1} ({FOOTPRINTS[(c - 1) // 8]})"
 
 
 def workload_pair(name, seed):
@@ -636,10 +647,9 @@ def main():
     fps = job_rate(world, args.steps, total_ms)
     ms0, n0, px0 = per_level[0]
     achieved = PD_BYTES_PER_PX_ITER * px0 / (ms0 / 1000.0) / 1e9
-    # the profiled traffic applies while level 0 runs at the profiled depth
-    # (on 64-wide tiles)
-    l0_depth = tuned[0] if tuned else None
-    traffic = PD_L0_DRAM_BYTES_PER_LAUNCH if l0_depth == PD_L0_PROFILED_DEPTH else None
+    # the profiled traffic applies while level 0 runs the profiled schedule
+    l0_choice = tuned[0] if tuned else None
+    traffic = PD_L0_DRAM_BYTES_PER_LAUNCH if l0_choice == PD_L0_PROFILED_CHOICE else None
     peaks, src = measured_peaks()
     peak = float(peaks["hbm_gbs"])
     pd_ms = sum(m for m, _, _ in per_level) / args.steps
@@ -655,10 +665,7 @@ def main():
                    "iters": iters, "camera": "kannala_brandt f=320 fov=190",
                    "l2": "flushed between steps (256 MB write)",
                    "pd_schedule_per_level": (
-                       ["cluster" if c == 0 else
-                        f"blocking x{c} (64x64 footprints)" if c <= 8 else
-                        f"blocking x{c - 8} (32x32 footprints)" if c <= 16 else
-                        f"blocking x{c - 16} (64x32 footprints)" for c in tuned]
+                       [schedule_label(c) for c in tuned]
                        if tuned else "default (cluster <= 128 px, blocking 6 / 8 above)"),
                    "autotuned": bool(tuned), "graph": True,
                    "parallelism": f"replicas x{world}"},
@@ -672,7 +679,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "traffic_note": "DRAM bytes per level-0 launch, ncu, cold L2",
-                     "kernel": f"k_pd level 0 (1024x1024), blocking depth {l0_depth}",
+                     "kernel": "k_pd level 0 (1024x1024), " + (
+                         schedule_label(l0_choice) if l0_choice is not None else "default"),
                      "launches_per_frame": n0 // max(args.steps, 1),
                      "algorithmic_bytes_per_launch": PD_BYTES_PER_PX_ITER * px0 / max(n0, 1),
                      "peak_source": f"{src} hbm_gbs",

@@ -92,11 +92,13 @@ fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
  * iterations (best of 3 after a warm-up, CUDA events on the handle's
  * stream) of each candidate -- the whole-level cluster schedule where the
  * level fits one cluster, and temporal blocking with 1..8 iterations per
- * launch on 64 x 64, 32 x 32 or 64 x 32 footprints -- and keeps the fastest for later
- * solves when block_iters = 0 and pd_schedule = 0.  choice (may be NULL)
- * receives per level 0 = cluster, 1..8 = that depth on 64 x 64 footprints,
- * 9..16 = depth (choice - 8) on 32 x 32 footprints, 17..24 = depth
- * (choice - 16) on 64 x 32 footprints.  On TGV handles the
+ * launch on 64 x 64 (512 threads), 32 x 32, 64 x 32 or 64 x 64 (1024
+ * threads) footprints -- and keeps the fastest for later solves when
+ * block_iters = 0 and pd_schedule = 0.  choice (may be NULL) receives per
+ * level 0 = cluster, 1..8 = that depth on 64 x 64 footprints of 512
+ * threads, 9..16 = depth (choice - 8) on 32 x 32 footprints, 17..24 = depth
+ * (choice - 16) on 64 x 32 footprints, 25..32 = depth (choice - 24) on
+ * 64 x 64 footprints of 1024 threads.  On TGV handles the
  * candidates are 0 = a dual and a primal launch per iteration and 1..8 =
  * temporal-blocking depth.  Overwrites the levels' state; synchronises the
  * stream.  All candidates give identical results. */

@@ -357,12 +357,13 @@ int pd_block(const fs_handle* h, int l) {
 }
 
 // A schedule choice of fs_autotune / fs_set_schedule: 0 = cluster (Huber-TV)
-// or a launch per step (TGV); 1..8, 9..16, 17..24 = blocking depth on 64 x 64,
-// 32 x 32, 64 x 32 footprints (TGV: 1..8 = depth); -1 = none.
+// or a launch per step (TGV); 1..8, 9..16, 17..24, 25..32 = blocking depth on
+// 64 x 64 (512 threads), 32 x 32, 64 x 32, 64 x 64 (1024 threads) footprints
+// (TGV: 1..8 = depth); -1 = none.
 void decode_choice(int c, bool tgv, int& depth, int& variant) {
   if (c <= 0 || tgv) { depth = c; variant = -1; return; }
   depth = 1 + (c - 1) % 8;
-  variant = c <= 8 ? PD_TILE_64 : (c <= 16 ? PD_TILE_32 : PD_TILE_64x32);
+  variant = c <= 8 ? PD_TILE_64 : c <= 16 ? PD_TILE_32 : c <= 24 ? PD_TILE_64x32 : PD_TILE_64_T1024;
 }
 
 // Whether level l runs the whole-level cluster schedule.
@@ -1311,11 +1312,11 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
     L.tuned_variant = -1;
     float best = 3.4e38f;
     int best_c = -1;
-    // candidates: 0 = cluster; 1..8 = depth with 64-wide tiles; 9..16 =
-    // depth 1..8 with 32-wide tiles.  TGV: 0 = a launch per step, 1..8 =
+    // candidates: 0 = cluster; 1..32 = depth 1..8 on each of the four
+    // footprints (decode_choice).  TGV: 0 = a launch per step, 1..8 =
     // blocking depth.
     const bool tgv = h->prm.regularizer == FS_REG_TGV;
-    const int first = tgv ? 0 : (L.cluster >= 0 ? 0 : 1), last = tgv ? 8 : 24;
+    const int first = tgv ? 0 : (L.cluster >= 0 ? 0 : 1), last = tgv ? 8 : 32;
     for (int cand = first; cand <= last && st == FS_OK; ++cand) {
       h->prm.pd_schedule = cand == 0 ? 0 : 1;
       h->prm.block_iters = saved_block;
@@ -1374,7 +1375,7 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
   const bool tgv = h->prm.regularizer == FS_REG_TGV;
   for (int l = 0; l < h->L; ++l) {
     int c = choice[l];
-    if (c < -1 || c > (tgv ? 8 : 24))
+    if (c < -1 || c > (tgv ? 8 : 32))
       return fail(FS_EINVAL, "level %d: schedule %d out of range", l, c);
     if (c == 0 && !tgv && h->lv[l].cluster < 0)
       return fail(FS_EINVAL, "level %d does not fit one thread-block cluster", l);

@@ -6,7 +6,7 @@
 namespace fs {
 
 // k_pd footprints: 64 x 64 (512 threads), 32 x 32 and 64 x 32 (256 threads)
-enum PDVariant { PD_TILE_64 = 0, PD_TILE_32 = 1, PD_TILE_64x32 = 2 };
+enum PDVariant { PD_TILE_64 = 0, PD_TILE_32 = 1, PD_TILE_64x32 = 2, PD_TILE_64_T1024 = 3 };
 enum PDClusterVariant { PD_CLUSTER_16 = 0, PD_CLUSTER_32 = 1 };
 
 __global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView L);

@@ -292,6 +292,9 @@ static cudaError_t launch_pd_s(int variant, const LevelView& L, const PDState& i
     case PD_TILE_64: return launch_pd_t<64, 8, 8, S>(L, in, out, pp, B, n, chained, st);
     case PD_TILE_32: return launch_pd_t<32, 8, 4, S>(L, in, out, pp, B, n, chained, st);
     case PD_TILE_64x32: return launch_pd_t<64, 4, 8, S>(L, in, out, pp, B, n, chained, st);
+    // the 64 x 64 footprint with 1024 threads of 4 rows (64 registers):
+    // twice the resident warps of 512 threads of 8 rows
+    case PD_TILE_64_T1024: return launch_pd_t<64, 16, 4, S>(L, in, out, pp, B, n, chained, st);
     default: return cudaErrorInvalidValue;
   }
 }
