@@ -35,13 +35,14 @@ PD_BYTES_PER_PX_ITER = 52.0   # unblocked FP32 traffic of one pixel-iteration (9
 # command and figures are in profiles/k_pd_level0_kb1024.md)
 PD_L0_DRAM_BYTES_PER_LAUNCH = 47.7e6
 PD_L0_PROFILED_CHOICE = 31
-FOOTPRINTS = ["64x64 footprints, 512 threads", "32x32 footprints", "64x32 footprints",
-              "64x64 footprints, 1024 threads"]
+FOOTPRINTS = ["64x64 footprints, 512 threads", "32x32 footprints, 256 threads",
+              "64x32 footprints", "64x64 footprints, 1024 threads",
+              "32x32 footprints, 1024 threads", "32x32 footprints, 512 threads"]
 
 
 def schedule_label(c):
-    """fs_autotune's per-level choice in words (0 = cluster; 1..32 = depth
-    1..8 on each of the four footprints)."""
+    """fs_autotune's per-level choice in words (0 = cluster; 1..48 = depth
+    1..8 on each of the six footprints)."""
     if c == 0:
         return "cluster"
     return f"blocking x{(c - 1) % 8 + 1} ({FOOTPRINTS[(c - 1) // 8]})"

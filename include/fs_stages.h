@@ -92,13 +92,15 @@ fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
  * iterations (best of 3 after a warm-up, CUDA events on the handle's
  * stream) of each candidate -- the whole-level cluster schedule where the
  * level fits one cluster, and temporal blocking with 1..8 iterations per
- * launch on 64 x 64 (512 threads), 32 x 32, 64 x 32 or 64 x 64 (1024
- * threads) footprints -- and keeps the fastest for later solves when
+ * launch on six footprints -- and keeps the fastest for later solves when
  * block_iters = 0 and pd_schedule = 0.  choice (may be NULL) receives per
- * level 0 = cluster, 1..8 = that depth on 64 x 64 footprints of 512
- * threads, 9..16 = depth (choice - 8) on 32 x 32 footprints, 17..24 = depth
- * (choice - 16) on 64 x 32 footprints, 25..32 = depth (choice - 24) on
- * 64 x 64 footprints of 1024 threads.  On TGV handles the
+ * level 0 = cluster, or 8 v + d = depth d (1..8) on footprint v:
+ * v = 0: 64 x 64 pixels, 512 threads of 8 rows (choices 1..8);
+ * v = 1: 32 x 32, 256 threads of 4 rows (9..16);
+ * v = 2: 64 x 32, 256 threads of 8 rows (17..24);
+ * v = 3: 64 x 64, 1024 threads of 4 rows (25..32);
+ * v = 4: 32 x 32, 1024 threads of 1 row (33..40);
+ * v = 5: 32 x 32, 512 threads of 2 rows (41..48).  On TGV handles the
  * candidates are 0 = a dual and a primal launch per iteration and 1..8 =
  * temporal-blocking depth.  Overwrites the levels' state; synchronises the
  * stream.  All candidates give identical results. */

@@ -357,13 +357,15 @@ int pd_block(const fs_handle* h, int l) {
 }
 
 // A schedule choice of fs_autotune / fs_set_schedule: 0 = cluster (Huber-TV)
-// or a launch per step (TGV); 1..8, 9..16, 17..24, 25..32 = blocking depth on
-// 64 x 64 (512 threads), 32 x 32, 64 x 32, 64 x 64 (1024 threads) footprints
+// or a launch per step (TGV); 8 v + 1 .. 8 v + 8 = blocking depth 1..8 on
+// footprint variant v (PDVariant: 64 x 64 of 512 threads, 32 x 32 of 256,
+// 64 x 32, 64 x 64 of 1024, 32 x 32 of 1024, 32 x 32 of 512), so 1..48
 // (TGV: 1..8 = depth); -1 = none.
+constexpr int kMaxChoice = 8 * PD_TILE_COUNT;
 void decode_choice(int c, bool tgv, int& depth, int& variant) {
   if (c <= 0 || tgv) { depth = c; variant = -1; return; }
   depth = 1 + (c - 1) % 8;
-  variant = c <= 8 ? PD_TILE_64 : c <= 16 ? PD_TILE_32 : c <= 24 ? PD_TILE_64x32 : PD_TILE_64_T1024;
+  variant = (c - 1) / 8;
 }
 
 // Whether level l runs the whole-level cluster schedule.
@@ -1316,7 +1318,7 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
     // footprints (decode_choice).  TGV: 0 = a launch per step, 1..8 =
     // blocking depth.
     const bool tgv = h->prm.regularizer == FS_REG_TGV;
-    const int first = tgv ? 0 : (L.cluster >= 0 ? 0 : 1), last = tgv ? 8 : 32;
+    const int first = tgv ? 0 : (L.cluster >= 0 ? 0 : 1), last = tgv ? 8 : kMaxChoice;
     for (int cand = first; cand <= last && st == FS_OK; ++cand) {
       h->prm.pd_schedule = cand == 0 ? 0 : 1;
       h->prm.block_iters = saved_block;
@@ -1375,7 +1377,7 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
   const bool tgv = h->prm.regularizer == FS_REG_TGV;
   for (int l = 0; l < h->L; ++l) {
     int c = choice[l];
-    if (c < -1 || c > (tgv ? 8 : 32))
+    if (c < -1 || c > (tgv ? 8 : kMaxChoice))
       return fail(FS_EINVAL, "level %d: schedule %d out of range", l, c);
     if (c == 0 && !tgv && h->lv[l].cluster < 0)
       return fail(FS_EINVAL, "level %d does not fit one thread-block cluster", l);

@@ -6,7 +6,15 @@
 namespace fs {
 
 // k_pd footprints: 64 x 64 (512 threads), 32 x 32 and 64 x 32 (256 threads)
-enum PDVariant { PD_TILE_64 = 0, PD_TILE_32 = 1, PD_TILE_64x32 = 2, PD_TILE_64_T1024 = 3 };
+enum PDVariant {
+  PD_TILE_64 = 0,         // 64 x 64 footprint, 64 x 8 threads of 8 rows
+  PD_TILE_32 = 1,         // 32 x 32, 32 x 8 threads of 4 rows
+  PD_TILE_64x32 = 2,      // 64 x 32, 64 x 4 threads of 8 rows
+  PD_TILE_64_T1024 = 3,   // 64 x 64, 64 x 16 threads of 4 rows
+  PD_TILE_32_T1024 = 4,   // 32 x 32, 32 x 32 threads of 1 row
+  PD_TILE_32_T512 = 5,    // 32 x 32, 32 x 16 threads of 2 rows
+  PD_TILE_COUNT = 6
+};
 enum PDClusterVariant { PD_CLUSTER_16 = 0, PD_CLUSTER_32 = 1 };
 
 __global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView L);

@@ -295,6 +295,11 @@ static cudaError_t launch_pd_s(int variant, const LevelView& L, const PDState& i
     // the 64 x 64 footprint with 1024 threads of 4 rows (64 registers):
     // twice the resident warps of 512 threads of 8 rows
     case PD_TILE_64_T1024: return launch_pd_t<64, 16, 4, S>(L, in, out, pp, B, n, chained, st);
+    // small levels: the 32 x 32 footprint spread over more threads, which
+    // shortens each thread's dependent chain per iteration (the small levels
+    // are latency-bound, not issue-bound)
+    case PD_TILE_32_T1024: return launch_pd_t<32, 32, 1, S>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_32_T512: return launch_pd_t<32, 16, 2, S>(L, in, out, pp, B, n, chained, st);
     default: return cudaErrorInvalidValue;
   }
 }
