@@ -105,7 +105,15 @@ typedef struct {
  * Eq. 7 (g the unit tangent gamma'); FS_DERIV_CENTRAL (1) = half of
  * I1(x + w + g) - I1(x + w - g), exact on a quadratic image and free of the
  * sample I1(x + w) that Eq. 7 shares with the residual rho0, whose noise
- * otherwise biases every warp's step towards +u. */
+ * otherwise biases every warp's step towards +u.
+ * accel_gamma: 0 = constant steps and relaxation theta.  > 0 = the step
+ * schedule of Chambolle-Pock's Algorithm 2, which Sec. IV-C's "theta updated
+ * every iteration" names: iteration k of a warp uses tau_k, sigma_k and
+ * theta_k = 1 / sqrt(1 + 2 accel_gamma tau_k), then tau_{k+1} = theta_k
+ * tau_k, sigma_{k+1} = sigma_k / theta_k, from tau_0 = sigma_0 = 1/sqrt(8)
+ * at every warp (theta is then unused).  Needs precond = 0, the Huber-TV
+ * regulariser and FP32 storage (else FS_EINVAL).  The L1 data term is not
+ * uniformly convex, so the schedule carries no rate guarantee here. */
 #define FS_REG_HUBER_TV 0
 #define FS_REG_TGV 1
 #define FS_DERIV_FORWARD 0
@@ -125,13 +133,14 @@ typedef struct {
   int regularizer;         /* FS_REG_HUBER_TV or FS_REG_TGV                   */
   float alpha0, alpha1;    /* TGV weights (regularizer = FS_REG_TGV)          */
   int deriv;               /* FS_DERIV_FORWARD or FS_DERIV_CENTRAL            */
+  float accel_gamma;       /* 0, or the gamma of the accelerated schedule      */
 } fs_params;
 
 typedef struct fs_handle fs_handle;
 
 /* Fill *out with the defaults (lambda 50, eps 0.01, du_max 0.2, beta 9,
  * eta 0.85, theta 1, precond 1, block_iters 0, use_graph 0, Huber-TV,
- * alpha0 17, alpha1 1.2, deriv FS_DERIV_FORWARD). */
+ * alpha0 17, alpha1 1.2, deriv FS_DERIV_FORWARD, accel_gamma 0). */
 fs_status fs_default_params(fs_params* out);
 
 /* Create the per-rig state for W x H pairs and `levels` pyramid levels
@@ -261,7 +270,8 @@ fs_status fs_batch_destroy(fs_batch* b);
  *   d_u     W x H disparity, read as the start value and overwritten
  *   d_p     2 x W x H dual variable (x then y plane), read and overwritten
  *   prm     NULL for the defaults; lambda, huber_eps, beta, eta, theta,
- *           precond and block_iters are used
+ *           precond and block_iters are used; accel_gamma must be 0
+ *           (FS_EINVAL otherwise)
  *   cuda_stream  stream for the work (NULL = legacy default stream)
  * All pointers are device pointers, dense row-major (pitch W), owned by
  * the caller.  W, H >= 2, iters >= 1; W * H > FS_NOALLOC_MAX_PIXELS

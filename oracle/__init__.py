@@ -34,7 +34,8 @@ from .geometry import (trajectory_field, trajectory_vector, calibration_field,
 from .pyramid import level_sizes, scaled_calib, fov_mask, downsample, upsample
 from .variational import (Params, grad_masks, grad, div, tensor_sqrt, precondition,
                           dual_step, shrink, primal_step, pd_iteration,
-                          warp_linearize, clip_update, energy)
+                          warp_linearize, clip_update, energy, accel_schedule,
+                          check_accel)
 from .solve import solve, solve_level_warps, warm_start_w
 from .tgv import div_q, grad_v, tgv_energy, tgv_iteration, tgv_steps
 
@@ -46,6 +47,7 @@ __all__ = [
     "level_sizes", "scaled_calib", "fov_mask", "downsample", "upsample",
     "Params", "grad_masks", "grad", "div", "tensor_sqrt", "precondition",
     "dual_step", "shrink", "primal_step", "pd_iteration", "warp_linearize",
-    "clip_update", "energy", "solve", "solve_level_warps", "warm_start_w",
+    "clip_update", "energy", "accel_schedule", "check_accel", "solve",
+    "solve_level_warps", "warm_start_w",
     "grad_v", "div_q", "tgv_steps", "tgv_iteration", "tgv_energy",
 ]

@@ -30,7 +30,7 @@ from .geometry import (calibration_field, prerotate, trajectory_field,
 from .pyramid import downsample_fast, fov_mask, level_sizes, scaled_calib, upsample
 from .interp import bicubic
 from .tgv import tgv_iteration, tgv_steps
-from .variational import (Params, clip_update, grad_masks, pd_iteration,
+from .variational import (Params, check_accel, clip_update, grad_masks, pd_iteration,
                           precondition, tensor_sqrt, warp_linearize)
 
 
@@ -63,7 +63,7 @@ def solve_level_warps(I0l, I1l, gamma, lv, u, w, p1, p2, warps, iters,
     for om in range(warps):
         Iu, rho0, g = warp_linearize(I0l, I1l, w, gamma, M, prm.deriv)
         st = dict(u=u.copy(), ubar=u.copy(), p1=p1, p2=p2, Iu=Iu, rho0=rho0,
-                  u_w=u.copy())
+                  u_w=u.copy(), k=0)
         if tgv is not None:
             st.update(tgv, vb1=tgv["v1"].copy(), vb2=tgv["v2"].copy())
         if on_iter is not None:
@@ -117,6 +117,7 @@ def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params()
     w_init (H, W, 2), given with d_init, is a video stream's continuation:
     w is taken as given (the previous frame's w) instead of being rebuilt.
     """
+    check_accel(prm)
     cam0 = calib_from_dict(cam0)
     cam1 = calib_from_dict(cam1)
     I0 = np.asarray(I0, dtype=np.float64)

@@ -57,6 +57,9 @@ class Params:
     alpha1: float = 1.2      # Sec. IV-C, TGV first-order weight
     deriv: str = "forward"   # I_u: "forward" = Eq. 7; "central" = half the
                              # difference of the samples at x + w +- g
+    accel_gamma: float = 0.0  # > 0: the step schedule of Chambolle-Pock's
+                              # Algorithm 2 (Sec. IV-C's "theta updated every
+                              # iteration"); scalar steps only (precond False)
 
 
 def grad_masks(M):
@@ -188,13 +191,53 @@ def primal_step(u, p1, p2, a, b, c, m1, m2, tau, Iu, rho0, u_w, lam, M):
     return np.where(M, shrink(uh, Iu, rho0, u_w, tau, lam), u)
 
 
+def accel_schedule(gamma, n, tau0=1.0 / np.sqrt(8.0), sig0=1.0 / np.sqrt(8.0)):
+    """Steps of Chambolle-Pock's Algorithm 2 for n iterations: iteration k
+    uses tau_k and sigma_k, relaxes with theta_k = 1 / sqrt(1 + 2 gamma tau_k),
+    then tau_{k+1} = theta_k tau_k and sigma_{k+1} = sigma_k / theta_k.
+    Returns arrays (tau, sigma, theta) of length n."""
+    tau = np.empty(n)
+    sig = np.empty(n)
+    th = np.empty(n)
+    t, s = tau0, sig0
+    for k in range(n):
+        tau[k], sig[k] = t, s
+        th[k] = 1.0 / np.sqrt(1.0 + 2.0 * gamma * t)
+        t, s = th[k] * t, s / th[k]
+    return tau, sig, th
+
+
+def check_accel(prm: Params):
+    if prm.accel_gamma < 0 or not np.isfinite(prm.accel_gamma):
+        raise ValueError("accel_gamma must be finite and >= 0")
+    if prm.accel_gamma > 0 and (prm.precond or prm.regularizer != "huber_tv"):
+        raise ValueError("the accelerated schedule needs scalar steps (precond False) "
+                         "and the Huber-TV regulariser")
+
+
 def pd_iteration(st, lv, prm: Params):
-    """One iteration on state dict st (u, ubar, p1, p2) with level data lv."""
+    """One iteration on state dict st (u, ubar, p1, p2) with level data lv.
+
+    With prm.accel_gamma > 0 the scalar steps and the relaxation follow
+    accel_schedule, restarted at every warp: st["k"] counts the warp's
+    iterations (solve_level_warps sets it to 0); tau_k applies on the mask
+    only (u is held outside it) and sigma_k everywhere, as the unaccelerated
+    scalar steps do."""
+    if prm.accel_gamma > 0:
+        k = st["k"]
+        tau_s, sig_s, th_s = accel_schedule(prm.accel_gamma, k + 1)
+        sig = np.full(lv["M"].shape, sig_s[k])
+        tau = np.where(lv["M"], tau_s[k], 0.0)
+        theta = th_s[k]
+        st["k"] = k + 1
+    else:
+        sig, tau, theta = lv["sig1"], lv["tau"], prm.theta
     p1, p2 = dual_step(st["p1"], st["p2"], st["ubar"], lv["a"], lv["b"], lv["c"],
-                       lv["m1"], lv["m2"], lv["sig1"], lv["sig2"], prm.eps)
+                       lv["m1"], lv["m2"], sig, sig if prm.accel_gamma > 0 else lv["sig2"],
+                       prm.eps)
     u_new = primal_step(st["u"], p1, p2, lv["a"], lv["b"], lv["c"], lv["m1"], lv["m2"],
-                        lv["tau"], st["Iu"], st["rho0"], st["u_w"], prm.lam, lv["M"])
-    ubar = u_new + prm.theta * (u_new - st["u"])
+                        tau, st["Iu"], st["rho0"], st["u_w"], prm.lam, lv["M"])
+    ubar = u_new + theta * (u_new - st["u"])
     st.update(u=u_new, ubar=ubar, p1=p1, p2=p2)
     return st
 

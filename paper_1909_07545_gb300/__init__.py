@@ -75,7 +75,8 @@ class FsParams(ctypes.Structure):
                 ("block_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("pd_schedule", ctypes.c_int), ("storage", ctypes.c_int),
                 ("regularizer", ctypes.c_int), ("alpha0", ctypes.c_float),
-                ("alpha1", ctypes.c_float), ("deriv", ctypes.c_int)]
+                ("alpha1", ctypes.c_float), ("deriv", ctypes.c_int),
+                ("accel_gamma", ctypes.c_float)]
 
 
 _PARAM_FIELDS = {f[0] for f in FsParams._fields_}

@@ -248,6 +248,10 @@ struct fs_handle {
   std::vector<std::string> gname;
   unsigned long long* gband_dev = nullptr;
   int* gflag = nullptr;
+  // the accelerated step schedule (accel_gamma > 0): one float4 per
+  // iteration of a warp, for the last iteration count it was built for
+  float4* sched = nullptr;
+  int sched_cap = 0, sched_iters = 0;
 };
 
 namespace fs {
@@ -371,7 +375,7 @@ void decode_choice(int c, bool tgv, int& depth, int& variant) {
 // Whether level l runs the whole-level cluster schedule.
 bool use_cluster(const fs_handle* h, int l) {
   const HostLevel& L = h->lv[l];
-  if (L.cluster < 0 || h->prm.pd_schedule != 0) return false;
+  if (L.cluster < 0 || h->prm.pd_schedule != 0 || h->prm.accel_gamma > 0) return false;
   if (h->prm.block_iters <= 0 && L.tuned >= 1) return false;   // tuner chose blocking
   return true;
 }
@@ -386,9 +390,50 @@ int pd_launches(int iters, int B) {
   return n;
 }
 
+// The accelerated schedule's table for at least `iters` iterations per
+// warp, built in FP64 on the host and stored as FP32 (synchronous; called
+// outside any graph capture, before the launches that read it).  The table
+// for n iterations is a prefix of the one for more, so it only grows; a
+// reallocation moves it, and the handle's cached graph is dropped then
+// (batches key their graphs on the table's address).
+fs_status ensure_schedule(fs_handle* h, int iters) {
+  if (!(h->prm.accel_gamma > 0) || h->sched_iters >= iters) return FS_OK;
+  if (iters > h->sched_cap) {
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->sched) cudaFree(h->sched);
+    h->sched = nullptr;
+    h->sched_cap = 0;
+    if (cudaMalloc(&h->sched, (size_t)iters * sizeof(float4)) != cudaSuccess) {
+      cudaGetLastError();
+      h->sched = nullptr;
+      return fail(FS_ENOMEM, "accelerated schedule allocation failed");
+    }
+    h->sched_cap = iters;
+  }
+  std::vector<float4> tab((size_t)iters);
+  const double t0 = 1.0 / std::sqrt(8.0), g = h->prm.accel_gamma, eps = h->prm.huber_eps;
+  double t = t0, s = t0;
+  for (int k = 0; k < iters; ++k) {
+    const double th = 1.0 / std::sqrt(1.0 + 2.0 * g * t);
+    const double dinv = 1.0 / (1.0 + s * eps);
+    tab[k] = make_float4((float)(t / t0), (float)dinv, (float)(s * dinv), (float)th);
+    t *= th;
+    s /= th;
+  }
+  FS_CUDA(cudaStreamSynchronize(h->stream));
+  FS_CUDA(cudaMemcpy(h->sched, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  h->sched_iters = iters;
+  return FS_OK;
+}
+
 fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
   HostLevel& L = h->lv[l];
   PDParams pp{h->prm.lambda, h->prm.huber_eps, h->prm.theta};
+  if (h->prm.accel_gamma > 0) {
+    if (!h->sched || h->sched_iters < iters)
+      return fail(FS_EINVAL, "accelerated schedule not built for %d iterations", iters);
+    pp.sched = h->sched;
+  }
   if (h->prm.regularizer == FS_REG_TGV) {
     TgvParams tp{h->prm.lambda, h->prm.theta, h->prm.alpha0, h->prm.alpha1, h->prm.precond};
     // block_iters when set, else the tuned depth, else 4 (0 = launch per step)
@@ -414,6 +459,7 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
     if ((iters - done) % (nl - k)) ++n;
     const PDState& in = (k % 2 == 0) ? A : Bs;
     const PDState& out = (k % 2 == 0) ? Bs : A;
+    pp.k0 = done;
     cudaError_t e = launch_pd(variant, L.v, in, out, pp, B, n, st, k > 0);
     if (e != cudaSuccess) return fail(FS_ECUDA, "launch of k_pd failed: %s", cudaGetErrorString(e));
     done += n;
@@ -449,9 +495,11 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
       if (h->prm.regularizer == FS_REG_TGV)
         FS_LAUNCH("k_tgv_warp_start", launch_tgv_warp_start(L.v, st));
       return FS_OK;
-    case FS_STAGE_PD:
+    case FS_STAGE_PD: {
       if (count < 1) return fail(FS_EINVAL, "pd: count must be >= 1");
-      return run_pd(h, l, count, st);
+      fs_status s = ensure_schedule(h, count);
+      return s != FS_OK ? s : run_pd(h, l, count, st);
+    }
     case FS_STAGE_CLIP:
       k_clip<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, h->prm.du_max);
       FS_LAUNCHED("k_clip");
@@ -620,6 +668,7 @@ fs_status fs_default_params(fs_params* out) {
   out->alpha0 = 17.f;
   out->alpha1 = 1.2f;
   out->deriv = FS_DERIV_FORWARD;
+  out->accel_gamma = 0.f;
   return FS_OK;
 }
 
@@ -650,6 +699,12 @@ fs_status fs_internal_validate(const fs_calib cam[2], const fs_pose* pose, int W
         (!(p.alpha0 >= 0) || !(p.alpha1 > 0) || !std::isfinite(p.alpha0) ||
          !std::isfinite(p.alpha1) || p.storage != 0))
       return fail(FS_EINVAL, "TGV needs alpha0 >= 0, alpha1 > 0 and FP32 storage");
+    if (!(p.accel_gamma >= 0) || !std::isfinite(p.accel_gamma))
+      return fail(FS_EINVAL, "accel_gamma must be finite and >= 0");
+    if (p.accel_gamma > 0 &&
+        (p.precond != 0 || p.regularizer != FS_REG_HUBER_TV || p.storage != 0))
+      return fail(FS_EINVAL,
+                  "accel_gamma > 0 needs precond = 0, the Huber-TV regulariser and FP32 storage");
   }
   size_t bytes = 0;
   return fs_state_bytes(W, H, levels, prm, &bytes);   // level sizes
@@ -890,6 +945,7 @@ static fs_status solve_launch(fs_handle* h, const float* d_I0, const float* d_I1
   if (warps < 1 || iters < 1) return fail(FS_EINVAL, "warps and iters must be >= 1");
   if (cont && !h->has_state) return fail(FS_EINVAL, "fs_solve_continue: the handle holds no result");
   if (h->timing && (s = prepare_timing(h, warps)) != FS_OK) return s;
+  if ((s = ensure_schedule(h, iters)) != FS_OK) return s;
   if (!h->prm.use_graph) {
     h->has_state = false;
     s = enqueue_solve(h, d_I0, d_I1, d_init, warps, iters, d_disp, d_depth, h->stream, nullptr,
@@ -984,6 +1040,7 @@ fs_status fs_destroy(fs_handle* h) {
   if (h->stage) cudaFree(h->stage);
   if (h->eacc) cudaFree(h->eacc);
   if (h->gband_dev) cudaFree(h->gband_dev);
+  if (h->sched) cudaFree(h->sched);
   if (h->arena) cudaFree(h->arena);
   delete h;
   return FS_OK;
@@ -1061,9 +1118,12 @@ extern "C" fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0,
   if (warps < 1 || iters < 1) return fail(FS_EINVAL, "warps and iters must be >= 1");
   const int n = (int)b->h.size();
   std::vector<const void*> key;
-  key.reserve(5 * n);
+  key.reserve(6 * n);
   for (int i = 0; i < n; ++i) {
     if (!d_I0[i] || !d_I1[i]) return fail(FS_EINVAL, "null input image for pair %d", i);
+    fs_status s;
+    if ((s = ensure_schedule(b->h[i], iters)) != FS_OK) return s;
+    key.push_back(b->h[i]->sched);
     key.push_back(d_I0[i]);
     key.push_back(d_I1[i]);
     key.push_back(d_init ? d_init[i] : nullptr);
@@ -1301,6 +1361,7 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
   fs_status s;
   if ((s = check_handle(h)) != FS_OK) return s;
   if (iters < 1) return fail(FS_EINVAL, "iters must be >= 1");
+  if ((s = ensure_schedule(h, iters)) != FS_OK) return s;
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   h->has_state = false;   // the trial runs overwrite every level's state
   cudaEvent_t e0, e1;
@@ -1318,7 +1379,8 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
     // footprints (decode_choice).  TGV: 0 = a launch per step, 1..8 =
     // blocking depth.
     const bool tgv = h->prm.regularizer == FS_REG_TGV;
-    const int first = tgv ? 0 : (L.cluster >= 0 ? 0 : 1), last = tgv ? 8 : kMaxChoice;
+    const bool cl = L.cluster >= 0 && !(h->prm.accel_gamma > 0);
+    const int first = tgv ? 0 : (cl ? 0 : 1), last = tgv ? 8 : kMaxChoice;
     for (int cand = first; cand <= last && st == FS_OK; ++cand) {
       h->prm.pd_schedule = cand == 0 ? 0 : 1;
       h->prm.block_iters = saved_block;
@@ -1379,7 +1441,7 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
     int c = choice[l];
     if (c < -1 || c > (tgv ? 8 : kMaxChoice))
       return fail(FS_EINVAL, "level %d: schedule %d out of range", l, c);
-    if (c == 0 && !tgv && h->lv[l].cluster < 0)
+    if (c == 0 && !tgv && (h->lv[l].cluster < 0 || h->prm.accel_gamma > 0))
       return fail(FS_EINVAL, "level %d does not fit one thread-block cluster", l);
   }
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }

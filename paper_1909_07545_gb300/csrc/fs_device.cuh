@@ -311,6 +311,12 @@ struct PDState {
 
 struct PDParams {
   float lam, eps, theta;
+  // Chambolle-Pock Algorithm 2 steps (scalar steps only), per iteration of
+  // a warp: x = tau_k / tau_0, y = 1 / (1 + sigma_k eps), z = sigma_k y,
+  // w = theta_k; nullptr for the constant steps.  k0 = the warp's iterations
+  // done before this launch.
+  const float4* sched = nullptr;
+  int k0 = 0;
 };
 
 }  // namespace fs

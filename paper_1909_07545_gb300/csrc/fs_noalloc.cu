@@ -103,6 +103,9 @@ extern "C" fs_status fs_pd_iterate_noalloc(const float* d_I0, const unsigned cha
   if (!(p.lambda > 0) || !(p.huber_eps >= 0) || !(p.theta >= 0 && p.theta <= 1) ||
       p.block_iters < 0 || p.block_iters > 8)
     return fs_internal_set_error(FS_EINVAL, "fs_pd_iterate_noalloc: parameter out of range");
+  if (p.accel_gamma != 0.f)      // the schedule table lives on a handle
+    return fs_internal_set_error(FS_EINVAL,
+                                 "fs_pd_iterate_noalloc: accel_gamma is not supported here");
   unsigned char* base = nullptr;
   fs_status s = scratch_for_current_device(&base, msg, sizeof(msg));
   if (s != FS_OK) return fs_internal_set_error(s, msg);

@@ -33,7 +33,11 @@ namespace cg = cooperative_groups;
 
 namespace fs {
 
-template <int FW, int NY, int R, int S>
+// ACC: the accelerated step schedule of pp.sched (FP32 storage, scalar
+// steps): iteration it of the launch uses entry pp.k0 + it for sigma (all
+// pixels), tau and the L1 step (scaled from the stored tau_0 values, 0 off
+// the mask) and theta.
+template <int FW, int NY, int R, int S, bool ACC>
 __global__ void __launch_bounds__(FW * NY, FW * NY >= 512 ? 1 : 2)
 k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int chained) {
   constexpr int FH = NY * R;
@@ -47,7 +51,7 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
   const int oy = (int)blockIdx.y * IH - B;
   const int gx = ox + tx;
   const bool col_in = gx >= 0 && gx < L.W;
-  const float theta = pp.theta;
+  float theta = pp.theta;
 
   // Let the next launch of the chain be scheduled as soon as every CTA of
   // this one is resident (it waits for this grid's completion before it
@@ -108,12 +112,22 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
   float t1r[R], t2r[R];
 #pragma unroll 1
   for (int it = 0; it < n_iters; ++it) {
+    float4 sk = make_float4(1.f, 0.f, 0.f, 0.f);
+    if constexpr (ACC) {
+      sk = pp.sched[pp.k0 + it];
+      theta = sk.w;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int fy = ty * R + r;
       const float right = s_ub[fy][txr];
       const float below = (r + 1 < R) ? ub[r + 1] : s_ub[min(fy + 1, FH - 1)][tx];
-      px_dual(mb >> (3 * r), ub[r], right, below, c[r], p1[r], p2[r], t1r[r], t2r[r]);
+      PxConst cr = c[r];
+      if constexpr (ACC) {
+        cr.dinv = sk.y;
+        cr.sd = sk.z;
+      }
+      px_dual(mb >> (3 * r), ub[r], right, below, cr, p1[r], p2[r], t1r[r], t2r[r]);
       s_t1[fy][tx] = t1r[r];
       if (r == R - 1) s_t2[fy][tx] = t2r[r];
     }
@@ -125,7 +139,12 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
       // thread above (the top row of the footprint is halo: its own value)
       const float t2_up = r > 0 ? t2r[r - 1] : (ty > 0 ? s_t2[fy - 1][tx] : t2r[0]);
       const float dv = px_div(t1r[r], s_t1[fy][txl], t2r[r], t2_up);
-      const float un = px_primal(u[r], dv, c[r]);
+      PxConst cr = c[r];
+      if constexpr (ACC) {
+        cr.tau = __fmul_rn(c[r].tau, sk.x);
+        cr.step = __fmul_rn(c[r].step, sk.x);
+      }
+      const float un = px_primal(u[r], dv, cr);
       ub[r] = px_relax(un, u[r], theta);
       u[r] = un;
       s_ub[fy][tx] = ub[r];
@@ -266,7 +285,7 @@ k_pd_cluster(LevelView L, PDParams pp, int n_iters) {
   }
 }
 
-template <int FW, int NY, int R, int S>
+template <int FW, int NY, int R, int S, bool ACC = false>
 static cudaError_t launch_pd_t(const LevelView& L, const PDState& in, const PDState& out,
                                const PDParams& pp, int B, int n, bool chained,
                                cudaStream_t st) {
@@ -281,7 +300,7 @@ static cudaError_t launch_pd_t(const LevelView& L, const PDState& in, const PDSt
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k_pd<FW, NY, R, S>, L, in, out, pp, B, n, chained ? 1 : 0);
+  return cudaLaunchKernelEx(&cfg, k_pd<FW, NY, R, S, ACC>, L, in, out, pp, B, n, chained ? 1 : 0);
 }
 
 template <int S>
@@ -304,8 +323,25 @@ static cudaError_t launch_pd_s(int variant, const LevelView& L, const PDState& i
   }
 }
 
+// The accelerated schedule (FP32 storage only) on each footprint.
+static cudaError_t launch_pd_acc(int variant, const LevelView& L, const PDState& in,
+                                 const PDState& out, const PDParams& pp, int B, int n,
+                                 cudaStream_t st, bool chained) {
+  if (L.st != ST_F32) return cudaErrorInvalidValue;
+  switch (variant) {
+    case PD_TILE_64: return launch_pd_t<64, 8, 8, ST_F32, true>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_32: return launch_pd_t<32, 8, 4, ST_F32, true>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_64x32: return launch_pd_t<64, 4, 8, ST_F32, true>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_64_T1024: return launch_pd_t<64, 16, 4, ST_F32, true>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_32_T1024: return launch_pd_t<32, 32, 1, ST_F32, true>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_32_T512: return launch_pd_t<32, 16, 2, ST_F32, true>(L, in, out, pp, B, n, chained, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_pd(int variant, const LevelView& L, const PDState& in, const PDState& out,
                       const PDParams& pp, int B, int n, cudaStream_t st, bool chained) {
+  if (pp.sched) return launch_pd_acc(variant, L, in, out, pp, B, n, st, chained);
   switch (L.st) {
     case ST_F16: return launch_pd_s<ST_F16>(variant, L, in, out, pp, B, n, st, chained);
     case ST_BF16: return launch_pd_s<ST_BF16>(variant, L, in, out, pp, B, n, st, chained);

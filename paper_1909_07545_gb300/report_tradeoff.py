@@ -5,14 +5,16 @@ a smaller du_max needs more warps but tracks the epipolar curve better).
 
     python -m paper_1909_07545_gb300.report_tradeoff [--size 800] [--levels 5]
         [--iters 10] [--scene equidistant|kb] [--deriv forward,central]
-        [--out report.json]
+        [--precond 1] [--accel-gamma 0] [--out report.json]
 
 Run from the repository root (it uses the ``synth`` scene generator).  The
 scene is the 180-degree equidistant generator (3 textured planes at 1-5 m,
 0.1 m baseline, noise-free) or the 190-degree Kannala-Brandt one (20
 objects at 0.5-20 m, 0.12 m baseline, small rotation, Gaussian image noise
 0.01) at the given size; --deriv lists how I_u is taken (the forward
-difference of Eq. 7 and / or the central one).  Every solve is one CUDA graph replay timed
+difference of Eq. 7 and / or the central one); --precond 0 takes scalar
+steps, and --accel-gamma lists gammas of the accelerated step schedule
+(0 = constant steps; > 0 needs --precond 0).  Every solve is one CUDA graph replay timed
 with CUDA events (mean of 3 after one untimed solve).  Errors are over the
 FOV mask where the ground truth is defined: mean and median end-point error
 and the fractions of pixels off by more than 1 and 5 px.
@@ -37,6 +39,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--scene", choices=("equidistant", "kb"), default="equidistant")
     ap.add_argument("--deriv", default="forward")
+    ap.add_argument("--precond", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--accel-gamma", default="0")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     sys.path.insert(0, os.getcwd())
@@ -54,10 +58,12 @@ def main():
     I0 = torch.as_tensor(np.float32(p["I0"]), device="cuda")
     I1 = torch.as_tensor(np.float32(p["I1"]), device="cuda")
     rows = []
-    combos = [(dv, float(v)) for dv in args.deriv.split(",") for v in args.du_max.split(",")]
-    for deriv, dm in combos:
+    combos = [(dv, float(v), float(ga)) for dv in args.deriv.split(",")
+              for v in args.du_max.split(",") for ga in args.accel_gamma.split(",")]
+    for deriv, dm, ga in combos:
         s = Solver(p["cam0"], p["cam1"], p["R"], p["t"], W, W, args.levels, lam=p["lam"],
-                   huber_eps=p["eps"], du_max=dm, use_graph=1, deriv=deriv)
+                   huber_eps=p["eps"], du_max=dm, use_graph=1, deriv=deriv,
+                   precond=args.precond, accel_gamma=ga)
         s.autotune(args.iters)
         mask = s.read(0, "MASK").cpu().numpy() > 0.5
         v = valid & mask
@@ -74,14 +80,15 @@ def main():
             e1.record()
             torch.cuda.synchronize()
             err = synth.disparity_errors(d.double().cpu().numpy(), g, v)
-            rows.append(dict(deriv=deriv, du_max=dm, warps=n, ms=e0.elapsed_time(e1) / 3, **err))
+            rows.append(dict(deriv=deriv, accel_gamma=ga, precond=args.precond, du_max=dm, warps=n, ms=e0.elapsed_time(e1) / 3, **err))
             print(json.dumps(rows[-1]), flush=True)
         s.close()
     print(f"\n{args.scene} {W}x{W}, {args.levels} levels, {args.iters} iterations per warp")
-    print("| I_u | du_max | N | ms/frame | EPE mean | EPE median | tau>1 | tau>5 |")
-    print("|---|---:|---:|---:|---:|---:|---:|---:|")
+    print("| I_u | precond | gamma | du_max | N | ms/frame | EPE mean | EPE median | tau>1 | tau>5 |")
+    print("|---|---:|---:|---:|---:|---:|---:|---:|---:|---:|")
     for r in rows:
-        print(f"| {r['deriv']} | {r['du_max']} | {r['warps']} | {r['ms']:.2f} | {r['epe_mean']:.3f} | "
+        print(f"| {r['deriv']} | {r['precond']} | {r['accel_gamma']} | {r['du_max']} | {r['warps']} | "
+              f"{r['ms']:.2f} | {r['epe_mean']:.3f} | "
               f"{r['epe_median']:.3f} | {100 * r['tau1']:.1f} % | {100 * r['tau5']:.1f} % |")
     if args.out:
         with open(args.out, "w") as f:

@@ -83,12 +83,15 @@ def test_host_side_validation(lib):
     assert st == -1 and "parameter" in msg
     for bad in (dict(regularizer="tgv", storage="f16"), dict(regularizer="tgv", alpha1=0.0),
                 dict(regularizer="tgv", alpha0=-1.0), dict(regularizer=2), dict(deriv=2),
-                dict(deriv=-1)):
+                dict(deriv=-1), dict(accel_gamma=-1.0), dict(accel_gamma=0.1),
+                dict(accel_gamma=0.1, precond=0, storage="f16"),
+                dict(accel_gamma=0.1, precond=0, regularizer="tgv")):
         st, msg = _create([EQ, EQ], prm=fsb.default_params(**bad))
         assert st == -1, bad
     p = fsb.default_params()
     assert p.regularizer == 0 and p.alpha0 == pytest.approx(17.0) and p.alpha1 == pytest.approx(1.2)
     assert p.deriv == 0 and fsb.default_params(deriv="central").deriv == 1   # Eq. 7 by default
+    assert p.accel_gamma == 0.0
     with pytest.raises(TypeError):
         fsb.default_params(derivative="central")                   # no silent typo
     h = ctypes.c_void_p()

@@ -141,6 +141,31 @@ def test_central_derivative_matches_oracle():
     s.close()
 
 
+@pytest.mark.parametrize("gamma", [0.05, 0.5])
+def test_accelerated_schedule_matches_oracle(small, gamma):
+    # Chambolle-Pock Algorithm 2 steps (accel_gamma), restarted every warp
+    ref = _oracle(small, warps=3, iters=40, precond=False, accel_gamma=gamma)
+    sens = oracle_sensitivity(small, ref, warps=3, iters=40, precond=False, accel_gamma=gamma)
+    s = make_solver(small, precond=0, accel_gamma=gamma)
+    disp, depth = s.solve(small["I0"], small["I1"], 3, 40)
+    _compare(small, ref, disp, depth, sens)
+    d0 = np64(disp)
+    s.close()
+    # every schedule gives the same bits: blocking depths, footprints, the
+    # tuner, graph replay (iteration k of a warp reads entry k of the table
+    # whichever launch it falls in)
+    for prm in (dict(pd_schedule=1, block_iters=1), dict(pd_schedule=1, block_iters=7),
+                dict(use_graph=1)):
+        t = make_solver(small, precond=0, accel_gamma=gamma, **prm)
+        if prm.get("use_graph"):
+            choice = t.autotune(40)
+            assert all(c >= 1 for c in choice)          # no cluster schedule here
+            t.solve(small["I0"], small["I1"], 3, 40)
+        d, _ = t.solve(small["I0"], small["I1"], 3, 40)
+        assert np.array_equal(np64(d), d0), prm
+        t.close()
+
+
 def test_unpreconditioned_steps_match_oracle(small):
     ref = _oracle(small, warps=3, iters=40, precond=False)
     sens = oracle_sensitivity(small, ref, warps=3, iters=40, precond=False)

@@ -215,6 +215,50 @@ def test_energy_descends_over_a_warp(seed):
     assert abs(finals[0] - finals[1]) <= 1e-6 * finals[0]
 
 
+def test_accel_schedule_recursion():
+    # Chambolle-Pock Algorithm 2: tau_k sigma_k stays tau_0 sigma_0, theta_k
+    # lies in (0, 1], tau_k falls, and tau_k ~ 1 / (gamma k) for large k
+    # (tau_{k+1}^-2 = tau_k^-2 + 2 gamma tau_k^-1 / (1 + ...) grows by about
+    # 2 gamma / tau_k per step); gamma = 0 is the constant theta = 1 schedule
+    from oracle import accel_schedule
+    t0 = 1 / np.sqrt(8)
+    tau, sig, th = accel_schedule(0.0, 50)
+    assert np.all(tau == t0) and np.all(sig == t0) and np.all(th == 1.0)
+    g = 0.3
+    tau, sig, th = accel_schedule(g, 200000)
+    assert np.allclose(tau * sig, t0 * t0, rtol=1e-12)
+    assert np.all((th > 0) & (th <= 1)) and np.all(np.diff(tau) < 0)
+    assert np.allclose(th, 1 / np.sqrt(1 + 2 * g * tau), rtol=1e-15)
+    assert np.allclose(tau[1:], th[:-1] * tau[:-1], rtol=1e-15)
+    k = np.arange(len(tau))
+    assert abs(tau[-1] * g * k[-1] - 1.0) < 0.01
+
+
+def test_accel_iteration_reduces_to_theta_one_and_settles():
+    # gamma = 0 gives the plain scalar iteration bit for bit; gamma > 0 (an
+    # accelerated schedule on a data term that is not uniformly convex, so
+    # no rate is guaranteed) still lowers the energy and ends near the
+    # minimum of the constant-step run
+    finals = {}
+    for gamma in (0.0, 1e-300, 0.05):
+        prm, lv, st = _level(10, 12, 2, False, lam=5.0, eps=0.05)
+        if gamma:
+            prm = Params(lam=5.0, eps=0.05, precond=False, accel_gamma=gamma)
+        st["k"] = 0
+        args = lambda s: (s["u"], s["u_w"], s["Iu"], s["rho0"], lv["a"], lv["b"], lv["c"],
+                          lv["m1"], lv["m2"], lv["M"], prm.lam, prm.eps)
+        E0 = energy(*args(st))
+        for _ in range(1500):
+            pd_iteration(st, lv, prm)
+        finals[gamma] = (energy(*args(st)), st["u"].copy())
+        assert finals[gamma][0] < 0.8 * E0
+    assert np.array_equal(finals[0.0][1], finals[1e-300][1])
+    assert finals[0.05][0] <= finals[0.0][0] * (1 + 1e-3)
+    with pytest.raises(ValueError):
+        from oracle import check_accel
+        check_accel(Params(accel_gamma=0.1, precond=True))
+
+
 def test_warp_linearize_on_affine_image():
     # Eq. 5 equals Eq. 4 for an affine I1; rho0 = I1(x + w) - I0(x) exactly
     H, W = 16, 20
