@@ -92,8 +92,8 @@ fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
  * iterations (best of 3 after a warm-up, CUDA events on the handle's
  * stream) of each candidate -- the whole-level cluster schedule where the
  * level fits one cluster, and temporal blocking with 1..8 iterations per
- * launch on six footprints -- and keeps the fastest for later solves when
- * block_iters = 0 and pd_schedule = 0.  choice (may be NULL) receives per
+ * launch on each of six footprints -- and keeps the fastest for later
+ * solves when block_iters = 0 and pd_schedule = 0.  choice (may be NULL) receives per
  * level 0 = cluster, or 8 v + d = depth d (1..8) on footprint v:
  * v = 0: 64 x 64 pixels, 512 threads of 8 rows (choices 1..8);
  * v = 1: 32 x 32, 256 threads of 4 rows (9..16);
