@@ -364,10 +364,13 @@ int pd_block(const fs_handle* h, int l) {
 // or a launch per step (TGV); 8 v + 1 .. 8 v + 8 = blocking depth 1..8 on
 // footprint variant v (PDVariant: 64 x 64 of 512 threads, 32 x 32 of 256,
 // 64 x 32, 64 x 64 of 1024, 32 x 32 of 1024, 32 x 32 of 512), so 1..48
-// (TGV: 1..8 = depth); -1 = none.
+// (TGV: 8 v + 1 .. 8 v + 8 = depth on the TGV footprint v, 0..2, so 1..24);
+// -1 = none.
 constexpr int kMaxChoice = 8 * PD_TILE_COUNT;
+constexpr int kMaxTgvChoice = 8 * kTgvVariants;
 void decode_choice(int c, bool tgv, int& depth, int& variant) {
-  if (c <= 0 || tgv) { depth = c; variant = -1; return; }
+  (void)tgv;
+  if (c <= 0) { depth = c; variant = -1; return; }
   depth = 1 + (c - 1) % 8;
   variant = (c - 1) / 8;
 }
@@ -436,9 +439,11 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
   }
   if (h->prm.regularizer == FS_REG_TGV) {
     TgvParams tp{h->prm.lambda, h->prm.theta, h->prm.alpha0, h->prm.alpha1, h->prm.precond};
-    // block_iters when set, else the tuned depth, else 4 (0 = launch per step)
+    // block_iters when set, else the tuned depth, else 4 (0 = launch per
+    // step); the tuned footprint, else the 256-thread one
     int B = h->prm.block_iters > 0 ? h->prm.block_iters : (L.tuned >= 0 ? L.tuned : 4);
-    FS_LAUNCH("k_tgv", launch_tgv_iterations(L.v, tp, B, iters, st));
+    int v = (h->prm.block_iters <= 0 && L.tuned_variant >= 0) ? L.tuned_variant : 0;
+    FS_LAUNCH("k_tgv", launch_tgv_iterations(L.v, tp, B, v, iters, st));
     return FS_OK;
   }
   if (use_cluster(h, l)) {
@@ -1397,8 +1402,8 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
       if (st == FS_OK && t < best) { best = t; best_c = cand; }
     };
     if (h->prm.regularizer == FS_REG_TGV) {
-      // 0 = a launch per step, 1..8 = blocking depth
-      for (int cand = 0; cand <= 8; ++cand) try_cand(cand);
+      // 0 = a launch per step, then every depth 1..8 on each footprint
+      for (int cand = 0; cand <= kMaxTgvChoice; ++cand) try_cand(cand);
     } else {
       // 0 = cluster where the level fits one, then every depth 1..8 on every
       // footprint.  (Timing each footprint at a few depths first and only
@@ -1449,7 +1454,7 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
   const bool tgv = h->prm.regularizer == FS_REG_TGV;
   for (int l = 0; l < h->L; ++l) {
     int c = choice[l];
-    if (c < -1 || c > (tgv ? 8 : kMaxChoice))
+    if (c < -1 || c > (tgv ? kMaxTgvChoice : kMaxChoice))
       return fail(FS_EINVAL, "level %d: schedule %d out of range", l, c);
     if (c == 0 && !tgv && (h->lv[l].cluster < 0 || h->prm.accel_gamma > 0))
       return fail(FS_EINVAL, "level %d does not fit one thread-block cluster", l);

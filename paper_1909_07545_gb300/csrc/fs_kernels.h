@@ -42,11 +42,14 @@ cudaError_t launch_warm_start(const LevelView& L, float du_max, cudaStream_t st)
 cudaError_t launch_continue(const LevelView& L, cudaStream_t st);
 
 // TGV-L1 (k_tgv.cu): n iterations, with B = 0 as a dual and a primal launch
-// each, else temporally blocked with at most B (1..8) per launch (identical
-// results); v, vbar, q <- 0; vbar <- v at a warp's start.
+// each, else temporally blocked with at most B (1..8) per launch on 32 x 32
+// footprints of 256 (variant 0), 1024 (1) or 512 (2) threads, or 64 x 32
+// footprints of 512 (3) or 1024 (4) threads (identical results); v, vbar,
+// q <- 0; vbar <- v at a warp's start.
+constexpr int kTgvVariants = 5;
 struct TgvParams;
-cudaError_t launch_tgv_iterations(const LevelView& L, const TgvParams& tp, int B, int n,
-                                  cudaStream_t st);
+cudaError_t launch_tgv_iterations(const LevelView& L, const TgvParams& tp, int B, int variant,
+                                  int n, cudaStream_t st);
 cudaError_t launch_tgv_reset(const LevelView& L, cudaStream_t st);
 // Energy terms of a level summed into acc[0..2] (data, regulariser, L1
 // residual); acc must be zeroed first (k_energy.cu).

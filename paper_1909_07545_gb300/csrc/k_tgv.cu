@@ -22,6 +22,8 @@
 // = 1 / (max row sum of |T^1/2| |grad| + 1) from the stored Huber-TV sigma;
 // sigma_q = 1/2; tau_v = 1 / (1 + the active differences touching the
 // pixel); all 0 off the FOV mask, where nothing moves.
+#include <atomic>
+
 #include "fs_kernels.h"
 #include "pd_tgv_math.cuh"
 
@@ -115,15 +117,24 @@ struct TgvState {
 };
 
 template <int FW, int NY, int R>
-__global__ void __launch_bounds__(FW * NY, 2)
+__global__ void __launch_bounds__(FW * NY, FW * NY >= 512 ? 1 : 2)
 k_tgv_blocked(LevelView L, TgvState in, TgvState out, TgvParams tp, int B, int n_iters,
               int chained) {
   constexpr int FH = NY * R;
   // neighbours' values: ubar, vbar (read by the dual from the right / below)
-  // and t, masked q (read by the primal from the left / above)
-  __shared__ float s_ub[FH][FW], s_vb1[FH][FW], s_vb2[FH][FW];
-  __shared__ float s_t1[FH][FW], s_t2[FH][FW];
-  __shared__ float s_qx1[FH][FW], s_qx2[FH][FW], s_qy1[FH][FW], s_qy2[FH][FW];
+  // and t, masked q (read by the primal from the left / above); nine FH x FW
+  // planes of dynamic shared memory (tgv_smem_bytes)
+  extern __shared__ float tgv_smem[];
+  typedef float Plane[FW];
+  Plane* s_ub = reinterpret_cast<Plane*>(tgv_smem + 0 * FH * FW);
+  Plane* s_vb1 = reinterpret_cast<Plane*>(tgv_smem + 1 * FH * FW);
+  Plane* s_vb2 = reinterpret_cast<Plane*>(tgv_smem + 2 * FH * FW);
+  Plane* s_t1 = reinterpret_cast<Plane*>(tgv_smem + 3 * FH * FW);
+  Plane* s_t2 = reinterpret_cast<Plane*>(tgv_smem + 4 * FH * FW);
+  Plane* s_qx1 = reinterpret_cast<Plane*>(tgv_smem + 5 * FH * FW);
+  Plane* s_qx2 = reinterpret_cast<Plane*>(tgv_smem + 6 * FH * FW);
+  Plane* s_qy1 = reinterpret_cast<Plane*>(tgv_smem + 7 * FH * FW);
+  Plane* s_qy2 = reinterpret_cast<Plane*>(tgv_smem + 8 * FH * FW);
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int IW = FW - 2 * B, IH = FH - 2 * B;
@@ -282,29 +293,62 @@ TgvState alternate(const LevelView& L) {
   return s;
 }
 
-constexpr int kTgvFW = 32, kTgvNY = 8, kTgvR = 4;
-
-cudaError_t launch_blocked(const LevelView& L, const TgvState& in, const TgvState& out,
-                           const TgvParams& tp, int B, int n, bool chained, cudaStream_t st) {
-  const int IW = kTgvFW - 2 * B, IH = kTgvNY * kTgvR - 2 * B;
+template <int FW, int NY, int R>
+cudaError_t launch_blocked_t(const LevelView& L, const TgvState& in, const TgvState& out,
+                             const TgvParams& tp, int B, int n, bool chained, cudaStream_t st) {
+  const int IW = FW - 2 * B, IH = NY * R - 2 * B;
   if (IW <= 0 || IH <= 0 || n < 0 || n > B) return cudaErrorInvalidValue;
+  constexpr size_t smem = 9 * (size_t)FW * NY * R * sizeof(float);
+  if constexpr (smem > 48 * 1024) {      // above the default limit: opt in once per device
+    static std::atomic<unsigned long long> opted{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(opted.load() & bit)) {
+      e = cudaFuncSetAttribute(k_tgv_blocked<FW, NY, R>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      opted.fetch_or(bit);
+    }
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((L.W + IW - 1) / IW, (L.H + IH - 1) / IH, 1);
-  cfg.blockDim = dim3(kTgvFW, kTgvNY, 1);
+  cfg.blockDim = dim3(FW, NY, 1);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k_tgv_blocked<kTgvFW, kTgvNY, kTgvR>, L, in, out, tp, B, n,
+  return cudaLaunchKernelEx(&cfg, k_tgv_blocked<FW, NY, R>, L, in, out, tp, B, n,
                             chained ? 1 : 0);
+}
+
+// The 32 x 32 footprint on 256 threads of 4 rows (variant 0), 1024 threads
+// of 1 row (1) or 512 threads of 2 rows (2): more threads shorten each
+// thread's dependent chain per iteration on the latency-bound levels.  The
+// 64 x 32 footprint on 512 threads of 4 rows (3) or 1024 threads of 2 rows
+// (4): less halo recomputed per interior pixel on the large levels (72 KB
+// of shared memory).
+cudaError_t launch_blocked(int variant, const LevelView& L, const TgvState& in,
+                           const TgvState& out, const TgvParams& tp, int B, int n, bool chained,
+                           cudaStream_t st) {
+  switch (variant) {
+    case 0: return launch_blocked_t<32, 8, 4>(L, in, out, tp, B, n, chained, st);
+    case 1: return launch_blocked_t<32, 32, 1>(L, in, out, tp, B, n, chained, st);
+    case 2: return launch_blocked_t<32, 16, 2>(L, in, out, tp, B, n, chained, st);
+    case 3: return launch_blocked_t<64, 8, 4>(L, in, out, tp, B, n, chained, st);
+    case 4: return launch_blocked_t<64, 16, 2>(L, in, out, tp, B, n, chained, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_tgv_iterations(const LevelView& L, const TgvParams& tp, int B, int n,
-                                  cudaStream_t st) {
+cudaError_t launch_tgv_iterations(const LevelView& L, const TgvParams& tp, int B, int variant,
+                                  int n, cudaStream_t st) {
   if (B <= 0) {                       // a dual and a primal launch per iteration
     const dim3 g = tgrid(L.W, L.H), b(32, 8);
     for (int k = 0; k < n; ++k) {
@@ -321,8 +365,8 @@ cudaError_t launch_tgv_iterations(const LevelView& L, const TgvParams& tp, int B
   for (int k = 0, done = 0; k < nl; ++k) {
     int m = (n - done) / (nl - k);
     if ((n - done) % (nl - k)) ++m;
-    cudaError_t e = launch_blocked(L, (k % 2 == 0) ? A : Bs, (k % 2 == 0) ? Bs : A, tp, B, m,
-                                   k > 0, st);
+    cudaError_t e = launch_blocked(variant, L, (k % 2 == 0) ? A : Bs, (k % 2 == 0) ? Bs : A,
+                                   tp, B, m, k > 0, st);
     if (e != cudaSuccess) return e;
     done += m;
   }

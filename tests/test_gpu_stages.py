@@ -288,11 +288,12 @@ def test_tgv_iterations_match_oracle(precond, small, ragged):
 @pytest.mark.parametrize("which", ["small", "ragged"])
 def test_tgv_schedules_are_bit_exact(which, small, ragged):
     # a dual and a primal launch per iteration, and temporal blocking at
-    # several depths, compute the same per-pixel arithmetic
+    # several depths on each footprint (32 x 32 of 256, 1024, 512 threads;
+    # 64 x 32 of 512, 1024), compute the same per-pixel arithmetic
     pair = small if which == "small" else ragged
     H, W = pair["I0"].shape
     outs = []
-    for block in (0, 1, 3, 4, 8):
+    for block in (0, 1, 3, 4, 8, 9, 12, 16, 17, 21, 24, 25, 28, 32, 33, 36, 40):
         rng = np.random.default_rng(32)
         u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
         v = rng.uniform(-0.3, 0.3, (2, H, W))
