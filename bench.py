@@ -655,8 +655,9 @@ def main():
     peak = float(peaks["hbm_gbs"])
     pd_ms = sum(m for m, _, _ in per_level) / args.steps
     # launches per frame: 2 copy/pre-rotate, L-1 downsample, L tensor, 1 zero,
-    # L-1 upsample, warps*L (warp + clip), PD launches, 1 depth
-    per_frame_other = 2 + (L - 1) + L + 1 + (L - 1) + 2 * warps * L + 1
+    # L-1 upsample, per level one warp, warps-1 fused clip + warp and one
+    # clip, PD launches, 1 depth
+    per_frame_other = 2 + (L - 1) + L + 1 + (L - 1) + (warps + 1) * L + 1
     line = {
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

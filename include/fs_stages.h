@@ -46,8 +46,10 @@ typedef enum {
   FS_STAGE_PD = 4,         /* `count` primal-dual iterations (Eq. 11, 13)     */
   FS_STAGE_CLIP = 5,       /* clip delta-u, u_w + du -> u, w += du g (Alg. 1) */
   FS_STAGE_TRAJECTORY = 6, /* rebuild gamma' of the level (Sec. III-B)        */
-  FS_STAGE_WARM = 7        /* warm start from u: w <- walk of u along gamma',
+  FS_STAGE_WARM = 7,       /* warm start from u: w <- walk of u along gamma',
                               ceil(|u|/du_max) equal steps; ubar, u_w <- u, p <- 0 */
+  FS_STAGE_CLIP_WARP = 8   /* FS_STAGE_CLIP then FS_STAGE_WARP in one launch (what
+                              fs_solve runs between two warps; same results) */
 } fs_stage;
 
 /* Copy a level buffer to / from dense device memory of planes x H_l x W_l

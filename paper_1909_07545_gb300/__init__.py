@@ -32,7 +32,8 @@ BUF_PLANES = {0: 1, 1: 1, 2: 1, 3: 2, 4: 3, 5: 2, 6: 1, 7: 1, 8: 1, 9: 2, 10: 2,
               13: 2, 14: 2, 15: 2, 16: 4}
 REGULARIZER = {"huber_tv": 0, "tgv": 1}
 DERIV = {"forward": 0, "central": 1}
-STAGE = dict(DOWNSAMPLE=0, TENSOR=1, UPSAMPLE=2, WARP=3, PD=4, CLIP=5, TRAJECTORY=6, WARM=7)
+STAGE = dict(DOWNSAMPLE=0, TENSOR=1, UPSAMPLE=2, WARP=3, PD=4, CLIP=5, TRAJECTORY=6, WARM=7,
+             CLIP_WARP=8)
 
 STATUS = {0: "FS_OK", -1: "FS_EINVAL", -2: "FS_ENOMEM", -3: "FS_ECUDA", -4: "FS_ECALIB",
           -5: "FS_ETIMEOUT", -6: "FS_ECANCELLED"}

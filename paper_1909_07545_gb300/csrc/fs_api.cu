@@ -509,6 +509,12 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
       k_clip<<<grid2(L.W, L.H), kBlock2, 0, st>>>(L.v, h->prm.du_max);
       FS_LAUNCHED("k_clip");
       return FS_OK;
+    case FS_STAGE_CLIP_WARP:
+      FS_LAUNCH("k_clip_warp", launch_clip_warp(L.v, h->prm.du_max,
+                                                h->prm.deriv == FS_DERIV_CENTRAL, st));
+      if (h->prm.regularizer == FS_REG_TGV)
+        FS_LAUNCH("k_tgv_warp_start", launch_tgv_warp_start(L.v, st));
+      return FS_OK;
     case FS_STAGE_WARM:
       FS_LAUNCH("k_warm_start", launch_warm_start(L.v, h->prm.du_max, st));
       if (h->prm.regularizer == FS_REG_TGV) FS_LAUNCH("k_tgv_reset", launch_tgv_reset(L.v, st));
@@ -524,6 +530,12 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
     default:
       return fail(FS_EINVAL, "unknown stage %d", stage);
   }
+}
+
+// The end of a warp (clip + update, Eq. 8-9) and, when another warp
+// follows, its start (warp + linearise) in one fused launch.
+fs_status clip_then_warp(fs_handle* h, int l, bool next, cudaStream_t st) {
+  return run_stage(h, l, next ? FS_STAGE_CLIP_WARP : FS_STAGE_CLIP, 0, st);
 }
 
 fs_status enqueue_depth(fs_handle* h, float* disp, float* depth, cudaStream_t st) {
@@ -571,12 +583,12 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
       if ((s = run_stage(h, 0, FS_STAGE_WARM, 0, st)) != FS_OK) return s;
     }
     if ((s = run_stage(h, 0, FS_STAGE_TENSOR, 0, st)) != FS_OK) return s;
+    if ((s = run_stage(h, 0, FS_STAGE_WARP, 0, st)) != FS_OK) return s;
     for (int w = 0; w < warps; ++w) {
-      if ((s = run_stage(h, 0, FS_STAGE_WARP, 0, st)) != FS_OK) return s;
       if (h->timing) FS_CUDA(record_event(h->ev[2 * w], st));
       if ((s = run_pd(h, 0, iters, st)) != FS_OK) return s;
       if (h->timing) FS_CUDA(record_event(h->ev[2 * w + 1], st));
-      if ((s = run_stage(h, 0, FS_STAGE_CLIP, 0, st)) != FS_OK) return s;
+      if ((s = clip_then_warp(h, 0, w + 1 < warps, st)) != FS_OK) return s;
     }
     if (h->timing) {
       h->ev_warps = warps;
@@ -603,12 +615,12 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
     } else if ((s = run_stage(h, l, FS_STAGE_UPSAMPLE, 0, st)) != FS_OK) {
       return s;
     }
+    if ((s = run_stage(h, l, FS_STAGE_WARP, 0, st)) != FS_OK) return s;
     for (int w = 0; w < warps; ++w) {
-      if ((s = run_stage(h, l, FS_STAGE_WARP, 0, st)) != FS_OK) return s;
       if (h->timing) FS_CUDA(record_event(h->ev[2 * (l * warps + w)], st));
       if ((s = run_pd(h, l, iters, st)) != FS_OK) return s;
       if (h->timing) FS_CUDA(record_event(h->ev[2 * (l * warps + w) + 1], st));
-      if ((s = run_stage(h, l, FS_STAGE_CLIP, 0, st)) != FS_OK) return s;
+      if ((s = clip_then_warp(h, l, w + 1 < warps, st)) != FS_OK) return s;
     }
   }
   if (h->timing) {

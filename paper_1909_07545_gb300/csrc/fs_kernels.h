@@ -59,6 +59,8 @@ cudaError_t launch_tgv_warp_start(const LevelView& L, cudaStream_t st);
 cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond,
                           cudaStream_t st);
 cudaError_t launch_warp(const LevelView& L, int central, cudaStream_t st);
+// k_clip of one warp fused with k_warp of the next (same results).
+cudaError_t launch_clip_warp(const LevelView& L, float du_max, int central, cudaStream_t st);
 cudaError_t launch_tensor_abc(const LevelView& L, float* dst, cudaStream_t st);
 cudaError_t launch_pack_s(const SPlane& src, int storage, float* dst, int W, int H, int P,
                           cudaStream_t st);

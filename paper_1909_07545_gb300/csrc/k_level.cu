@@ -277,6 +277,26 @@ __global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
 // `central` half the difference of the samples at x + w +- g (free of the
 // I1w noise that the forward difference shares with rho0).  Starts a warp:
 // ubar = u_w = u.
+// The linearisation at one FOV pixel for warp vector w (shared by k_warp and
+// k_clip_warp, so both give the same bits).
+template <int S>
+__device__ __forceinline__ void warp_px(const LevelView& L, int x, int y, size_t i, float2 w,
+                                        int central, float& Iu, float& rho0, float2& g) {
+  g = make_float2(0.f, 0.f);
+  float2 gr = sample_bicubic2(L.gamma, L.W, L.H, L.P, x, w.x, y, w.y);
+  float n = sqrtf(gr.x * gr.x + gr.y * gr.y);
+  if (n >= 1e-6f) g = make_float2(gr.x / n, gr.y / n);
+  float I1w = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x, y, w.y);
+  float I1g = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x + g.x, y, w.y + g.y);
+  if (central) {
+    float I1m = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x - g.x, y, w.y - g.y);
+    Iu = 0.5f * (I1g - I1m);
+  } else {
+    Iu = I1g - I1w;
+  }
+  rho0 = I1w - sld<S>(L.I0, i);
+}
+
 template <int S>
 __global__ void k_warp(LevelView L, int central) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -285,21 +305,7 @@ __global__ void k_warp(LevelView L, int central) {
   size_t i = (size_t)y * L.P + x;
   float Iu = 0.f, rho0 = 0.f;
   float2 g = make_float2(0.f, 0.f);
-  if (L.mask[i] & MASK_IN) {
-    float2 w = L.w[i];
-    float2 gr = sample_bicubic2(L.gamma, L.W, L.H, L.P, x, w.x, y, w.y);
-    float n = sqrtf(gr.x * gr.x + gr.y * gr.y);
-    if (n >= 1e-6f) g = make_float2(gr.x / n, gr.y / n);
-    float I1w = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x, y, w.y);
-    float I1g = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x + g.x, y, w.y + g.y);
-    if (central) {
-      float I1m = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x - g.x, y, w.y - g.y);
-      Iu = 0.5f * (I1g - I1m);
-    } else {
-      Iu = I1g - I1w;
-    }
-    rho0 = I1w - sld<S>(L.I0, i);
-  }
+  if (L.mask[i] & MASK_IN) warp_px<S>(L, x, y, i, L.w[i], central, Iu, rho0, g);
   sst<S>(L.Iu, i, Iu);
   sst<S>(L.rho0, i, rho0);
   L.g[i] = g;
@@ -311,21 +317,59 @@ __global__ void k_warp(LevelView L, int central) {
 // ------------------------------------------------------------ clip + update
 // du = clamp(u - u_w, +-du_max); u_{w+1} = u_w + du; w += du g (Algorithm 1,
 // Eq. 8-9).  The primal state continues from u_{w+1}.
+__device__ __forceinline__ float clip_px(const LevelView& L, size_t i, float du_max,
+                                         float2& w) {
+  float uw = L.uw[i];
+  float du = fminf(fmaxf(__fsub_rn(L.u[i], uw), -du_max), du_max);
+  float2 g = L.g[i];
+  w = L.w[i];
+  w = make_float2(fmaf(du, g.x, w.x), fmaf(du, g.y, w.y));
+  return __fadd_rn(uw, du);
+}
+
 __global__ void k_clip(LevelView L, float du_max) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
   size_t i = (size_t)y * L.P + x;
   if (!(L.mask[i] & MASK_IN)) return;
-  float uw = L.uw[i];
-  float du = fminf(fmaxf(L.u[i] - uw, -du_max), du_max);
-  float un = uw + du;
+  float2 w;
+  float un = clip_px(L, i, du_max, w);
   L.u[i] = un;
   L.ubar[i] = un;
   L.uw[i] = un;
-  float2 w = L.w[i], g = L.g[i];
-  L.w[i] = make_float2(w.x + du * g.x, w.y + du * g.y);
+  L.w[i] = w;
 }
+
+// The end of one warp and the start of the next in one pass: k_clip then
+// k_warp at every pixel, with the updated w and u kept in registers (each
+// pixel's clip and linearisation read only that pixel's state; the gathers
+// read I1 and gamma', which neither writes).
+template <int S>
+__global__ void k_clip_warp(LevelView L, float du_max, int central) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  size_t i = (size_t)y * L.P + x;
+  float Iu = 0.f, rho0 = 0.f;
+  float2 g = make_float2(0.f, 0.f);
+  float u;
+  if (L.mask[i] & MASK_IN) {
+    float2 w;
+    u = clip_px(L, i, du_max, w);
+    L.w[i] = w;
+    L.u[i] = u;
+    warp_px<S>(L, x, y, i, w, central, Iu, rho0, g);
+  } else {
+    u = L.u[i];
+  }
+  sst<S>(L.Iu, i, Iu);
+  sst<S>(L.rho0, i, rho0);
+  L.g[i] = g;
+  L.ubar[i] = u;
+  L.uw[i] = u;
+}
+
 
 // ------------------------------------------------------------ triangulation
 // Range along the camera-0 ray of x from the rays pi^-1(x) and pi^-1(x + w)
@@ -461,6 +505,10 @@ cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond
 }
 cudaError_t launch_warp(const LevelView& L, int central, cudaStream_t st) {
   FS_STORAGE_SWITCH(L.st, (k_warp<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, central)))
+}
+
+cudaError_t launch_clip_warp(const LevelView& L, float du_max, int central, cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_clip_warp<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, du_max, central)))
 }
 cudaError_t launch_tensor_abc(const LevelView& L, float* dst, cudaStream_t st) {
   FS_STORAGE_SWITCH(L.st, (k_tensor_abc<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, dst)))

@@ -178,6 +178,30 @@ def test_warp_linearize(small, ragged, deriv):
         s.close()
 
 
+@pytest.mark.parametrize("prm", [dict(), dict(deriv="central"), dict(storage="f16"),
+                                 dict(regularizer="tgv")])
+def test_fused_clip_warp_equals_clip_then_warp(small, ragged, prm):
+    # what fs_solve runs between two warps (FS_STAGE_CLIP_WARP, one launch)
+    # gives the same bits as the clip and warp stages run one after the other
+    for pair in (small, ragged):
+        outs = []
+        for fused in (False, True):
+            s = make_solver(pair, **prm)
+            s.solve(pair["I0"], pair["I1"], 1, 10)
+            if fused:
+                s.stage(0, "CLIP_WARP")
+            else:
+                s.stage(0, "CLIP")
+                s.stage(0, "WARP")
+            bufs = ["U", "UBAR", "UW", "W", "G", "IU", "RHO0"]
+            if prm.get("regularizer") == "tgv":
+                bufs += ["V", "VBAR"]
+            outs.append([np64(s.read(0, b)) for b in bufs])
+            s.close()
+        for a, b in zip(*outs):
+            assert np.array_equal(a, b)
+
+
 def _pd_inputs(pair, rng):
     H, W = pair["I0"].shape
     u = rng.uniform(0, 4, (H, W))
