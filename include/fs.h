@@ -45,6 +45,14 @@ typedef enum {
   FS_ECANCELLED = -6 /* the request was cancelled before it ran (server)     */
 } fs_status;
 
+/* Host-side fault injection for tests: while the environment variable
+ * FS_FAULT_ALLOC is "all" or names an allocation site -- "arena" (the
+ * per-handle state of fs_create), "guard" (guard-band bookkeeping),
+ * "stage" (fs_solve_host's staging planes), "sched" (the accelerated
+ * schedule's table), "energy" (fs_energy's accumulators), "planes" (a served
+ * rig's image and output planes) -- that device allocation fails without
+ * reaching the device, and the call returns FS_ENOMEM. */
+
 /* Radially symmetric camera models, pixel = c + f * r(theta) * (X, Y)/|(X, Y)|
  * with theta the angle off the optical axis (Sec. III-B allows any model
  * with a defined projection and cites the unified, enhanced unified and

@@ -207,6 +207,20 @@ fs_status fs_internal_set_error(fs_status s, const char* msg) {
   return s;
 }
 
+// Every device allocation of the library goes through here.  Host-side fault
+// injection for tests: while the environment variable FS_FAULT_ALLOC names
+// this allocation's site ("arena", "planes", "stage", "sched", "energy",
+// "guard") or is "all", the allocation fails with cudaErrorMemoryAllocation
+// without reaching the device.
+cudaError_t fs_internal_malloc(void** p, size_t bytes, const char* site) {
+  const char* f = std::getenv("FS_FAULT_ALLOC");
+  if (f && (std::strcmp(f, "all") == 0 || std::strcmp(f, site) == 0)) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 struct fs_handle {
   fs_calib cam[2];
   fs_pose pose;
@@ -406,7 +420,8 @@ fs_status ensure_schedule(fs_handle* h, int iters) {
     if (h->sched) cudaFree(h->sched);
     h->sched = nullptr;
     h->sched_cap = 0;
-    if (cudaMalloc(&h->sched, (size_t)iters * sizeof(float4)) != cudaSuccess) {
+    if (fs_internal_malloc((void**)&h->sched, (size_t)iters * sizeof(float4), "sched") !=
+        cudaSuccess) {
       cudaGetLastError();
       h->sched = nullptr;
       return fail(FS_ENOMEM, "accelerated schedule allocation failed");
@@ -779,7 +794,7 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     for (int l = 0; l < levels; ++l) n_planes += 21 + (p.regularizer == FS_REG_TGV ? 20 : 0);
     bytes += (n_planes + 1) * h->guard;
   }
-  cudaError_t e = cudaMalloc(&h->arena, bytes);
+  cudaError_t e = fs_internal_malloc(&h->arena, bytes, "arena");
   if (e != cudaSuccess) {
     delete h;
     return fail(FS_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -833,13 +848,19 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
   for (size_t j = 0; e == cudaSuccess && j < h->gband.size(); ++j)
     e = cudaMemsetAsync((char*)h->arena + h->gband[j], 0xFF, h->guard, h->stream);
   if (e == cudaSuccess && h->guard) {
-    e = cudaMalloc(&h->gband_dev, h->gband.size() * sizeof(unsigned long long) + sizeof(int));
-    if (e == cudaSuccess) {
-      h->gflag = (int*)(h->gband_dev + h->gband.size());
-      e = cudaMemcpyAsync(h->gband_dev, h->gband.data(),
-                          h->gband.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                          h->stream);
+    e = fs_internal_malloc((void**)&h->gband_dev,
+                           h->gband.size() * sizeof(unsigned long long) + sizeof(int), "guard");
+    if (e != cudaSuccess) {
+      h->gband_dev = nullptr;
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->arena);
+      delete h;
+      return fail(FS_ENOMEM, "guard-band table allocation failed: %s", cudaGetErrorString(e));
     }
+    h->gflag = (int*)(h->gband_dev + h->gband.size());
+    e = cudaMemcpyAsync(h->gband_dev, h->gband.data(),
+                        h->gband.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                        h->stream);
   }
   if (e != cudaSuccess) {
     cudaStreamSynchronize(h->stream);
@@ -1031,7 +1052,7 @@ fs_status fs_solve_host(fs_handle* h, const float* h_I0, const float* h_I1, cons
   if (!h_I0 || !h_I1) return fail(FS_EINVAL, "null input image");
   size_t n = (size_t)h->W * h->H;
   if (!h->stage) {
-    cudaError_t e = cudaMalloc(&h->stage, 5 * n * sizeof(float));
+    cudaError_t e = fs_internal_malloc((void**)&h->stage, 5 * n * sizeof(float), "stage");
     if (e != cudaSuccess) { h->stage = nullptr; return fail(FS_ENOMEM, "staging allocation failed"); }
   }
   float *dI0 = h->stage, *dI1 = h->stage + n, *dinit = h->stage + 2 * n;
@@ -1441,7 +1462,7 @@ extern "C" fs_status fs_energy(fs_handle* h, int level, double out[4]) {
   if (level < 0 || level >= h->L) return fail(FS_EINVAL, "level %d out of range", level);
   if (!out) return fail(FS_EINVAL, "null output");
   if (!h->eacc) {
-    cudaError_t e = cudaMalloc(&h->eacc, 3 * sizeof(double));
+    cudaError_t e = fs_internal_malloc((void**)&h->eacc, 3 * sizeof(double), "energy");
     if (e != cudaSuccess) { h->eacc = nullptr; return fail(FS_ENOMEM, "energy accumulator: %s", cudaGetErrorString(e)); }
   }
   double acc[3];

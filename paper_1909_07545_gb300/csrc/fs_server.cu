@@ -34,6 +34,7 @@
 extern fs_status fs_internal_set_error(fs_status s, const char* msg);
 extern fs_status fs_internal_validate(const fs_calib cam[2], const fs_pose* pose, int W, int H,
                                       int levels, const fs_params* prm);
+extern cudaError_t fs_internal_malloc(void** p, size_t bytes, const char* site);
 
 namespace {
 
@@ -168,7 +169,7 @@ fs_status make_resident(fs_server* s, Rig* rg, std::string* msg) {
     rg->h = nullptr;
     return st;
   }
-  cudaError_t e = cudaMalloc(&rg->planes, 4 * rg->n() * sizeof(float));
+  cudaError_t e = fs_internal_malloc((void**)&rg->planes, 4 * rg->n() * sizeof(float), "planes");
   if (e != cudaSuccess) {
     fs_destroy(rg->h);
     rg->h = nullptr;
