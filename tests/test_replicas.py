@@ -50,3 +50,21 @@ def test_single_process_needs_no_collective():
     import bench
     assert bench.reduce_max([1.0, 2.0]) == [1.0, 2.0]
     assert bench.job_rate(1, 20, 400.0) == pytest.approx(50.0)
+
+
+def test_schedule_labels_decode_the_tuner_encoding():
+    # 0 = cluster; 8 v + d = depth d on footprint v (the fs_autotune encoding)
+    import bench
+    assert bench.schedule_label(0) == "cluster"
+    assert bench.schedule_label(7) == "blocking x7 (64x64 footprints, 512 threads)"
+    assert bench.schedule_label(16) == "blocking x8 (32x32 footprints, 256 threads)"
+    assert bench.schedule_label(31) == "blocking x7 (64x64 footprints, 1024 threads)"
+    assert bench.schedule_label(40) == "blocking x8 (32x32 footprints, 1024 threads)"
+    assert bench.schedule_label(41) == "blocking x1 (32x32 footprints, 512 threads)"
+    assert len(bench.FOOTPRINTS) * 8 == 48
+    # one label per footprint variant of the kernels
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(bench.__file__), "paper_1909_07545_gb300", "csrc",
+                            "fs_kernels.h")).read()
+    assert int(re.search(r"PD_TILE_COUNT = (\d+)", src).group(1)) == len(bench.FOOTPRINTS)
