@@ -410,7 +410,8 @@ def run_reference(args, pair, rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": pair["name"], "W": W, "H": H, "levels": pair["levels"],
                    "warps": pair["warps"], "iters": pair["iters"]},
-        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1,
+                         "host_cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"{per_step} primal-dual iterations of the finest "
                                    f"{W}x{H} level per step, extrapolated to a frame by "
                                    f"pixel-iterations ({pxit_frame:.3e} per frame)"},
@@ -712,7 +713,8 @@ def main():
         os.environ.setdefault("OMP_NUM_THREADS", "1")
         rate, n, dt = cpu_baseline(pair, args.cpu_seconds)
         line["cpu_baseline"] = {
-            "value": rate / pxit_frame, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "value": rate / pxit_frame, "unit": "frames/s", "cores": 1,
+            "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{n} primal-dual iterations of the finest {W}x{H} level in {dt:.1f} s "
                       f"(FP64 numpy, one thread), extrapolated to a frame by pixel-iterations "
                       f"({pxit_frame:.3e} per frame)"}
