@@ -42,9 +42,12 @@ FOOTPRINTS = ["64x64 footprints, 512 threads", "32x32 footprints, 256 threads",
 
 def schedule_label(c):
     """fs_autotune's per-level choice in words (0 = cluster; 1..48 = depth
-    1..8 on each of the six footprints)."""
+    1..8 on each of the six footprints; 49..55 = depth 9..15 on 32x32
+    footprints of 1024 threads)."""
     if c == 0:
         return "cluster"
+    if c > 8 * len(FOOTPRINTS):           # depths 9..15 on the 1024-thread 32x32 footprint
+        return f"blocking x{c - 8 * len(FOOTPRINTS) + 8} ({FOOTPRINTS[4]})"
     return f"blocking x{(c - 1) % 8 + 1} ({FOOTPRINTS[(c - 1) // 8]})"
 
 

@@ -102,7 +102,8 @@ fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
  * v = 2: 64 x 32, 256 threads of 8 rows (17..24);
  * v = 3: 64 x 64, 1024 threads of 4 rows (25..32);
  * v = 4: 32 x 32, 1024 threads of 1 row (33..40);
- * v = 5: 32 x 32, 512 threads of 2 rows (41..48).  On TGV handles the
+ * v = 5: 32 x 32, 512 threads of 2 rows (41..48);
+ * and 49..55 = depth 9..15 on 32 x 32 footprints of 1024 threads.  On TGV handles the
  * candidates are 0 = a dual and a primal launch per iteration and 8 v + d =
  * temporal-blocking depth d on a 32 x 32 footprint of 256 (v = 0, choices
  * 1..8), 1024 (v = 1, 9..16) or 512 threads (v = 2, 17..24), or a 64 x 32

@@ -377,14 +377,21 @@ int pd_block(const fs_handle* h, int l) {
 // A schedule choice of fs_autotune / fs_set_schedule: 0 = cluster (Huber-TV)
 // or a launch per step (TGV); 8 v + 1 .. 8 v + 8 = blocking depth 1..8 on
 // footprint variant v (PDVariant: 64 x 64 of 512 threads, 32 x 32 of 256,
-// 64 x 32, 64 x 64 of 1024, 32 x 32 of 1024, 32 x 32 of 512), so 1..48
-// (TGV: 8 v + 1 .. 8 v + 8 = depth on the TGV footprint v, 0..2, so 1..24);
-// -1 = none.
-constexpr int kMaxChoice = 8 * PD_TILE_COUNT;
+// 64 x 32, 64 x 64 of 1024, 32 x 32 of 1024, 32 x 32 of 512), so 1..48;
+// 49..55 = depth 9..15 on 32 x 32 footprints of 1024 threads (deeper
+// blocking for the small levels, whose launches cost more than the extra
+// halo: they leave most SMs idle); TGV: 8 v + 1 .. 8 v + 8 = depth on the
+// TGV footprint v, 0..4, so 1..40; -1 = none.
+constexpr int kDeepChoices = 7;
+constexpr int kMaxChoice = 8 * PD_TILE_COUNT + kDeepChoices;
 constexpr int kMaxTgvChoice = 8 * kTgvVariants;
 void decode_choice(int c, bool tgv, int& depth, int& variant) {
-  (void)tgv;
   if (c <= 0) { depth = c; variant = -1; return; }
+  if (!tgv && c > 8 * PD_TILE_COUNT) {
+    depth = 8 + (c - 8 * PD_TILE_COUNT);
+    variant = PD_TILE_32_T1024;
+    return;
+  }
   depth = 1 + (c - 1) % 8;
   variant = (c - 1) / 8;
 }

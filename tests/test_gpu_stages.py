@@ -410,7 +410,7 @@ def test_pd_footprints_are_bit_exact(which, small, ragged):
     # schedule, which the oracle comparison above pins
     pair = small if which == "small" else ragged
     outs = []
-    for choice in (-1, 3, 8, 12, 16, 19, 24, 26, 31, 32, 34, 40, 43, 48):
+    for choice in (-1, 3, 8, 12, 16, 19, 24, 26, 31, 32, 34, 40, 43, 48, 49, 52, 55):
         rng = np.random.default_rng(12)
         u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
         s = make_solver(pair)

@@ -61,6 +61,8 @@ def test_schedule_labels_decode_the_tuner_encoding():
     assert bench.schedule_label(31) == "blocking x7 (64x64 footprints, 1024 threads)"
     assert bench.schedule_label(40) == "blocking x8 (32x32 footprints, 1024 threads)"
     assert bench.schedule_label(41) == "blocking x1 (32x32 footprints, 512 threads)"
+    assert bench.schedule_label(49) == "blocking x9 (32x32 footprints, 1024 threads)"
+    assert bench.schedule_label(55) == "blocking x15 (32x32 footprints, 1024 threads)"
     assert len(bench.FOOTPRINTS) * 8 == 48
     # one label per footprint variant of the kernels
     import os
