@@ -13,7 +13,10 @@
 //    written back; the halo is recomputed by the neighbouring CTAs.  Two CTA
 //    barriers per iteration.  The state is read from one buffer set and
 //    written to the other, so no CTA sees a neighbour's updated interior
-//    while it loads its halo.
+//    while it loads its halo.  Six footprints (PDVariant) trade registers
+//    per thread (R rows) against resident warps and halo recomputation; the
+//    autotuner picks one per level.  ACC instantiations read the accelerated
+//    step schedule, one table entry per iteration of the warp.
 //
 // 2. k_pd_cluster -- the whole level resident in one thread-block cluster
 //    (at most 16 CTAs, one tile each, no halo), for the coarse levels.  Each
