@@ -152,3 +152,17 @@ def test_server_config_validation(lib):
     assert lib.fs_server_drain(None, 0.0) == -1
     assert lib.fs_server_stats_read(None, None, 0) == -1
     assert lib.fs_server_destroy(None) == 0
+
+
+def test_headers_are_plain_c99():
+    # a C caller's view: the three public headers compile as strict C99
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-fsyntax-only", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c_abi_check.c")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
