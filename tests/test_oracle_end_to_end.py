@@ -104,3 +104,30 @@ def test_continuation_with_the_rebuilt_field_is_the_disparity_warm_start():
     assert np.array_equal(a["disp"], b["disp"]) and np.array_equal(a["w"], b["w"])
     c = oracle.solve(*args, 1, 8, prm, d_init=r0["disp"], w_init=r0["w"] + 0.5)
     assert np.abs(c["disp"] - a["disp"])[M].max() > 1e-3
+
+
+def test_image_noise_biases_the_two_derivative_forms_oppositely():
+    # reading of Eq. 7 under noise: the forward difference shares I1(x + w)
+    # with rho0, so independent image noise pushes every warp's step towards
+    # +u and the plane comes out too near; the central difference has no such
+    # term, and noise in I_u alone shrinks the steps (the attenuation of a
+    # noisy regressor), a smaller bias the other way
+    p = synth.fronto_plane(0, model="equidistant", depth=2.0, cycles_per_px=0.05,
+                           baseline=0.2, supersample=4)
+    rng = np.random.default_rng(5)
+    p["I0"] = p["I0"] + rng.normal(0, 0.01, p["I0"].shape)
+    p["I1"] = p["I1"] + rng.normal(0, 0.01, p["I1"].shape)
+    cam = oracle.calib_from_dict(p["cam0"])
+    H, W = p["I0"].shape
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    r = oracle.unproject(cam, px, py)
+    theta = np.arccos(np.clip(r[..., 2], -1, 1))
+    bias = {}
+    for deriv in ("forward", "central"):
+        prm = oracle.Params(lam=p["lam"], eps=p["eps"], deriv=deriv)
+        out = oracle.solve(p["I0"], p["I1"], p["cam0"], p["cam1"], p["R"], p["t"],
+                           p["levels"], p["warps"], p["iters"], prm)
+        sel = nd.binary_erosion(out["mask"], iterations=4) & (theta < np.radians(60))
+        bias[deriv] = float(np.median(out["depth"][sel] * r[..., 2][sel] / 2.0 - 1.0))
+    assert bias["forward"] < -0.05                      # too near: disparity too large
+    assert 0.0 < bias["central"] < -bias["forward"]     # too far, by less
