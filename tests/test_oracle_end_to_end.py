@@ -131,3 +131,27 @@ def test_image_noise_biases_the_two_derivative_forms_oppositely():
         bias[deriv] = float(np.median(out["depth"][sel] * r[..., 2][sel] / 2.0 - 1.0))
     assert bias["forward"] < -0.05                      # too near: disparity too large
     assert 0.0 < bias["central"] < -bias["forward"]     # too far, by less
+
+
+def test_accelerated_steps_damp_the_noise_driven_drift():
+    # the shrinking tau_k of the accelerated schedule (reading of Sec. IV-C's
+    # "theta updated every iteration") takes smaller late steps in each warp,
+    # so the forward-difference drift of the noisy plane above is smaller
+    p = synth.fronto_plane(0, model="equidistant", depth=2.0, cycles_per_px=0.05,
+                           baseline=0.2, supersample=4)
+    rng = np.random.default_rng(5)
+    p["I0"] = p["I0"] + rng.normal(0, 0.01, p["I0"].shape)
+    p["I1"] = p["I1"] + rng.normal(0, 0.01, p["I1"].shape)
+    cam = oracle.calib_from_dict(p["cam0"])
+    H, W = p["I0"].shape
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    r = oracle.unproject(cam, px, py)
+    theta = np.arccos(np.clip(r[..., 2], -1, 1))
+    bias = []
+    for gamma in (0.0, 1.0):
+        prm = oracle.Params(lam=p["lam"], eps=p["eps"], precond=False, accel_gamma=gamma)
+        out = oracle.solve(p["I0"], p["I1"], p["cam0"], p["cam1"], p["R"], p["t"],
+                           p["levels"], p["warps"], p["iters"], prm)
+        sel = nd.binary_erosion(out["mask"], iterations=4) & (theta < np.radians(60))
+        bias.append(float(np.median(out["depth"][sel] * r[..., 2][sel] / 2.0 - 1.0)))
+    assert bias[0] < bias[1] < 0.0 and bias[1] - bias[0] > 0.01
