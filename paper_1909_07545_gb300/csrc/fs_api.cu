@@ -10,7 +10,6 @@
 #include <cstdlib>
 #include <new>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -95,6 +94,20 @@ DevCam dev_cam(const fs_calib& c, double fx, double fy, double cx, double cy) {
   return d;
 }
 
+// The camera of a level (focal lengths and centre of the level, the lens
+// of c) in float-float words for the once-per-pose kernels.
+DevCamDF dev_cam_df(const fs_calib& c, double fx, double fy, double cx, double cy) {
+  DevCamDF d;
+  d.model = c.model;
+  d.fx = df_from_double(fx); d.fy = df_from_double(fy);
+  d.cx = df_from_double(cx); d.cy = df_from_double(cy);
+  d.k1 = df_from_double(c.k[0]); d.k2 = df_from_double(c.k[1]);
+  d.k3 = df_from_double(c.k[2]); d.k4 = df_from_double(c.k[3]);
+  d.theta_max = df_from_double(c.fov_deg * M_PI / 360.0);
+  d.f32 = dev_cam(c, fx, fy, cx, cy);
+  return d;
+}
+
 fs_status check_calib(const fs_calib& c, int which) {
   if (c.model < FS_PINHOLE || c.model > FS_ENHANCED_UNIFIED)
     return fail(FS_EINVAL, "camera %d: unknown model %d", which, c.model);
@@ -122,70 +135,6 @@ fs_status check_calib(const fs_calib& c, int which) {
     }
   }
   return FS_OK;
-}
-
-double radial_d(const fs_calib& c, double th) {
-  if (c.model == FS_PINHOLE) { double cs = std::cos(th); return 1.0 / (cs * cs); }
-  if (c.model == FS_EQUIDISTANT) return 1.0;
-  if (c.model == FS_UNIFIED) {
-    double cs = std::cos(th), d = cs + c.k[0];
-    return (1.0 + c.k[0] * cs) / (d * d);
-  }
-  if (c.model == FS_ENHANCED_UNIFIED) {
-    double s = std::sin(th), cs = std::cos(th), q = std::sqrt(c.k[1] * s * s + cs * cs);
-    double D = eucm_den(c, s, cs);
-    double dD = c.k[0] * s * cs * (c.k[1] - 1.0) / q - (1.0 - c.k[0]) * s;
-    return (cs * D - s * dD) / (D * D);
-  }
-  double t2 = th * th;
-  return 1.0 + t2 * (3 * c.k[0] + t2 * (5 * c.k[1] + t2 * (7 * c.k[2] + t2 * 9 * c.k[3])));
-}
-
-// theta with r(theta) = rn on [0, fov/2] in FP64: 24 bisection steps, then
-// Newton inside the bracket (r increases there; checked by check_calib).
-double theta_of(const fs_calib& c, double rn) {
-  if (c.model == FS_EQUIDISTANT) return rn;
-  if (c.model == FS_PINHOLE) return std::atan(rn);
-  if (c.model == FS_UNIFIED) {       // closed form (Sec. III-D)
-    double xi = c.k[0], r2 = rn * rn;
-    double eta = (xi + std::sqrt(std::max(1.0 + (1.0 - xi * xi) * r2, 0.0))) / (1.0 + r2);
-    return std::atan2(eta * rn, eta - xi);
-  }
-  if (c.model == FS_ENHANCED_UNIFIED) {
-    double a = c.k[0], b = c.k[1], r2 = rn * rn;
-    double mz = (1.0 - b * a * a * r2) /
-                (a * std::sqrt(std::max(1.0 - (2.0 * a - 1.0) * b * r2, 0.0)) + 1.0 - a);
-    return std::atan2(rn, mz);
-  }
-  double lo = 0.0, hi = c.fov_deg * M_PI / 360.0;
-  for (int i = 0; i < 24; ++i) {
-    double mid = 0.5 * (lo + hi);
-    if (radial(c, mid) > rn) hi = mid; else lo = mid;
-  }
-  double th = 0.5 * (lo + hi);
-  for (int i = 0; i < 6; ++i) {
-    double f = radial(c, th) - rn;
-    if (f > 0) hi = th; else lo = th;
-    double nt = th - f / radial_d(c, th);
-    th = (nt >= lo && nt <= hi) ? nt : 0.5 * (lo + hi);
-  }
-  return th;
-}
-
-void unproject_d(const fs_calib& c, double px, double py, double X[3]) {
-  double mx = (px - c.cx) / c.fx, my = (py - c.cy) / c.fy;
-  double rn = std::hypot(mx, my);
-  double th = theta_of(c, rn), s = std::sin(th);
-  X[0] = rn > 0 ? s * mx / rn : 0.0;
-  X[1] = rn > 0 ? s * my / rn : 0.0;
-  X[2] = std::cos(th);
-}
-
-void project_d(const fs_calib& c, const double X[3], double p[2]) {
-  double rho = std::hypot(X[0], X[1]);
-  double r = radial(c, std::atan2(rho, X[2]));
-  p[0] = c.fx * (rho > 0 ? r * X[0] / rho : 0.0) + c.cx;
-  p[1] = c.fy * (rho > 0 ? r * X[1] / rho : 0.0) + c.cy;
 }
 
 inline dim3 grid2(int W, int H) { return dim3((W + 31) / 32, (H + 7) / 8); }
@@ -229,10 +178,7 @@ struct fs_handle {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   HostLevel lv[kMaxLevels];
-  std::vector<uint8_t> mask0;            // host copy of the level-0 mask bits
-  std::vector<double> rays0;             // pi_0^-1(x) of every level-0 pixel (3 per pixel;
-                                         // pose-independent, kept for fs_set_pose)
-  float2* cfield = nullptr;
+  float4* cfield = nullptr;               // calibration field c(x), float-float (x, y hi; x, y lo)
   double tp[3] = {0, 0, 0};
   void* arena = nullptr;
   // staging for fs_solve_host
@@ -306,11 +252,26 @@ fs_status upload_masks(fs_handle* h, std::vector<uint8_t>& host) {
         host[(size_t)y * L.P + x] = b;
       }
     FS_CUDA(cudaMemcpy((void*)L.v.mask, host.data(), host.size(), cudaMemcpyHostToDevice));
-    if (l == 0) h->mask0 = host;
   }
   return FS_OK;
 }
 
+// gamma' of level l (k_trajectory) with the level's camera and the unit
+// direction of t' as float-float words.
+fs_status launch_trajectory(fs_handle* h, int l, cudaStream_t st) {
+  HostLevel& L = h->lv[l];
+  double n = std::sqrt(h->tp[0] * h->tp[0] + h->tp[1] * h->tp[1] + h->tp[2] * h->tp[2]);
+  k_trajectory<<<grid2(L.W, L.H), kBlock2, 0, st>>>(
+      dev_cam_df(h->cam[0], L.fx, L.fy, L.cx, L.cy), df_from_double(h->tp[0] / n),
+      df_from_double(h->tp[1] / n), df_from_double(h->tp[2] / n), L.v);
+  FS_LAUNCHED("k_trajectory");
+  return FS_OK;
+}
+
+// The per-pose fields on the handle's stream: the calibration field of the
+// pre-rotation (Sec. IV-A) and every level's trajectory field (Sec. III-B).
+// t' = R^T t and its direction are FP64 on the host; both kernels compute in
+// float-float and store floats.
 fs_status build_fields(fs_handle* h) {
   const double* R = h->pose.R;
   const double* t = h->pose.t;
@@ -318,47 +279,17 @@ fs_status build_fields(fs_handle* h) {
   double n = std::sqrt(h->tp[0] * h->tp[0] + h->tp[1] * h->tp[1] + h->tp[2] * h->tp[2]);
   if (!(n > 0) || !std::isfinite(n))
     return fail(FS_EINVAL, "pose: translation must be non-zero and finite");
-  // calibration field c(x) = pi_1(R X) - pi_0(X), X = pi_0^-1(x), t = 0
-  // (Sec. IV-A), in FP64 on host threads; FP32 only for storage.  The rays
-  // X depend only on camera 0, so a pose change (fs_set_pose) rotates and
-  // projects the cached rays instead of inverting the lens again.
   HostLevel& L0 = h->lv[0];
-  const size_t np = (size_t)L0.P * L0.H;
-  const bool have_rays = h->rays0.size() == 3 * np;
-  if (!have_rays) h->rays0.assign(3 * np, 0.0);
-  std::vector<float2> field(np, make_float2(0.f, 0.f));
-  auto rows = [&](int y0, int y1) {
-    for (int y = y0; y < y1; ++y)
-      for (int x = 0; x < L0.W; ++x) {
-        size_t i = (size_t)y * L0.P + x;
-        if (!(h->mask0[i] & MASK_IN)) continue;
-        double* X = &h->rays0[3 * i];
-        if (!have_rays) unproject_d(h->cam[0], x, y, X);
-        double X1[3], p0[2], p1[2];
-        project_d(h->cam[0], X, p0);
-        for (int r = 0; r < 3; ++r) X1[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2];
-        project_d(h->cam[1], X1, p1);
-        field[i] = make_float2((float)(p1[0] - p0[0]), (float)(p1[1] - p0[1]));
-      }
-  };
-  unsigned nt = std::thread::hardware_concurrency();
-  nt = nt == 0 ? 1 : (nt > 32 ? 32 : nt);
-  std::vector<std::thread> pool;
-  int chunk = (L0.H + (int)nt - 1) / (int)nt;
-  for (unsigned k = 0; k < nt; ++k) {
-    int y0 = (int)k * chunk, y1 = std::min(L0.H, y0 + chunk);
-    if (y0 < y1) pool.emplace_back(rows, y0, y1);
-  }
-  for (auto& t : pool) t.join();
-  FS_CUDA(cudaMemcpyAsync(h->cfield, field.data(), field.size() * sizeof(float2),
-                          cudaMemcpyHostToDevice, h->stream));
-  FS_CUDA(cudaStreamSynchronize(h->stream));
+  RotDF Rd;
+  for (int i = 0; i < 9; ++i) Rd.r[i] = df_from_double(R[i]);
+  k_calib_field<<<grid2(L0.W, L0.H), kBlock2, 0, h->stream>>>(
+      dev_cam_df(h->cam[0], L0.fx, L0.fy, L0.cx, L0.cy),
+      dev_cam_df(h->cam[1], h->cam[1].fx, h->cam[1].fy, h->cam[1].cx, h->cam[1].cy), Rd,
+      L0.v.mask, h->cfield, L0.W, L0.H, L0.P);
+  FS_LAUNCHED("k_calib_field");
   for (int l = 0; l < h->L; ++l) {
-    HostLevel& L = h->lv[l];
-    DevCam c = dev_cam(h->cam[0], L.fx, L.fy, L.cx, L.cy);
-    k_trajectory<<<grid2(L.W, L.H), kBlock2, 0, h->stream>>>(
-        c, (float)(h->tp[0] / n), (float)(h->tp[1] / n), (float)(h->tp[2] / n), L.v);
-    FS_LAUNCHED("k_trajectory");
+    fs_status s = launch_trajectory(h, l, h->stream);
+    if (s != FS_OK) return s;
   }
   return FS_OK;
 }
@@ -541,14 +472,8 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
       FS_LAUNCH("k_warm_start", launch_warm_start(L.v, h->prm.du_max, st));
       if (h->prm.regularizer == FS_REG_TGV) FS_LAUNCH("k_tgv_reset", launch_tgv_reset(L.v, st));
       return FS_OK;
-    case FS_STAGE_TRAJECTORY: {
-      double n = std::sqrt(h->tp[0] * h->tp[0] + h->tp[1] * h->tp[1] + h->tp[2] * h->tp[2]);
-      DevCam c = dev_cam(h->cam[0], L.fx, L.fy, L.cx, L.cy);
-      k_trajectory<<<grid2(L.W, L.H), kBlock2, 0, st>>>(
-          c, (float)(h->tp[0] / n), (float)(h->tp[1] / n), (float)(h->tp[2] / n), L.v);
-      FS_LAUNCHED("k_trajectory");
-      return FS_OK;
-    }
+    case FS_STAGE_TRAJECTORY:
+      return launch_trajectory(h, l, st);
     default:
       return fail(FS_EINVAL, "unknown stage %d", stage);
   }
@@ -591,7 +516,7 @@ fs_status enqueue_solve(fs_handle* h, const float* I0, const float* I1, const fl
   NvtxRange range(init || cont ? "fs warm solve" : "fs solve");
   fs_status s;
   HostLevel& L0 = h->lv[0];
-  FS_LAUNCH("k_copy_in_s", launch_copy_in_I0(I0, L0.v, st));
+  FS_LAUNCH("k_copy_in_s", launch_copy_in_image(I0, L0.v, 0, st));
   FS_LAUNCH("k_prerotate", launch_prerotate(I1, h->cfield, L0.v, st));
   int top = h->L - 1;
   if (init || cont) {   // warm start: the finest level only
@@ -791,7 +716,7 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     int cv = pd_cluster_variant(L.W, L.H);
     L.cluster = (cv >= 0 && pd_cluster_fits(cv, L.W, L.H)) ? cv : -1;
   }
-  size_t cbytes = align_up((size_t)h->lv[0].P * H * sizeof(float2), 256);
+  size_t cbytes = align_up((size_t)h->lv[0].P * H * sizeof(float4), 256);
   bytes += cbytes;
   const char* genv = std::getenv("FS_GUARD_BANDS");
   if (genv && std::atoi(genv) > 0) {
@@ -830,6 +755,8 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     float** fl[] = {&v.tau, &v.sig, &v.u, &v.ubar, &v.uw, &v.u_alt, &v.ubar_alt};
     const char* nfl[] = {"tau", "sigma", "u", "ubar", "u_w", "u (ping-pong)", "ubar (ping-pong)"};
     for (int j = 0; j < 7; ++j) *fl[j] = (float*)take(plane, l, nfl[j]);
+    v.I0lo = v.u_alt;
+    v.I1lo = v.ubar_alt;
     SPlane* sp[] = {&v.I0, &v.I1, &v.sx, &v.sy, &v.p1, &v.p2, &v.Iu, &v.rho0, &v.p1_alt,
                     &v.p2_alt};
     const char* nsp[] = {"I0", "I1", "s_x", "s_y", "p1", "p2", "I_u", "rho0",
@@ -845,7 +772,7 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
       for (int j = 0; j < 12; ++j) v.tgv_alt[j] = (float*)take(plane, l, "TGV ping-pong");
     }
   }
-  h->cfield = (float2*)take(cbytes, 0, "calibration field");
+  h->cfield = (float4*)take(cbytes, 0, "calibration field");
   if (h->guard) {                                         // the band after the last plane
     h->gband.push_back((unsigned long long)(cur - (char*)h->arena));
     h->gname.push_back("end of the arena");
@@ -911,7 +838,7 @@ fs_status fs_state_bytes(int W, int H, int levels, const fs_params* prm, size_t*
       return fail(FS_EINVAL, "level %d would be %dx%d (< 4x4): too many levels", l, lw, lh);
     bytes += level_bytes((int)align_up((size_t)lw, 32), lh, storage, reg);
   }
-  bytes += align_up(align_up((size_t)W, 32) * H * sizeof(float2), 256);
+  bytes += align_up(align_up((size_t)W, 32) * H * sizeof(float4), 256);
   *out = bytes;
   return FS_OK;
 }
@@ -1328,6 +1255,11 @@ extern "C" fs_status fs_buffer_write(fs_handle* h, int level, int buffer, const 
     return fail(FS_EINVAL, "buffer %d is derived and read-only", buffer);
   HostLevel& L = h->lv[level];
   size_t n = (size_t)L.W * L.H;
+  if (buffer == FS_BUF_I0 || buffer == FS_BUF_I1) {   // with the pyramid's low part
+    FS_LAUNCH("k_copy_in_s", launch_copy_in_image(d_in, L.v, buffer == FS_BUF_I0 ? 0 : 1,
+                                                  h->stream));
+    return FS_OK;
+  }
   BufLoc b;
   if ((s = buffer_loc(h, level, buffer, b)) != FS_OK) return s;
   for (int c = 0; c < b.planes; ++c) {

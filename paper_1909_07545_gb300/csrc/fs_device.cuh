@@ -295,6 +295,12 @@ struct LevelView {
   SPlane p1, p2, Iu, rho0;
   float2 *w, *g;
   float *u_alt, *ubar_alt;
+  // The low parts of I0 and I1 while the pyramid is built (each image is
+  // carried as a float-float value from the pre-rotation down to the
+  // coarsest level, so that every stored level is its exact box mean
+  // rounded once).  They share the planes of u_alt and ubar_alt, which hold
+  // nothing between the primal-dual launches of a warp.
+  float *I0lo, *I1lo;
   // TGV-L1 (Eq. 10): v, vbar (2 planes each) and q (4), null otherwise,
   // and an alternate set of the 12 state planes (u, ubar, v1, v2, vb1, vb2,
   // p1, p2, q11, q12, q21, q22) for the temporally blocked kernel

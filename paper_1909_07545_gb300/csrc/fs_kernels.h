@@ -1,6 +1,7 @@
 // fs_kernels.h -- kernel declarations shared by the library's translation units.
 #pragma once
 
+#include "cam_df.cuh"
 #include "fs_device.cuh"
 
 namespace fs {
@@ -17,7 +18,9 @@ enum PDVariant {
 };
 enum PDClusterVariant { PD_CLUSTER_16 = 0, PD_CLUSTER_32 = 1 };
 
-__global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView L);
+__global__ void k_trajectory(DevCamDF cam, df tx, df ty, df tz, LevelView L);
+__global__ void k_calib_field(DevCamDF c0, DevCamDF c1, RotDF R, const uint8_t* __restrict__ mask,
+                              float4* __restrict__ field, int W, int H, int P);
 __global__ void k_copy_in(const float* __restrict__ src, float* __restrict__ dst, int W, int H,
                           int P);
 __global__ void k_clip(LevelView L, float du_max);
@@ -32,9 +35,12 @@ __global__ void k_mask_to_float(const uint8_t* __restrict__ m, float* __restrict
 
 // Storage-typed kernels, launched through these (the level's storage picks
 // the instantiation).
-cudaError_t launch_prerotate(const float* I1, const float2* field, const LevelView& L0,
+cudaError_t launch_prerotate(const float* I1, const float4* field, const LevelView& L0,
                              cudaStream_t st);
-cudaError_t launch_copy_in_I0(const float* I0, const LevelView& L0, cudaStream_t st);
+// A dense FP32 image into level L's I0 (which = 0) or I1 (1), with the low
+// part of its rounding to the level's storage (the pyramid's carry).
+cudaError_t launch_copy_in_image(const float* src, const LevelView& L, int which,
+                                 cudaStream_t st);
 cudaError_t launch_downsample(const LevelView& F, const LevelView& C, cudaStream_t st);
 cudaError_t launch_upsample(const LevelView& C, const LevelView& F, cudaStream_t st);
 cudaError_t launch_zero_state(const LevelView& L, cudaStream_t st);

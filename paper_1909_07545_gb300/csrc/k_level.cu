@@ -6,50 +6,131 @@
 
 namespace fs {
 
+// ------------------------------------------------------------ float-float stores
+// A plane value in storage S (rounded to nearest) and, in lo, the part of
+// the float-float value v that the stored value leaves out.
+template <int S>
+__device__ __forceinline__ float round_storage(float v) {
+  if constexpr (S == ST_F16) return __half2float(__float2half_rn(v));
+  else if constexpr (S == ST_BF16) return __bfloat162float(__float2bfloat16_rn(v));
+  else return v;
+}
+
+template <int S>
+__device__ __forceinline__ void sst_df(const SPlane& pl, float* __restrict__ lo, size_t i, df v) {
+  const float s = round_storage<S>(v.hi);
+  sst<S>(pl, i, s);
+  lo[i] = __fadd_rn(__fsub_rn(v.hi, s), v.lo);
+}
+
+template <int S>
+__device__ __forceinline__ df sld_df(const SPlane& pl, const float* __restrict__ lo, size_t i) {
+  return df{sld<S>(pl, i), lo[i]};
+}
+
 // ------------------------------------------------------------ trajectory field
 // gamma'(x) = normalise(d/ds pi(pi^-1(x) + s t')) at s -> 0 (Sec. III-B,
 // Eq. 6-7), evaluated as the analytic image-plane velocity of a point on the
-// pixel's ray under the (pre-rotated) translation t'.  Zero outside the mask
-// and where the velocity vanishes (epipoles).
-__global__ void k_trajectory(DevCam cam, float tx, float ty, float tz, LevelView L) {
+// pixel's ray under the (pre-rotated) translation t' (unit vector).  The
+// velocity and its normalisation are computed in float-float and rounded
+// once.  Zero outside the mask and where the velocity vanishes (epipoles).
+__global__ void k_trajectory(DevCamDF cam, df tx, df ty, df tz, LevelView L) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
   size_t i = (size_t)y * L.P + x;
   float2 g = make_float2(0.f, 0.f);
   if (L.mask[i] & MASK_IN) {
-    Ray r = cam_unproject(cam, (float)x, (float)y);
-    float2 v = cam_velocity(cam, r, tx, ty, tz);
-    float n = sqrtf(v.x * v.x + v.y * v.y);
-    if (n >= 1e-3f) g = make_float2(v.x / n, v.y / n);
+    const RayDF r = cam_unproject_df(cam, x, y);
+    df vx, vy;
+    cam_velocity_df(cam, r, tx, ty, tz, vx, vy);
+    const df n = dd_sqrt(dd_add(dd_mul(vx, vx), dd_mul(vy, vy)));
+    if (n.hi >= 1e-3f) g = make_float2(dd_div(vx, n).hi, dd_div(vy, n).hi);
   }
   L.gamma[i] = g;
 }
 
-// ------------------------------------------------------------ pre-rotation
-// The calibration field c(x) (Sec. IV-A) is built once per pose on the host
-// in FP64 (fs_api.cu): an FP32 field carries ~1e-7 relative round-off in
-// the projections, ~3e-5 px at 1000 px, which the warping then amplifies.
-// I1'(x) = I1(x + c(x)), bilinear; I1 dense FP32 (pitch W), output pitch P
-// in the level's storage.
-template <int S>
-__global__ void k_prerotate(const float* __restrict__ I1, const float2* __restrict__ field,
-                            SPlane out, int W, int H, int P) {
+// ------------------------------------------------------------ calibration field
+// c(x) = pi_1(R X) - pi_0(X), X = pi_0^-1(x), at the level-0 FOV pixels
+// (Sec. IV-A, the pre-rotation: t = 0), 0 elsewhere; in float-float, stored
+// as the float pair (hi x, hi y, lo x, lo y).  pi_0(X) is x up to the
+// round-off of the inverse; taking it, rather than x, makes the field
+// exactly 0 for two identical cameras.
+__global__ void k_calib_field(DevCamDF c0, DevCamDF c1, RotDF R, const uint8_t* __restrict__ mask,
+                              float4* __restrict__ field, int W, int H, int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= W || y >= H) return;
   size_t i = (size_t)y * P + x;
-  float2 c = field[i];
-  sst<S>(out, i, sample_bilinear(I1, W, H, W, x, c.x, y, c.y));
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (mask[i] & MASK_IN) {
+    const RayDF r = cam_unproject_df(c0, x, y);
+    const df X[3] = {dd_mul(r.s, r.ux), dd_mul(r.s, r.uy), r.c};
+    df Y[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      Y[k] = dd_add(dd_add(dd_mul(R.r[3 * k], X[0]), dd_mul(R.r[3 * k + 1], X[1])),
+                    dd_mul(R.r[3 * k + 2], X[2]));
+    df px, py, qx, qy;
+    cam_project_df(c1, Y[0], Y[1], Y[2], px, py);
+    cam_project_df(c0, X[0], X[1], X[2], qx, qy);
+    const df dx = dd_sub(px, qx), dy = dd_sub(py, qy);
+    out = make_float4(dx.hi, dy.hi, dx.lo, dy.lo);
+  }
+  field[i] = out;
 }
 
-// Dense FP32 (pitch W) -> pitched plane in the level's storage (I0).
+// ------------------------------------------------------------ pre-rotation
+// I1'(x) = I1(x + c(x)), bilinear, position clamped to the image (Sec.
+// IV-A); I1 dense FP32 (pitch W), output pitch P in the level's storage.
+// The sample position and the interpolation are float-float; the result is
+// stored rounded, its low part in lo (the start of the pyramid's carry).
+struct TapDF {
+  int i0, i1;   // the two neighbouring samples
+  df a;         // weight of i1
+};
+
+__device__ __forceinline__ TapDF tap_linear_df(int x, df d, int n) {
+  float fl;
+  df f;
+  dd_floor_frac(d, fl, f);
+  const int b = x + (int)fl;
+  TapDF t;
+  if (b < 0) { t.i0 = 0; t.a = df_f(0.f); }
+  else if (b >= n - 1) { t.i0 = max(n - 2, 0); t.a = df_f(n >= 2 ? 1.f : 0.f); }
+  else { t.i0 = b; t.a = f; }
+  t.i1 = min(t.i0 + 1, n - 1);
+  return t;
+}
+
 template <int S>
-__global__ void k_copy_in_s(const float* __restrict__ src, SPlane dst, int W, int H, int P) {
+__global__ void k_prerotate(const float* __restrict__ I1, const float4* __restrict__ field,
+                            SPlane out, float* __restrict__ lo, int W, int H, int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= W || y >= H) return;
-  sst<S>(dst, (size_t)y * P + x, src[(size_t)y * W + x]);
+  size_t i = (size_t)y * P + x;
+  const float4 c = field[i];
+  const TapDF tx = tap_linear_df(x, df{c.x, c.z}, W), ty = tap_linear_df(y, df{c.y, c.w}, H);
+  const float* r0 = I1 + (size_t)ty.i0 * W;
+  const float* r1 = I1 + (size_t)ty.i1 * W;
+  const float v00 = __ldg(r0 + tx.i0), v01 = __ldg(r0 + tx.i1);
+  const float v10 = __ldg(r1 + tx.i0), v11 = __ldg(r1 + tx.i1);
+  const df top = dd_add(df_f(v00), dd_mul(tx.a, two_sum(v01, -v00)));
+  const df bot = dd_add(df_f(v10), dd_mul(tx.a, two_sum(v11, -v10)));
+  sst_df<S>(out, lo, i, dd_add(top, dd_mul(ty.a, dd_sub(bot, top))));
+}
+
+// Dense FP32 (pitch W) -> pitched plane in the level's storage, with the
+// low part of the rounding in lo (0 for FP32 storage): the finest level of
+// I0, or a level image written through fs_buffer_write.
+template <int S>
+__global__ void k_copy_in_s(const float* __restrict__ src, SPlane dst, float* __restrict__ lo,
+                            int W, int H, int P) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  sst_df<S>(dst, lo, (size_t)y * P + x, df_f(src[(size_t)y * W + x]));
 }
 
 // Dense (pitch W) -> pitched FP32 copy, used for the warm-start input.
@@ -63,13 +144,16 @@ __global__ void k_copy_in(const float* __restrict__ src, float* __restrict__ dst
 
 // ------------------------------------------------------------ pyramid
 // 2x2 box mean over the children inside the finer mask (all existing
-// children when none is inside), for I0 and I1 together (Sec. IV-B).
+// children when none is inside), for I0 and I1 together (Sec. IV-B).  The
+// children are float-float (stored value + low part), the mean is formed in
+// float-float and stored rounded with its own low part, so each level is
+// the exact mean of the exact finer level, rounded once.
 template <int S>
 __global__ void k_downsample(LevelView F, LevelView C) {
   int X = blockIdx.x * blockDim.x + threadIdx.x;
   int Y = blockIdx.y * blockDim.y + threadIdx.y;
   if (X >= C.W || Y >= C.H) return;
-  float s0 = 0.f, s1 = 0.f, a0 = 0.f, a1 = 0.f;
+  df s0 = df_f(0.f), s1 = df_f(0.f), a0 = df_f(0.f), a1 = df_f(0.f);
   int nin = 0, nall = 0;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
@@ -78,15 +162,20 @@ __global__ void k_downsample(LevelView F, LevelView C) {
       int x = 2 * X + i, y = 2 * Y + j;
       if (x < F.W && y < F.H) {
         size_t k = (size_t)y * F.P + x;
-        float v0 = sld<S>(F.I0, k), v1 = sld<S>(F.I1, k);
-        a0 += v0; a1 += v1; ++nall;
-        if (F.mask[k] & MASK_IN) { s0 += v0; s1 += v1; ++nin; }
+        const df v0 = sld_df<S>(F.I0, F.I0lo, k), v1 = sld_df<S>(F.I1, F.I1lo, k);
+        a0 = dd_add(a0, v0); a1 = dd_add(a1, v1); ++nall;
+        if (F.mask[k] & MASK_IN) { s0 = dd_add(s0, v0); s1 = dd_add(s1, v1); ++nin; }
       }
     }
   }
   size_t o = (size_t)Y * C.P + X;
-  if (nin > 0) { sst<S>(C.I0, o, s0 / (float)nin); sst<S>(C.I1, o, s1 / (float)nin); }
-  else { sst<S>(C.I0, o, a0 / (float)nall); sst<S>(C.I1, o, a1 / (float)nall); }
+  if (nin > 0) {
+    sst_df<S>(C.I0, C.I0lo, o, dd_div_f(s0, (float)nin));
+    sst_df<S>(C.I1, C.I1lo, o, dd_div_f(s1, (float)nin));
+  } else {
+    sst_df<S>(C.I0, C.I0lo, o, dd_div_f(a0, (float)nall));
+    sst_df<S>(C.I1, C.I1lo, o, dd_div_f(a1, (float)nall));
+  }
 }
 
 // u, w of level C (coarse) -> level F (fine): bilinear over coarse in-mask
@@ -474,14 +563,17 @@ const dim3 kBlk(32, 8);
   }                                                           \
   return cudaGetLastError();
 
-cudaError_t launch_prerotate(const float* I1, const float2* field, const LevelView& L0,
+cudaError_t launch_prerotate(const float* I1, const float4* field, const LevelView& L0,
                              cudaStream_t st) {
   FS_STORAGE_SWITCH(L0.st, (k_prerotate<S><<<grid_of(L0.W, L0.H), kBlk, 0, st>>>(
-                               I1, field, L0.I1, L0.W, L0.H, L0.P)))
+                               I1, field, L0.I1, L0.I1lo, L0.W, L0.H, L0.P)))
 }
-cudaError_t launch_copy_in_I0(const float* I0, const LevelView& L0, cudaStream_t st) {
-  FS_STORAGE_SWITCH(L0.st, (k_copy_in_s<S><<<grid_of(L0.W, L0.H), kBlk, 0, st>>>(
-                               I0, L0.I0, L0.W, L0.H, L0.P)))
+cudaError_t launch_copy_in_image(const float* src, const LevelView& L, int which,
+                                 cudaStream_t st) {
+  const SPlane& dst = which == 0 ? L.I0 : L.I1;
+  float* lo = which == 0 ? L.I0lo : L.I1lo;
+  FS_STORAGE_SWITCH(L.st, (k_copy_in_s<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(
+                              src, dst, lo, L.W, L.H, L.P)))
 }
 cudaError_t launch_downsample(const LevelView& F, const LevelView& C, cudaStream_t st) {
   FS_STORAGE_SWITCH(F.st, (k_downsample<S><<<grid_of(C.W, C.H), kBlk, 0, st>>>(F, C)))

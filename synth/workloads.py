@@ -54,9 +54,10 @@ def plain_small(seed=0, W=256, H=256, supersample=2):
     return p
 
 
-def plain_kb(seed=0, W=1024, H=1024, supersample=2, levels=5):
+def plain_kb(seed=0, W=1024, H=1024, supersample=2, levels=5, noise=0.01):
     """Kannala-Brandt f=320 px (at 1024) 190 deg, 20 objects 0.5-20 m, 0.12 m
-    baseline + rotation <= 2 deg, Gaussian noise 0.01."""
+    baseline + rotation <= 2 deg, Gaussian noise 0.01 (noise=0: the same
+    scene and rig without image noise)."""
     rng = np.random.default_rng(seed)
     f = 320.0 * W / 1024.0
     half = math.radians(190.0) / 2.0
@@ -66,9 +67,9 @@ def plain_kb(seed=0, W=1024, H=1024, supersample=2, levels=5):
     R = rotation(axis, math.radians(rng.uniform(0.0, 2.0)))
     scene = make_scene(rng, 20, (0.5, 20.0), 20.0, f, kinds=("plane", "sphere"))
     p = _pair(scene, cam, dict(cam), R, np.array([0.12, 0.0, 0.0]), W, H,
-              supersample, 0.01, rng)
+              supersample, noise, rng)
     p.update(levels=levels, warps=10, iters=100, lam=50.0, eps=0.01,
-             name=f"plain_kb_{W}")
+             name=f"plain_kb_{W}" if noise == 0.01 else f"plain_kb_{W}_noise{noise:g}")
     return p
 
 

@@ -119,22 +119,20 @@ def oracle_sensitivity(pair, ref, levels=None, warps=None, iters=None, d_init=No
 
 
 # Disparity parity gate, GPU FP32 vs FP64 oracle (same float32 inputs,
-# pyramid, warps and iterations).  The warping makes a few pixels
-# ill-conditioned: the FP64 oracle itself moves there by up to ~0.2 px under
-# FP32-sized perturbations (oracle_sensitivity), so no FP32 implementation
-# holds a 5e-3 px bound at every pixel.  The gate:
-#   mean |dd| over the FOV mask <= 1e-4 px, or no more than the mean of the
-#   oracle's own largest probe response where that is larger (the noisy
-#   scenes, whose warps amplify FP32-sized perturbations);
-#   |dd| <= 5e-3 px on at least 99.8 % of the mask;
-#   the pixels above 5e-3 px are at most 2 x as many as the oracle's own
-#   under the probes (+ 10), and no |dd| exceeds max(5e-3, 2 x the largest
-#   probe response).
-# The report also gives the largest |dd| over the pixels no probe moves by
-# more than 1e-3 px (max_well_conditioned), for information.
+# pyramid, warps and iterations), at the tolerance the benchmark spec states: max
+# |dd| <= 5e-3 px and mean |dd| <= 1e-4 px.
+#   mean |dd| over the whole FOV mask <= 1e-4 px;
+#   max |dd| <= 5e-3 px over the well-conditioned pixels, those that none of
+#   the oracle's own FP32-sized probes (oracle_sensitivity) moves by more
+#   than 1e-3 px;
+#   on the ill-conditioned rest (its size is reported): no |dd| above
+#   max(5e-3, 2 x the largest probe response), and no more pixels above
+#   5e-3 px than 2 x the probes' own count + 10.  The warping makes a few
+#   pixels ill-conditioned (small I_u against rho0, competing basins at
+#   occlusions): the FP64 oracle itself moves there by up to ~0.2 px under
+#   FP32-sized perturbations, so no FP32 implementation holds 5e-3 px there.
 MAX_TOL = 5e-3
 MEAN_TOL = 1e-4
-QUANTILE = 0.998
 WELL_CONDITIONED = 1e-3
 
 
@@ -142,16 +140,19 @@ def disparity_parity(d_gpu, ref, sens):
     M = ref["mask"]
     err = np.abs(d_gpu - ref["disp"])[M]
     s = sens[M]
+    well = s <= WELL_CONDITIONED
     n_gpu = int((err > MAX_TOL).sum())
     n_probe = int((s > MAX_TOL).sum())
-    well = s <= WELL_CONDITIONED
-    report = dict(mean=float(err.mean()), q998=float(np.quantile(err, QUANTILE)),
-                  max=float(err.max()),
+    report = dict(mean=float(err.mean()), max=float(err.max()),
                   max_well_conditioned=float(err[well].max()) if well.any() else 0.0,
-                  n_ill_conditioned=int((~well).sum()), n_over=n_gpu, n_over_probe=n_probe,
+                  mean_well_conditioned=float(err[well].mean()) if well.any() else 0.0,
+                  n_well_conditioned=int(well.sum()), n_ill_conditioned=int((~well).sum()),
+                  max_ill_conditioned=float(err[~well].max()) if (~well).any() else 0.0,
+                  n_over=n_gpu, n_over_probe=n_probe,
                   probe_max=float(s.max()), probe_mean=float(s.mean()))
-    ok = (report["mean"] <= max(MEAN_TOL, report["probe_mean"]) and report["q998"] <= MAX_TOL
-          and n_gpu <= 2 * n_probe + 10 and report["max"] <= max(MAX_TOL, 2 * report["probe_max"]))
+    ok = (report["mean"] <= MEAN_TOL and report["max_well_conditioned"] <= MAX_TOL
+          and report["max_ill_conditioned"] <= max(MAX_TOL, 2 * report["probe_max"])
+          and n_gpu <= 2 * n_probe + 10)
     return ok, report
 
 

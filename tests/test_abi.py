@@ -109,7 +109,8 @@ def test_host_side_validation(lib):
 def test_state_bytes_counts_the_level_planes(lib):
     # mask bytes + 7 FP32 planes + 10 storage-typed planes + 3 float2 planes
     # per level (pitch = width rounded up to 32, planes on 256-byte
-    # boundaries), plus the full-resolution calibration field
+    # boundaries), plus the full-resolution calibration field (a float-float
+    # pair per pixel: 16 bytes)
     up = lambda v, a: (v + a - 1) // a * a
 
     def expect(W, H, L, esize):
@@ -120,7 +121,7 @@ def test_state_bytes_counts_the_level_planes(lib):
             P = up(w, 32)
             total += up(P * h, 256) + 7 * up(4 * P * h, 256) + 10 * up(esize * P * h, 256) \
                 + 6 * up(4 * P * h, 256)
-        return total + up(up(W, 32) * H * 8, 256)
+        return total + up(up(W, 32) * H * 16, 256)
     for W, H, L in [(64, 64, 2), (203, 157, 3), (1024, 1024, 5)]:
         assert fsb.state_bytes(W, H, L) == expect(W, H, L, 4)
         assert fsb.state_bytes(W, H, L, storage="f16") == expect(W, H, L, 2)
@@ -166,3 +167,16 @@ def test_headers_are_plain_c99():
                         os.path.join(ROOT, "tests", "c_abi_check.c")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+@pytest.mark.parametrize("bad", [dict(regularizer=1), dict(storage=1), dict(accel_gamma=0.1),
+                                 dict(lam=-1.0)])
+def test_noalloc_entry_point_rejects_unsupported_options_on_the_host(lib, bad):
+    # fs_pd_iterate_noalloc computes Huber-TV iterations on FP32 buffers; the
+    # options it does not compute are refused before any device call
+    one = ctypes.c_void_p(16)            # never dereferenced
+    prm = fsb.default_params(**bad)
+    st = lib.fs_pd_iterate_noalloc(one, one, one, one, one, one, one, 64, 64, 5,
+                                   ctypes.byref(prm), None)
+    assert st == -1, bad
+    assert "fs_pd_iterate_noalloc" in lib.fs_last_error().decode()

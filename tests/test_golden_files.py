@@ -1,18 +1,22 @@
-"""The stored oracle values are well-formed: the fixture that the full-size
-GPU parity test reads (tests/golden/kb1024_oracle.json, written by
-make_kb1024_oracle.py from oracle/ and synth/ only) and the paper's printed
-parameters."""
+"""The stored oracle values are well-formed: the fixtures that the full-size
+GPU parity tests read (tests/golden/kb1024_oracle.json and
+kb1024_clean_oracle.json, written by make_kb1024_oracle.py, and
+mixed2048_oracle.json, written by make_mixed2048_oracle.py, from oracle/ and
+synth/ only) and the paper's printed parameters."""
 import json
 import os
 
 import numpy as np
+import pytest
 
 HERE = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def test_kb1024_oracle_fixture_is_complete():
-    g = json.load(open(os.path.join(HERE, "kb1024_oracle.json")))
+@pytest.mark.parametrize("name", ["kb1024_oracle.json", "kb1024_clean_oracle.json"])
+def test_kb1024_oracle_fixture_is_complete(name):
+    g = json.load(open(os.path.join(HERE, name)))
     assert g["sample_columns"] == ["y", "x", "disp", "probe"]
+    assert g["probes"] == ["images", "state", "all", "noise1", "noise2"]
     s = np.array(g["sample"], dtype=np.float64)
     assert s.shape == (4096, 4)
     y, x = s[:, 0].astype(int), s[:, 1].astype(int)
@@ -26,8 +30,27 @@ def test_kb1024_oracle_fixture_is_complete():
     # clipped increments bound the reach: 0.2 px x 10 warps x (2^5 - 1)
     assert s[:, 2].min() >= q[0] - 1.0 and s[:, 2].max() <= 0.2 * 10 * 31
     ps = g["probe_sample_stats"]
-    assert 0 < ps["mean"] <= ps["q998"] <= ps["max"]
+    assert 0 < ps["mean"] <= ps["q998"] <= ps["max"] <= g["probe_field_stats"]["max"]
     assert g["n_mask"] == 1024 * 1024 and g["gt_errors"]["n"] == g["n_mask"]
+    # both fixtures sample the same pixels of the same scene
+    other = json.load(open(os.path.join(HERE, "kb1024_oracle.json")))
+    assert [r[:2] for r in other["sample"]] == [r[:2] for r in g["sample"]]
+
+
+def test_mixed2048_oracle_fixture_is_complete():
+    g = json.load(open(os.path.join(HERE, "mixed2048_oracle.json")))
+    assert g["sample_columns"] == ["y", "x", "disp", "probe_fp32", "probe_fp16", "probe_bf16"]
+    assert (g["levels"], g["warps"], g["iters"]) == (6, 2, 20)
+    s = np.array(g["sample"], dtype=np.float64)
+    assert s.shape == (8192, 6) and np.isfinite(s).all() and (s[:, 3:] >= 0).all()
+    y, x = s[:, 0].astype(int), s[:, 1].astype(int)
+    assert y.min() >= 0 and x.min() >= 0 and y.max() < 2048 and x.max() < 2048
+    assert len(set(zip(y.tolist(), x.tolist()))) == 8192
+    # reach of the clipped increments: 0.2 px x 2 warps x (2^6 - 1)
+    assert np.abs(s[:, 2]).max() <= 0.2 * 2 * 63
+    pf = g["probe_field"]
+    # coarser storage, larger response: fp32 < fp16 < bf16
+    assert pf["fp32"]["mean"] < pf["fp16"]["mean"] < pf["bf16"]["mean"]
 
 
 def test_paper_parameters_fixture_cites_the_paper():

@@ -2,8 +2,9 @@
 
 Same float32 inputs, pyramid, warp and iteration counts on both sides.  The
 disparity gate (gpu_helpers.disparity_parity): mean |dd| <= 1e-4 px over the
-FOV mask, |dd| <= 5e-3 px on 99.8 % of it, and the rest no worse than the
-oracle's own response to FP32-sized perturbations.
+FOV mask, max |dd| <= 5e-3 px over the pixels the oracle's own FP32-sized
+probes leave within 1e-3 px, and the ill-conditioned rest no worse than the
+oracle's own response to those probes.
 """
 import numpy as np
 import pytest
@@ -366,24 +367,32 @@ def test_large_frame_properties():
     assert math.isfinite(float(d[M].mean()))
 
 
-def test_bench_configuration_at_full_counts():
+@pytest.mark.parametrize("fixture", ["kb1024_oracle.json", "kb1024_clean_oracle.json"])
+def test_bench_configuration_at_full_counts(fixture):
     # the timed configuration itself: 1024^2 Kannala-Brandt, 5 levels x 10
-    # warps x 100 iterations, autotuned schedule in a CUDA graph, against
+    # warps x 100 iterations, autotuned schedule in a CUDA graph, on the
+    # workload's noisy scene and on the same scene without noise, against
     # the oracle's disparity at 4096 seeded FOV pixels and its quantiles
-    # (tests/golden/kb1024_oracle.json, written by make_kb1024_oracle.py).
-    # The scene's noise makes this solve ill-conditioned (the oracle itself
-    # moves by a mean 2e-3 px and up to ~1 px under FP32-sized
-    # perturbations), so the gate is the small-size one made relative to the
-    # stored probe responses: mean, 99.8th percentile and maximum of |dd| no
-    # more than twice the oracle's own (floors 1e-4 / 5e-3 / 5e-3 px), and
-    # the quantiles of the field within twice their probe shift (floor
-    # 2e-3 px).  What holds at any size: the same bits as the default
-    # schedule, zero / NaN off the FOV, the reach of the clipped increments.
+    # (tests/golden/*.json, written by make_kb1024_oracle.py).
+    # At ten warps per level the solve is chaotic at a fraction of the
+    # pixels, noise or not: the FP64 oracle itself moves there by up to a few
+    # pixels under FP32-sized perturbations (the five probes of the
+    # fixture), mostly at occlusion boundaries, so the benchmark spec's per-pixel
+    # bound cannot hold for any FP32 implementation at this count.  The gate
+    # compares distributions with the oracle's own: mean, 99.8th percentile
+    # and maximum of |dd| at the sampled pixels no more than twice the
+    # probes' (floors 1e-4 / 5e-3 / 5e-3 px), no more sampled pixels above
+    # 5e-3 px than twice the probes' count + 4, and the quantiles of the
+    # field within twice their probe shift (floor 2e-3 px); on the noise-free
+    # scene also max |dd| <= 5e-3 px at the samples no probe moves by more
+    # than 1e-3 px.  What holds at
+    # any size: the same bits as the default schedule, zero / NaN off the
+    # FOV, the reach of the clipped increments.
     import json
     import os
-    with open(os.path.join(os.path.dirname(__file__), "golden", "kb1024_oracle.json")) as f:
+    with open(os.path.join(os.path.dirname(__file__), "golden", fixture)) as f:
         gold = json.load(f)
-    p = f32pair(synth.plain_kb(0))
+    p = f32pair(synth.plain_kb(0, noise=0.0 if "clean" in fixture else 0.01))
     outs = []
     for tuned in (True, False):
         s = make_solver(p, use_graph=1)
@@ -402,10 +411,19 @@ def test_bench_configuration_at_full_counts():
     ys, xs, dref, probe = (np.array(c) for c in zip(*gold["sample"]))
     err = np.abs(d[ys.astype(int), xs.astype(int)] - dref)
     ps = gold["probe_sample_stats"]
-    rep = dict(mean=err.mean(), q998=float(np.quantile(err, 0.998)), max=err.max(), probe=ps)
+    well = probe <= 1e-3
+    rep = dict(mean=err.mean(), q998=float(np.quantile(err, 0.998)), max=err.max(),
+               n_over=int((err > 5e-3).sum()), n_over_probe=int((probe > 5e-3).sum()),
+               n_well=int(well.sum()), max_well=float(err[well].max()), probe=ps)
+    print(fixture, rep)
     assert rep["mean"] <= max(1e-4, 2 * ps["mean"]), rep
     assert rep["q998"] <= max(5e-3, 2 * ps["q998"]), rep
     assert rep["max"] <= max(5e-3, 2 * ps["max"]), rep
+    assert rep["n_over"] <= 2 * rep["n_over_probe"] + 4, rep
+    if "clean" in fixture:
+        # without image noise, the benchmark spec's bound holds at full count on the
+        # samples that no probe moves by more than 1e-3 px
+        assert rep["max_well"] <= 5e-3, rep
     qs = np.quantile(d[M], gold["quantile_levels"])
     tol = np.maximum(2e-3, 2 * np.array(gold["probe_quantile_shift"]))
     assert np.all(np.abs(qs - gold["disp_quantiles"]) <= tol), (qs, gold["disp_quantiles"], tol)
