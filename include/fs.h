@@ -278,8 +278,9 @@ fs_status fs_batch_destroy(fs_batch* b);
  *   d_u     W x H disparity, read as the start value and overwritten
  *   d_p     2 x W x H dual variable (x then y plane), read and overwritten
  *   prm     NULL for the defaults; lambda, huber_eps, beta, eta, theta,
- *           precond and block_iters are used; accel_gamma must be 0
- *           (FS_EINVAL otherwise)
+ *           precond and block_iters are used; accel_gamma must be 0,
+ *           regularizer FS_REG_HUBER_TV and storage 0 (FS_EINVAL
+ *           otherwise); deriv plays no part (I_u is given)
  *   cuda_stream  stream for the work (NULL = legacy default stream)
  * All pointers are device pointers, dense row-major (pitch W), owned by
  * the caller.  W, H >= 2, iters >= 1; W * H > FS_NOALLOC_MAX_PIXELS

@@ -106,6 +106,15 @@ extern "C" fs_status fs_pd_iterate_noalloc(const float* d_I0, const unsigned cha
   if (p.accel_gamma != 0.f)      // the schedule table lives on a handle
     return fs_internal_set_error(FS_EINVAL,
                                  "fs_pd_iterate_noalloc: accel_gamma is not supported here");
+  // what this entry point computes: Huber-TV iterations on FP32 buffers
+  // (p.deriv has no role here: I_u is an input)
+  if (p.regularizer != FS_REG_HUBER_TV)
+    return fs_internal_set_error(FS_EINVAL,
+                                 "fs_pd_iterate_noalloc: only the Huber-TV regulariser is "
+                                 "supported here (regularizer must be FS_REG_HUBER_TV)");
+  if (p.storage != 0)
+    return fs_internal_set_error(FS_EINVAL,
+                                 "fs_pd_iterate_noalloc: buffers are FP32 (storage must be 0)");
   unsigned char* base = nullptr;
   fs_status s = scratch_for_current_device(&base, msg, sizeof(msg));
   if (s != FS_OK) return fs_internal_set_error(s, msg);

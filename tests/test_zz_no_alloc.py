@@ -78,15 +78,31 @@ def _noalloc(lib, pair, M, u, uw, p, Iu, rho0, iters, block):
 
 
 def test_noalloc_matches_handle_path_on_two_calls(lib):
-    # first call 256 x 256, second a smaller ragged 203 x 157 pair, other data
-    cases = [(f32pair(synth.plain_small(0)), 11, 23, 4), (ragged_pair(0), 12, 17, 3)]
+    # first call 256 x 256, second a smaller ragged 203 x 157 pair, other data,
+    # then a single iteration (one launch: the state is copied back into the
+    # caller's buffers).  Both paths run the same kernels on the same inputs,
+    # so the results are the same bits.
+    cases = [(f32pair(synth.plain_small(0)), 11, 23, 4), (ragged_pair(0), 12, 17, 3),
+             (ragged_pair(1), 13, 1, 4)]
     for pair, seed, iters, block in cases:
         u, uw, p, Iu, rho0 = _inputs(pair, seed)
         M, u, (ref_u, ref_p) = _handle_path(pair, u, uw, p, Iu, rho0, iters, block)
         got_u, got_p = _noalloc(lib, pair, M, u, uw, p, Iu, rho0, iters, block)
-        tol = 2e-6 * iters                  # the primal-dual parity tolerance
-        assert np.abs(got_u - ref_u).max() <= tol
-        assert np.abs(got_p - ref_p).max() <= tol
+        assert np.array_equal(got_u, ref_u), iters
+        assert np.array_equal(got_p, ref_p), iters
+
+
+@pytest.mark.parametrize("bad", [dict(regularizer=1), dict(storage=1), dict(storage=2),
+                                 dict(accel_gamma=0.1)])
+def test_noalloc_rejects_what_it_does_not_compute(lib, bad):
+    # TGV, 16-bit storage and the accelerated schedule are fs_handle features:
+    # asking for them here is an error, not a silent Huber-TV FP32 run
+    import paper_1909_07545_gb300 as fsb
+    one = ctypes.c_void_p(16)            # never dereferenced: the checks come first
+    prm = fsb.default_params(**bad)
+    st = lib.fs_pd_iterate_noalloc(one, one, one, one, one, one, one, 64, 64, 5,
+                                   ctypes.byref(prm), None)
+    assert st == -1, bad
 
 
 def test_noalloc_rejects_oversize(lib):
