@@ -29,15 +29,31 @@ sys.path.insert(0, ROOT)
 
 METRIC = "frames/s & p99 latency, 1024² fisheye pair; primal-dual Gpix-iter/s vs plain"
 PD_BYTES_PER_PX_ITER = 52.0   # unblocked FP32 traffic of one pixel-iteration (9 reads + 4 writes)
-# DRAM bytes (read + write) of one level-0 k_pd launch of this workload on
-# 64 x 64 footprints of 1024 threads at 7 iterations per launch (schedule
-# choice 31), from one ncu capture of the current kernel (cold L2; the
-# command and figures are in profiles/k_pd_level0_kb1024.md)
-PD_L0_DRAM_BYTES_PER_LAUNCH = 47.7e6
-PD_L0_PROFILED_CHOICE = 31
+# ncu DRAM bytes (read + write) of one level-0 k_pd launch of this workload,
+# per schedule choice, each from one capture of the current kernel (cold L2;
+# commands and figures in profiles/k_pd_level0_kb1024.md).  A choice without
+# a capture reports traffic null.
+PD_L0_DRAM_BYTES_PER_LAUNCH = {31: 47.7e6}
+# FP32 instructions of one pixel-iteration of the primal-dual step as written
+# in pd_math.cuh, an FMA counted as one: dual 24 (2 differences, 7 products,
+# 9 FMAs, the reciprocal square root, a min and 4 mask selects), divergence 3,
+# primal 5 (FMA, difference, clamp, sum), relaxation 2
+PD_FP32_INSTR_PER_PX_ITER = 34
+# FP32 lanes of GB300: 152 SMs x 128 lanes, one instruction per lane and clock
+FP32_LANES = 152 * 128
 FOOTPRINTS = ["64x64 footprints, 512 threads", "32x32 footprints, 256 threads",
               "64x32 footprints", "64x64 footprints, 1024 threads",
               "32x32 footprints, 1024 threads", "32x32 footprints, 512 threads"]
+FOOTPRINT_SIZE = [(64, 64), (32, 32), (64, 32), (64, 64), (32, 32), (32, 32)]
+
+
+def decode_choice(c):
+    """(depth, footprint index) of a schedule choice 1..55 (0: cluster -> None)."""
+    if c is None or c <= 0:
+        return None
+    if c > 8 * len(FOOTPRINTS):
+        return c - 8 * len(FOOTPRINTS) + 8, 4
+    return (c - 1) % 8 + 1, (c - 1) // 8
 
 
 def schedule_label(c):
@@ -170,42 +186,94 @@ def l2_probe_gbs(stream, reps=50):
     return 2 * n * 4 * reps / (e0.elapsed_time(e1) / 1000.0) / 1e9
 
 
-def cpu_baseline(pair, target_s=15.0):
-    """The FP64 oracle on a bounded sample of the same frame: the finest
-    level's primal-dual iterations of one warp, extrapolated per pixel-iteration."""
+def _oracle_frame(pair):
+    """One whole frame of the FP64 oracle (a worker of the host-core legs);
+    returns its solve time in seconds."""
     import oracle
-    from oracle.solve import level_data
-    prm = oracle.Params(lam=pair["lam"], eps=pair["eps"])
-    cam = oracle.calib_from_dict(pair["cam0"])
-    H, W = pair["I0"].shape
-    M = oracle.fov_mask(cam, W, H)
-    lv = level_data(pair["I0"], M, prm)
-    rng = np.random.default_rng(0)
-    st = dict(u=np.zeros((H, W)), ubar=np.zeros((H, W)), p1=np.zeros((H, W)),
-              p2=np.zeros((H, W)), Iu=np.where(M, rng.uniform(-0.1, 0.1, (H, W)), 0.0),
-              rho0=np.where(M, rng.uniform(-0.05, 0.05, (H, W)), 0.0), u_w=np.zeros((H, W)))
-    n = 0
     t0 = time.perf_counter()
-    while True:
-        oracle.pd_iteration(st, lv, prm)
-        n += 1
-        if time.perf_counter() - t0 > target_s:
-            break
-    dt = time.perf_counter() - t0
-    return n * W * H / dt, n, dt
+    oracle.solve(pair["I0"], pair["I1"], pair["cam0"], pair["cam1"], pair["R"], pair["t"],
+                 pair["levels"], pair["warps"], pair["iters"],
+                 oracle.Params(lam=pair["lam"], eps=pair["eps"]))
+    return time.perf_counter() - t0
+
+
+def _one_thread():
+    os.environ["OMP_NUM_THREADS"] = "1"
+
+
+def baseline_pairs(n):
+    """n independent 256^2 pairs of the smallest workload (3 levels, 5 warps x
+    50 iterations), images rounded to float32 as the GPU receives them."""
+    import synth
+    out = []
+    for k in range(n):
+        p = synth.plain_small(k)
+        p["I0"] = np.float32(p["I0"]).astype(np.float64)
+        p["I1"] = np.float32(p["I1"]).astype(np.float64)
+        out.append(p)
+    return out
+
+
+def oracle_pool(n):
+    """A spawned pool of n one-thread oracle processes."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(n, initializer=_one_thread)
+
+
+def cpu_baseline(pxit_target, one_thread_frames=4, pool_steps=2):
+    """The FP64 oracle as it stands on this host's cores, on whole frames of
+    the 256^2 workload (3 levels, 5 warps x 50 iterations): one thread
+    (frames one after another in this process) and all cores (one process per
+    core, each its own pair, frames at once).  Returns the measured 256^2
+    figures and both rates converted to frames of the target workload by
+    pixel-iterations (pxit_target per frame)."""
+    n = os.cpu_count() or 1
+    pairs = baseline_pairs(n)
+    pxit = sum(level_pixels(256, 256, 3)) * 5 * 50
+    t1 = [_oracle_frame(pairs[k % n]) for k in range(one_thread_frames)]
+    one_fps = len(t1) / sum(t1)
+    with oracle_pool(n) as pool:
+        pool.map(_oracle_frame, pairs)                 # start-up and warm-up
+        walls = []
+        for _ in range(pool_steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_frame, pairs)
+            walls.append(time.perf_counter() - t0)
+    all_fps = n / float(np.mean(walls))
+    scale = pxit / pxit_target
+    return {
+        "value": all_fps * scale, "unit": "frames/s", "cores": n, "kind": "oracle",
+        "sample": f"whole frames of the 256x256 equidistant workload (3 levels, 5 warps x 50 "
+                  f"iterations, {pxit:.3e} pixel-iterations each), FP64 numpy: {pool_steps} "
+                  f"rounds of {n} frames at once, one process per core on its own pair; the "
+                  f"value is converted to 1024x1024 frames by pixel-iterations "
+                  f"({pxit_target:.3e} per frame)",
+        "measured_256": {"all_cores_frames_per_s": all_fps, "cores": n,
+                         "one_thread_frames_per_s": one_fps,
+                         "one_thread_s_per_frame": float(np.mean(t1)),
+                         "all_cores_round_s": float(np.mean(walls))},
+        "one_thread": {"value": one_fps * scale, "unit": "frames/s", "cores": 1},
+    }
 
 
 def render_rigs(seed, n_rigs=16, n_frames=3):
     """The serving workload's rigs: sizes drawn from 640 / 1024 / 1280 px,
     each its own seeded Kannala-Brandt calibration, relative pose and scene,
     n_frames consecutive frames of its smooth path."""
-    import synth
+    import multiprocessing as mp
     rng = np.random.default_rng(1000 + seed)
     sizes = [int(v) for v in rng.choice([640, 1024, 1280], size=n_rigs)]
     t0 = time.perf_counter()
-    rigs = [synth.rig_sequence(10000 * (seed + 1) + i, W, W, n_frames=n_frames)
-            for i, W in enumerate(sizes)]
+    with mp.get_context("spawn").Pool(min(n_rigs, os.cpu_count() or 1)) as pool:
+        rigs = pool.map(_render_rig, [(10000 * (seed + 1) + i, W, n_frames)
+                                      for i, W in enumerate(sizes)])
     return rigs, sizes, time.perf_counter() - t0
+
+
+def _render_rig(args):
+    import synth
+    s, W, n_frames = args
+    return synth.rig_sequence(s, W, W, n_frames=n_frames)
 
 
 def serve_leg(rigs, sizes, seed, seconds, rate, inflight, warm_mode=1, storage="f32"):
@@ -319,40 +387,56 @@ def serve_leg(rigs, sizes, seed, seconds, rate, inflight, warm_mode=1, storage="
     }
 
 
+def _render_uneven(args):
+    import synth
+    seed, j, i, W = args
+    return synth.plain_kb(100000 * (seed + 1) + 1000 * j + i, W=W, H=W, supersample=1,
+                          levels=synth.auto_levels(W))
+
+
+def render_uneven(seed, per_size, sizes):
+    """The batching workload's pairs, rendered by a spawned process pool."""
+    import multiprocessing as mp
+    jobs = [(seed, j, i, W) for j, W in enumerate(sizes) for i in range(per_size)]
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        return pool.map(_render_uneven, jobs)
+
+
 def uneven_batch_leg(seed, stream, steps, warmup, storage="f16", per_size=16,
                      sizes=(512, 800, 1024, 1280)):
     """Batching: per_size pairs of each size, every pair its own seeded
     Kannala-Brandt calibration, relative pose and scene (the 1024 generator
     scaled), 4-6 pyramid levels (level count: coarsest level >= 40 px),
-    10 warps x 100 iterations, 16-bit storage, each handle autotuned, all
-    pairs in one fs_batch graph.  Returns frames/s per finest-level bound."""
+    10 warps x 100 iterations, 16-bit storage, all pairs in one fs_batch
+    graph, the schedule autotuned once per size.  Beside it, the plain path
+    on the same pairs: FP32 storage, one pair after another, each through
+    its own graph.  Returns frames/s of both (the batch per finest-level
+    bound)."""
     import torch
 
-    import synth
     from paper_1909_07545_gb300 import Batch, Solver
     t0 = time.perf_counter()
-    pairs = []
-    for j, W in enumerate(sizes):
-        for i in range(per_size):
-            pairs.append(synth.plain_kb(100000 * (seed + 1) + 1000 * j + i, W=W, H=W,
-                                        supersample=1, levels=synth.auto_levels(W)))
+    pairs = render_uneven(seed, per_size, sizes)
     render_s = time.perf_counter() - t0
-    sols, I0s, I1s = [], [], []
-    for p in pairs:
-        W = p["I0"].shape[1]
-        x = Solver(p["cam0"], p["cam1"], p["R"], p["t"], W, W, p["levels"], stream=stream,
-                   lam=p["lam"], huber_eps=p["eps"], use_graph=1, storage=storage)
-        x.autotune(p["iters"])
-        sols.append(x)
-        I0s.append(torch.as_tensor(np.float32(p["I0"]), device="cuda"))
-        I1s.append(torch.as_tensor(np.float32(p["I1"]), device="cuda"))
-    bt = Batch(sols, stream=stream)
+    I0s = [torch.as_tensor(np.float32(p["I0"]), device="cuda") for p in pairs]
+    I1s = [torch.as_tensor(np.float32(p["I1"]), device="cuda") for p in pairs]
     outs_d = [torch.empty_like(a) for a in I0s]
     outs_z = [torch.empty_like(a) for a in I0s]
-    res = {}
-    for k in (0, 1, 2, 4):
-        bt.set_finest_limit(k)
-        run = lambda: bt.solve(I0s, I1s, 10, 100, disps=outs_d, depths=outs_z)
+
+    def handles(st):
+        sols, tuned = [], {}
+        for p in pairs:
+            W = p["I0"].shape[1]
+            x = Solver(p["cam0"], p["cam1"], p["R"], p["t"], W, W, p["levels"], stream=stream,
+                       lam=p["lam"], huber_eps=p["eps"], use_graph=1, storage=st)
+            if W not in tuned:
+                tuned[W] = x.autotune(p["iters"])
+            else:
+                x.set_schedule(tuned[W])
+            sols.append(x)
+        return sols, tuned
+
+    def timed(run):
         for _ in range(warmup):
             run()
         stream.synchronize()
@@ -363,10 +447,25 @@ def uneven_batch_leg(seed, stream, steps, warmup, storage="f16", per_size=16,
             run()
         e1.record(stream)
         stream.synchronize()
-        ms = e0.elapsed_time(e1) / steps
+        return e0.elapsed_time(e1) / steps
+
+    sols, tuned = handles(storage)
+    bt = Batch(sols, stream=stream)
+    res = {}
+    for k in (0, 1, 2, 4):
+        bt.set_finest_limit(k)
+        ms = timed(lambda: bt.solve(I0s, I1s, 10, 100, disps=outs_d, depths=outs_z))
         res[f"finest{k}"] = {"frames_per_s": len(pairs) * 1000.0 / ms, "ms_per_batch": ms}
     bt.close()
     for x in sols:
+        x.close()
+    plain, _ = handles("f32")
+
+    def one_by_one():
+        for x, a, b, d, z in zip(plain, I0s, I1s, outs_d, outs_z):
+            x.solve(a, b, 10, 100, disp=d, depth=z)
+    plain_ms = timed(one_by_one)
+    for x in plain:
         x.close()
     px_iter = sum(sum(level_pixels(p["I0"].shape[1], p["I0"].shape[0], p["levels"])) * 1000
                   for p in pairs)
@@ -375,52 +474,80 @@ def uneven_batch_leg(seed, stream, steps, warmup, storage="f16", per_size=16,
                         f"Kannala-Brandt 190 deg, own calibration and pose each, "
                         f"4-6 levels x 10 warps x 100 iterations, {storage} storage, one graph",
             "by_finest_limit": res, "best_frames_per_s": best,
-            "gpix_iter_s_best": px_iter * best / len(pairs) / 1e9, "render_s": render_s}
+            "gpix_iter_s_best": px_iter * best / len(pairs) / 1e9,
+            "plain_f32_one_by_one": {"frames_per_s": len(pairs) * 1000.0 / plain_ms,
+                                     "ms_per_64": plain_ms},
+            "schedule_per_size": {str(W): [schedule_label(c) for c in t]
+                                  for W, t in tuned.items()},
+            "render_s": render_s}
+
+
+def oracle_sample_parity(d, workload, seed):
+    """|d - oracle| at the stored oracle samples of this configuration
+    (tests/golden/kb1024_oracle.json: 4096 seeded FOV pixels of the full-count
+    solve, written from oracle/ and synth/ only, with the oracle's own
+    response at each to five FP32-sized probes).  None for another workload."""
+    if workload != "plain_kb_1024" or seed != 0:
+        return None
+    with open(os.path.join(ROOT, "tests", "golden", "kb1024_oracle.json")) as f:
+        g = json.load(f)
+    c = np.array(g["sample"], dtype=np.float64)
+    y, x, dref, probe = c[:, 0].astype(int), c[:, 1].astype(int), c[:, 2], c[:, 3]
+    err = np.abs(np.asarray(d, dtype=np.float64)[y, x] - dref)
+    well = probe <= 1e-3
+    return {"pixels": len(err), "mean": float(err.mean()),
+            "q998": float(np.quantile(err, 0.998)), "max": float(err.max()),
+            "n_over_5e-3": int((err > 5e-3).sum()),
+            "well_conditioned": {"pixels": int(well.sum()), "max": float(err[well].max()),
+                                 "mean": float(err[well].mean())},
+            "oracle_probe": {"mean": float(probe.mean()),
+                             "q998": float(np.quantile(probe, 0.998)),
+                             "max": float(probe.max()),
+                             "n_over_5e-3": int((probe > 5e-3).sum())}}
 
 
 def run_reference(args, pair, rank):
-    """--impl reference: the FP64 oracle on the host cores, per step a bounded
-    sample of the frame (primal-dual iterations of the finest level)."""
-    import oracle
-    from oracle.solve import level_data
+    """--impl reference: the FP64 oracle as it stands on the host cores.  Each
+    step is a bounded, whole piece of the work: one frame of the 256^2
+    workload (3 levels, 5 warps x 50 iterations) on every core at once, one
+    process per core on its own pair; ms_per_step is that measured time, and
+    the value converts the rate to frames of the target workload by
+    pixel-iterations."""
     if rank != 0:
         return
-    prm = oracle.Params(lam=pair["lam"], eps=pair["eps"])
-    cam = oracle.calib_from_dict(pair["cam0"])
     H, W = pair["I0"].shape
-    M = oracle.fov_mask(cam, W, H)
-    lv = level_data(pair["I0"], M, prm)
-    st = dict(u=np.zeros((H, W)), ubar=np.zeros((H, W)), p1=np.zeros((H, W)),
-              p2=np.zeros((H, W)), Iu=np.where(M, 0.05, 0.0), rho0=np.where(M, 0.01, 0.0),
-              u_w=np.zeros((H, W)))
-    per_step = 5
-    for _ in range(args.warmup):
-        for _ in range(per_step):
-            oracle.pd_iteration(st, lv, prm)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        for _ in range(per_step):
-            oracle.pd_iteration(st, lv, prm)
-        times.append(time.perf_counter() - t0)
-    pxit_frame = sum(level_pixels(W, H, pair["levels"])) * pair["warps"] * pair["iters"]
-    rate = per_step * W * H / float(np.mean(times))      # px-iter/s
-    fps = rate / pxit_frame
+    pxit_target = sum(level_pixels(W, H, pair["levels"])) * pair["warps"] * pair["iters"]
+    n = os.cpu_count() or 1
+    pairs = baseline_pairs(n)
+    pxit = sum(level_pixels(256, 256, 3)) * 5 * 50
+    with oracle_pool(n) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_frame, pairs)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_frame, pairs)
+            times.append(time.perf_counter() - t0)
+    step_s = float(np.mean(times))
+    fps256 = n / step_s
+    fps = fps256 * pxit / pxit_target
     line = {
         "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 / fps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1000.0 * step_s, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": pair["name"], "W": W, "H": H, "levels": pair["levels"],
-                   "warps": pair["warps"], "iters": pair["iters"]},
-        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1,
-                         "host_cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"{per_step} primal-dual iterations of the finest "
-                                   f"{W}x{H} level per step, extrapolated to a frame by "
-                                   f"pixel-iterations ({pxit_frame:.3e} per frame)"},
+                   "warps": pair["warps"], "iters": pair["iters"],
+                   "camera": "kannala_brandt f=320 fov=190"},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": n, "kind": "oracle",
+                         "sample": f"per step, {n} whole frames of the 256x256 equidistant "
+                                   f"workload (3 levels, 5 warps x 50 iterations) at once, one "
+                                   f"process per core; converted to 1024x1024 frames by "
+                                   f"pixel-iterations ({pxit:.3e} against {pxit_target:.3e})",
+                         "measured_256_frames_per_s": fps256},
         "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
-        "gpix_iter_s": rate / 1e9,
+        "gpix_iter_s": fps256 * pxit / 1e9,
     }
     print(json.dumps(line), flush=True)
 
@@ -435,18 +562,17 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--block-iters", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip fs_autotune (default schedule per level)")
-    ap.add_argument("--batch", type=int, default=4,
-                    help="pairs per fs_batch for the batched-throughput figure (<= 1 skips)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
-                    help="length of the open-loop serving run (0 skips serving)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the open-loop FP32 serving run (0 skips serving)")
+    ap.add_argument("--serve-f16-seconds", type=float, default=10.0,
+                    help="length of the FP16-storage serving run (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=600.0, help="offered requests/s")
     ap.add_argument("--serve-inflight", type=int, default=8)
     ap.add_argument("--serve-warm-mode", type=int, default=1, choices=[0, 1])
-    ap.add_argument("--uneven-batch", action="store_true",
-                    help="also time 64 pairs of 512/800/1024/1280 px in one batch graph")
+    ap.add_argument("--no-uneven-batch", dest="uneven_batch", action="store_false",
+                    help="skip the 64 uneven pairs (512/800/1024/1280 px) in one batch graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -512,6 +638,8 @@ def main():
             dist.barrier()
         t_wall = time.perf_counter() - t_wall
         clk = clocks.stop()
+        parity = oracle_sample_parity(disp.cpu().numpy(), args.workload,
+                                      replica_seed(args.seed, rank))
         step_ms = np.array([a.elapsed_time(b) for a, b in ev])
         total_ms, = reduce_max([float(step_ms.sum())], dist, "cuda")
 
@@ -544,7 +672,7 @@ def main():
         l2_gbs = l2_probe_gbs(stream)
 
         # a per-frame pose change: fs_set_pose recomputes the calibration field
-        # (FP64 on host threads from the cached rays) and the trajectory fields
+        # and the trajectory fields (float-float kernels on the handle's stream)
         s.set_pose(pair["R"], pair["t"])
         stream.synchronize()
         t0 = time.perf_counter()
@@ -554,8 +682,7 @@ def main():
         set_pose_ms = (time.perf_counter() - t0) / 5 * 1000.0
         s.close()
 
-        # variants of the same frame: 16-bit storage, and batches of
-        # independent handles solved concurrently through one fs_batch graph
+        # variants of the same frame: 16-bit storage, the TGV-L1 regulariser
         def timed(run, n):
             for _ in range(args.warmup):
                 run()
@@ -595,7 +722,10 @@ def main():
             lv = x.timing_read(reset=True)
             variants[storage] = {"value": job_rate(world, 1, ms), "unit": "frames/s",
                                  "ms_per_frame": ms,
-                                 "pd_per_level_ms": [m / vsteps for m, _, _ in lv]}
+                                 "pd_per_level_ms": [m / vsteps for m, _, _ in lv],
+                                 "vs_oracle": oracle_sample_parity(
+                                     disp.cpu().numpy(), args.workload,
+                                     replica_seed(args.seed, rank))}
             x.close()
         # the paper's own regulariser, TGV-L1 (Eq. 10-11): same frame, FP32
         x = Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, L, stream=stream,
@@ -606,25 +736,6 @@ def main():
                                "ms_per_frame": ms,
                                "schedule_per_level": tgv_sched or "default (blocking 4)"}
         x.close()
-        if args.batch > 1:
-            from paper_1909_07545_gb300 import Batch
-            for storage in ("f32", "f16"):
-                sols = [make(storage) for _ in range(args.batch)]
-                bt = Batch(sols, stream=stream)
-                outs_d = [torch.empty((H, W), device="cuda") for _ in sols]
-                outs_z = [torch.empty((H, W), device="cuda") for _ in sols]
-                # k: pairs allowed on their finest level at once (0 = no bound)
-                for k in (0, 1, 2):
-                    bt.set_finest_limit(k)
-                    ms = timed(lambda: bt.solve([I0] * len(sols), [I1] * len(sols), warps,
-                                                iters, disps=outs_d, depths=outs_z), vsteps)
-                    variants[f"batched_{storage}_finest{k}"] = {
-                        "value": job_rate(world, len(sols), ms), "unit": "frames/s",
-                        "pairs_per_batch": len(sols), "finest_limit": k, "ms_per_batch": ms}
-                bt.close()
-                for x in sols:
-                    x.close()
-
     uneven = None
     if args.uneven_batch:
         uneven = uneven_batch_leg(replica_seed(args.seed, rank), stream, 3, 3)
@@ -638,9 +749,11 @@ def main():
                             args.serve_inflight, args.serve_warm_mode)
         serving["render_s"] = render_s
         serving["gpus"] = 1
-        # the same requests with FP16 storage (FP32 arithmetic)
-        serving_f16 = serve_leg(rigs, sizes, args.seed, args.serve_seconds, args.serve_rate,
-                                args.serve_inflight, args.serve_warm_mode, storage="f16")
+        # the same request stream with FP16 storage (FP32 arithmetic), shorter
+        if args.serve_f16_seconds > 0:
+            serving_f16 = serve_leg(rigs, sizes, args.seed, args.serve_f16_seconds,
+                                    args.serve_rate, args.serve_inflight, args.serve_warm_mode,
+                                    storage="f16")
 
     if rank != 0:
         if dist:
@@ -651,12 +764,29 @@ def main():
     ms_per_step = total_ms / args.steps
     fps = job_rate(world, args.steps, total_ms)
     ms0, n0, px0 = per_level[0]
-    achieved = PD_BYTES_PER_PX_ITER * px0 / (ms0 / 1000.0) / 1e9
-    # the profiled traffic applies while level 0 runs the profiled schedule
+    launch_s = ms0 / 1000.0 / max(n0, 1)                # mean level-0 launch duration
     l0_choice = tuned[0] if tuned else None
-    traffic = PD_L0_DRAM_BYTES_PER_LAUNCH if l0_choice == PD_L0_PROFILED_CHOICE else None
+    dec = decode_choice(l0_choice)
     peaks, src = measured_peaks()
     peak = float(peaks["hbm_gbs"])
+    # Algorithmic bytes of one level-0 launch (the blocked figure of the
+    # roofline model): one pass over every footprint, 52 B per pixel
+    # (9 words read, 4 written), the footprints overlapping by
+    # (FW / IW) x (FH / IH) with IW = FW - 2 B interior columns.
+    if dec is not None:
+        B, v = dec
+        FW, FH = FOOTPRINT_SIZE[v]
+        overlap = FW / (FW - 2 * B) * FH / (FH - 2 * B)
+    else:
+        B, FW, FH, overlap = None, None, None, 1.0
+    px_l0 = W * H
+    bytes_launch = PD_BYTES_PER_PX_ITER * px_l0 * overlap
+    achieved = bytes_launch / launch_s / 1e9
+    compulsory = PD_BYTES_PER_PX_ITER * px_l0 / launch_s / 1e9
+    traffic = PD_L0_DRAM_BYTES_PER_LAUNCH.get(l0_choice)
+    iters_per_launch = px0 / max(n0, 1) / px_l0
+    alu_achieved = PD_FP32_INSTR_PER_PX_ITER * px_l0 * iters_per_launch / launch_s
+    alu_peak = FP32_LANES * (clk["sm_mhz"] if clk else 2070.0) * 1e6
     pd_ms = sum(m for m, _, _ in per_level) / args.steps
     # launches per frame: 2 copy/pre-rotate, L-1 downsample, L tensor, 1 zero,
     # L-1 upsample, per level one warp, warps-1 fused clip + warp and one
@@ -684,18 +814,33 @@ def main():
                "per_level_ms": [m / args.steps for m, _, _ in per_level]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "traffic_note": "DRAM bytes per level-0 launch, ncu, cold L2",
+                     "traffic_note": "ncu DRAM read + write bytes of one level-0 launch of "
+                                     "this schedule, cold L2 (null: no capture of it)",
                      "kernel": "k_pd level 0 (1024x1024), " + (
                          schedule_label(l0_choice) if l0_choice is not None else "default"),
                      "launches_per_frame": n0 // max(args.steps, 1),
-                     "algorithmic_bytes_per_launch": PD_BYTES_PER_PX_ITER * px0 / max(n0, 1),
+                     "launch_us": launch_s * 1e6,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "algorithmic_bytes_note": "52 B per level-0 pixel x footprint overlap "
+                                               f"({FW}x{FH} footprints, halo {B}: x{overlap:.3f})",
                      "peak_source": f"{src} hbm_gbs",
-                     "algorithmic_bytes_per_px_iter": PD_BYTES_PER_PX_ITER},
+                     "compulsory_frac": compulsory / peak,
+                     "compulsory_note": "one pass, 52 B per level-0 pixel per launch, no halo",
+                     "alu": {"achieved": alu_achieved / 1e12, "peak": alu_peak / 1e12,
+                             "unit": "T FP32 instr/s",
+                             "frac": alu_achieved / alu_peak,
+                             "halo_recompute": overlap,
+                             "note": f"{PD_FP32_INSTR_PER_PX_ITER} FP32 instructions per "
+                                     "level-0 pixel-iteration (the halo recomputation, "
+                                     "x halo_recompute, not counted); peak = 152 SMs x 128 "
+                                     "lanes x median SM clock"}},
         "gpu_launches": int(args.steps * (pd_launches + per_frame_other)),
         "clocks": clk,
         "wall_s": t_wall,
     }
     line["variants"] = variants
+    if parity is not None:
+        line["parity"] = parity
     line["set_pose_ms"] = set_pose_ms
     # the same level-0 figure against the L2 bandwidth the frame's working set
     # (about 60 MB at level 0) actually streams from
@@ -705,22 +850,16 @@ def main():
                                           "32 MB in + 32 MB out, L2-resident"}
     if serving is not None:
         line["serving"] = serving
+    if serving_f16 is not None:
         line["serving_f16"] = {k: serving_f16[k] for k in
-                               ("workload", "frames_per_s", "p50_ms", "p99_ms", "max_ms",
-                                "saturated_frames_per_s", "requests", "failed")}
+                               ("workload", "seconds", "frames_per_s", "p50_ms", "p99_ms",
+                                "max_ms", "saturated_frames_per_s", "requests", "failed")}
     if uneven is not None:
         line["uneven_batch"] = uneven
     line["e2e"] = {"value": world / e2e_s, "unit": "frames/s",
                    "h2d_bytes_per_step": 2 * W * H * 4, "d2h_bytes_per_step": 2 * W * H * 4}
-    if not args.no_cpu_baseline:
-        os.environ.setdefault("OMP_NUM_THREADS", "1")
-        rate, n, dt = cpu_baseline(pair, args.cpu_seconds)
-        line["cpu_baseline"] = {
-            "value": rate / pxit_frame, "unit": "frames/s", "cores": 1,
-            "host_cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} primal-dual iterations of the finest {W}x{H} level in {dt:.1f} s "
-                      f"(FP64 numpy, one thread), extrapolated to a frame by pixel-iterations "
-                      f"({pxit_frame:.3e} per frame)"}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(pxit_frame)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
