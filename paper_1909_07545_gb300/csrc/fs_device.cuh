@@ -260,6 +260,30 @@ __device__ __forceinline__ float sld(const SPlane& pl, size_t i) {
   else return __ldg((const float*)pl.p + i);
 }
 
+// Loads of planes that another CTA of the same launch may have written (the
+// persistent schedule): CG = true reads through L2 only (ld.global.cg), so a
+// line an SM's L1 cached earlier in the launch is never served stale.
+// CG = false is the plain load the launch-per-stage kernels use.
+template <bool CG>
+__device__ __forceinline__ float ldf(const float* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <bool CG>
+__device__ __forceinline__ float2 ldf2(const float2* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <int S, bool CG>
+__device__ __forceinline__ float sld_m(const SPlane& pl, size_t i) {
+  if constexpr (!CG) return sld<S>(pl, i);
+  else if constexpr (S == ST_F16) return __half2float(__ldcg((const __half*)pl.p + i));
+  else if constexpr (S == ST_BF16) return __bfloat162float(__ldcg((const __nv_bfloat16*)pl.p + i));
+  else return __ldcg((const float*)pl.p + i);
+}
+
 template <int S>
 __device__ __forceinline__ void sst(const SPlane& pl, size_t i, float v) {
   if constexpr (S == ST_F16) ((__half*)pl.p)[i] = __float2half_rn(v);

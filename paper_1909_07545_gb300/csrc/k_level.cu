@@ -3,6 +3,7 @@
 // pre-rotation, pyramid down/up-sampling, tensor and step sizes,
 // warp + linearisation, clip + update, triangulation.
 #include "fs_kernels.h"
+#include "level_px.cuh"
 
 namespace fs {
 
@@ -178,45 +179,14 @@ __global__ void k_downsample(LevelView F, LevelView C) {
   }
 }
 
-// u, w of level C (coarse) -> level F (fine): bilinear over coarse in-mask
-// samples with renormalised weights, values x2, 0 outside the fine mask.
-// Also sets ubar = u_w = u and p = 0 on the fine level.
+// u, w of level C (coarse) -> level F (fine): upsample_px at every pixel.
 template <int S>
 __global__ void k_upsample(LevelView C, LevelView F) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= F.W || y >= F.H) return;
-  size_t o = (size_t)y * F.P + x;
-  float u = 0.f, wx = 0.f, wy = 0.f;
-  if (F.mask[o] & MASK_IN) {
-    float X = fminf(fmaxf(((float)x + 0.5f) * 0.5f - 0.5f, 0.f), (float)(C.W - 1));
-    float Y = fminf(fmaxf(((float)y + 0.5f) * 0.5f - 0.5f, 0.f), (float)(C.H - 1));
-    int x0 = min((int)floorf(X), max(C.W - 2, 0));
-    int y0 = min((int)floorf(Y), max(C.H - 2, 0));
-    int x1 = min(x0 + 1, C.W - 1), y1 = min(y0 + 1, C.H - 1);
-    float ax = X - (float)x0, ay = Y - (float)y0;
-    int xs[4] = {x0, x1, x0, x1}, ys[4] = {y0, y0, y1, y1};
-    float ws[4] = {(1.f - ax) * (1.f - ay), ax * (1.f - ay), (1.f - ax) * ay, ax * ay};
-    float den = 0.f, nu = 0.f, nx = 0.f, ny = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      size_t ci = (size_t)ys[k] * C.P + xs[k];
-      if (C.mask[ci] & MASK_IN) {
-        float2 cw = C.w[ci];
-        den += ws[k];
-        nu += ws[k] * C.u[ci];
-        nx += ws[k] * cw.x;
-        ny += ws[k] * cw.y;
-      }
-    }
-    if (den > 0.f) {
-      float s = 2.f / den;
-      u = nu * s; wx = nx * s; wy = ny * s;
-    }
-  }
-  F.u[o] = u; F.ubar[o] = u; F.uw[o] = u;
-  F.w[o] = make_float2(wx, wy);
-  sst<S>(F.p1, o, 0.f); sst<S>(F.p2, o, 0.f);
+  float2 w;
+  upsample_px<S, false>(C, F, x, y, w);
 }
 
 // Warm start at the finest level from a disparity already in L.u: w is
@@ -275,117 +245,19 @@ __global__ void k_zero_state(LevelView L) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
-  size_t o = (size_t)y * L.P + x;
-  L.u[o] = 0.f; L.ubar[o] = 0.f; L.uw[o] = 0.f;
-  sst<S>(L.p1, o, 0.f); sst<S>(L.p2, o, 0.f);
-  L.w[o] = make_float2(0.f, 0.f);
+  zero_px<S>(L, (size_t)y * L.P + x);
 }
 
 // ------------------------------------------------------------ tensor + steps
-struct TensorAt {
-  float sx, sy;            // T^1/2 = I - s s^T
-  float aa, bb, cc;        // |a|, |b|, |c|
-};
-
-// T^1/2 = e n n^T + n_perp n_perp^T = I - (1 - e) n n^T  (Eq. 12) with
-// e = exp(-beta |grad I0|^eta), grad I0 by central differences on the mask
-// (one-sided at its edge, 0 where both neighbours leave it).
-template <int S>
-__device__ __forceinline__ TensorAt tensor_at(const LevelView& L, int x, int y, float beta,
-                                              float eta) {
-  TensorAt t;
-  size_t i = (size_t)y * L.P + x;
-  if (!(L.mask[i] & MASK_IN)) { t.sx = t.sy = 0.f; t.aa = 1.f; t.bb = 0.f; t.cc = 1.f; return t; }
-  auto I0 = [&](size_t k) { return sld<S>(L.I0, k); };
-  float c = I0(i);
-  bool r = x + 1 < L.W && (L.mask[i + 1] & MASK_IN);
-  bool l = x > 0 && (L.mask[i - 1] & MASK_IN);
-  bool d = y + 1 < L.H && (L.mask[i + L.P] & MASK_IN);
-  bool u = y > 0 && (L.mask[i - L.P] & MASK_IN);
-  float gx = 0.f, gy = 0.f;
-  if (r && l) gx = 0.5f * (I0(i + 1) - I0(i - 1));
-  else if (r) gx = I0(i + 1) - c;
-  else if (l) gx = c - I0(i - 1);
-  if (d && u) gy = 0.5f * (I0(i + L.P) - I0(i - L.P));
-  else if (d) gy = I0(i + L.P) - c;
-  else if (u) gy = c - I0(i - L.P);
-  float mag = sqrtf(gx * gx + gy * gy);
-  if (mag < 1e-12f) { t.sx = t.sy = 0.f; t.aa = 1.f; t.bb = 0.f; t.cc = 1.f; return t; }
-  float nx = gx / mag, ny = gy / mag;
-  float one_minus_e = -expm1f(-beta * powf(mag, eta));
-  float s = sqrtf(one_minus_e);
-  t.sx = s * nx;
-  t.sy = s * ny;
-  t.aa = fabsf(1.f - one_minus_e * nx * nx);
-  t.bb = fabsf(one_minus_e * nx * ny);
-  t.cc = fabsf(1.f - one_minus_e * ny * ny);
-  return t;
-}
-
-// Diagonal preconditioning (Pock-Chambolle 2011, alpha = 1) from the row and
-// column sums of the entrywise bound |T^1/2| |grad| of K = T^1/2 grad:
-//   sigma(x) = 1 / max(2(|a| m1 + |b| m2), 2(|b| m1 + |c| m2))
-//   tau(x)   = 1 / ((|a|+|b|) m1 + (|b|+|c|) m2 at x,
-//                   + (|a|+|b|) m1 at x - e1, + (|b|+|c|) m2 at x - e2)
 template <int S>
 __global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
-  size_t i = (size_t)y * L.P + x;
-  uint8_t m = L.mask[i];
-  TensorAt t = tensor_at<S>(L, x, y, beta, eta);
-  sst<S>(L.sx, i, t.sx);
-  sst<S>(L.sy, i, t.sy);
-  if (!precond) {
-    const float s = 0.35355339059327373f;   // 1/sqrt(8)
-    L.tau[i] = (m & MASK_IN) ? s : 0.f;       // tau = 0 holds u outside the mask
-    L.sig[i] = s;
-    return;
-  }
-  float m1 = (m & MASK_GX) ? 1.f : 0.f, m2 = (m & MASK_GY) ? 1.f : 0.f;
-  float r1 = 2.f * (t.aa * m1 + t.bb * m2);
-  float r2 = 2.f * (t.bb * m1 + t.cc * m2);
-  float r = fmaxf(r1, r2);
-  L.sig[i] = r > 0.f ? 1.f / r : 0.f;
-  float col = (t.aa + t.bb) * m1 + (t.bb + t.cc) * m2;
-  if (x > 0 && (L.mask[i - 1] & MASK_GX)) {
-    TensorAt tl = tensor_at<S>(L, x - 1, y, beta, eta);
-    col += tl.aa + tl.bb;
-  }
-  if (y > 0 && (L.mask[i - L.P] & MASK_GY)) {
-    TensorAt tu = tensor_at<S>(L, x, y - 1, beta, eta);
-    col += tu.bb + tu.cc;
-  }
-  L.tau[i] = (col > 0.f && (m & MASK_IN)) ? 1.f / col : 0.f;
+  tensor_px<S>(L, x, y, beta, eta, precond);
 }
 
 // ------------------------------------------------------------ warp + linearise
-// g = bicubic gamma'(x + w) renormalised (0 if |g| < 1e-6); I1w = I1(x + w);
-// rho0 = I1w - I0 (Eq. 3, 9); I_u = I1(x + w + g) - I1w (Eq. 5, 7), or with
-// `central` half the difference of the samples at x + w +- g (free of the
-// I1w noise that the forward difference shares with rho0).  Starts a warp:
-// ubar = u_w = u.
-// The linearisation at one FOV pixel for warp vector w (shared by k_warp and
-// k_clip_warp, so both give the same bits).
-template <int S>
-__device__ __forceinline__ void warp_px(const LevelView& L, int x, int y, size_t i, float2 w,
-                                        int central, float& Iu, float& rho0, float2& g) {
-  g = make_float2(0.f, 0.f);
-  float2 gr = sample_bicubic2(L.gamma, L.W, L.H, L.P, x, w.x, y, w.y);
-  float n = sqrtf(gr.x * gr.x + gr.y * gr.y);
-  if (n >= 1e-6f) g = make_float2(gr.x / n, gr.y / n);
-  float I1w = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x, y, w.y);
-  float I1g = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x + g.x, y, w.y + g.y);
-  if (central) {
-    float I1m = sample_bilinear_s<S>(L.I1, L.W, L.H, L.P, x, w.x - g.x, y, w.y - g.y);
-    Iu = 0.5f * (I1g - I1m);
-  } else {
-    Iu = I1g - I1w;
-  }
-  rho0 = I1w - sld<S>(L.I0, i);
-}
-
 template <int S>
 __global__ void k_warp(LevelView L, int central) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -404,18 +276,6 @@ __global__ void k_warp(LevelView L, int central) {
 }
 
 // ------------------------------------------------------------ clip + update
-// du = clamp(u - u_w, +-du_max); u_{w+1} = u_w + du; w += du g (Algorithm 1,
-// Eq. 8-9).  The primal state continues from u_{w+1}.
-__device__ __forceinline__ float clip_px(const LevelView& L, size_t i, float du_max,
-                                         float2& w) {
-  float uw = L.uw[i];
-  float du = fminf(fmaxf(__fsub_rn(L.u[i], uw), -du_max), du_max);
-  float2 g = L.g[i];
-  w = L.w[i];
-  w = make_float2(fmaf(du, g.x, w.x), fmaf(du, g.y, w.y));
-  return __fadd_rn(uw, du);
-}
-
 __global__ void k_clip(LevelView L, float du_max) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -423,7 +283,7 @@ __global__ void k_clip(LevelView L, float du_max) {
   size_t i = (size_t)y * L.P + x;
   if (!(L.mask[i] & MASK_IN)) return;
   float2 w;
-  float un = clip_px(L, i, du_max, w);
+  float un = clip_px<false>(L, i, du_max, w);
   L.u[i] = un;
   L.ubar[i] = un;
   L.uw[i] = un;
@@ -445,7 +305,7 @@ __global__ void k_clip_warp(LevelView L, float du_max, int central) {
   float u;
   if (L.mask[i] & MASK_IN) {
     float2 w;
-    u = clip_px(L, i, du_max, w);
+    u = clip_px<false>(L, i, du_max, w);
     L.w[i] = w;
     L.u[i] = u;
     warp_px<S>(L, x, y, i, w, central, Iu, rho0, g);

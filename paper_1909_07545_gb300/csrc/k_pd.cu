@@ -2,21 +2,13 @@
 //
 // Per-pixel arithmetic: pd_math.cuh (identical in both schedules).
 //
-// 1. k_pd -- temporal blocking, for levels too large to stay on chip.
-//    One CTA owns a footprint of FW x (NY * R) pixels: an interior tile plus
-//    a halo of B pixels on every side.  Thread (tx, ty) keeps the column tx,
-//    rows ty*R .. ty*R + R - 1 of the footprint in registers (state u, ubar,
-//    p and the per-warp constants); shared memory only carries what
-//    neighbours exchange (ubar, and the masked products T^1/2 p).  One
-//    iteration makes the dependency cone grow by one pixel in every
-//    direction, so after n <= B iterations the interior is exact and is
-//    written back; the halo is recomputed by the neighbouring CTAs.  Two CTA
-//    barriers per iteration.  The state is read from one buffer set and
-//    written to the other, so no CTA sees a neighbour's updated interior
-//    while it loads its halo.  Six footprints (PDVariant) trade registers
-//    per thread (R rows) against resident warps and halo recomputation; the
-//    autotuner picks one per level.  ACC instantiations read the accelerated
-//    step schedule, one table entry per iteration of the warp.
+// 1. k_pd -- temporal blocking, for levels too large to stay on chip: one
+//    CTA per footprint, the body in pd_tile.cuh (an interior tile plus a halo
+//    of B pixels, n <= B iterations per launch).  Six footprints (PDVariant)
+//    trade registers per thread (R rows) against resident warps and halo
+//    recomputation; the autotuner picks one per level.  ACC instantiations
+//    read the accelerated step schedule, one table entry per iteration of
+//    the warp.
 //
 // 2. k_pd_cluster -- the whole level resident in one thread-block cluster
 //    (at most 16 CTAs, one tile each, no halo), for the coarse levels.  Each
@@ -30,16 +22,12 @@
 #include <cooperative_groups.h>
 
 #include "fs_kernels.h"
-#include "pd_math.cuh"
+#include "pd_tile.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace fs {
 
-// ACC: the accelerated step schedule of pp.sched (FP32 storage, scalar
-// steps): iteration it of the launch uses entry pp.k0 + it for sigma (all
-// pixels), tau and the L1 step (scaled from the stored tau_0 values, 0 off
-// the mask) and theta.
 template <int FW, int NY, int R, int S, bool ACC>
 __global__ void __launch_bounds__(FW * NY, FW * NY >= 512 ? 1 : 2)
 k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int chained) {
@@ -47,126 +35,9 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
   __shared__ float s_ub[FH][FW];
   __shared__ float s_t1[FH][FW];
   __shared__ float s_t2[FH][FW];
-
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int IW = FW - 2 * B, IH = FH - 2 * B;
-  const int ox = (int)blockIdx.x * IW - B;
-  const int oy = (int)blockIdx.y * IH - B;
-  const int gx = ox + tx;
-  const bool col_in = gx >= 0 && gx < L.W;
-  float theta = pp.theta;
-
-  // Let the next launch of the chain be scheduled as soon as every CTA of
-  // this one is resident (it waits for this grid's completion before it
-  // reads the state, below).
-  if (chained) cudaTriggerProgrammaticLaunchCompletion();
-
-  float u[R], ub[R], p1[R], p2[R];
-  PxConst c[R];
-  unsigned mb = 0;
-  // Addresses clamped into the level and a validity flag per row: every
-  // load below is unconditional, so all of a thread's loads are in flight
-  // at once instead of one row's after another's.
-  const int gxc = min(max(gx, 0), L.W - 1);
-  unsigned idx[R];            // < 2^31: levels are at most 32768 x 32768
-  bool ok[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int gy = oy + ty * R + r;
-    ok[r] = col_in && gy >= 0 && gy < L.H;
-    idx[r] = (unsigned)(min(max(gy, 0), L.H - 1) * L.P + gxc);
-  }
-  // per-warp constants first: written by earlier kernels, not by the
-  // preceding launch of this chain
-  {
-    PxRaw raw[R];
-    unsigned char m8[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      px_fetch<S>(L, idx[r], ok[r], raw[r]);
-      m8[r] = ok[r] ? L.mask[idx[r]] : 0;
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      px_make(raw[r], pp.lam, pp.eps, c[r]);
-      mb |= (unsigned)m8[r] << (3 * r);
-    }
-  }
-  // the state is the preceding launch's output
-  if (chained) cudaGridDependencySynchronize();
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const float a = in.u[idx[r]], b = in.ubar[idx[r]];
-    const float q1 = sld<S>(in.p1, idx[r]), q2 = sld<S>(in.p2, idx[r]);
-    u[r] = ok[r] ? a : 0.f;
-    ub[r] = ok[r] ? b : 0.f;
-    p1[r] = ok[r] ? q1 : 0.f;
-    p2[r] = ok[r] ? q2 : 0.f;
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) s_ub[ty * R + r][tx] = ub[r];
-  __syncthreads();
-
-  const int txr = min(tx + 1, FW - 1);
-  const int txl = max(tx - 1, 0);
-
-  // a thread's own products stay in registers; shared memory carries t1 to
-  // the right-hand neighbour and the last row's t2 to the thread below
-  float t1r[R], t2r[R];
-#pragma unroll 1
-  for (int it = 0; it < n_iters; ++it) {
-    float4 sk = make_float4(1.f, 0.f, 0.f, 0.f);
-    if constexpr (ACC) {
-      sk = pp.sched[pp.k0 + it];
-      theta = sk.w;
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int fy = ty * R + r;
-      const float right = s_ub[fy][txr];
-      const float below = (r + 1 < R) ? ub[r + 1] : s_ub[min(fy + 1, FH - 1)][tx];
-      PxConst cr = c[r];
-      if constexpr (ACC) {
-        cr.dinv = sk.y;
-        cr.sd = sk.z;
-      }
-      px_dual(mb >> (3 * r), ub[r], right, below, cr, p1[r], p2[r], t1r[r], t2r[r]);
-      s_t1[fy][tx] = t1r[r];
-      if (r == R - 1) s_t2[fy][tx] = t2r[r];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int fy = ty * R + r;
-      // the row above: this thread's previous row, or the last row of the
-      // thread above (the top row of the footprint is halo: its own value)
-      const float t2_up = r > 0 ? t2r[r - 1] : (ty > 0 ? s_t2[fy - 1][tx] : t2r[0]);
-      const float dv = px_div(t1r[r], s_t1[fy][txl], t2r[r], t2_up);
-      PxConst cr = c[r];
-      if constexpr (ACC) {
-        cr.tau = __fmul_rn(c[r].tau, sk.x);
-        cr.step = __fmul_rn(c[r].step, sk.x);
-      }
-      const float un = px_primal(u[r], dv, cr);
-      ub[r] = px_relax(un, u[r], theta);
-      u[r] = un;
-      s_ub[fy][tx] = ub[r];
-    }
-    __syncthreads();
-  }
-
-  if (!col_in || tx < B || tx >= FW - B) return;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int fy = ty * R + r;
-    const int gy = oy + fy;
-    if (fy < B || fy >= FH - B || gy < 0 || gy >= L.H) continue;
-    const size_t i = (size_t)gy * L.P + gx;
-    out.u[i] = u[r];
-    out.ubar[i] = ub[r];
-    sst<S>(out.p1, i, p1[r]);
-    sst<S>(out.p2, i, p2[r]);
-  }
+  pd_tile<FW, NY, R, S, ACC, false>(L, in, out, pp, B, n_iters, (int)blockIdx.x,
+                                    (int)blockIdx.y, (int)threadIdx.x, (int)threadIdx.y, s_ub,
+                                    s_t1, s_t2, chained != 0);
 }
 
 template <int TW, int NY, int R, int S>

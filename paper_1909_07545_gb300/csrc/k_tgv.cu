@@ -186,6 +186,9 @@ k_tgv_blocked(LevelView L, TgvState in, TgvState out, TgvParams tp, int B, int n
       mb |= mm << (3 * r);
     }
   }
+  // the state is the preceding launch's output, read through L2 (a chained
+  // launch may start while the launch two before it still caches lines of
+  // this buffer set in L1)
   if (chained) cudaGridDependencySynchronize();
   float u[R], ub[R], v1[R], v2[R], vb1[R], vb2[R], p1[R], p2[R], q11[R], q12[R], q21[R],
       q22[R];
@@ -194,7 +197,7 @@ k_tgv_blocked(LevelView L, TgvState in, TgvState out, TgvParams tp, int B, int n
     const unsigned k = idx[r];
     float a[12];
 #pragma unroll
-    for (int j = 0; j < 12; ++j) a[j] = in.s[j][k];
+    for (int j = 0; j < 12; ++j) a[j] = __ldcg(in.s[j] + k);
     const float z = ok[r] ? 1.f : 0.f;   // off the level: inert zeros
     u[r] = a[0] * z; ub[r] = a[1] * z; v1[r] = a[2] * z; v2[r] = a[3] * z;
     vb1[r] = a[4] * z; vb2[r] = a[5] * z; p1[r] = a[6] * z; p2[r] = a[7] * z;

@@ -35,16 +35,17 @@ struct PxRaw {
 
 // Fetch from plane index i; v = false (a pixel outside the level) gives the
 // inputs of a pixel that never moves (all 0).  i must be a valid index even
-// when v is false (callers clamp it), so the loads need no branch.
-template <int S>
+// when v is false (callers clamp it), so the loads need no branch.  CG: the
+// planes may have been written earlier in the same launch (sld_m).
+template <int S, bool CG = false>
 __device__ __forceinline__ void px_fetch(const LevelView& L, size_t i, bool v, PxRaw& r) {
-  r.sx = sld<S>(L.sx, i);
-  r.sy = sld<S>(L.sy, i);
-  r.sig = L.sig[i];
-  r.tau = L.tau[i];
-  r.Iu = sld<S>(L.Iu, i);
-  r.rho0 = sld<S>(L.rho0, i);
-  r.uw = L.uw[i];
+  r.sx = sld_m<S, CG>(L.sx, i);
+  r.sy = sld_m<S, CG>(L.sy, i);
+  r.sig = ldf<CG>(L.sig + i);
+  r.tau = ldf<CG>(L.tau + i);
+  r.Iu = sld_m<S, CG>(L.Iu, i);
+  r.rho0 = sld_m<S, CG>(L.rho0, i);
+  r.uw = ldf<CG>(L.uw + i);
   if (!v) r.sx = r.sy = r.sig = r.tau = r.Iu = r.rho0 = r.uw = 0.f;
 }
 

@@ -1,0 +1,161 @@
+// pd_tile.cuh -- one CTA's temporally blocked primal-dual footprint (Eq. 11,
+// 13): the body of k_pd, shared with the persistent schedule (k_persist.cu)
+// so that both compute the same bits.
+//
+// The CTA owns a footprint of FW x (NY * R) pixels: an interior tile (bx,
+// by) of (FW - 2B) x (NY R - 2B) pixels plus a halo of B pixels on every
+// side.  Thread (tx, ty) keeps the column tx, rows ty*R .. ty*R + R - 1 of
+// the footprint in registers (state u, ubar, p and the per-warp constants);
+// shared memory only carries what neighbours exchange (ubar, and the masked
+// products T^1/2 p).  One iteration makes the dependency cone grow by one
+// pixel in every direction, so after n <= B iterations the interior is exact
+// and is written back; the halo is recomputed by the neighbouring tiles.  Two
+// CTA barriers per iteration.  The state is read from one buffer set and
+// written to the other, so no tile sees a neighbour's updated interior while
+// it loads its halo.
+#pragma once
+
+#include "pd_math.cuh"
+
+namespace fs {
+
+// ACC: the accelerated step schedule of pp.sched (FP32 storage, scalar
+// steps): iteration it of the block uses entry pp.k0 + it for sigma (all
+// pixels), tau and the L1 step (scaled from the stored tau_0 values, 0 off
+// the mask) and theta.  CG: the inputs may have been written by other CTAs
+// of the same launch (loads through L2 only).  chained: a programmatic
+// dependent launch of k_pd (constants loaded before the wait for the
+// preceding launch, the state after it).  s_ub, s_t1, s_t2: shared arrays of
+// FH x FW floats.  Every thread of the CTA (FW x NY) must call it.
+template <int FW, int NY, int R, int S, bool ACC, bool CG>
+__device__ __forceinline__ void pd_tile(const LevelView& L, const PDState& in,
+                                        const PDState& out, const PDParams& pp, int B,
+                                        int n_iters, int bx, int by, int tx, int ty,
+                                        float (*s_ub)[FW], float (*s_t1)[FW],
+                                        float (*s_t2)[FW], bool chained) {
+  constexpr int FH = NY * R;
+  const int IW = FW - 2 * B, IH = FH - 2 * B;
+  const int ox = bx * IW - B;
+  const int oy = by * IH - B;
+  const int gx = ox + tx;
+  const bool col_in = gx >= 0 && gx < L.W;
+  float theta = pp.theta;
+
+  // Let the next launch of the chain be scheduled as soon as every CTA of
+  // this one is resident (it waits for this grid's completion before it
+  // reads the state, below).
+  if (chained) cudaTriggerProgrammaticLaunchCompletion();
+
+  float u[R], ub[R], p1[R], p2[R];
+  PxConst c[R];
+  unsigned mb = 0;
+  // Addresses clamped into the level and a validity flag per row: every
+  // load below is unconditional, so all of a thread's loads are in flight
+  // at once instead of one row's after another's.
+  const int gxc = min(max(gx, 0), L.W - 1);
+  unsigned idx[R];            // < 2^31: levels are at most 32768 x 32768
+  bool ok[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gy = oy + ty * R + r;
+    ok[r] = col_in && gy >= 0 && gy < L.H;
+    idx[r] = (unsigned)(min(max(gy, 0), L.H - 1) * L.P + gxc);
+  }
+  // per-warp constants first: written by earlier kernels, not by the
+  // preceding launch of this chain
+  {
+    PxRaw raw[R];
+    unsigned char m8[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      px_fetch<S, CG>(L, idx[r], ok[r], raw[r]);
+      m8[r] = ok[r] ? L.mask[idx[r]] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      px_make(raw[r], pp.lam, pp.eps, c[r]);
+      mb |= (unsigned)m8[r] << (3 * r);
+    }
+  }
+  // The state is the preceding launch's output.  It is read through L2:
+  // a chained launch starts while up to two launches before it still run
+  // (each triggers the next at its start), so an SM's L1 may hold lines of
+  // this buffer set that the launch two before cached before it was
+  // rewritten.
+  if (chained) cudaGridDependencySynchronize();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float a = ldf<true>(in.u + idx[r]), b = ldf<true>(in.ubar + idx[r]);
+    const float q1 = sld_m<S, true>(in.p1, idx[r]), q2 = sld_m<S, true>(in.p2, idx[r]);
+    u[r] = ok[r] ? a : 0.f;
+    ub[r] = ok[r] ? b : 0.f;
+    p1[r] = ok[r] ? q1 : 0.f;
+    p2[r] = ok[r] ? q2 : 0.f;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) s_ub[ty * R + r][tx] = ub[r];
+  __syncthreads();
+
+  const int txr = min(tx + 1, FW - 1);
+  const int txl = max(tx - 1, 0);
+
+  // a thread's own products stay in registers; shared memory carries t1 to
+  // the right-hand neighbour and the last row's t2 to the thread below
+  float t1r[R], t2r[R];
+#pragma unroll 1
+  for (int it = 0; it < n_iters; ++it) {
+    float4 sk = make_float4(1.f, 0.f, 0.f, 0.f);
+    if constexpr (ACC) {
+      sk = pp.sched[pp.k0 + it];
+      theta = sk.w;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int fy = ty * R + r;
+      const float right = s_ub[fy][txr];
+      const float below = (r + 1 < R) ? ub[r + 1] : s_ub[min(fy + 1, FH - 1)][tx];
+      PxConst cr = c[r];
+      if constexpr (ACC) {
+        cr.dinv = sk.y;
+        cr.sd = sk.z;
+      }
+      px_dual(mb >> (3 * r), ub[r], right, below, cr, p1[r], p2[r], t1r[r], t2r[r]);
+      s_t1[fy][tx] = t1r[r];
+      if (r == R - 1) s_t2[fy][tx] = t2r[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int fy = ty * R + r;
+      // the row above: this thread's previous row, or the last row of the
+      // thread above (the top row of the footprint is halo: its own value)
+      const float t2_up = r > 0 ? t2r[r - 1] : (ty > 0 ? s_t2[fy - 1][tx] : t2r[0]);
+      const float dv = px_div(t1r[r], s_t1[fy][txl], t2r[r], t2_up);
+      PxConst cr = c[r];
+      if constexpr (ACC) {
+        cr.tau = __fmul_rn(c[r].tau, sk.x);
+        cr.step = __fmul_rn(c[r].step, sk.x);
+      }
+      const float un = px_primal(u[r], dv, cr);
+      ub[r] = px_relax(un, u[r], theta);
+      u[r] = un;
+      s_ub[fy][tx] = ub[r];
+    }
+    __syncthreads();
+  }
+
+  if (!col_in || tx < B || tx >= FW - B) return;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int fy = ty * R + r;
+    const int gy = oy + fy;
+    if (fy < B || fy >= FH - B || gy < 0 || gy >= L.H) continue;
+    const size_t i = (size_t)gy * L.P + gx;
+    out.u[i] = u[r];
+    out.ubar[i] = ub[r];
+    sst<S>(out.p1, i, p1[r]);
+    sst<S>(out.p2, i, p2[r]);
+  }
+}
+
+}  // namespace fs

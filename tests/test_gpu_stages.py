@@ -445,6 +445,27 @@ def test_pd_footprints_are_bit_exact(which, small, ragged):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_pd_footprints_agree_across_chained_launches(storage):
+    # every footprint at the same depth (5) on 14 iterations of a 64 x 64
+    # level: four chained launches of 4, 4, 3 and 3 iterations.  With 16-bit
+    # storage the dual is rounded at every launch boundary, so only equal
+    # boundaries give equal bits; those must agree whatever the footprint.
+    # (Chained launches overlap on an SM when their CTAs are small; state
+    # read through L1 then came from a launch two steps back.)
+    p = f32pair(synth.plain_small(0, W=64, H=64))
+    outs = []
+    for choice in (5, 13, 21, 29, 37, 45):       # depth 5 on footprints 0..5
+        s = make_solver(p, levels=1, storage=storage, pd_schedule=1)
+        s.set_schedule([choice])
+        s.solve(p["I0"], p["I1"], 1, 14)
+        outs.append((np64(s.read(0, "U")), np64(s.read(0, "P"))))
+        s.close()
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
 def test_clip_update(ragged):
     pair = ragged
     s = make_solver(pair)
