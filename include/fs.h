@@ -96,7 +96,16 @@ typedef struct {
  * pd_schedule: 0 = automatic (levels up to 128 x 128 run all iterations of
  * a warp in one launch of a thread-block cluster holding the whole level,
  * when the GPU can host that cluster; larger levels use temporal blocking),
- * 1 = temporal blocking on every level.  Both give identical results.
+ * 1 = temporal blocking on every level, FS_SCHED_PERSISTENT (2) = the
+ * persistent schedule: after the pre-rotation and the pyramid, every level
+ * and warp of a cold solve -- and, in fs_batch_solve, of every pair of the
+ * batch -- runs in one persistent launch over a device work list of
+ * (pair, level, tile, step) items, each tile waiting only on its neighbours
+ * (footprints and depths from fs_autotune's choices).  It needs the Huber-TV
+ * regulariser and accel_gamma = 0; warm starts and continuations of such a
+ * handle use temporal blocking.  A solve in this schedule waits for its
+ * work to finish and returns FS_ETIMEOUT if a wait of the launch ran out
+ * (fs_set_wait_limit).  All three give identical results.
  * storage: 0 = FP32; 1 = FP16, 2 = BF16 storage of the images, the warped
  * gradient and residual (I_u, rho0), the tensor T^1/2 and the dual field p,
  * while the disparity (u, u_omega), the warp vector and every operation stay
@@ -124,6 +133,7 @@ typedef struct {
  * uniformly convex, so the schedule carries no rate guarantee here. */
 #define FS_REG_HUBER_TV 0
 #define FS_REG_TGV 1
+#define FS_SCHED_PERSISTENT 2
 #define FS_DERIV_FORWARD 0
 #define FS_DERIV_CENTRAL 1
 typedef struct {

@@ -139,6 +139,21 @@ fs_status fs_guard_check(fs_handle* h);
  * range. */
 fs_status fs_guard_clobber(fs_handle* h, int band, size_t offset, int* out);
 
+/* The persistent schedule (pd_schedule = FS_SCHED_PERSISTENT): every wait of
+ * a work item on its neighbours or on the coarser level gives up after
+ * `seconds` of GPU global time; the launch then sets its status to
+ * FS_ETIMEOUT, every CTA of it returns at its next claim or wait, and the
+ * solve returns FS_ETIMEOUT (the level state is then unspecified; the next
+ * solve starts afresh).  Default 2 s; seconds must be in (0, 3600].  A
+ * batch uses the smallest limit among its handles. */
+fs_status fs_set_wait_limit(fs_handle* h, double seconds);
+
+/* Testing aid for the bound above: stall = 1 makes the first work items of
+ * the finest level of this handle's persistent solves wait for a counter
+ * that nothing advances, so that wait runs out; stall = 0 restores the
+ * schedule.  A batch stalls when any of its handles does. */
+fs_status fs_persist_stall(fs_handle* h, int stall);
+
 #ifdef __cplusplus
 }
 #endif

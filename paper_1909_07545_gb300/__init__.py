@@ -19,7 +19,7 @@ import os
 import numpy as np
 
 __all__ = ["Solver", "Batch", "Server", "FsError", "load_library", "default_params",
-           "state_bytes", "BUF", "STAGE", "LIB_PATH", "EXPORTED"]
+           "state_bytes", "BUF", "STAGE", "SCHEDULE", "LIB_PATH", "EXPORTED"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfs.so")
 
@@ -32,6 +32,7 @@ BUF_PLANES = {0: 1, 1: 1, 2: 1, 3: 2, 4: 3, 5: 2, 6: 1, 7: 1, 8: 1, 9: 2, 10: 2,
               13: 2, 14: 2, 15: 2, 16: 4}
 REGULARIZER = {"huber_tv": 0, "tgv": 1}
 DERIV = {"forward": 0, "central": 1}
+SCHEDULE = {"auto": 0, "blocking": 1, "persistent": 2}
 STAGE = dict(DOWNSAMPLE=0, TENSOR=1, UPSAMPLE=2, WARP=3, PD=4, CLIP=5, TRAJECTORY=6, WARM=7,
              CLIP_WARP=8)
 
@@ -46,7 +47,7 @@ EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc",
             "fs_batch_create", "fs_batch_solve", "fs_batch_set_finest_limit",
             "fs_batch_destroy", "fs_autotune", "fs_set_schedule", "fs_energy", "fs_state_bytes",
-            "fs_guard_check", "fs_guard_clobber",
+            "fs_guard_check", "fs_guard_clobber", "fs_set_wait_limit", "fs_persist_stall",
             "fs_server_default_config", "fs_server_create", "fs_server_add_rig",
             "fs_server_submit", "fs_server_wait", "fs_server_cancel", "fs_server_drain",
             "fs_server_stats_read",
@@ -144,6 +145,8 @@ def load_library():
         "fs_set_schedule": [_P, _P],
         "fs_guard_check": [_P],
         "fs_guard_clobber": [_P, i, ctypes.c_size_t, ctypes.POINTER(i)],
+        "fs_set_wait_limit": [_P, d],
+        "fs_persist_stall": [_P, i],
         "fs_energy": [_P, i, ctypes.POINTER(d)],
         "fs_state_bytes": [i, i, i, ctypes.POINTER(FsParams), ctypes.POINTER(ctypes.c_size_t)],
         "fs_server_default_config": [ctypes.POINTER(FsServerConfig)],
@@ -187,6 +190,8 @@ def default_params(**overrides) -> FsParams:
             v = REGULARIZER[v]
         if k == "deriv" and isinstance(v, str):
             v = DERIV[v]
+        if k == "pd_schedule" and isinstance(v, str):
+            v = SCHEDULE[v]
         name = "lambda_" if k in ("lam", "lambda") else k
         if name not in _PARAM_FIELDS:
             raise TypeError(f"unknown solver parameter {k!r}")
@@ -369,6 +374,14 @@ class Solver:
         n = ctypes.c_int()
         _check(self.lib.fs_guard_clobber(self.h, int(band), int(offset), ctypes.byref(n)))
         return n.value
+
+    def set_wait_limit(self, seconds):
+        """fs_set_wait_limit: the bound of every wait of the persistent schedule."""
+        _check(self.lib.fs_set_wait_limit(self.h, float(seconds)))
+
+    def persist_stall(self, on=True):
+        """fs_persist_stall: make a wait of the persistent schedule run out (testing aid)."""
+        _check(self.lib.fs_persist_stall(self.h, 1 if on else 0))
 
     def timing_enable(self, on=True):
         _check(self.lib.fs_timing_enable(self.h, 1 if on else 0))

@@ -16,8 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfs.so")
 
-SOURCES = ["fs_api.cu", "k_level.cu", "k_pd.cu", "k_tgv.cu", "k_energy.cu", "fs_noalloc.cu",
-           "fs_server.cu"]
+SOURCES = ["fs_api.cu", "k_level.cu", "k_pd.cu", "k_persist.cu", "k_tgv.cu", "k_energy.cu",
+           "fs_noalloc.cu", "fs_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

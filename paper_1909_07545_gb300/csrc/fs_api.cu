@@ -7,6 +7,7 @@
 #include <cstring>
 #include <algorithm>
 #include <climits>
+#include <cstdint>
 #include <cstdlib>
 #include <new>
 #include <string>
@@ -170,6 +171,10 @@ cudaError_t fs_internal_malloc(void** p, size_t bytes, const char* site) {
   return cudaMalloc(p, bytes);
 }
 
+namespace {
+struct PersistPlan;   // the persistent schedule's work list (below)
+}  // namespace
+
 struct fs_handle {
   fs_calib cam[2];
   fs_pose pose;
@@ -212,6 +217,12 @@ struct fs_handle {
   // iteration of a warp, for the last iteration count it was built for
   float4* sched = nullptr;
   int sched_cap = 0, sched_iters = 0;
+  // the persistent schedule (pd_schedule = FS_SCHED_PERSISTENT): the work
+  // list of this handle's cold solves, the bound of every wait in it, and
+  // the testing aid that makes one wait run out
+  PersistPlan* plan = nullptr;
+  unsigned long long wait_ns = 2000000000ull;
+  int persist_stall = 0;
 };
 
 namespace fs {
@@ -610,6 +621,242 @@ size_t level_bytes(int P, int H, int storage, int regularizer) {
   return plane8 + 7 * plane + 10 * splane + 3 * 2 * plane + tgv;
 }
 
+// ------------------------------------------------------------------ persistent schedule
+
+// The device work list of one persistent launch (k_persist.cu) over one or
+// more handles' cold solves, and what it was built for.
+struct PersistPlan {
+  void* dev = nullptr;                   // jobs | phases | items | ctrl | done | level_done
+  PersistJob* jobs = nullptr;
+  PersistPhase* phases = nullptr;
+  int* items = nullptr;
+  PersistCtrl* ctrl = nullptr;
+  unsigned* done = nullptr;
+  unsigned* level_done = nullptr;
+  size_t zero_bytes = 0;                 // ctrl .. level_done, cleared before every launch
+  int n_items = 0, grid = 0, storage = 0;
+  unsigned long long wait_ns = 0;
+  int* h_status = nullptr;               // pinned copy of ctrl->status after the launch
+  std::vector<long long> key;
+};
+
+static void persist_free(PersistPlan* P) {
+  if (!P) return;
+  if (P->dev) cudaFree(P->dev);
+  if (P->h_status) cudaFreeHost(P->h_status);
+  delete P;
+}
+
+// The footprint and halo depth level l of a persistent solve uses: the
+// tuned choice's footprint width (64 -> 64 x 64, 32 -> 32 x 32, both of 1024
+// threads) and depth, else block_iters, else 64 x 64 at depth 7 on levels of
+// at least 128 x 128 and 32 x 32 at depth 8 below.  The depth is capped at
+// 2 fw / 5, so that a footprint reaches at most two tiles to each side
+// (B <= 2 (fw - 2 B)): a tile's work items then wait on at most 25 tiles.
+static void persist_geometry(const fs_handle* h, int l, int& variant, int& B) {
+  const HostLevel& L = h->lv[l];
+  int fw = (L.W >= 128 && L.H >= 128) ? 64 : 32;
+  B = fw == 64 ? 7 : 8;
+  if (h->prm.block_iters > 0) {
+    B = h->prm.block_iters;
+  } else if (L.tuned >= 1 && L.tuned_variant >= 0) {
+    B = L.tuned;
+    fw = (L.tuned_variant == PD_TILE_32 || L.tuned_variant == PD_TILE_32_T1024 ||
+          L.tuned_variant == PD_TILE_32_T512) ? 32 : 64;
+  }
+  B = std::max(1, std::min(B, 2 * fw / 5));
+  variant = fw == 64 ? PD_TILE_64_T1024 : PD_TILE_32_T1024;
+}
+
+// Blocks per warp: ceil(iters / B), raised to an even count of at least 2,
+// so the state ends in the primary buffer set (a block may run 0 iterations
+// and only copy its interior across).
+static int persist_blocks(int iters, int B) {
+  int n = (iters + B - 1) / B;
+  if (n % 2 == 1) ++n;
+  return std::max(n, 2);
+}
+
+static std::vector<long long> persist_key(const std::vector<fs_handle*>& hs, int warps, int iters) {
+  std::vector<long long> key{warps, iters};
+  for (fs_handle* h : hs) {
+    key.push_back((long long)(uintptr_t)h);
+    key.push_back(h->persist_stall);
+    key.push_back((long long)h->wait_ns);
+    for (int l = 0; l < h->L; ++l) {
+      int v, B;
+      persist_geometry(h, l, v, B);
+      key.push_back(v * 64 + B);
+    }
+  }
+  return key;
+}
+
+// Build (or keep) the work list for the cold solves of hs, every one with
+// the same storage type.  Items are ordered by their depth along each pair's
+// chain of phases (coarsest level first), ties by pair: every item's
+// dependencies then come earlier in the claim order.
+static fs_status persist_plan(PersistPlan*& P, const std::vector<fs_handle*>& hs, int warps,
+                              int iters) {
+  std::vector<long long> key = persist_key(hs, warps, iters);
+  if (P && P->key == key) return FS_OK;
+  persist_free(P);
+  P = nullptr;
+  std::vector<PersistJob> jobs;
+  struct Ph { long long depth; int pair; PersistPhase p; };
+  std::vector<Ph> all;
+  int n_done = 0, n_slots = 0;
+  unsigned long long wait_ns = ~0ull;
+  for (size_t pi = 0; pi < hs.size(); ++pi) {
+    fs_handle* h = hs[pi];
+    wait_ns = std::min(wait_ns, h->wait_ns);
+    long long depth = 0;
+    int coarse_slot = -1, coarse_tiles = 0;
+    for (int l = h->L - 1; l >= 0; --l) {
+      HostLevel& HL = h->lv[l];
+      PersistJob J;
+      memset(&J, 0, sizeof(J));
+      J.L = HL.v;
+      if (l + 1 < h->L) J.C = h->lv[l + 1].v;
+      J.pp = PDParams{h->prm.lambda, h->prm.huber_eps, h->prm.theta};
+      J.top = l == h->L - 1;
+      persist_geometry(h, l, J.variant, J.B);
+      const int fw = J.variant == PD_TILE_64_T1024 ? 64 : 32;
+      J.IW = fw - 2 * J.B;
+      J.IH = fw - 2 * J.B;
+      J.radius = (J.B + J.IW - 1) / J.IW;          // 1 or 2 (persist_geometry's cap)
+      J.tiles_x = (HL.W + J.IW - 1) / J.IW;
+      J.tiles_y = (HL.H + J.IH - 1) / J.IH;
+      const int tiles = J.tiles_x * J.tiles_y;
+      J.done_base = n_done;
+      n_done += tiles;
+      J.level_slot = n_slots++;
+      J.coarse_slot = coarse_slot;
+      J.coarse_tiles = coarse_tiles;
+      J.beta = h->prm.beta;
+      J.eta = h->prm.eta;
+      J.du_max = h->prm.du_max;
+      J.precond = h->prm.precond;
+      J.central = h->prm.deriv == FS_DERIV_CENTRAL;
+      J.stall = h->persist_stall && l == 0;
+      const int job = (int)jobs.size();
+      jobs.push_back(J);
+      const int nb = persist_blocks(iters, J.B);
+      all.push_back({depth++, (int)pi, PersistPhase{0, job, PERSIST_PRE, 0, 0, 0, 0, 0}});
+      for (int w = 0; w < warps; ++w) {
+        for (int k = 0, done_it = 0; k < nb; ++k) {
+          int n = (iters - done_it) / (nb - k);         // spread the iterations evenly
+          if ((iters - done_it) % (nb - k)) ++n;
+          done_it += n;
+          all.push_back({depth++, (int)pi,
+                         PersistPhase{0, job, PERSIST_PD, 1 + w * (nb + 1) + k, k, n, 0, 0}});
+        }
+        all.push_back({depth++, (int)pi,
+                       PersistPhase{0, job, PERSIST_CLIP, 1 + w * (nb + 1) + nb, 0, 0,
+                                    w + 1 < warps, w + 1 == warps}});
+      }
+      coarse_slot = J.level_slot;
+      coarse_tiles = tiles;
+    }
+  }
+  std::stable_sort(all.begin(), all.end(), [](const Ph& a, const Ph& b) {
+    return a.depth != b.depth ? a.depth < b.depth : a.pair < b.pair;
+  });
+  std::vector<PersistPhase> phases;
+  std::vector<int> items;
+  phases.reserve(all.size());
+  for (Ph& x : all) {
+    const PersistJob& J = jobs[x.p.job];
+    x.p.first = (int)items.size();
+    const int tiles = J.tiles_x * J.tiles_y;
+    if ((long long)items.size() + tiles > INT_MAX / 2)
+      return fail(FS_EINVAL, "persistent schedule: too many work items");
+    items.insert(items.end(), tiles, (int)phases.size());
+    phases.push_back(x.p);
+  }
+  PersistPlan* Q = new (std::nothrow) PersistPlan();
+  if (!Q) return fail(FS_ENOMEM, "host allocation failed");
+  const size_t bj = align_up(jobs.size() * sizeof(PersistJob), 256);
+  const size_t bp = align_up(phases.size() * sizeof(PersistPhase), 256);
+  const size_t bi = align_up(items.size() * sizeof(int), 256);
+  const size_t bc = align_up(sizeof(PersistCtrl), 256);
+  const size_t bd = align_up((size_t)n_done * sizeof(unsigned), 256);
+  const size_t bl = align_up((size_t)n_slots * sizeof(unsigned), 256);
+  if (fs_internal_malloc(&Q->dev, bj + bp + bi + bc + bd + bl, "persist") != cudaSuccess) {
+    cudaGetLastError();
+    Q->dev = nullptr;
+    persist_free(Q);
+    return fail(FS_ENOMEM, "persistent schedule: work-list allocation failed");
+  }
+  if (cudaHostAlloc((void**)&Q->h_status, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    Q->h_status = nullptr;
+    persist_free(Q);
+    return fail(FS_ENOMEM, "persistent schedule: status word allocation failed");
+  }
+  *Q->h_status = 0;
+  char* c = (char*)Q->dev;
+  Q->jobs = (PersistJob*)c;
+  Q->phases = (PersistPhase*)(c + bj);
+  Q->items = (int*)(c + bj + bp);
+  Q->ctrl = (PersistCtrl*)(c + bj + bp + bi);
+  Q->done = (unsigned*)(c + bj + bp + bi + bc);
+  Q->level_done = (unsigned*)(c + bj + bp + bi + bc + bd);
+  Q->zero_bytes = bc + bd + bl;
+  Q->n_items = (int)items.size();
+  Q->storage = hs[0]->prm.storage;
+  Q->wait_ns = wait_ns;
+  const int cap = persist_max_ctas(Q->storage);
+  Q->grid = std::max(1, std::min(cap, Q->n_items));
+  cudaError_t e = cudaMemcpy(Q->jobs, jobs.data(), jobs.size() * sizeof(PersistJob),
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(Q->phases, phases.data(), phases.size() * sizeof(PersistPhase),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(Q->items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess || cap < 1) {
+    persist_free(Q);
+    return fail(FS_ECUDA, "persistent schedule: %s",
+                e != cudaSuccess ? cudaGetErrorString(e) : "kernel does not fit the device");
+  }
+  Q->key = key;
+  P = Q;
+  return FS_OK;
+}
+
+// The persistent solve of hs on stream st: per pair the input copy,
+// pre-rotation and pyramid, then one launch for every level and warp of
+// every pair, the status word to the host, and per pair the depth.
+static fs_status enqueue_persist(PersistPlan* P, const std::vector<fs_handle*>& hs,
+                                 const float* const* I0, const float* const* I1,
+                                 float* const* disp, float* const* depth, cudaStream_t st) {
+  fs_status s;
+  for (size_t i = 0; i < hs.size(); ++i) {
+    fs_handle* h = hs[i];
+    FS_LAUNCH("k_copy_in_s", launch_copy_in_image(I0[i], h->lv[0].v, 0, st));
+    FS_LAUNCH("k_prerotate", launch_prerotate(I1[i], h->cfield, h->lv[0].v, st));
+    for (int l = 0; l + 1 < h->L; ++l)
+      if ((s = run_stage(h, l, FS_STAGE_DOWNSAMPLE, 0, st)) != FS_OK) return s;
+  }
+  FS_CUDA(cudaMemsetAsync(P->ctrl, 0, P->zero_bytes, st));
+  FS_LAUNCH("k_persist", launch_persist(P->storage, P->jobs, P->phases, P->items, P->n_items,
+                                        P->ctrl, P->done, P->level_done, P->wait_ns, P->grid,
+                                        st));
+  FS_CUDA(cudaMemcpyAsync(P->h_status, &P->ctrl->status, sizeof(int), cudaMemcpyDeviceToHost,
+                          st));
+  for (size_t i = 0; i < hs.size(); ++i)
+    if ((s = enqueue_depth(hs[i], disp[i], depth[i], st)) != FS_OK) return s;
+  return FS_OK;
+}
+
+// Whether a cold solve of h runs the persistent schedule.
+static bool persist_applies(const fs_handle* h, bool warm) {
+  return h->prm.pd_schedule == FS_SCHED_PERSISTENT && !warm &&
+         h->prm.regularizer == FS_REG_HUBER_TV && !(h->prm.accel_gamma > 0);
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -656,7 +903,8 @@ fs_status fs_internal_validate(const fs_calib cam[2], const fs_pose* pose, int W
     const fs_params& p = *prm;
     if (!(p.lambda > 0) || !(p.huber_eps >= 0) || !(p.du_max > 0) || !(p.beta >= 0) ||
         !(p.eta > 0) || !(p.theta >= 0 && p.theta <= 1) || p.block_iters < 0 ||
-        p.block_iters > 8 || p.pd_schedule < 0 || p.pd_schedule > 1 || p.storage < 0 ||
+        p.block_iters > 8 || p.pd_schedule < 0 || p.pd_schedule > FS_SCHED_PERSISTENT ||
+        p.storage < 0 ||
         p.storage > 2 || p.regularizer < 0 || p.regularizer > 1 || p.deriv < 0 || p.deriv > 1)
       return fail(FS_EINVAL, "parameter out of range");
     if (p.regularizer == FS_REG_TGV &&
@@ -669,6 +917,10 @@ fs_status fs_internal_validate(const fs_calib cam[2], const fs_pose* pose, int W
         (p.precond != 0 || p.regularizer != FS_REG_HUBER_TV || p.storage != 0))
       return fail(FS_EINVAL,
                   "accel_gamma > 0 needs precond = 0, the Huber-TV regulariser and FP32 storage");
+    if (p.pd_schedule == FS_SCHED_PERSISTENT &&
+        (p.regularizer != FS_REG_HUBER_TV || p.accel_gamma > 0))
+      return fail(FS_EINVAL,
+                  "the persistent schedule needs the Huber-TV regulariser and accel_gamma = 0");
   }
   size_t bytes = 0;
   return fs_state_bytes(W, H, levels, prm, &bytes);   // level sizes
@@ -908,6 +1160,50 @@ extern "C" fs_status fs_guard_clobber(fs_handle* h, int band, size_t offset, int
 // fs_solve and fs_solve_continue: direct launches, or a CUDA graph captured
 // once per set of buffers and replayed.  In guard-band mode every solve ends
 // with fs_guard_check (which synchronises the stream).
+// A cold solve in the persistent schedule: the work list for (warps, iters)
+// and the handle's tuned geometry, the launch sequence (in the handle's
+// graph when use_graph is set), then the wait for it and its status.
+static fs_status solve_persist(fs_handle* h, const float* d_I0, const float* d_I1, int warps,
+                               int iters, float* d_disp, float* d_depth) {
+  fs_status s;
+  std::vector<fs_handle*> hs{h};
+  PersistPlan* before = h->plan;
+  if ((s = persist_plan(h->plan, hs, warps, iters)) != FS_OK) return s;
+  h->has_state = false;
+  if (!h->prm.use_graph) {
+    s = enqueue_persist(h->plan, hs, &d_I0, &d_I1, &d_disp, &d_depth, h->stream);
+  } else {
+    const void* key[7] = {d_I0, d_I1, nullptr, d_disp, d_depth, (const void*)2, h->plan};
+    bool hit = h->gexec && before == h->plan && warps == h->gwarps && iters == h->giters &&
+               memcmp(key, h->gkey, sizeof(key)) == 0;
+    if (!hit) {
+      if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+      if (!h->cap_stream) FS_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      FS_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      s = enqueue_persist(h->plan, hs, &d_I0, &d_I1, &d_disp, &d_depth, h->cap_stream);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+      if (s != FS_OK) { if (g) cudaGraphDestroy(g); return s; }
+      if (e != cudaSuccess) return fail(FS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&h->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { h->gexec = nullptr; return fail(FS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+      memcpy(h->gkey, key, sizeof(key));
+      h->gwarps = warps;
+      h->giters = iters;
+    }
+    FS_CUDA(cudaGraphLaunch(h->gexec, h->stream));
+  }
+  if (s != FS_OK) return s;
+  FS_CUDA(cudaStreamSynchronize(h->stream));
+  if (*h->plan->h_status != 0)
+    return fail((fs_status)*h->plan->h_status,
+                "persistent schedule: a wait ran out after %.3f s (neighbour or coarser level "
+                "not finished)", (double)h->plan->wait_ns * 1e-9);
+  h->has_state = true;
+  return FS_OK;
+}
+
 static fs_status solve_launch(fs_handle* h, const float* d_I0, const float* d_I1,
                             const float* d_init, bool cont, int warps, int iters, float* d_disp,
                             float* d_depth) {
@@ -918,6 +1214,8 @@ static fs_status solve_launch(fs_handle* h, const float* d_I0, const float* d_I1
   if (cont && !h->has_state) return fail(FS_EINVAL, "fs_solve_continue: the handle holds no result");
   if (h->timing && (s = prepare_timing(h, warps)) != FS_OK) return s;
   if ((s = ensure_schedule(h, iters)) != FS_OK) return s;
+  if (persist_applies(h, d_init || cont)) return solve_persist(h, d_I0, d_I1, warps, iters,
+                                                               d_disp, d_depth);
   if (!h->prm.use_graph) {
     h->has_state = false;
     s = enqueue_solve(h, d_I0, d_I1, d_init, warps, iters, d_disp, d_depth, h->stream, nullptr,
@@ -1013,6 +1311,7 @@ fs_status fs_destroy(fs_handle* h) {
   if (h->eacc) cudaFree(h->eacc);
   if (h->gband_dev) cudaFree(h->gband_dev);
   if (h->sched) cudaFree(h->sched);
+  persist_free(h->plan);
   if (h->arena) cudaFree(h->arena);
   delete h;
   return FS_OK;
@@ -1032,10 +1331,12 @@ struct fs_batch {
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void*> key;
   int warps = 0, iters = 0;
+  PersistPlan* plan = nullptr;            // the persistent schedule's work list
 };
 
 static void batch_free(fs_batch* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  persist_free(b->plan);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   for (cudaEvent_t e : b->finest) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -1101,6 +1402,44 @@ extern "C" fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0,
     key.push_back(d_init ? d_init[i] : nullptr);
     key.push_back(d_disp[i]);
     key.push_back(d_depth[i]);
+  }
+  // every pair cold, in the persistent schedule, one storage type: one
+  // persistent launch for the whole batch
+  bool persist = true;
+  for (int i = 0; i < n; ++i)
+    persist = persist && persist_applies(b->h[i], d_init && d_init[i]) &&
+              b->h[i]->prm.storage == b->h[0]->prm.storage;
+  if (persist) {
+    PersistPlan* before = b->plan;
+    fs_status s;
+    if ((s = persist_plan(b->plan, b->h, warps, iters)) != FS_OK) return s;
+    key.push_back(b->plan);
+    bool phit = b->gexec && before == b->plan && warps == b->warps && iters == b->iters &&
+                key == b->key;
+    if (!phit) {
+      if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+      FS_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+      s = enqueue_persist(b->plan, b->h, d_I0, d_I1, d_disp, d_depth, b->origin);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(b->origin, &g);
+      if (s != FS_OK) { if (g) cudaGraphDestroy(g); return s; }
+      if (e != cudaSuccess) return fail(FS_ECUDA, "batch capture failed: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&b->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { b->gexec = nullptr; return fail(FS_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e)); }
+      b->key = key;
+      b->warps = warps;
+      b->iters = iters;
+    }
+    for (int i = 0; i < n; ++i) b->h[i]->has_state = false;
+    FS_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+    FS_CUDA(cudaStreamSynchronize(b->stream));
+    if (*b->plan->h_status != 0)
+      return fail((fs_status)*b->plan->h_status,
+                  "persistent schedule: a wait ran out after %.3f s (neighbour or coarser level "
+                  "not finished)", (double)b->plan->wait_ns * 1e-9);
+    for (int i = 0; i < n; ++i) b->h[i]->has_state = true;
+    return FS_OK;
   }
   bool hit = b->gexec && warps == b->warps && iters == b->iters && key == b->key;
   if (!hit) {
@@ -1437,6 +1776,21 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
     HostLevel& L = h->lv[l];
     decode_choice(c, tgv, L.tuned, L.tuned_variant);
   }
+  return FS_OK;
+}
+
+extern "C" fs_status fs_set_wait_limit(fs_handle* h, double seconds) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  if (!(seconds > 0 && seconds <= 3600)) return fail(FS_EINVAL, "wait limit must be in (0, 3600] s");
+  h->wait_ns = (unsigned long long)(seconds * 1e9);
+  return FS_OK;
+}
+
+extern "C" fs_status fs_persist_stall(fs_handle* h, int stall) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  h->persist_stall = stall ? 1 : 0;
   return FS_OK;
 }
 

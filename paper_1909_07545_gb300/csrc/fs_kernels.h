@@ -90,4 +90,70 @@ bool pd_cluster_fits(int variant, int W, int H);
 cudaError_t launch_pd_cluster(int variant, const LevelView& L, const PDParams& pp, int n,
                               cudaStream_t st);
 
+// ---------------------------------------------------------------- persistent schedule
+// A whole solve (or a batch of them) as one launch over a work list
+// (k_persist.cu).  A job is one pyramid level of one pair; its interior tiles
+// are the units of work.  Every tile of a job runs the same chain of items:
+//   PRE            tensor and step sizes, zero state (coarsest level) or
+//                  upsampling from the coarser level, warp + linearisation
+//   PD(w, k)       primal-dual block k of warp w (pd_tile, halo B)
+//   CLIP(w)        clip + update, and the next warp's linearisation
+// Item s of a tile's chain starts once every tile its footprint reaches --
+// the tile and its neighbours within `radius` tiles (the eight around it
+// when the halo B is at most the interior width) -- has finished item s - 1
+// (their counters in `done`), and a PRE once the coarser level of the same
+// pair has finished (its counter in level_done).
+// Items are claimed in an order in which every item's dependencies come
+// earlier, so a claimed item only ever waits on items that running CTAs
+// hold.
+enum PersistKind { PERSIST_PRE = 0, PERSIST_PD = 1, PERSIST_CLIP = 2 };
+
+struct PersistJob {
+  LevelView L;               // the level
+  LevelView C;               // the coarser level (upsampling source); unused at the top
+  PDParams pp;
+  int top;                   // the pair's coarsest level: zero state instead of upsampling
+  int variant;               // PD_TILE_64_T1024 or PD_TILE_32_T1024
+  int B;                     // halo depth of the primal-dual blocks
+  int IW, IH;                // interior tile size
+  int radius;                // tiles a footprint reaches on each side: ceil(B / IW), 1 or 2
+  int tiles_x, tiles_y;
+  int done_base;             // this job's first counter in `done`
+  int level_slot;            // this job's counter in level_done
+  int coarse_slot;           // the coarser level's counter (-1 at the top)
+  int coarse_tiles;          // tiles of the coarser level (its finished count)
+  float beta, eta, du_max;
+  int precond, central;
+  int stall;                 // testing aid: the PRE items wait on a counter nothing sets
+};
+
+struct PersistPhase {        // one item kind for every tile of one job
+  int first;                 // index of its first item
+  int job;
+  int kind;                  // PersistKind
+  int seq;                   // position in the tile chain (0 = PRE)
+  int block;                 // PD: block index within the warp (ping-pong parity)
+  int n_iter;                // PD: iterations of the block
+  int next_warp;             // CLIP: 1 if another warp follows (fused linearisation)
+  int last;                  // CLIP of the last warp: the level is done after it
+};
+
+// Device control block of one launch: the claim counter, the abort flag and
+// the status (0, or FS_ETIMEOUT when a wait gave up).
+struct PersistCtrl {
+  unsigned next;
+  unsigned abort;
+  int status;
+  unsigned pad;
+};
+
+// The persistent launch: `grid` CTAs of 1024 threads over n_items items.
+// wait_ns bounds every wait (global-timer nanoseconds).
+cudaError_t launch_persist(int storage, const PersistJob* jobs, const PersistPhase* phases,
+                           const int* item_phase, int n_items, PersistCtrl* ctrl, unsigned* done,
+                           unsigned* level_done, unsigned long long wait_ns, int grid,
+                           cudaStream_t st);
+// CTAs of the persistent kernel that fit on the device at once.
+int persist_max_ctas(int storage);
+
 }  // namespace fs
