@@ -7,7 +7,7 @@
 // work with the same per-pixel functions the launch-per-stage kernels use
 // (level_px.cuh, pd_tile.cuh), and publishes its completion:
 //
-//   producer: stores -> every thread: fence -> CTA barrier -> st.release done[t]
+//   producer: stores -> CTA barrier -> thread 0: fence, st.release done[t]
 //   consumer: warp 0: ld.acquire done[n] >= s -> CTA barrier -> loads
 //
 // Planes written during the launch are read through L2 only (the CG loads
@@ -190,19 +190,22 @@ k_persist(const PersistJob* __restrict__ jobs, const PersistPhase* __restrict__ 
           unsigned* done, unsigned* level_done, unsigned long long wait_ns) {
   extern __shared__ float smem[];               // three planes of the largest footprint
   __shared__ int s_item, s_ok;
-  // The next item is claimed while the current one is worked on (the
-  // claim's latency hides behind the work).  A CTA then holds two items, the
-  // second not started; the smallest unfinished item is always being worked
-  // on, so the launch still makes progress.
+  __shared__ PersistPhase s_ph;
+  // The next item is claimed while the current one is worked on, and thread
+  // 0 decodes it while the CTA drains (the claim's and the decode's
+  // latencies hide behind the work).  A CTA then holds two items, the second
+  // not started; the smallest unfinished item is always being worked on, so
+  // the launch still makes progress.
   if (threadIdx.x == 0) {
     const int i = (int)atomicAdd(&ctrl->next, 1u);
     s_item = i < n_items ? i : -1;
+    if (i < n_items) s_ph = phases[item_phase[i]];
   }
   __syncthreads();
   for (;;) {
     const int i = s_item;
     if (i < 0) return;
-    const PersistPhase ph = phases[item_phase[i]];
+    const PersistPhase ph = s_ph;
     const PersistJob& J = jobs[ph.job];
     const int t = i - ph.first;
     const int bx = t % J.tiles_x, by = t / J.tiles_x;
@@ -217,17 +220,18 @@ k_persist(const PersistJob* __restrict__ jobs, const PersistPhase* __restrict__ 
     if (ph.kind == PERSIST_PRE) pre_item<S>(J, bx, by);
     else if (ph.kind == PERSIST_PD) pd_item<S>(J, ph, bx, by, smem);
     else clip_item<S>(J, ph, bx, by);
-    // Publish: every thread fences its own stores (a fence orders only the
-    // calling thread's writes), the barrier joins them, then one release.
-    __threadfence();
+    // Publish: the barrier joins every thread's stores, thread 0's fence
+    // orders them (cumulatively, through the barrier) before the release.
     __syncthreads();
     if (threadIdx.x == 0) {
+      const bool more = nxt < n_items;
+      PersistPhase nph{};
+      if (more) nph = phases[item_phase[nxt]];
+      __threadfence();
       st_release(done + J.done_base + t, (unsigned)ph.seq + 1u);
-      if (ph.last) {
-        __threadfence();
-        atomicAdd(level_done + J.level_slot, 1u);
-      }
-      s_item = (nxt < n_items && !ld_acquire(&ctrl->abort)) ? nxt : -1;
+      if (ph.last) atomicAdd(level_done + J.level_slot, 1u);
+      s_item = (more && !ld_acquire(&ctrl->abort)) ? nxt : -1;
+      s_ph = nph;
     }
     __syncthreads();
   }
