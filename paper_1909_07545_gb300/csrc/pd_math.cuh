@@ -77,11 +77,15 @@ __device__ __forceinline__ void px_zero(PxConst& c) {
 
 // Dual ascent at one pixel: ub, right = ubar(x + e1), below = ubar(x + e2).
 // Updates p1, p2 and returns the masked products t1, t2 of T^1/2 p.
+// MASKED = false is for pixels whose mask bits are all set (in the FOV, both
+// forward neighbours too): the masks then select every value as it is, so
+// skipping them gives the same bits.
+template <bool MASKED = true>
 __device__ __forceinline__ void px_dual(unsigned m, float ub, float right, float below,
                                         const PxConst& c, float& p1, float& p2, float& t1,
                                         float& t2) {
-  const float g1 = (m & MASK_GX) ? __fsub_rn(right, ub) : 0.f;
-  const float g2 = (m & MASK_GY) ? __fsub_rn(below, ub) : 0.f;
+  const float g1 = (!MASKED || (m & MASK_GX)) ? __fsub_rn(right, ub) : 0.f;
+  const float g2 = (!MASKED || (m & MASK_GY)) ? __fsub_rn(below, ub) : 0.f;
   const float d = fmaf(c.sx, g1, __fmul_rn(c.sy, g2));
   const float k1 = fmaf(-c.sx, d, g1);
   const float k2 = fmaf(-c.sy, d, g2);
@@ -94,8 +98,8 @@ __device__ __forceinline__ void px_dual(unsigned m, float ub, float right, float
   p1 = q1;
   p2 = q2;
   const float dp = fmaf(c.sx, q1, __fmul_rn(c.sy, q2));
-  t1 = (m & MASK_GX) ? fmaf(-c.sx, dp, q1) : 0.f;
-  t2 = (m & MASK_GY) ? fmaf(-c.sy, dp, q2) : 0.f;
+  t1 = (!MASKED || (m & MASK_GX)) ? fmaf(-c.sx, dp, q1) : 0.f;
+  t2 = (!MASKED || (m & MASK_GY)) ? fmaf(-c.sy, dp, q2) : 0.f;
 }
 
 // div(T^1/2 p) at a pixel from its own and its left / upper neighbours'

@@ -19,6 +19,65 @@
 
 namespace fs {
 
+// The n_iters iterations of pd_tile on a thread's R rows (state in
+// registers, neighbours through shared memory); MASKED as in px_dual.
+template <int FW, int NY, int R, bool ACC, bool MASKED>
+__device__ __forceinline__ void pd_iterate(const PDParams& pp, int n_iters, int tx, int ty,
+                                           unsigned mb, const PxConst (&c)[R], float (&u)[R],
+                                           float (&ub)[R], float (&p1)[R], float (&p2)[R],
+                                           float theta, float (*s_ub)[FW], float (*s_t1)[FW],
+                                           float (*s_t2)[FW]) {
+  constexpr int FH = NY * R;
+  const int txr = min(tx + 1, FW - 1);
+  const int txl = max(tx - 1, 0);
+
+  // a thread's own products stay in registers; shared memory carries t1 to
+  // the right-hand neighbour and the last row's t2 to the thread below
+  float t1r[R], t2r[R];
+#pragma unroll 1
+  for (int it = 0; it < n_iters; ++it) {
+    float4 sk = make_float4(1.f, 0.f, 0.f, 0.f);
+    if constexpr (ACC) {
+      sk = pp.sched[pp.k0 + it];
+      theta = sk.w;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int fy = ty * R + r;
+      const float right = s_ub[fy][txr];
+      const float below = (r + 1 < R) ? ub[r + 1] : s_ub[min(fy + 1, FH - 1)][tx];
+      PxConst cr = c[r];
+      if constexpr (ACC) {
+        cr.dinv = sk.y;
+        cr.sd = sk.z;
+      }
+      px_dual<MASKED>(mb >> (3 * r), ub[r], right, below, cr, p1[r], p2[r], t1r[r], t2r[r]);
+      s_t1[fy][tx] = t1r[r];
+      if (r == R - 1) s_t2[fy][tx] = t2r[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int fy = ty * R + r;
+      // the row above: this thread's previous row, or the last row of the
+      // thread above (the top row of the footprint is halo: its own value)
+      const float t2_up = r > 0 ? t2r[r - 1] : (ty > 0 ? s_t2[fy - 1][tx] : t2r[0]);
+      const float dv = px_div(t1r[r], s_t1[fy][txl], t2r[r], t2_up);
+      PxConst cr = c[r];
+      if constexpr (ACC) {
+        cr.tau = __fmul_rn(c[r].tau, sk.x);
+        cr.step = __fmul_rn(c[r].step, sk.x);
+      }
+      const float un = px_primal(u[r], dv, cr);
+      ub[r] = px_relax(un, u[r], theta);
+      u[r] = un;
+      s_ub[fy][tx] = ub[r];
+    }
+    __syncthreads();
+  }
+
+}
+
 // ACC: the accelerated step schedule of pp.sched (FP32 storage, scalar
 // steps): iteration it of the block uses entry pp.k0 + it for sigma (all
 // pixels), tau and the L1 step (scaled from the stored tau_0 values, 0 off
@@ -96,53 +155,18 @@ __device__ __forceinline__ void pd_tile(const LevelView& L, const PDState& in,
   for (int r = 0; r < R; ++r) s_ub[ty * R + r][tx] = ub[r];
   __syncthreads();
 
-  const int txr = min(tx + 1, FW - 1);
-  const int txl = max(tx - 1, 0);
-
-  // a thread's own products stay in registers; shared memory carries t1 to
-  // the right-hand neighbour and the last row's t2 to the thread below
-  float t1r[R], t2r[R];
-#pragma unroll 1
-  for (int it = 0; it < n_iters; ++it) {
-    float4 sk = make_float4(1.f, 0.f, 0.f, 0.f);
-    if constexpr (ACC) {
-      sk = pp.sched[pp.k0 + it];
-      theta = sk.w;
-    }
+  // Every footprint pixel inside the level with all three mask bits set
+  // (the FOV covers it, with both forward neighbours): the loop without the
+  // mask selects computes the same bits with fewer instructions.
+  bool full = mb == (R == 1 ? 7u : R == 2 ? 077u : R == 4 ? 07777u : 077777777u);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int fy = ty * R + r;
-      const float right = s_ub[fy][txr];
-      const float below = (r + 1 < R) ? ub[r + 1] : s_ub[min(fy + 1, FH - 1)][tx];
-      PxConst cr = c[r];
-      if constexpr (ACC) {
-        cr.dinv = sk.y;
-        cr.sd = sk.z;
-      }
-      px_dual(mb >> (3 * r), ub[r], right, below, cr, p1[r], p2[r], t1r[r], t2r[r]);
-      s_t1[fy][tx] = t1r[r];
-      if (r == R - 1) s_t2[fy][tx] = t2r[r];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int fy = ty * R + r;
-      // the row above: this thread's previous row, or the last row of the
-      // thread above (the top row of the footprint is halo: its own value)
-      const float t2_up = r > 0 ? t2r[r - 1] : (ty > 0 ? s_t2[fy - 1][tx] : t2r[0]);
-      const float dv = px_div(t1r[r], s_t1[fy][txl], t2r[r], t2_up);
-      PxConst cr = c[r];
-      if constexpr (ACC) {
-        cr.tau = __fmul_rn(c[r].tau, sk.x);
-        cr.step = __fmul_rn(c[r].step, sk.x);
-      }
-      const float un = px_primal(u[r], dv, cr);
-      ub[r] = px_relax(un, u[r], theta);
-      u[r] = un;
-      s_ub[fy][tx] = ub[r];
-    }
-    __syncthreads();
-  }
+  for (int r = 0; r < R; ++r) full = full && ok[r];
+  if (__syncthreads_and(full))
+    pd_iterate<FW, NY, R, ACC, false>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta, s_ub,
+                                      s_t1, s_t2);
+  else
+    pd_iterate<FW, NY, R, ACC, true>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta, s_ub,
+                                     s_t1, s_t2);
 
   if (!col_in || tx < B || tx >= FW - B) return;
 #pragma unroll
