@@ -33,7 +33,7 @@ PD_BYTES_PER_PX_ITER = 52.0   # unblocked FP32 traffic of one pixel-iteration (9
 # per schedule choice, each from one capture of the current kernel (cold L2;
 # commands and figures in profiles/k_pd_level0_kb1024.md).  A choice without
 # a capture reports traffic null.
-PD_L0_DRAM_BYTES_PER_LAUNCH = {31: 47.7e6}
+PD_L0_DRAM_BYTES_PER_LAUNCH = {31: 47.3e6}
 # FP32 instructions of one pixel-iteration of the primal-dual step as written
 # in pd_math.cuh, an FMA counted as one: dual 24 (2 differences, 7 products,
 # 9 FMAs, the reciprocal square root, a min and 4 mask selects), divergence 3,

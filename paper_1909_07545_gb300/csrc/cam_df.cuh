@@ -103,16 +103,13 @@ __device__ __forceinline__ df cam_theta_df(const DevCamDF& c, df rn) {
     const df den = dd_add(dd_mul(a, dd_sqrt(rad)), dd_sub(one, a));
     return clamp_fov_df(c, dd_atan2(rn, dd_div(num, den)));
   }
-  // Kannala-Brandt: the bracketed FP32 solve, then two Newton steps on
-  // r(theta) - rn with the residual in float-float
+  // Kannala-Brandt: the bracketed FP32 solve (relative error ~1e-7), then one
+  // Newton step on r(theta) - rn with the residual in float-float, which
+  // squares that error
   df th = df_f(cam_theta(c.f32, rn.hi));
-#pragma unroll 1
-  for (int k = 0; k < 2; ++k) {
-    df r, dr;
-    cam_r_df(c, th, th, th, r, dr);                 // sin / cos unused by this model
-    const df f = dd_sub(r, rn);
-    th = dd_sub(th, dd_div(f, dr));
-  }
+  df r, dr;
+  cam_r_df(c, th, th, th, r, dr);                   // sin / cos unused by this model
+  th = dd_sub(th, dd_div(dd_sub(r, rn), dr));
   return clamp_fov_df(c, th);
 }
 

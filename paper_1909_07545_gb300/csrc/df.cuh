@@ -126,13 +126,16 @@ constexpr DfSeries taylor_series(int first) {
 static __constant__ const DfSeries kCosSeries = taylor_series(0);
 static __constant__ const DfSeries kSinSeries = taylor_series(1);
 
-// sin and cos of x, |x| <= pi.
+// sin and cos of x, |x| <= pi.  Terms k < n: for |x| <= 1.8 (every angle of
+// a lens up to 206 degrees) the first omitted term is below 2e-18 at n = 12,
+// so 12 are taken there and all 17 beyond.
 __device__ __forceinline__ void dd_sincos(df x, df& s, df& c) {
   const df y = dd_mul(x, x);
-  df ps = df{kSinSeries.hi[kTaylorTerms - 1], kSinSeries.lo[kTaylorTerms - 1]};
-  df pc = df{kCosSeries.hi[kTaylorTerms - 1], kCosSeries.lo[kTaylorTerms - 1]};
+  const int n = fabsf(x.hi) <= 1.8f ? 12 : kTaylorTerms;
+  df ps = df{kSinSeries.hi[n - 1], kSinSeries.lo[n - 1]};
+  df pc = df{kCosSeries.hi[n - 1], kCosSeries.lo[n - 1]};
 #pragma unroll 1
-  for (int k = kTaylorTerms - 2; k >= 0; --k) {
+  for (int k = n - 2; k >= 0; --k) {
     ps = dd_add(dd_mul(ps, y), df{kSinSeries.hi[k], kSinSeries.lo[k]});
     pc = dd_add(dd_mul(pc, y), df{kCosSeries.hi[k], kCosSeries.lo[k]});
   }

@@ -291,13 +291,19 @@ fs_status build_fields(fs_handle* h) {
   if (!(n > 0) || !std::isfinite(n))
     return fail(FS_EINVAL, "pose: translation must be non-zero and finite");
   HostLevel& L0 = h->lv[0];
-  RotDF Rd;
-  for (int i = 0; i < 9; ++i) Rd.r[i] = df_from_double(R[i]);
-  k_calib_field<<<grid2(L0.W, L0.H), kBlock2, 0, h->stream>>>(
-      dev_cam_df(h->cam[0], L0.fx, L0.fy, L0.cx, L0.cy),
-      dev_cam_df(h->cam[1], h->cam[1].fx, h->cam[1].fy, h->cam[1].cx, h->cam[1].cy), Rd,
-      L0.v.mask, h->cfield, L0.W, L0.H, L0.P);
-  FS_LAUNCHED("k_calib_field");
+  bool identity = memcmp(&h->cam[0], &h->cam[1], sizeof(fs_calib)) == 0;
+  for (int i = 0; i < 9 && identity; ++i) identity = R[i] == ((i % 4 == 0) ? 1.0 : 0.0);
+  if (identity) {       // the same lens, no rotation: c(x) = pi_0(pi_0^-1(x)) - x = 0
+    FS_CUDA(cudaMemsetAsync(h->cfield, 0, (size_t)L0.P * L0.H * sizeof(float4), h->stream));
+  } else {
+    RotDF Rd;
+    for (int i = 0; i < 9; ++i) Rd.r[i] = df_from_double(R[i]);
+    k_calib_field<<<grid2(L0.W, L0.H), kBlock2, 0, h->stream>>>(
+        dev_cam_df(h->cam[0], L0.fx, L0.fy, L0.cx, L0.cy),
+        dev_cam_df(h->cam[1], h->cam[1].fx, h->cam[1].fy, h->cam[1].cx, h->cam[1].cy), Rd,
+        L0.v.mask, h->cfield, L0.W, L0.H, L0.P);
+    FS_LAUNCHED("k_calib_field");
+  }
   for (int l = 0; l < h->L; ++l) {
     fs_status s = launch_trajectory(h, l, h->stream);
     if (s != FS_OK) return s;

@@ -52,11 +52,11 @@ __global__ void k_trajectory(DevCamDF cam, df tx, df ty, df tz, LevelView L) {
 }
 
 // ------------------------------------------------------------ calibration field
-// c(x) = pi_1(R X) - pi_0(X), X = pi_0^-1(x), at the level-0 FOV pixels
-// (Sec. IV-A, the pre-rotation: t = 0), 0 elsewhere; in float-float, stored
-// as the float pair (hi x, hi y, lo x, lo y).  pi_0(X) is x up to the
-// round-off of the inverse; taking it, rather than x, makes the field
-// exactly 0 for two identical cameras.
+// c(x) = pi_1(R X) - x, X = pi_0^-1(x), at the level-0 FOV pixels (Sec. IV-A,
+// the pre-rotation: t = 0), 0 elsewhere; in float-float, stored as the float
+// pair (hi x, hi y, lo x, lo y).  x stands for pi_0(X), which it equals to
+// about 1e-13 px.  (Two identical cameras with R = I have the field exactly
+// 0; the host writes that one without this kernel.)
 __global__ void k_calib_field(DevCamDF c0, DevCamDF c1, RotDF R, const uint8_t* __restrict__ mask,
                               float4* __restrict__ field, int W, int H, int P) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,10 +72,9 @@ __global__ void k_calib_field(DevCamDF c0, DevCamDF c1, RotDF R, const uint8_t* 
     for (int k = 0; k < 3; ++k)
       Y[k] = dd_add(dd_add(dd_mul(R.r[3 * k], X[0]), dd_mul(R.r[3 * k + 1], X[1])),
                     dd_mul(R.r[3 * k + 2], X[2]));
-    df px, py, qx, qy;
+    df px, py;
     cam_project_df(c1, Y[0], Y[1], Y[2], px, py);
-    cam_project_df(c0, X[0], X[1], X[2], qx, qy);
-    const df dx = dd_sub(px, qx), dy = dd_sub(py, qy);
+    const df dx = dd_sub(px, df_f((float)x)), dy = dd_sub(py, df_f((float)y));
     out = make_float4(dx.hi, dy.hi, dx.lo, dy.lo);
   }
   field[i] = out;

@@ -3,13 +3,16 @@ primal-dual iterations of one level, on a seeded synthetic workload.
 
     python -m paper_1909_07545_gb300.profile_frame --mode frame --frames 2
     python -m paper_1909_07545_gb300.profile_frame --mode pd --level 0 --iters 100
+    python -m paper_1909_07545_gb300.profile_frame --mode frame --pd-schedule persistent
+    python -m paper_1909_07545_gb300.profile_frame --mode pose
 
 Run from the repository root (it uses the ``synth`` scene generator).  No
 CUDA graph is used, so every kernel is a separate launch a profiler can
 select.  In frame mode one untimed frame runs first (after the autotuner,
 with --autotune) and the profiled frames are bracketed by
 cudaProfilerStart / Stop, so ``ncu --profile-from-start off`` captures
-exactly those frames.
+exactly those frames.  Pose mode brackets one fs_set_pose (the calibration
+and trajectory fields) the same way.
 """
 from __future__ import annotations
 
@@ -24,7 +27,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="plain_kb_1024",
                     choices=["plain_kb_1024", "plain_small_256"])
-    ap.add_argument("--mode", default="frame", choices=["frame", "pd"])
+    ap.add_argument("--mode", default="frame", choices=["frame", "pd", "pose"])
+    ap.add_argument("--pd-schedule", default="auto", choices=["auto", "blocking", "persistent"])
     ap.add_argument("--frames", type=int, default=1)
     ap.add_argument("--level", type=int, default=0)
     ap.add_argument("--iters", type=int, default=100)
@@ -49,7 +53,7 @@ def main():
     H, W = pair["I0"].shape
     s = Solver(pair["cam0"], pair["cam1"], pair["R"], pair["t"], W, H, pair["levels"],
                lam=pair["lam"], huber_eps=pair["eps"], block_iters=args.block_iters,
-               regularizer=args.regularizer)
+               regularizer=args.regularizer, pd_schedule=args.pd_schedule)
     if args.autotune:
         print("autotuned schedule per level (0 = cluster, else blocking depth):",
               s.autotune(pair["iters"]))
@@ -68,6 +72,14 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         print(f"frame: {L} levels x {warps} warps x {iters} iterations, {args.frames} frame(s)")
+    elif args.mode == "pose":
+        s.set_pose(pair["R"], pair["t"])        # warm-up, outside the profiled range
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        s.set_pose(pair["R"], pair["t"])
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(f"pose: {W}x{H}, {pair['levels']} levels")
     else:
         # state of a realistic warp at the chosen level, then the PD stage alone
         s.solve(I0, I1, 1, 10)
