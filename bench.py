@@ -628,7 +628,7 @@ def main():
     ap.add_argument("--serve-f16-seconds", type=float, default=10.0,
                     help="length of the FP16-storage serving run (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=600.0, help="offered requests/s")
-    ap.add_argument("--serve-inflight", type=int, default=8)
+    ap.add_argument("--serve-inflight", type=int, default=2)
     ap.add_argument("--serve-warm-mode", type=int, default=1, choices=[0, 1])
     ap.add_argument("--no-uneven-batch", dest="uneven_batch", action="store_false",
                     help="skip the 64 uneven pairs (512/800/1024/1280 px) in one batch graph")

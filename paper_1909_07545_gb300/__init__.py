@@ -488,7 +488,7 @@ class Server:
     for.
     """
 
-    def __init__(self, budget_bytes=0, max_inflight=8, warps=3, iters=50, cold_warps=10,
+    def __init__(self, budget_bytes=0, max_inflight=2, warps=3, iters=50, cold_warps=10,
                  cold_iters=100, warm_mode=1, autotune=1):
         import torch
         if not torch.cuda.is_available():

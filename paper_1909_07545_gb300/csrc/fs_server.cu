@@ -332,7 +332,7 @@ fs_status fs_server_default_config(fs_server_config* out) {
   if (!out) return set_error(FS_EINVAL, "null config");
   memset(out, 0, sizeof(*out));
   out->hbm_budget = (size_t)40 << 30;
-  out->max_inflight = 8;
+  out->max_inflight = 2;
   out->warps = 3;
   out->iters = 50;
   out->cold_warps = 10;

@@ -138,7 +138,7 @@ def test_state_bytes_counts_the_level_planes(lib):
 def test_server_config_validation(lib):
     cfg = fsb.FsServerConfig()
     assert lib.fs_server_default_config(ctypes.byref(cfg)) == 0
-    assert cfg.hbm_budget == 40 << 30 and cfg.max_inflight == 8
+    assert cfg.hbm_budget == 40 << 30 and cfg.max_inflight == 2
     assert (cfg.warps, cfg.iters, cfg.cold_warps, cfg.cold_iters) == (3, 50, 10, 100)
     assert cfg.warm_mode == 1 and cfg.autotune == 1
     s = ctypes.c_void_p()
