@@ -43,28 +43,41 @@ PD_FP32_INSTR_PER_PX_ITER = 34
 FP32_LANES = 152 * 128
 FOOTPRINTS = ["64x64 footprints, 512 threads", "32x32 footprints, 256 threads",
               "64x32 footprints", "64x64 footprints, 1024 threads",
-              "32x32 footprints, 1024 threads", "32x32 footprints, 512 threads"]
-FOOTPRINT_SIZE = [(64, 64), (32, 32), (64, 32), (64, 64), (32, 32), (32, 32)]
+              "32x32 footprints, 1024 threads", "32x32 footprints, 512 threads",
+              "64x64 footprints 48 columns apart, 1024 threads, TMA-staged"]
+FOOTPRINT_SIZE = [(64, 64), (32, 32), (64, 32), (64, 64), (32, 32), (32, 32), (64, 64)]
+TMA_FOOTPRINT = 6          # index of the TMA-staged footprint (choices 56..63)
+FIRST_TMA_CHOICE = 56
+
+
+def interior(v, B):
+    """Interior (columns, rows) of footprint v at blocking depth B: the TMA
+    footprints own 48 columns (8-column margins for the copies' 16-byte
+    alignment), the others FW - 2B."""
+    FW, FH = FOOTPRINT_SIZE[v]
+    return (48 if v == TMA_FOOTPRINT else FW - 2 * B), FH - 2 * B
 
 
 def decode_choice(c):
-    """(depth, footprint index) of a schedule choice 1..55 (0: cluster -> None)."""
+    """(depth, footprint index) of a schedule choice 1..63 (0: cluster -> None)."""
     if c is None or c <= 0:
         return None
-    if c > 8 * len(FOOTPRINTS):
-        return c - 8 * len(FOOTPRINTS) + 8, 4
+    if c >= FIRST_TMA_CHOICE:
+        return c - FIRST_TMA_CHOICE + 1, TMA_FOOTPRINT
+    if c > 48:
+        return c - 48 + 8, 4
     return (c - 1) % 8 + 1, (c - 1) // 8
 
 
 def schedule_label(c):
     """fs_autotune's per-level choice in words (0 = cluster; 1..48 = depth
     1..8 on each of the six footprints; 49..55 = depth 9..15 on 32x32
-    footprints of 1024 threads)."""
+    footprints of 1024 threads; 56..63 = depth 1..8 on the TMA-staged
+    footprints)."""
     if c == 0:
         return "cluster"
-    if c > 8 * len(FOOTPRINTS):           # depths 9..15 on the 1024-thread 32x32 footprint
-        return f"blocking x{c - 8 * len(FOOTPRINTS) + 8} ({FOOTPRINTS[4]})"
-    return f"blocking x{(c - 1) % 8 + 1} ({FOOTPRINTS[(c - 1) // 8]})"
+    B, v = decode_choice(c)
+    return f"blocking x{B} ({FOOTPRINTS[v]})"
 
 
 def workload_pair(name, seed):
@@ -851,13 +864,14 @@ def main():
     # Algorithmic bytes of one level-0 launch (the blocked figure of the
     # roofline model): one pass over every footprint, 52 B per pixel
     # (9 words read, 4 written), the footprints overlapping by
-    # (FW / IW) x (FH / IH) with IW = FW - 2 B interior columns.
+    # (FW / IW) x (FH / IH) with IW x IH interior pixels (interior()).
     if dec is not None:
         B, v = dec
         FW, FH = FOOTPRINT_SIZE[v]
-        overlap = FW / (FW - 2 * B) * FH / (FH - 2 * B)
+        IW, IH = interior(v, B)
+        overlap = FW / IW * FH / IH
     else:
-        B, FW, FH, overlap = None, None, None, 1.0
+        B, FW, FH, IW, IH, overlap = None, None, None, None, None, 1.0
     px_l0 = W * H
     bytes_launch = PD_BYTES_PER_PX_ITER * px_l0 * overlap
     achieved = bytes_launch / launch_s / 1e9
@@ -895,13 +909,15 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "traffic_note": "ncu DRAM read + write bytes of one level-0 launch of "
                                      "this schedule, cold L2 (null: no capture of it)",
-                     "kernel": "k_pd level 0 (1024x1024), " + (
+                     "kernel": ("k_pd_tma" if dec is not None and dec[1] == TMA_FOOTPRINT
+                                else "k_pd") + " level 0 (1024x1024), " + (
                          schedule_label(l0_choice) if l0_choice is not None else "default"),
                      "launches_per_frame": n0 // max(args.steps, 1),
                      "launch_us": launch_s * 1e6,
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "algorithmic_bytes_note": "52 B per level-0 pixel x footprint overlap "
-                                               f"({FW}x{FH} footprints, halo {B}: x{overlap:.3f})",
+                                               f"({FW}x{FH} footprints, depth {B}, "
+                                               f"interior {IW}x{IH}: x{overlap:.3f})",
                      "peak_source": f"{src} hbm_gbs",
                      "compulsory_frac": compulsory / peak,
                      "compulsory_note": "one pass, 52 B per level-0 pixel per launch, no halo",

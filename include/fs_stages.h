@@ -103,7 +103,12 @@ fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
  * v = 3: 64 x 64, 1024 threads of 4 rows (25..32);
  * v = 4: 32 x 32, 1024 threads of 1 row (33..40);
  * v = 5: 32 x 32, 512 threads of 2 rows (41..48);
- * and 49..55 = depth 9..15 on 32 x 32 footprints of 1024 threads.  On TGV handles the
+ * 49..55 = depth 9..15 on 32 x 32 footprints of 1024 threads; and 56..63 =
+ * depth 1..8 on 64 x 64 footprints of 1024 threads laid out 48 columns
+ * apart, whose inputs the tensor memory accelerator copies into shared
+ * memory while the CTA iterates on the previous footprint (one resident
+ * CTA per SM walks the footprints; offered where the driver encodes the
+ * level's tensor maps).  On TGV handles the
  * candidates are 0 = a dual and a primal launch per iteration and 8 v + d =
  * temporal-blocking depth d on a 32 x 32 footprint of 256 (v = 0, choices
  * 1..8), 1024 (v = 1, 9..16) or 512 threads (v = 2, 17..24), or a 64 x 32
@@ -139,20 +144,40 @@ fs_status fs_guard_check(fs_handle* h);
  * range. */
 fs_status fs_guard_clobber(fs_handle* h, int band, size_t offset, int* out);
 
-/* The persistent schedule (pd_schedule = FS_SCHED_PERSISTENT): every wait of
- * a work item on its neighbours or on the coarser level gives up after
- * `seconds` of GPU global time; the launch then sets its status to
- * FS_ETIMEOUT, every CTA of it returns at its next claim or wait, and the
- * solve returns FS_ETIMEOUT (the level state is then unspecified; the next
- * solve starts afresh).  Default 2 s; seconds must be in (0, 3600].  A
- * batch uses the smallest limit among its handles. */
+/* The persistent schedule (pd_schedule = FS_SCHED_PERSISTENT) and the
+ * TMA-staged footprints (below): every wait of a work item on its
+ * neighbours or on the coarser level, or of a CTA on its copies, gives up
+ * after `seconds` of GPU global time.  In the persistent schedule the
+ * launch then sets its status to FS_ETIMEOUT, every CTA of it returns at
+ * its next claim or wait, and the solve returns FS_ETIMEOUT (the level
+ * state is then unspecified; the next solve starts afresh); for the TMA
+ * footprints see fs_check_waits.  Default 2 s; seconds must be in
+ * (0, 3600].  A persistent batch uses the smallest limit among its
+ * handles. */
 fs_status fs_set_wait_limit(fs_handle* h, double seconds);
 
 /* Testing aid for the bound above: stall = 1 makes the first work items of
  * the finest level of this handle's persistent solves wait for a counter
- * that nothing advances, so that wait runs out; stall = 0 restores the
- * schedule.  A batch stalls when any of its handles does. */
+ * that nothing advances, so that wait runs out, and makes the first launch
+ * of every level that runs the TMA-staged footprints (choices 56..63) wait
+ * for 16 bytes that no copy delivers; stall = 0 restores the schedule.  A
+ * batch stalls when any of its handles does.  Both this call and
+ * fs_set_wait_limit drop the handle's captured graph (the bound and the
+ * stall are launch arguments); a batch's graph keeps the values it was
+ * captured with. */
 fs_status fs_persist_stall(fs_handle* h, int stall);
+
+/* The TMA-staged primal-dual footprints (fs_autotune choices 56..63): each
+ * launch's CTAs wait on a shared-memory barrier for the copies of every
+ * footprint, bounded like the persistent schedule (fs_set_wait_limit).  A
+ * wait that runs out makes its CTA return and records FS_ETIMEOUT in the
+ * handle.  fs_check_waits synchronises the handle's stream and returns
+ * FS_ETIMEOUT (the state of the levels involved is then unspecified) when a
+ * wait ran out since the last check, clearing the record, else FS_OK.
+ * fs_solve_host checks by itself when the handle's schedule uses these
+ * footprints; fs_solve, fs_solve_continue and fs_batch_solve enqueue work
+ * and leave the check to the caller. */
+fs_status fs_check_waits(fs_handle* h);
 
 #ifdef __cplusplus
 }

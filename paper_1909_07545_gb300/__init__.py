@@ -48,6 +48,7 @@ EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_batch_create", "fs_batch_solve", "fs_batch_set_finest_limit",
             "fs_batch_destroy", "fs_autotune", "fs_set_schedule", "fs_energy", "fs_state_bytes",
             "fs_guard_check", "fs_guard_clobber", "fs_set_wait_limit", "fs_persist_stall",
+            "fs_check_waits",
             "fs_server_default_config", "fs_server_create", "fs_server_add_rig",
             "fs_server_submit", "fs_server_wait", "fs_server_cancel", "fs_server_drain",
             "fs_server_stats_read",
@@ -147,6 +148,7 @@ def load_library():
         "fs_guard_clobber": [_P, i, ctypes.c_size_t, ctypes.POINTER(i)],
         "fs_set_wait_limit": [_P, d],
         "fs_persist_stall": [_P, i],
+        "fs_check_waits": [_P],
         "fs_energy": [_P, i, ctypes.POINTER(d)],
         "fs_state_bytes": [i, i, i, ctypes.POINTER(FsParams), ctypes.POINTER(ctypes.c_size_t)],
         "fs_server_default_config": [ctypes.POINTER(FsServerConfig)],
@@ -380,8 +382,14 @@ class Solver:
         _check(self.lib.fs_set_wait_limit(self.h, float(seconds)))
 
     def persist_stall(self, on=True):
-        """fs_persist_stall: make a wait of the persistent schedule run out (testing aid)."""
+        """fs_persist_stall: make a wait of the persistent schedule or of the
+        TMA-staged footprints run out (testing aid)."""
         _check(self.lib.fs_persist_stall(self.h, 1 if on else 0))
+
+    def check_waits(self):
+        """fs_check_waits: raise FsError (FS_ETIMEOUT) if a copy wait of the
+        TMA-staged footprints ran out since the last check."""
+        _check(self.lib.fs_check_waits(self.h))
 
     def timing_enable(self, on=True):
         _check(self.lib.fs_timing_enable(self.h, 1 if on else 0))

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfs.so")
 
-SOURCES = ["fs_api.cu", "k_level.cu", "k_pd.cu", "k_persist.cu", "k_tgv.cu", "k_energy.cu",
+SOURCES = ["fs_api.cu", "k_level.cu", "k_pd.cu", "k_pd_tma.cu", "k_persist.cu", "k_tgv.cu", "k_energy.cu",
            "fs_noalloc.cu", "fs_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

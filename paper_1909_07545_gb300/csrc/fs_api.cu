@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "fs.h"
@@ -66,6 +67,11 @@ struct HostLevel {
   int tuned = -1;                           // autotuned choice: 0 cluster, 1..8 depth, -1 none
   int tuned_variant = -1;                   // autotuned tile variant, -1: by size
   LevelView v{};
+  // tensor maps of the TMA-staged primal-dual footprints, reading buffer
+  // set 0 (primary) and set 1 (alternate); tma_ok = false if the driver
+  // could not encode them (the TMA choices are then refused)
+  PdTmaMaps tma[2];
+  bool tma_ok = false;
 };
 
 // Denominator of the enhanced unified model, alpha sqrt(beta s^2 + c^2) +
@@ -107,6 +113,63 @@ DevCamDF dev_cam_df(const fs_calib& c, double fx, double fy, double cx, double c
   d.theta_max = df_from_double(c.fov_deg * M_PI / 360.0);
   d.f32 = dev_cam(c, fx, fy, cx, cy);
   return d;
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (the library
+// links the runtime only); null if the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// A 2-D tensor map of a W x H plane of es-byte elements with a row pitch of
+// P elements, copied in boxes of bw x bh elements; out-of-range elements
+// of a box read as zero.
+bool encode_plane(CUtensorMap* m, const void* base, int es, int W, int H, int P, int bw,
+                  int bh) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const CUtensorMapDataType t = es == 4   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                : es == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                          : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const cuuint64_t dim[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t stride[1] = {(cuuint64_t)P * (cuuint64_t)es};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t step[2] = {1, 1};
+  return enc(m, t, 2, const_cast<void*>(base), dim, stride, box, step,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The maps of k_pd_tma for level L (64 x 64 boxes; the mask's 80 x 64).
+bool build_tma_maps(HostLevel& L) {
+  const LevelView& v = L.v;
+  const int es = (int)storage_size(v.st);
+  bool ok = true;
+  for (int set = 0; set < 2 && ok; ++set) {
+    PdTmaMaps& m = L.tma[set];
+    auto f32 = [&](CUtensorMap* t, const void* p) { return encode_plane(t, p, 4, v.W, v.H, v.P, 64, 64); };
+    auto spl = [&](CUtensorMap* t, const SPlane& p) { return encode_plane(t, p.p, es, v.W, v.H, v.P, 64, 64); };
+    ok = f32(&m.sig, v.sig) && f32(&m.tau, v.tau) && f32(&m.uw, v.uw) && spl(&m.sx, v.sx) &&
+         spl(&m.sy, v.sy) && spl(&m.Iu, v.Iu) && spl(&m.rho0, v.rho0) &&
+         encode_plane(&m.mask, v.mask, 1, v.W, v.H, v.P, 80, 64) &&
+         f32(&m.u, set == 0 ? v.u : v.u_alt) && f32(&m.ubar, set == 0 ? v.ubar : v.ubar_alt) &&
+         spl(&m.p1, set == 0 ? v.p1 : v.p1_alt) && spl(&m.p2, set == 0 ? v.p2 : v.p2_alt);
+  }
+  L.tma_ok = ok;
+  return ok;
 }
 
 fs_status check_calib(const fs_calib& c, int which) {
@@ -223,6 +286,9 @@ struct fs_handle {
   PersistPlan* plan = nullptr;
   unsigned long long wait_ns = 2000000000ull;
   int persist_stall = 0;
+  // set to FS_ETIMEOUT by a TMA-staged primal-dual launch whose copy wait
+  // ran out (in the arena; read and cleared by fs_check_waits)
+  int* pd_status = nullptr;
 };
 
 namespace fs {
@@ -328,13 +394,21 @@ int pd_block(const fs_handle* h, int l) {
 // 64 x 32, 64 x 64 of 1024, 32 x 32 of 1024, 32 x 32 of 512), so 1..48;
 // 49..55 = depth 9..15 on 32 x 32 footprints of 1024 threads (deeper
 // blocking for the small levels, whose launches cost more than the extra
-// halo: they leave most SMs idle); TGV: 8 v + 1 .. 8 v + 8 = depth on the
-// TGV footprint v, 0..4, so 1..40; -1 = none.
+// halo: they leave most SMs idle); 56..63 = depth 1..8 on the TMA-staged
+// 64 x 64 footprints of 1024 threads (k_pd_tma); TGV: 8 v + 1 .. 8 v + 8 =
+// depth on the TGV footprint v, 0..4, so 1..40; -1 = none.
 constexpr int kDeepChoices = 7;
-constexpr int kMaxChoice = 8 * PD_TILE_COUNT + kDeepChoices;
+constexpr int kFirstTmaChoice = 8 * PD_TILE_COUNT + kDeepChoices + 1;
+constexpr int kMaxChoice = kFirstTmaChoice + 7;
 constexpr int kMaxTgvChoice = 8 * kTgvVariants;
+bool is_tma_choice(int c, bool tgv) { return !tgv && c >= kFirstTmaChoice && c <= kMaxChoice; }
 void decode_choice(int c, bool tgv, int& depth, int& variant) {
   if (c <= 0) { depth = c; variant = -1; return; }
+  if (is_tma_choice(c, tgv)) {
+    depth = 1 + c - kFirstTmaChoice;
+    variant = PD_TILE_64_TMA;
+    return;
+  }
   if (!tgv && c > 8 * PD_TILE_COUNT) {
     depth = 8 + (c - 8 * PD_TILE_COUNT);
     variant = PD_TILE_32_T1024;
@@ -350,6 +424,14 @@ bool use_cluster(const fs_handle* h, int l) {
   if (L.cluster < 0 || h->prm.pd_schedule != 0 || h->prm.accel_gamma > 0) return false;
   if (h->prm.block_iters <= 0 && L.tuned >= 1) return false;   // tuner chose blocking
   return true;
+}
+
+// Whether a solve of h runs the TMA-staged footprints on some level.
+bool uses_tma(const fs_handle* h) {
+  if (h->prm.regularizer == FS_REG_TGV || h->prm.block_iters > 0) return false;
+  for (int l = 0; l < h->L; ++l)
+    if (h->lv[l].tuned >= 1 && h->lv[l].tuned_variant == PD_TILE_64_TMA) return true;
+  return false;
 }
 
 // Number of k_pd launches for `iters` iterations with at most B per launch:
@@ -428,6 +510,8 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
                     : ((L.W >= 128 && L.H >= 128) ? PD_TILE_64 : PD_TILE_32);
   PDState A{L.v.u, L.v.ubar, L.v.p1, L.v.p2};
   PDState Bs{L.v.u_alt, L.v.ubar_alt, L.v.p1_alt, L.v.p2_alt};
+  const bool tma = variant == PD_TILE_64_TMA;
+  if (tma && !L.tma_ok) return fail(FS_EINVAL, "level %d: no tensor maps for the TMA footprints", l);
   int nl = pd_launches(iters, B);
   for (int k = 0, done = 0; k < nl; ++k) {
     int n = (iters - done) / (nl - k);          // spread the iterations evenly
@@ -435,8 +519,12 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
     const PDState& in = (k % 2 == 0) ? A : Bs;
     const PDState& out = (k % 2 == 0) ? Bs : A;
     pp.k0 = done;
-    cudaError_t e = launch_pd(variant, L.v, in, out, pp, B, n, st, k > 0);
-    if (e != cudaSuccess) return fail(FS_ECUDA, "launch of k_pd failed: %s", cudaGetErrorString(e));
+    cudaError_t e = tma ? launch_pd_tma(L.v, out, pp, B, n, k > 0, L.tma[k % 2], h->pd_status,
+                                        h->wait_ns, (h->persist_stall && k == 0) ? 1 : 0, st)
+                        : launch_pd(variant, L.v, in, out, pp, B, n, st, k > 0);
+    if (e != cudaSuccess)
+      return fail(FS_ECUDA, "launch of %s failed: %s", tma ? "k_pd_tma" : "k_pd",
+                  cudaGetErrorString(e));
     done += n;
   }
   if (nl % 2 == 1) {   // a single launch: bring the state back to the primary set
@@ -975,12 +1063,12 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     L.cluster = (cv >= 0 && pd_cluster_fits(cv, L.W, L.H)) ? cv : -1;
   }
   size_t cbytes = align_up((size_t)h->lv[0].P * H * sizeof(float4), 256);
-  bytes += cbytes;
+  bytes += cbytes + 256;                                  // + the status word
   const char* genv = std::getenv("FS_GUARD_BANDS");
   if (genv && std::atoi(genv) > 0) {
     // two rows of the widest element (float2) of level 0 on each side
     h->guard = align_up(2 * (size_t)h->lv[0].P * sizeof(float2), 256);
-    size_t n_planes = 1;                                  // the calibration field
+    size_t n_planes = 2;                                  // the calibration field, the status word
     for (int l = 0; l < levels; ++l) n_planes += 21 + (p.regularizer == FS_REG_TGV ? 20 : 0);
     bytes += (n_planes + 1) * h->guard;
   }
@@ -1031,6 +1119,8 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     }
   }
   h->cfield = (float4*)take(cbytes, 0, "calibration field");
+  h->pd_status = (int*)take(256, 0, "status word");
+  for (int l = 0; l < levels; ++l) build_tma_maps(h->lv[l]);
   if (h->guard) {                                         // the band after the last plane
     h->gband.push_back((unsigned long long)(cur - (char*)h->arena));
     h->gname.push_back("end of the arena");
@@ -1304,7 +1394,7 @@ fs_status fs_solve_host(fs_handle* h, const float* h_I0, const float* h_I1, cons
   if (h_disp) FS_CUDA(cudaMemcpyAsync(h_disp, ddisp, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
   if (h_depth) FS_CUDA(cudaMemcpyAsync(h_depth, ddepth, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
   FS_CUDA(cudaStreamSynchronize(h->stream));
-  return FS_OK;
+  return uses_tma(h) ? fs_check_waits(h) : FS_OK;
 }
 
 fs_status fs_destroy(fs_handle* h) {
@@ -1728,7 +1818,8 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
       // the 1024 x 1024 workload: the best depth, 7, lies between the
       // sampled ones, where another footprint was faster.)
       if (L.cluster >= 0 && !(h->prm.accel_gamma > 0)) try_cand(0);
-      for (int cand = 1; cand <= kMaxChoice; ++cand) try_cand(cand);
+      for (int cand = 1; cand <= kMaxChoice; ++cand)
+        if (L.tma_ok || !is_tma_choice(cand, false)) try_cand(cand);
     }
     decode_choice(best_c, h->prm.regularizer == FS_REG_TGV, L.tuned, L.tuned_variant);
     if (choice) choice[l] = best_c;
@@ -1775,6 +1866,8 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
       return fail(FS_EINVAL, "level %d: schedule %d out of range", l, c);
     if (c == 0 && !tgv && (h->lv[l].cluster < 0 || h->prm.accel_gamma > 0))
       return fail(FS_EINVAL, "level %d does not fit one thread-block cluster", l);
+    if (is_tma_choice(c, tgv) && !h->lv[l].tma_ok)
+      return fail(FS_EINVAL, "level %d: no tensor maps for the TMA footprints", l);
   }
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   for (int l = 0; l < h->L; ++l) {
@@ -1790,6 +1883,7 @@ extern "C" fs_status fs_set_wait_limit(fs_handle* h, double seconds) {
   if ((s = check_handle(h)) != FS_OK) return s;
   if (!(seconds > 0 && seconds <= 3600)) return fail(FS_EINVAL, "wait limit must be in (0, 3600] s");
   h->wait_ns = (unsigned long long)(seconds * 1e9);
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // captured the old bound
   return FS_OK;
 }
 
@@ -1797,7 +1891,23 @@ extern "C" fs_status fs_persist_stall(fs_handle* h, int stall) {
   fs_status s;
   if ((s = check_handle(h)) != FS_OK) return s;
   h->persist_stall = stall ? 1 : 0;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   return FS_OK;
+}
+
+extern "C" fs_status fs_check_waits(fs_handle* h) {
+  fs_status s;
+  if ((s = check_handle(h)) != FS_OK) return s;
+  int v = 0;
+  FS_CUDA(cudaMemcpyAsync(&v, h->pd_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  FS_CUDA(cudaStreamSynchronize(h->stream));
+  if (v == 0) return FS_OK;
+  FS_CUDA(cudaMemsetAsync(h->pd_status, 0, sizeof(int), h->stream));
+  FS_CUDA(cudaStreamSynchronize(h->stream));
+  return fail(FS_ETIMEOUT,
+              "a copy wait of the TMA-staged primal-dual footprints ran out (limit %.3g s); "
+              "the level state is unspecified",
+              (double)h->wait_ns * 1e-9);
 }
 
 extern "C" fs_status fs_stage_depth(fs_handle* h, float* d_disp, float* d_depth) {

@@ -245,7 +245,7 @@ __device__ __forceinline__ float2 sample_bicubic2(const float2* __restrict__ f, 
 enum Storage { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
 
 // Bytes of one element of a plane in storage st.
-__host__ __device__ inline size_t storage_size(int st) { return st == ST_F32 ? 4 : 2; }
+__host__ __device__ constexpr size_t storage_size(int st) { return st == ST_F32 ? 4 : 2; }
 
 // A plane of one of those fields; its element type is the level's storage,
 // fixed at compile time in every kernel that touches it (sld / sst).

@@ -1,6 +1,8 @@
 // fs_kernels.h -- kernel declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
+
 #include "cam_df.cuh"
 #include "fs_device.cuh"
 
@@ -16,6 +18,9 @@ enum PDVariant {
   PD_TILE_32_T512 = 5,    // 32 x 32, 32 x 16 threads of 2 rows
   PD_TILE_COUNT = 6
 };
+// The TMA-staged footprints of k_pd_tma.cu (64 x 64, 1024 threads of 4 rows,
+// 48 interior columns, depth <= 8): not a PDVariant of launch_pd.
+constexpr int PD_TILE_64_TMA = PD_TILE_COUNT;
 enum PDClusterVariant { PD_CLUSTER_16 = 0, PD_CLUSTER_32 = 1 };
 
 __global__ void k_trajectory(DevCamDF cam, df tx, df ty, df tz, LevelView L);
@@ -81,6 +86,27 @@ cudaError_t launch_unpack_s(const float* src, const SPlane& dst, int storage, in
 // before reading the state.
 cudaError_t launch_pd(int variant, const LevelView& L, const PDState& in, const PDState& out,
                       const PDParams& pp, int B, int n, cudaStream_t st, bool chained = false);
+
+// The tensor maps k_pd_tma copies a footprint through: the per-warp
+// constants and the mask of a level, and the state planes of the buffer set
+// the launch reads (each a 2-D tensor of the level's W x H pixels, pitch P;
+// boxes of 64 x 64 elements, the mask's 80 x 64).
+struct PdTmaMaps {
+  CUtensorMap sig, tau, uw, sx, sy, Iu, rho0, mask;
+  CUtensorMap u, ubar, p1, p2;
+};
+
+// n (<= B <= 8) primal-dual iterations on the TMA-staged footprints (one
+// resident CTA per SM walking the footprints), the state read through
+// `maps` and written to `out`; chained as in launch_pd.  A copy wait that
+// runs out after wait_ns of global time sets *status to FS_ETIMEOUT;
+// stall = 1 makes the first wait run out (testing aid).  Same results as
+// launch_pd.
+cudaError_t launch_pd_tma(const LevelView& L, const PDState& out, const PDParams& pp, int B,
+                          int n, bool chained, const PdTmaMaps& maps, int* status,
+                          unsigned long long wait_ns, int stall, cudaStream_t st);
+// Dynamic shared memory of one k_pd_tma CTA for a storage type.
+size_t pd_tma_smem_bytes(int storage);
 
 // Whole-level primal-dual in one thread-block cluster: the tile variant for a
 // W x H level (-1 if none), whether its cluster can be resident on this GPU,

@@ -34,7 +34,7 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
   constexpr int FH = NY * R;
   __shared__ float s_ub[FH][FW];
   __shared__ float s_t1[FH][FW];
-  __shared__ float s_t2[FH][FW];
+  __shared__ float s_t2[NY][FW];
   pd_tile<FW, NY, R, S, ACC, false>(L, in, out, pp, B, n_iters, (int)blockIdx.x,
                                     (int)blockIdx.y, (int)threadIdx.x, (int)threadIdx.y, s_ub,
                                     s_t1, s_t2, chained != 0);

@@ -33,6 +33,7 @@ __device__ __forceinline__ void pd_iterate(const PDParams& pp, int n_iters, int 
 
   // a thread's own products stay in registers; shared memory carries t1 to
   // the right-hand neighbour and the last row's t2 to the thread below
+  // (s_t2 holds one row per thread row: row ty is thread row ty's last)
   float t1r[R], t2r[R];
 #pragma unroll 1
   for (int it = 0; it < n_iters; ++it) {
@@ -53,7 +54,7 @@ __device__ __forceinline__ void pd_iterate(const PDParams& pp, int n_iters, int 
       }
       px_dual<MASKED>(mb >> (3 * r), ub[r], right, below, cr, p1[r], p2[r], t1r[r], t2r[r]);
       s_t1[fy][tx] = t1r[r];
-      if (r == R - 1) s_t2[fy][tx] = t2r[r];
+      if (r == R - 1) s_t2[ty][tx] = t2r[r];
     }
     __syncthreads();
 #pragma unroll
@@ -61,7 +62,7 @@ __device__ __forceinline__ void pd_iterate(const PDParams& pp, int n_iters, int 
       const int fy = ty * R + r;
       // the row above: this thread's previous row, or the last row of the
       // thread above (the top row of the footprint is halo: its own value)
-      const float t2_up = r > 0 ? t2r[r - 1] : (ty > 0 ? s_t2[fy - 1][tx] : t2r[0]);
+      const float t2_up = r > 0 ? t2r[r - 1] : (ty > 0 ? s_t2[ty - 1][tx] : t2r[0]);
       const float dv = px_div(t1r[r], s_t1[fy][txl], t2r[r], t2_up);
       PxConst cr = c[r];
       if constexpr (ACC) {
@@ -84,8 +85,9 @@ __device__ __forceinline__ void pd_iterate(const PDParams& pp, int n_iters, int 
 // the mask) and theta.  CG: the inputs may have been written by other CTAs
 // of the same launch (loads through L2 only).  chained: a programmatic
 // dependent launch of k_pd (constants loaded before the wait for the
-// preceding launch, the state after it).  s_ub, s_t1, s_t2: shared arrays of
-// FH x FW floats.  Every thread of the CTA (FW x NY) must call it.
+// preceding launch, the state after it).  s_ub, s_t1: shared arrays of
+// FH x FW floats, s_t2 of NY x FW.  Every thread of the CTA (FW x NY) must
+// call it.
 template <int FW, int NY, int R, int S, bool ACC, bool CG>
 __device__ __forceinline__ void pd_tile(const LevelView& L, const PDState& in,
                                         const PDState& out, const PDParams& pp, int B,

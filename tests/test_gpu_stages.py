@@ -431,7 +431,8 @@ def test_pd_footprints_are_bit_exact(which, small, ragged):
     # schedule, which the oracle comparison above pins
     pair = small if which == "small" else ragged
     outs = []
-    for choice in (-1, 3, 8, 12, 16, 19, 24, 26, 31, 32, 34, 40, 43, 48, 49, 52, 55):
+    for choice in (-1, 3, 8, 12, 16, 19, 24, 26, 31, 32, 34, 40, 43, 48, 49, 52, 55, 56, 60,
+                   62, 63):
         rng = np.random.default_rng(12)
         u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
         s = make_solver(pair)
@@ -455,7 +456,7 @@ def test_pd_footprints_agree_across_chained_launches(storage):
     # read through L1 then came from a launch two steps back.)
     p = f32pair(synth.plain_small(0, W=64, H=64))
     outs = []
-    for choice in (5, 13, 21, 29, 37, 45):       # depth 5 on footprints 0..5
+    for choice in (5, 13, 21, 29, 37, 45, 60):   # depth 5 on footprints 0..5 and the TMA one
         s = make_solver(p, levels=1, storage=storage, pd_schedule=1)
         s.set_schedule([choice])
         s.solve(p["I0"], p["I1"], 1, 14)
