@@ -63,10 +63,15 @@ def test_schedule_labels_decode_the_tuner_encoding():
     assert bench.schedule_label(41) == "blocking x1 (32x32 footprints, 512 threads)"
     assert bench.schedule_label(49) == "blocking x9 (32x32 footprints, 1024 threads)"
     assert bench.schedule_label(55) == "blocking x15 (32x32 footprints, 1024 threads)"
-    assert len(bench.FOOTPRINTS) * 8 == 48
-    # one label per footprint variant of the kernels
+    assert bench.schedule_label(56) == ("blocking x1 (64x64 footprints 48 columns apart, "
+                                        "1024 threads, TMA-staged)")
+    assert bench.schedule_label(63).startswith("blocking x8 (64x64 footprints 48 columns")
+    assert bench.interior(bench.TMA_FOOTPRINT, 7) == (48, 50)
+    assert bench.interior(3, 7) == (50, 50)
+    # one label per footprint variant of the kernels, the TMA one last
     import os
     import re
     src = open(os.path.join(os.path.dirname(bench.__file__), "paper_1909_07545_gb300", "csrc",
                             "fs_kernels.h")).read()
-    assert int(re.search(r"PD_TILE_COUNT = (\d+)", src).group(1)) == len(bench.FOOTPRINTS)
+    assert int(re.search(r"PD_TILE_COUNT = (\d+)", src).group(1)) + 1 == len(bench.FOOTPRINTS)
+    assert "constexpr int PD_TILE_64_TMA = PD_TILE_COUNT;" in src
