@@ -279,7 +279,7 @@ fs_status fs_batch_destroy(fs_batch* b);
  * tensor and step sizes, then `iters` iterations of Eq. 11/13) directly on
  * the caller's buffers and allocates nothing: its intermediate planes live
  * in one fixed array compiled into the library, sized for
- * FS_NOALLOC_MAX_PIXELS pixels (37 bytes each, about 9.7 MB), which every
+ * FS_NOALLOC_MAX_PIXELS pixels (53 bytes each, about 13.9 MB), which every
  * GPU that loads the library holds until the process exits.
  *
  *   d_I0    W x H image (the tensor T^1/2 of Eq. 12 is built from it)

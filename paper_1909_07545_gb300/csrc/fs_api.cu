@@ -162,8 +162,8 @@ bool build_tma_maps(HostLevel& L) {
     PdTmaMaps& m = L.tma[set];
     auto f32 = [&](CUtensorMap* t, const void* p) { return encode_plane(t, p, 4, v.W, v.H, v.P, 64, 64); };
     auto spl = [&](CUtensorMap* t, const SPlane& p) { return encode_plane(t, p.p, es, v.W, v.H, v.P, 64, 64); };
-    ok = f32(&m.sig, v.sig) && f32(&m.tau, v.tau) && f32(&m.uw, v.uw) && spl(&m.sx, v.sx) &&
-         spl(&m.sy, v.sy) && spl(&m.Iu, v.Iu) && spl(&m.rho0, v.rho0) &&
+    ok = spl(&m.sx, v.sx) && spl(&m.sy, v.sy) && f32(&m.tau, v.tau) && f32(&m.dinv, v.dinv) &&
+         f32(&m.sd, v.sd) && f32(&m.step, v.step) && f32(&m.c0, v.c0) &&
          encode_plane(&m.mask, v.mask, 1, v.W, v.H, v.P, 80, 64) &&
          f32(&m.u, set == 0 ? v.u : v.u_alt) && f32(&m.ubar, set == 0 ? v.ubar : v.ubar_alt) &&
          spl(&m.p1, set == 0 ? v.p1 : v.p1_alt) && spl(&m.p2, set == 0 ? v.p2 : v.p2_alt);
@@ -512,6 +512,7 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
   PDState Bs{L.v.u_alt, L.v.ubar_alt, L.v.p1_alt, L.v.p2_alt};
   const bool tma = variant == PD_TILE_64_TMA;
   if (tma && !L.tma_ok) return fail(FS_EINVAL, "level %d: no tensor maps for the TMA footprints", l);
+  FS_LAUNCH("k_pd_consts", launch_pd_consts(L.v, h->prm.lambda, h->prm.huber_eps, st));
   int nl = pd_launches(iters, B);
   for (int k = 0, done = 0; k < nl; ++k) {
     int n = (iters - done) / (nl - k);          // spread the iterations evenly
@@ -702,8 +703,9 @@ fs_status check_handle(const fs_handle* h) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Device bytes of one level: the mask byte plane, 7 FP32 planes (tau,
-// sigma, u, ubar, u_w and the ping-pong u, ubar), 10 planes in the storage
+// Device bytes of one level: the mask byte plane, 11 FP32 planes (tau,
+// sigma, u, ubar, u_w, the ping-pong u, ubar and the primal-dual constants
+// dinv, sd, step, c0), 10 planes in the storage
 // type (I0, I1, s_x, s_y, p1, p2, I_u, rho0 and the ping-pong p1, p2) and 3
 // float2 planes (gamma, w, g); every plane starts on a 256-byte boundary.
 size_t level_bytes(int P, int H, int storage, int regularizer) {
@@ -712,7 +714,7 @@ size_t level_bytes(int P, int H, int storage, int regularizer) {
   size_t plane8 = align_up((size_t)P * H, 256);
   // v, vbar, q and the alternate set of the 12 TGV state planes
   size_t tgv = regularizer == FS_REG_TGV ? 20 * plane : 0;
-  return plane8 + 7 * plane + 10 * splane + 3 * 2 * plane + tgv;
+  return plane8 + 11 * plane + 10 * splane + 3 * 2 * plane + tgv;
 }
 
 // ------------------------------------------------------------------ persistent schedule
@@ -1069,7 +1071,7 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     // two rows of the widest element (float2) of level 0 on each side
     h->guard = align_up(2 * (size_t)h->lv[0].P * sizeof(float2), 256);
     size_t n_planes = 2;                                  // the calibration field, the status word
-    for (int l = 0; l < levels; ++l) n_planes += 21 + (p.regularizer == FS_REG_TGV ? 20 : 0);
+    for (int l = 0; l < levels; ++l) n_planes += 25 + (p.regularizer == FS_REG_TGV ? 20 : 0);
     bytes += (n_planes + 1) * h->guard;
   }
   cudaError_t e = fs_internal_malloc(&h->arena, bytes, "arena");
@@ -1098,9 +1100,11 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     v.W = L.W; v.H = L.H; v.P = L.P;
     v.st = p.storage;
     v.mask = (const uint8_t*)take(plane8, l, "mask");
-    float** fl[] = {&v.tau, &v.sig, &v.u, &v.ubar, &v.uw, &v.u_alt, &v.ubar_alt};
-    const char* nfl[] = {"tau", "sigma", "u", "ubar", "u_w", "u (ping-pong)", "ubar (ping-pong)"};
-    for (int j = 0; j < 7; ++j) *fl[j] = (float*)take(plane, l, nfl[j]);
+    float** fl[] = {&v.tau, &v.sig, &v.u, &v.ubar, &v.uw, &v.u_alt, &v.ubar_alt,
+                    &v.dinv, &v.sd, &v.step, &v.c0};
+    const char* nfl[] = {"tau", "sigma", "u", "ubar", "u_w", "u (ping-pong)", "ubar (ping-pong)",
+                         "dinv", "sigma dinv", "L1 step", "c0"};
+    for (int j = 0; j < 11; ++j) *fl[j] = (float*)take(plane, l, nfl[j]);
     v.I0lo = v.u_alt;
     v.I1lo = v.ubar_alt;
     SPlane* sp[] = {&v.I0, &v.I1, &v.sx, &v.sy, &v.p1, &v.p2, &v.Iu, &v.rho0, &v.p1_alt,
@@ -1187,6 +1191,7 @@ fs_status fs_state_bytes(int W, int H, int levels, const fs_params* prm, size_t*
     bytes += level_bytes((int)align_up((size_t)lw, 32), lh, storage, reg);
   }
   bytes += align_up(align_up((size_t)W, 32) * H * sizeof(float4), 256);
+  bytes += 256;                                   // the status word
   *out = bytes;
   return FS_OK;
 }

@@ -317,6 +317,11 @@ struct LevelView {
   float *tau, *sig;      // primal / dual step sizes
   float *u, *ubar, *uw;
   SPlane p1, p2, Iu, rho0;
+  // The per-pixel constants of a warp's primal-dual iterations (PxConst,
+  // pd_math.cuh) other than s and tau: 1 / (1 + sigma eps), sigma times
+  // that, |tau lam I_u| and u_w - rho0 / I_u; computed once per warp by
+  // k_pd_consts from sigma, tau, I_u, rho0 and u_w as stored.
+  float *dinv, *sd, *step, *c0;
   float2 *w, *g;
   float *u_alt, *ubar_alt;
   // The low parts of I0 and I1 while the pyramid is built (each image is

@@ -78,6 +78,12 @@ cudaError_t launch_pack_s(const SPlane& src, int storage, float* dst, int W, int
 cudaError_t launch_unpack_s(const float* src, const SPlane& dst, int storage, int W, int H,
                             int P, cudaStream_t st);
 
+// The per-warp constants of the primal-dual iterations (L.dinv, L.sd,
+// L.step, L.c0) from the level's sigma, tau, I_u, rho0 and u_w; launch_pd
+// and launch_pd_tma read them, so it runs after every change of those
+// planes (once per warp) and before the warp's first primal-dual launch.
+cudaError_t launch_pd_consts(const LevelView& L, float lam, float eps, cudaStream_t st);
+
 // Primal-dual iterations: n <= B iterations with halo B, tile variant
 // `variant`, state read from `in` and written to `out` (distinct buffers).
 // chained = true when the launch directly follows another k_pd launch on
@@ -87,12 +93,13 @@ cudaError_t launch_unpack_s(const float* src, const SPlane& dst, int storage, in
 cudaError_t launch_pd(int variant, const LevelView& L, const PDState& in, const PDState& out,
                       const PDParams& pp, int B, int n, cudaStream_t st, bool chained = false);
 
-// The tensor maps k_pd_tma copies a footprint through: the per-warp
-// constants and the mask of a level, and the state planes of the buffer set
-// the launch reads (each a 2-D tensor of the level's W x H pixels, pitch P;
-// boxes of 64 x 64 elements, the mask's 80 x 64).
+// The tensor maps k_pd_tma copies a footprint through: T^1/2, tau, the
+// per-warp constants (launch_pd_consts) and the mask of a level, and the
+// state planes of the buffer set the launch reads (each a 2-D tensor of the
+// level's W x H pixels, pitch P; boxes of 64 x 64 elements, the mask's
+// 80 x 64).
 struct PdTmaMaps {
-  CUtensorMap sig, tau, uw, sx, sy, Iu, rho0, mask;
+  CUtensorMap sx, sy, tau, dinv, sd, step, c0, mask;
   CUtensorMap u, ubar, p1, p2;
 };
 

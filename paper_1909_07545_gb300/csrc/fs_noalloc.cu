@@ -20,9 +20,10 @@ using namespace fs;
 namespace {
 
 constexpr size_t kMaxPixels = FS_NOALLOC_MAX_PIXELS;
-// planes: ubar, sx, sy, tau, sig, u_alt, ubar_alt, p1_alt, p2_alt (float)
-// followed by the mask bits (one byte per pixel)
-constexpr size_t kFloatPlanes = 9;
+// planes: ubar, sx, sy, tau, sig, u_alt, ubar_alt, p1_alt, p2_alt and the
+// per-warp constants dinv, sd, step, c0 (float) followed by the mask bits
+// (one byte per pixel)
+constexpr size_t kFloatPlanes = 13;
 constexpr size_t kNoAllocBytes = kMaxPixels * (kFloatPlanes * sizeof(float) + 1);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -141,6 +142,10 @@ extern "C" fs_status fs_pd_iterate_noalloc(const float* d_I0, const unsigned cha
   L.ubar_alt = f + 6 * n;
   L.p1_alt.p = f + 7 * n;
   L.p2_alt.p = f + 8 * n;
+  L.dinv = f + 9 * n;
+  L.sd = f + 10 * n;
+  L.step = f + 11 * n;
+  L.c0 = f + 12 * n;
   uint8_t* bits = (uint8_t*)(f + kFloatPlanes * n);
   L.mask = bits;
 
@@ -150,6 +155,7 @@ extern "C" fs_status fs_pd_iterate_noalloc(const float* d_I0, const unsigned cha
   k_mask_bits<<<grd, blk, 0, st>>>(d_mask, bits, W, H);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_tensor(L, p.beta, p.eta, p.precond, st);
+  if (e == cudaSuccess) e = launch_pd_consts(L, p.lambda, p.huber_eps, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(L.ubar, d_u, n * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) {

@@ -28,6 +28,35 @@ namespace cg = cooperative_groups;
 
 namespace fs {
 
+// The per-warp constants of the iterations (PxConst other than s, tau)
+// into L.dinv, L.sd, L.step, L.c0, from the stored sigma, tau, I_u, rho0
+// and u_w by the same px_make the other schedules apply (so the same bits).
+template <int S>
+__global__ void k_pd_consts(LevelView L, float lam, float eps) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= L.W || y >= L.H) return;
+  const size_t i = (size_t)y * L.P + x;
+  PxRaw raw;
+  px_fetch<S>(L, i, true, raw);
+  PxConst c;
+  px_make(raw, lam, eps, c);
+  L.dinv[i] = c.dinv;
+  L.sd[i] = c.sd;
+  L.step[i] = c.step;
+  L.c0[i] = c.c0;
+}
+
+cudaError_t launch_pd_consts(const LevelView& L, float lam, float eps, cudaStream_t st) {
+  const dim3 blk(32, 8), grd((L.W + 31) / 32, (L.H + 7) / 8);
+  switch (L.st) {
+    case ST_F16: k_pd_consts<ST_F16><<<grd, blk, 0, st>>>(L, lam, eps); break;
+    case ST_BF16: k_pd_consts<ST_BF16><<<grd, blk, 0, st>>>(L, lam, eps); break;
+    default: k_pd_consts<ST_F32><<<grd, blk, 0, st>>>(L, lam, eps); break;
+  }
+  return cudaGetLastError();
+}
+
 template <int FW, int NY, int R, int S, bool ACC>
 __global__ void __launch_bounds__(FW * NY, FW * NY >= 512 ? 1 : 2)
 k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int chained) {
@@ -35,9 +64,9 @@ k_pd(LevelView L, PDState in, PDState out, PDParams pp, int B, int n_iters, int 
   __shared__ float s_ub[FH][FW];
   __shared__ float s_t1[FH][FW];
   __shared__ float s_t2[NY][FW];
-  pd_tile<FW, NY, R, S, ACC, false>(L, in, out, pp, B, n_iters, (int)blockIdx.x,
-                                    (int)blockIdx.y, (int)threadIdx.x, (int)threadIdx.y, s_ub,
-                                    s_t1, s_t2, chained != 0);
+  pd_tile<FW, NY, R, S, ACC, false, true>(L, in, out, pp, B, n_iters, (int)blockIdx.x,
+                                          (int)blockIdx.y, (int)threadIdx.x, (int)threadIdx.y,
+                                          s_ub, s_t1, s_t2, chained != 0);
 }
 
 template <int TW, int NY, int R, int S>

@@ -50,9 +50,11 @@ template <int S>
 struct TmaLayout {
   static constexpr size_t f32 = (size_t)kFW * kFH * 4;                   // an FP32 plane
   static constexpr size_t sp = (size_t)kFW * kFH * storage_size(S);      // a storage plane
-  static constexpr size_t sig = 0, tau = f32, uw = 2 * f32, u = 3 * f32, ub = 4 * f32;
-  static constexpr size_t sx = 5 * f32, sy = sx + sp, Iu = sy + sp, rho0 = Iu + sp;
-  static constexpr size_t p1 = rho0 + sp, p2 = p1 + sp;
+  // FP32: tau and the per-warp constants dinv, sd, step, c0, then u, ubar;
+  // storage type: s_x, s_y, p1, p2
+  static constexpr size_t tau = 0, dinv = f32, sd = 2 * f32, step = 3 * f32, c0 = 4 * f32;
+  static constexpr size_t u = 5 * f32, ub = 6 * f32;
+  static constexpr size_t sx = 7 * f32, sy = sx + sp, p1 = sy + sp, p2 = p1 + sp;
   static constexpr size_t mask = p2 + sp;                                // kMaskW x kFH bytes
   static constexpr size_t x_ub = mask + (size_t)kMaskW * kFH;            // kFH x kFW floats
   static constexpr size_t x_t1 = x_ub + f32;                             // kFH x kFW floats
@@ -60,7 +62,7 @@ struct TmaLayout {
   static constexpr size_t bar = x_t2 + (size_t)kNY * kFW * 4;
   static constexpr size_t bytes = bar + 128;
   // bytes one footprint's copies deliver (boxes count whole, zero fill included)
-  static constexpr unsigned tx = (unsigned)(5 * f32 + 6 * sp + (size_t)kMaskW * kFH);
+  static constexpr unsigned tx = (unsigned)(7 * f32 + 4 * sp + (size_t)kMaskW * kFH);
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -118,13 +120,13 @@ __device__ __forceinline__ void request(const PdTmaMaps& m, unsigned char* smem,
   const int bx = tile % tiles_x, by = tile / tiles_x;
   const int x = bx * kIW - kXM, y = by * IH - B;
   if (consts) {
-    tma_load(smem_addr(smem + Lay::sig), &m.sig, x, y, bar);
     tma_load(smem_addr(smem + Lay::tau), &m.tau, x, y, bar);
-    tma_load(smem_addr(smem + Lay::uw), &m.uw, x, y, bar);
+    tma_load(smem_addr(smem + Lay::dinv), &m.dinv, x, y, bar);
+    tma_load(smem_addr(smem + Lay::sd), &m.sd, x, y, bar);
+    tma_load(smem_addr(smem + Lay::step), &m.step, x, y, bar);
+    tma_load(smem_addr(smem + Lay::c0), &m.c0, x, y, bar);
     tma_load(smem_addr(smem + Lay::sx), &m.sx, x, y, bar);
     tma_load(smem_addr(smem + Lay::sy), &m.sy, x, y, bar);
-    tma_load(smem_addr(smem + Lay::Iu), &m.Iu, x, y, bar);
-    tma_load(smem_addr(smem + Lay::rho0), &m.rho0, x, y, bar);
     tma_load(smem_addr(smem + Lay::mask), &m.mask, bx * kIW - kMaskOff, y, bar);
   }
   if (state) {
@@ -204,19 +206,22 @@ k_pd_tma(LevelView L, PDState out, PDParams pp, int B, int n_iters, int chained,
     PxConst c[kR];
     unsigned mb = 0;
     {
-      PxRaw raw[kR];
+      // (outside the level the copies read zeros: the constants of k_pd's
+      // all-zero inputs, except dinv = 0 instead of 1, which only scales a
+      // dual that is 0 there and stays 0)
 #pragma unroll
       for (int r = 0; r < kR; ++r) {
         const int k = (ty * kR + r) * kFW + tx;
-        raw[r].sig = reinterpret_cast<const float*>(smem + Lay::sig)[k];
-        raw[r].tau = reinterpret_cast<const float*>(smem + Lay::tau)[k];
-        raw[r].uw = reinterpret_cast<const float*>(smem + Lay::uw)[k];
-        raw[r].sx = sval<S>(smem + Lay::sx, k);
-        raw[r].sy = sval<S>(smem + Lay::sy, k);
-        raw[r].Iu = sval<S>(smem + Lay::Iu, k);
-        raw[r].rho0 = sval<S>(smem + Lay::rho0, k);
-        u[r] = reinterpret_cast<const float*>(smem + Lay::u)[k];
-        ub[r] = reinterpret_cast<const float*>(smem + Lay::ub)[k];
+        auto f32 = [&](size_t plane) { return reinterpret_cast<const float*>(smem + plane)[k]; };
+        c[r].tau = f32(Lay::tau);
+        c[r].dinv = f32(Lay::dinv);
+        c[r].sd = f32(Lay::sd);
+        c[r].step = f32(Lay::step);
+        c[r].c0 = f32(Lay::c0);
+        c[r].sx = sval<S>(smem + Lay::sx, k);
+        c[r].sy = sval<S>(smem + Lay::sy, k);
+        u[r] = f32(Lay::u);
+        ub[r] = f32(Lay::ub);
         p1[r] = sval<S>(smem + Lay::p1, k);
         p2[r] = sval<S>(smem + Lay::p2, k);
         mb |= (unsigned)smem[Lay::mask + (ty * kR + r) * kMaskW + tx + (kMaskOff - kXM)]
@@ -230,8 +235,6 @@ k_pd_tma(LevelView L, PDState out, PDParams pp, int B, int n_iters, int chained,
         mbar_expect_tx(bar, Lay::tx);
         request<S>(maps, smem, bar, next, tiles_x, IH, B, true, true);
       }
-#pragma unroll
-      for (int r = 0; r < kR; ++r) px_make(raw[r], pp.lam, pp.eps, c[r]);
     }
 #pragma unroll
     for (int r = 0; r < kR; ++r) s_ub[ty * kR + r][tx] = ub[r];

@@ -86,9 +86,11 @@ __device__ __forceinline__ void pd_iterate(const PDParams& pp, int n_iters, int 
 // of the same launch (loads through L2 only).  chained: a programmatic
 // dependent launch of k_pd (constants loaded before the wait for the
 // preceding launch, the state after it).  s_ub, s_t1: shared arrays of
-// FH x FW floats, s_t2 of NY x FW.  Every thread of the CTA (FW x NY) must
-// call it.
-template <int FW, int NY, int R, int S, bool ACC, bool CG>
+// FH x FW floats, s_t2 of NY x FW.  PRE: the per-warp constants are read
+// from L.dinv, L.sd, L.step, L.c0 (launch_pd_consts) instead of being
+// derived here from sigma, I_u, rho0 and u_w (the same bits either way).
+// Every thread of the CTA (FW x NY) must call it.
+template <int FW, int NY, int R, int S, bool ACC, bool CG, bool PRE = false>
 __device__ __forceinline__ void pd_tile(const LevelView& L, const PDState& in,
                                         const PDState& out, const PDParams& pp, int B,
                                         int n_iters, int bx, int by, int tx, int ty,
@@ -124,7 +126,25 @@ __device__ __forceinline__ void pd_tile(const LevelView& L, const PDState& in,
   }
   // per-warp constants first: written by earlier kernels, not by the
   // preceding launch of this chain
-  {
+  if constexpr (PRE) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const unsigned i = idx[r];
+      const float sx = sld_m<S, CG>(L.sx, i), sy = sld_m<S, CG>(L.sy, i);
+      const float tau = ldf<CG>(L.tau + i), dinv = ldf<CG>(L.dinv + i);
+      const float sd = ldf<CG>(L.sd + i), step = ldf<CG>(L.step + i), c0 = ldf<CG>(L.c0 + i);
+      const unsigned m8 = L.mask[i];
+      // outside the level: the constants of all-zero inputs (px_make)
+      c[r].sx = ok[r] ? sx : 0.f;
+      c[r].sy = ok[r] ? sy : 0.f;
+      c[r].tau = ok[r] ? tau : 0.f;
+      c[r].dinv = ok[r] ? dinv : 1.f;
+      c[r].sd = ok[r] ? sd : 0.f;
+      c[r].step = ok[r] ? step : 0.f;
+      c[r].c0 = ok[r] ? c0 : 0.f;
+      mb |= (ok[r] ? m8 : 0u) << (3 * r);
+    }
+  } else {
     PxRaw raw[R];
     unsigned char m8[R];
 #pragma unroll

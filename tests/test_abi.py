@@ -107,10 +107,10 @@ def test_host_side_validation(lib):
 
 
 def test_state_bytes_counts_the_level_planes(lib):
-    # mask bytes + 7 FP32 planes + 10 storage-typed planes + 3 float2 planes
+    # mask bytes + 11 FP32 planes + 10 storage-typed planes + 3 float2 planes
     # per level (pitch = width rounded up to 32, planes on 256-byte
     # boundaries), plus the full-resolution calibration field (a float-float
-    # pair per pixel: 16 bytes)
+    # pair per pixel: 16 bytes) and the 256-byte status word
     up = lambda v, a: (v + a - 1) // a * a
 
     def expect(W, H, L, esize):
@@ -119,9 +119,9 @@ def test_state_bytes_counts_the_level_planes(lib):
             if l:
                 w, h = (w + 1) // 2, (h + 1) // 2
             P = up(w, 32)
-            total += up(P * h, 256) + 7 * up(4 * P * h, 256) + 10 * up(esize * P * h, 256) \
+            total += up(P * h, 256) + 11 * up(4 * P * h, 256) + 10 * up(esize * P * h, 256) \
                 + 6 * up(4 * P * h, 256)
-        return total + up(up(W, 32) * H * 16, 256)
+        return total + up(up(W, 32) * H * 16, 256) + 256
     for W, H, L in [(64, 64, 2), (203, 157, 3), (1024, 1024, 5)]:
         assert fsb.state_bytes(W, H, L) == expect(W, H, L, 4)
         assert fsb.state_bytes(W, H, L, storage="f16") == expect(W, H, L, 2)

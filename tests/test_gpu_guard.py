@@ -154,7 +154,7 @@ def test_clobbered_band_is_reported(small):
         s = make_solver(small)
     n = s.guard_clobber()
     # before each plane, the calibration field and the status word, and the end
-    assert n == small["levels"] * 21 + 3
+    assert n == small["levels"] * 25 + 3
     s.guard_check()
     s.guard_clobber(band=5, offset=100)            # the band before level 0's u_w plane
     with pytest.raises(fsb.FsError, match="level 0 u_w"):

@@ -160,4 +160,3 @@ def test_tma_wait_runs_out_with_timeout_status(small):
     assert err.value.status == -5
     s.persist_stall(False)
     s.close()
-
