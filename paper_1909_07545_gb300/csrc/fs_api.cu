@@ -72,6 +72,10 @@ struct HostLevel {
   // could not encode them (the TMA choices are then refused)
   PdTmaMaps tma[2];
   bool tma_ok = false;
+  // the per-warp constants of the primal-dual iterations may not match the
+  // level's sigma, tau, I_u, rho0 and u_w (cleared by the warp-start
+  // kernels, which write both; run_pd recomputes them when set)
+  bool consts_stale = true;
 };
 
 // Denominator of the enhanced unified model, alpha sqrt(beta s^2 + c^2) +
@@ -512,7 +516,10 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
   PDState Bs{L.v.u_alt, L.v.ubar_alt, L.v.p1_alt, L.v.p2_alt};
   const bool tma = variant == PD_TILE_64_TMA;
   if (tma && !L.tma_ok) return fail(FS_EINVAL, "level %d: no tensor maps for the TMA footprints", l);
-  FS_LAUNCH("k_pd_consts", launch_pd_consts(L.v, h->prm.lambda, h->prm.huber_eps, st));
+  if (L.consts_stale) {
+    FS_LAUNCH("k_pd_consts", launch_pd_consts(L.v, h->prm.lambda, h->prm.huber_eps, st));
+    L.consts_stale = false;
+  }
   int nl = pd_launches(iters, B);
   for (int k = 0, done = 0; k < nl; ++k) {
     int n = (iters - done) / (nl - k);          // spread the iterations evenly
@@ -541,6 +548,11 @@ fs_status run_pd(fs_handle* h, int l, int iters, cudaStream_t st) {
 
 fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) {
   HostLevel& L = h->lv[l];
+  const int consts = h->prm.regularizer == FS_REG_TGV ? 0 : 1;
+  // every stage but the iterations and the warp starts can change sigma,
+  // tau, I_u, rho0 or u_w
+  if (stage != FS_STAGE_PD && stage != FS_STAGE_WARP && stage != FS_STAGE_CLIP_WARP)
+    L.consts_stale = true;
   switch (stage) {
     case FS_STAGE_DOWNSAMPLE:
       if (l + 1 >= h->L) return fail(FS_EINVAL, "downsample: level %d has no coarser level", l);
@@ -555,7 +567,9 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
       if (h->prm.regularizer == FS_REG_TGV) FS_LAUNCH("k_tgv_reset", launch_tgv_reset(L.v, st));
       return FS_OK;
     case FS_STAGE_WARP:
-      FS_LAUNCH("k_warp", launch_warp(L.v, h->prm.deriv == FS_DERIV_CENTRAL, st));
+      FS_LAUNCH("k_warp", launch_warp(L.v, h->prm.deriv == FS_DERIV_CENTRAL, h->prm.lambda,
+                                      h->prm.huber_eps, consts, st));
+      L.consts_stale = !consts;
       if (h->prm.regularizer == FS_REG_TGV)
         FS_LAUNCH("k_tgv_warp_start", launch_tgv_warp_start(L.v, st));
       return FS_OK;
@@ -570,7 +584,9 @@ fs_status run_stage(fs_handle* h, int l, int stage, int count, cudaStream_t st) 
       return FS_OK;
     case FS_STAGE_CLIP_WARP:
       FS_LAUNCH("k_clip_warp", launch_clip_warp(L.v, h->prm.du_max,
-                                                h->prm.deriv == FS_DERIV_CENTRAL, st));
+                                                h->prm.deriv == FS_DERIV_CENTRAL, h->prm.lambda,
+                                                h->prm.huber_eps, consts, st));
+      L.consts_stale = !consts;
       if (h->prm.regularizer == FS_REG_TGV)
         FS_LAUNCH("k_tgv_warp_start", launch_tgv_warp_start(L.v, st));
       return FS_OK;
@@ -936,6 +952,10 @@ static fs_status enqueue_persist(PersistPlan* P, const std::vector<fs_handle*>& 
       if ((s = run_stage(h, l, FS_STAGE_DOWNSAMPLE, 0, st)) != FS_OK) return s;
   }
   FS_CUDA(cudaMemsetAsync(P->ctrl, 0, P->zero_bytes, st));
+  // its items derive the iterations' constants themselves and do not write
+  // the constant planes
+  for (fs_handle* h : hs)
+    for (int l = 0; l < h->L; ++l) h->lv[l].consts_stale = true;
   FS_LAUNCH("k_persist", launch_persist(P->storage, P->jobs, P->phases, P->items, P->n_items,
                                         P->ctrl, P->done, P->level_done, P->wait_ns, P->grid,
                                         st));
@@ -1694,6 +1714,7 @@ extern "C" fs_status fs_buffer_write(fs_handle* h, int level, int buffer, const 
   if (buffer == FS_BUF_MASK || buffer == FS_BUF_TENSOR || buffer == FS_BUF_STEPS)
     return fail(FS_EINVAL, "buffer %d is derived and read-only", buffer);
   HostLevel& L = h->lv[level];
+  L.consts_stale = true;
   size_t n = (size_t)L.W * L.H;
   if (buffer == FS_BUF_I0 || buffer == FS_BUF_I1) {   // with the pyramid's low part
     FS_LAUNCH("k_copy_in_s", launch_copy_in_image(d_in, L.v, buffer == FS_BUF_I0 ? 0 : 1,

@@ -69,9 +69,14 @@ cudaError_t launch_energy(const LevelView& L, float lam, float eps, int tgv, flo
 cudaError_t launch_tgv_warp_start(const LevelView& L, cudaStream_t st);
 cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond,
                           cudaStream_t st);
-cudaError_t launch_warp(const LevelView& L, int central, cudaStream_t st);
+// consts = 1: also the per-warp constants of the primal-dual iterations
+// (the values launch_pd_consts computes), from the I_u, rho0 and u_w the
+// kernel writes.
+cudaError_t launch_warp(const LevelView& L, int central, float lam, float eps, int consts,
+                        cudaStream_t st);
 // k_clip of one warp fused with k_warp of the next (same results).
-cudaError_t launch_clip_warp(const LevelView& L, float du_max, int central, cudaStream_t st);
+cudaError_t launch_clip_warp(const LevelView& L, float du_max, int central, float lam, float eps,
+                             int consts, cudaStream_t st);
 cudaError_t launch_tensor_abc(const LevelView& L, float* dst, cudaStream_t st);
 cudaError_t launch_pack_s(const SPlane& src, int storage, float* dst, int W, int H, int P,
                           cudaStream_t st);
@@ -80,8 +85,9 @@ cudaError_t launch_unpack_s(const float* src, const SPlane& dst, int storage, in
 
 // The per-warp constants of the primal-dual iterations (L.dinv, L.sd,
 // L.step, L.c0) from the level's sigma, tau, I_u, rho0 and u_w; launch_pd
-// and launch_pd_tma read them, so it runs after every change of those
-// planes (once per warp) and before the warp's first primal-dual launch.
+// and launch_pd_tma read them.  The kernels that start a warp (launch_warp,
+// launch_clip_warp) write the same values; this one is for state that
+// reached the planes another way (buffer writes, the stage interface).
 cudaError_t launch_pd_consts(const LevelView& L, float lam, float eps, cudaStream_t st);
 
 // Primal-dual iterations: n <= B iterations with halo B, tile variant

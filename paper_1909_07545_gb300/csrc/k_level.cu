@@ -4,6 +4,7 @@
 // warp + linearisation, clip + update, triangulation.
 #include "fs_kernels.h"
 #include "level_px.cuh"
+#include "pd_math.cuh"
 
 namespace fs {
 
@@ -257,8 +258,32 @@ __global__ void k_tensor(LevelView L, float beta, float eta, int precond) {
 }
 
 // ------------------------------------------------------------ warp + linearise
+// The per-warp constants of the primal-dual iterations at pixel i
+// (launch_pd_consts' values: px_make of the stored sigma, tau, I_u, rho0
+// and u_w), written by the kernels that start a warp while they hold
+// I_u, rho0 and u_w.
 template <int S>
-__global__ void k_warp(LevelView L, int central) {
+__device__ __forceinline__ void pd_consts_px(const LevelView& L, size_t i, float Iu, float rho0,
+                                             float uw, float lam, float eps) {
+  PxRaw raw;
+  raw.sx = raw.sy = 0.f;                     // not used by px_make's outputs below
+  raw.sig = L.sig[i];
+  raw.tau = L.tau[i];
+  raw.Iu = round_storage<S>(Iu);
+  raw.rho0 = round_storage<S>(rho0);
+  raw.uw = uw;
+  PxConst c;
+  px_make(raw, lam, eps, c);
+  L.dinv[i] = c.dinv;
+  L.sd[i] = c.sd;
+  L.step[i] = c.step;
+  L.c0[i] = c.c0;
+}
+
+// consts: also write the per-warp constants of the primal-dual iterations
+// (pd_consts_px; Huber-TV handles).
+template <int S>
+__global__ void k_warp(LevelView L, int central, float lam, float eps, int consts) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
@@ -272,6 +297,7 @@ __global__ void k_warp(LevelView L, int central) {
   float u = L.u[i];
   L.ubar[i] = u;
   L.uw[i] = u;
+  if (consts) pd_consts_px<S>(L, i, Iu, rho0, u, lam, eps);
 }
 
 // ------------------------------------------------------------ clip + update
@@ -294,7 +320,8 @@ __global__ void k_clip(LevelView L, float du_max) {
 // pixel's clip and linearisation read only that pixel's state; the gathers
 // read I1 and gamma', which neither writes).
 template <int S>
-__global__ void k_clip_warp(LevelView L, float du_max, int central) {
+__global__ void k_clip_warp(LevelView L, float du_max, int central, float lam, float eps,
+                            int consts) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= L.W || y >= L.H) return;
@@ -316,6 +343,7 @@ __global__ void k_clip_warp(LevelView L, float du_max, int central) {
   L.g[i] = g;
   L.ubar[i] = u;
   L.uw[i] = u;
+  if (consts) pd_consts_px<S>(L, i, Iu, rho0, u, lam, eps);
 }
 
 
@@ -454,12 +482,16 @@ cudaError_t launch_tensor(const LevelView& L, float beta, float eta, int precond
   FS_STORAGE_SWITCH(L.st, (k_tensor<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, beta, eta,
                                                                           precond)))
 }
-cudaError_t launch_warp(const LevelView& L, int central, cudaStream_t st) {
-  FS_STORAGE_SWITCH(L.st, (k_warp<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, central)))
+cudaError_t launch_warp(const LevelView& L, int central, float lam, float eps, int consts,
+                        cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_warp<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, central, lam, eps,
+                                                                        consts)))
 }
 
-cudaError_t launch_clip_warp(const LevelView& L, float du_max, int central, cudaStream_t st) {
-  FS_STORAGE_SWITCH(L.st, (k_clip_warp<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, du_max, central)))
+cudaError_t launch_clip_warp(const LevelView& L, float du_max, int central, float lam, float eps,
+                             int consts, cudaStream_t st) {
+  FS_STORAGE_SWITCH(L.st, (k_clip_warp<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(
+                              L, du_max, central, lam, eps, consts)))
 }
 cudaError_t launch_tensor_abc(const LevelView& L, float* dst, cudaStream_t st) {
   FS_STORAGE_SWITCH(L.st, (k_tensor_abc<S><<<grid_of(L.W, L.H), kBlk, 0, st>>>(L, dst)))

@@ -447,6 +447,30 @@ def test_pd_footprints_are_bit_exact(which, small, ragged):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_warp_start_constants_equal_the_constant_kernel(storage):
+    # The warp-start kernels (k_warp, k_clip_warp) write the iterations'
+    # per-pixel constants while they hold I_u, rho0 and u_w; after a buffer
+    # write the primal-dual stage recomputes them with k_pd_consts from the
+    # stored planes.  Both must give the same bits: the same 9 iterations
+    # from the same state, once with each.
+    p = f32pair(synth.plain_small(0, W=160, H=128))
+    s = make_solver(p, levels=1, storage=storage, pd_schedule=1)
+    s.set_schedule([31])
+    s.solve(p["I0"], p["I1"], 2, 6)
+    s.stage(0, "CLIP_WARP")                      # constants from the fused kernel
+    state = {b: np64(s.read(0, b)) for b in ("U", "UBAR", "P")}
+    s.stage(0, "PD", 9)
+    fused = (np64(s.read(0, "U")), np64(s.read(0, "P")))
+    for b, v in state.items():                   # the same state; constants now stale
+        s.write(0, b, v)
+    s.stage(0, "PD", 9)
+    again = (np64(s.read(0, "U")), np64(s.read(0, "P")))
+    s.close()
+    for a, b in zip(fused, again):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_pd_footprints_agree_across_chained_launches(storage):
     # every footprint at the same depth (5) on 14 iterations of a 64 x 64
     # level: four chained launches of 4, 4, 3 and 3 iterations.  With 16-bit
