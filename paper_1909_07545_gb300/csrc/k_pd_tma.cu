@@ -244,11 +244,11 @@ k_pd_tma(LevelView L, PDState out, PDParams pp, int B, int n_iters, int chained,
     // set (pixels outside the level were filled with mask 0)
     float theta = pp.theta;
     if (__syncthreads_and(mb == 07777u))
-      pd_iterate<kFW, kNY, kR, ACC, false>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta,
-                                           s_ub, s_t1, s_t2);
+      pd_iterate_rows<kFW, kNY, kR, ACC, false>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2,
+                                                theta, s_ub, s_t1, s_t2);
     else
-      pd_iterate<kFW, kNY, kR, ACC, true>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta,
-                                          s_ub, s_t1, s_t2);
+      pd_iterate_rows<kFW, kNY, kR, ACC, true>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2,
+                                               theta, s_ub, s_t1, s_t2);
 
     // the interior back to global memory
     const int bx = tile % tiles_x, by = tile / tiles_x;

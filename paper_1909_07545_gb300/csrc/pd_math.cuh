@@ -122,3 +122,91 @@ __device__ __forceinline__ float px_primal(float u, float dv, const PxConst& c) 
 }
 
 }  // namespace fs
+
+// ------------------------------------------------------------ two pixels at once
+// The same steps on two pixels held as the components of float2 values,
+// with the packed FP32 operations of sm_100 and later (__ffma2_rn,
+// __fadd2_rn, __fmul2_rn round each component exactly as __fmaf_rn,
+// __fadd_rn, __fmul_rn do), so each component gets the bits of the scalar
+// functions above; a - b is taken as fma(b, -1, a), the same rounded value.
+// Minimum, maximum, the reciprocal square root and the mask selects stay
+// per component.  The iteration loop issues about half the FP32
+// instructions this way.
+namespace fs {
+
+struct PxConst2 {
+  float2 sx, sy, dinv, sd, tau, step, c0;
+};
+
+__device__ __forceinline__ PxConst2 px_pair(const PxConst& a, const PxConst& b) {
+  PxConst2 c;
+  c.sx = make_float2(a.sx, b.sx);
+  c.sy = make_float2(a.sy, b.sy);
+  c.dinv = make_float2(a.dinv, b.dinv);
+  c.sd = make_float2(a.sd, b.sd);
+  c.tau = make_float2(a.tau, b.tau);
+  c.step = make_float2(a.step, b.step);
+  c.c0 = make_float2(a.c0, b.c0);
+  return c;
+}
+
+// b - a, rounded once
+__device__ __forceinline__ float2 f2_sub(float2 b, float2 a) {
+  return __ffma2_rn(a, make_float2(-1.f, -1.f), b);
+}
+
+// px_dual on two pixels; m0, m1: their mask bits.
+template <bool MASKED = true>
+__device__ __forceinline__ void px_dual2(unsigned m0, unsigned m1, float2 ub, float2 right,
+                                         float2 below, const PxConst2& c, float2& p1,
+                                         float2& p2, float2& t1, float2& t2) {
+  float2 g1 = f2_sub(right, ub);
+  float2 g2 = f2_sub(below, ub);
+  if constexpr (MASKED) {
+    g1.x = (m0 & MASK_GX) ? g1.x : 0.f;
+    g1.y = (m1 & MASK_GX) ? g1.y : 0.f;
+    g2.x = (m0 & MASK_GY) ? g2.x : 0.f;
+    g2.y = (m1 & MASK_GY) ? g2.y : 0.f;
+  }
+  const float2 d = __ffma2_rn(c.sx, g1, __fmul2_rn(c.sy, g2));
+  const float2 nd = make_float2(-d.x, -d.y);
+  const float2 k1 = __ffma2_rn(c.sx, nd, g1);
+  const float2 k2 = __ffma2_rn(c.sy, nd, g2);
+  float2 q1 = __ffma2_rn(c.sd, k1, __fmul2_rn(p1, c.dinv));
+  float2 q2 = __ffma2_rn(c.sd, k2, __fmul2_rn(p2, c.dinv));
+  const float2 n2 = __ffma2_rn(q1, q1, __fmul2_rn(q2, q2));
+  const float2 s = make_float2(fminf(1.f, rsqrtf(n2.x)), fminf(1.f, rsqrtf(n2.y)));
+  q1 = __fmul2_rn(q1, s);
+  q2 = __fmul2_rn(q2, s);
+  p1 = q1;
+  p2 = q2;
+  const float2 dp = __ffma2_rn(c.sx, q1, __fmul2_rn(c.sy, q2));
+  const float2 ndp = make_float2(-dp.x, -dp.y);
+  t1 = __ffma2_rn(c.sx, ndp, q1);
+  t2 = __ffma2_rn(c.sy, ndp, q2);
+  if constexpr (MASKED) {
+    t1.x = (m0 & MASK_GX) ? t1.x : 0.f;
+    t1.y = (m1 & MASK_GX) ? t1.y : 0.f;
+    t2.x = (m0 & MASK_GY) ? t2.x : 0.f;
+    t2.y = (m1 & MASK_GY) ? t2.y : 0.f;
+  }
+}
+
+// px_div, px_primal and px_relax on two pixels.
+__device__ __forceinline__ float2 px_div2(float2 t1, float2 t1_left, float2 t2, float2 t2_up) {
+  return __fadd2_rn(f2_sub(t1, t1_left), f2_sub(t2, t2_up));
+}
+
+__device__ __forceinline__ float2 px_primal2(float2 u, float2 dv, const PxConst2& c) {
+  const float2 uh = __ffma2_rn(c.tau, dv, u);
+  const float2 r = f2_sub(c.c0, uh);
+  const float2 du = make_float2(fminf(fmaxf(r.x, -c.step.x), c.step.x),
+                                fminf(fmaxf(r.y, -c.step.y), c.step.y));
+  return __fadd2_rn(uh, du);
+}
+
+__device__ __forceinline__ float2 px_relax2(float2 un, float2 u, float2 theta) {
+  return __ffma2_rn(theta, f2_sub(un, u), un);
+}
+
+}  // namespace fs

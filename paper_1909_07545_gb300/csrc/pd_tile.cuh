@@ -79,6 +79,115 @@ __device__ __forceinline__ void pd_iterate(const PDParams& pp, int n_iters, int 
 
 }
 
+// pd_iterate with the rows paired for the packed FP32 operations (R even):
+// pair j holds rows j and j + H (H = R / 2), so the rows below pair j are
+// pair j + 1 and the rows above it pair j - 1; only the last pair's lower
+// neighbours and the first pair's upper ones come from other threads.  The
+// same values in the same order as pd_iterate (px_dual2 and friends), so
+// the same bits.
+template <int FW, int NY, int R, bool ACC, bool MASKED>
+__device__ __forceinline__ void pd_iterate2(const PDParams& pp, int n_iters, int tx, int ty,
+                                            unsigned mb, const PxConst (&c)[R], float (&u)[R],
+                                            float (&ub)[R], float (&p1)[R], float (&p2)[R],
+                                            float theta, float (*s_ub)[FW], float (*s_t1)[FW],
+                                            float (*s_t2)[FW]) {
+  static_assert(R % 2 == 0, "rows are paired");
+  constexpr int FH = NY * R, H = R / 2;
+  const int txr = min(tx + 1, FW - 1);
+  const int txl = max(tx - 1, 0);
+  PxConst2 c2[H];
+  float2 u2[H], ub2[H], p12[H], p22[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    c2[j] = px_pair(c[j], c[j + H]);
+    u2[j] = make_float2(u[j], u[j + H]);
+    ub2[j] = make_float2(ub[j], ub[j + H]);
+    p12[j] = make_float2(p1[j], p1[j + H]);
+    p22[j] = make_float2(p2[j], p2[j + H]);
+  }
+  float2 t12[H], t22[H];
+  float2 th2 = make_float2(theta, theta);
+#pragma unroll 1
+  for (int it = 0; it < n_iters; ++it) {
+    float4 sk = make_float4(1.f, 0.f, 0.f, 0.f);
+    if constexpr (ACC) {
+      sk = pp.sched[pp.k0 + it];
+      th2 = make_float2(sk.w, sk.w);
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const int f0 = ty * R + j, f1 = f0 + H;       // the pair's two footprint rows
+      const float2 right = make_float2(s_ub[f0][txr], s_ub[f1][txr]);
+      // below: rows j + 1 and j + H + 1 (the next pair), or for the last pair
+      // row R - 1... which is H (the first pair's second row) and the next
+      // thread's first row
+      const float2 below = (j + 1 < H) ? ub2[j + 1]
+                                       : make_float2(ub2[0].y, s_ub[min(ty * R + R, FH - 1)][tx]);
+      PxConst2 cr = c2[j];
+      if constexpr (ACC) {
+        cr.dinv = make_float2(sk.y, sk.y);
+        cr.sd = make_float2(sk.z, sk.z);
+      }
+      px_dual2<MASKED>(mb >> (3 * j), mb >> (3 * (j + H)), ub2[j], right, below, cr, p12[j],
+                       p22[j], t12[j], t22[j]);
+      s_t1[f0][tx] = t12[j].x;
+      s_t1[f1][tx] = t12[j].y;
+      if (j == H - 1) s_t2[ty][tx] = t22[j].y;       // row R - 1
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const int f0 = ty * R + j, f1 = f0 + H;
+      const float2 left = make_float2(s_t1[f0][txl], s_t1[f1][txl]);
+      // above: rows j - 1 and j + H - 1 (the previous pair), or for the first
+      // pair the thread above's last row (the top row of the footprint is
+      // halo: its own value) and row H - 1 (the last pair's first row)
+      const float2 up = (j > 0) ? t22[j - 1]
+                                : make_float2(ty > 0 ? s_t2[ty - 1][tx] : t22[0].x,
+                                              t22[H - 1].x);
+      const float2 dv = px_div2(t12[j], left, t22[j], up);
+      PxConst2 cr = c2[j];
+      if constexpr (ACC) {
+        cr.tau = __fmul2_rn(c2[j].tau, make_float2(sk.x, sk.x));
+        cr.step = __fmul2_rn(c2[j].step, make_float2(sk.x, sk.x));
+      }
+      const float2 un = px_primal2(u2[j], dv, cr);
+      ub2[j] = px_relax2(un, u2[j], th2);
+      u2[j] = un;
+      s_ub[f0][tx] = ub2[j].x;
+      s_ub[f1][tx] = ub2[j].y;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    u[j] = u2[j].x;
+    u[j + H] = u2[j].y;
+    ub[j] = ub2[j].x;
+    ub[j + H] = ub2[j].y;
+    p1[j] = p12[j].x;
+    p1[j + H] = p12[j].y;
+    p2[j] = p22[j].x;
+    p2[j + H] = p22[j].y;
+  }
+}
+
+// The iteration loop for R rows per thread: paired (pd_iterate2) when R is
+// even, else one row at a time.
+template <int FW, int NY, int R, bool ACC, bool MASKED>
+__device__ __forceinline__ void pd_iterate_rows(const PDParams& pp, int n_iters, int tx, int ty,
+                                                unsigned mb, const PxConst (&c)[R],
+                                                float (&u)[R], float (&ub)[R], float (&p1)[R],
+                                                float (&p2)[R], float theta, float (*s_ub)[FW],
+                                                float (*s_t1)[FW], float (*s_t2)[FW]) {
+  if constexpr (R % 2 == 0)
+    pd_iterate2<FW, NY, R, ACC, MASKED>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta, s_ub,
+                                        s_t1, s_t2);
+  else
+    pd_iterate<FW, NY, R, ACC, MASKED>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta, s_ub,
+                                       s_t1, s_t2);
+}
+
 // ACC: the accelerated step schedule of pp.sched (FP32 storage, scalar
 // steps): iteration it of the block uses entry pp.k0 + it for sigma (all
 // pixels), tau and the L1 step (scaled from the stored tau_0 values, 0 off
@@ -184,11 +293,11 @@ __device__ __forceinline__ void pd_tile(const LevelView& L, const PDState& in,
 #pragma unroll
   for (int r = 0; r < R; ++r) full = full && ok[r];
   if (__syncthreads_and(full))
-    pd_iterate<FW, NY, R, ACC, false>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta, s_ub,
-                                      s_t1, s_t2);
+    pd_iterate_rows<FW, NY, R, ACC, false>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta,
+                                           s_ub, s_t1, s_t2);
   else
-    pd_iterate<FW, NY, R, ACC, true>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta, s_ub,
-                                     s_t1, s_t2);
+    pd_iterate_rows<FW, NY, R, ACC, true>(pp, n_iters, tx, ty, mb, c, u, ub, p1, p2, theta,
+                                          s_ub, s_t1, s_t2);
 
   if (!col_in || tx < B || tx >= FW - B) return;
 #pragma unroll
