@@ -45,10 +45,13 @@ FP32_LANES = 152 * 128
 FOOTPRINTS = ["64x64 footprints, 512 threads", "32x32 footprints, 256 threads",
               "64x32 footprints", "64x64 footprints, 1024 threads",
               "32x32 footprints, 1024 threads", "32x32 footprints, 512 threads",
-              "64x64 footprints 48 columns apart, 1024 threads, TMA-staged"]
-FOOTPRINT_SIZE = [(64, 64), (32, 32), (64, 32), (64, 64), (32, 32), (32, 32), (64, 64)]
+              "64x64 footprints 48 columns apart, 1024 threads, TMA-staged",
+              "64x48 footprints, 768 threads"]
+FOOTPRINT_SIZE = [(64, 64), (32, 32), (64, 32), (64, 64), (32, 32), (32, 32), (64, 64),
+                  (64, 48)]
 TMA_FOOTPRINT = 6          # index of the TMA-staged footprint (choices 56..63)
 FIRST_TMA_CHOICE = 56
+FIRST_768_CHOICE = 64      # 64x48 footprints of 768 threads (choices 64..71)
 
 
 def interior(v, B):
@@ -60,9 +63,11 @@ def interior(v, B):
 
 
 def decode_choice(c):
-    """(depth, footprint index) of a schedule choice 1..63 (0: cluster -> None)."""
+    """(depth, footprint index) of a schedule choice 1..71 (0: cluster -> None)."""
     if c is None or c <= 0:
         return None
+    if c >= FIRST_768_CHOICE:
+        return c - FIRST_768_CHOICE + 1, 7
     if c >= FIRST_TMA_CHOICE:
         return c - FIRST_TMA_CHOICE + 1, TMA_FOOTPRINT
     if c > 48:
@@ -74,7 +79,7 @@ def schedule_label(c):
     """fs_autotune's per-level choice in words (0 = cluster; 1..48 = depth
     1..8 on each of the six footprints; 49..55 = depth 9..15 on 32x32
     footprints of 1024 threads; 56..63 = depth 1..8 on the TMA-staged
-    footprints)."""
+    footprints; 64..71 = depth 1..8 on 64x48 footprints of 768 threads)."""
     if c == 0:
         return "cluster"
     B, v = decode_choice(c)

@@ -108,7 +108,8 @@ fs_status fs_timing_read(fs_handle* h, double* ms, long long* launches,
  * apart, whose inputs the tensor memory accelerator copies into shared
  * memory while the CTA iterates on the previous footprint (one resident
  * CTA per SM walks the footprints; offered where the driver encodes the
- * level's tensor maps).  On TGV handles the
+ * level's tensor maps); and 64..71 = depth 1..8 on 64 x 48 footprints of
+ * 768 threads of 4 rows.  On TGV handles the
  * candidates are 0 = a dual and a primal launch per iteration and 8 v + d =
  * temporal-blocking depth d on a 32 x 32 footprint of 256 (v = 0, choices
  * 1..8), 1024 (v = 1, 9..16) or 512 threads (v = 2, 17..24), or a 64 x 32

@@ -399,15 +399,22 @@ int pd_block(const fs_handle* h, int l) {
 // 49..55 = depth 9..15 on 32 x 32 footprints of 1024 threads (deeper
 // blocking for the small levels, whose launches cost more than the extra
 // halo: they leave most SMs idle); 56..63 = depth 1..8 on the TMA-staged
-// 64 x 64 footprints of 1024 threads (k_pd_tma); TGV: 8 v + 1 .. 8 v + 8 =
-// depth on the TGV footprint v, 0..4, so 1..40; -1 = none.
+// 64 x 64 footprints of 1024 threads (k_pd_tma); 64..71 = depth 1..8 on
+// 64 x 48 footprints of 768 threads; TGV: 8 v + 1 .. 8 v + 8 = depth on the
+// TGV footprint v, 0..4, so 1..40; -1 = none.
 constexpr int kDeepChoices = 7;
 constexpr int kFirstTmaChoice = 8 * PD_TILE_COUNT + kDeepChoices + 1;
-constexpr int kMaxChoice = kFirstTmaChoice + 7;
+constexpr int kFirst768Choice = kFirstTmaChoice + 8;
+constexpr int kMaxChoice = kFirst768Choice + 7;
 constexpr int kMaxTgvChoice = 8 * kTgvVariants;
-bool is_tma_choice(int c, bool tgv) { return !tgv && c >= kFirstTmaChoice && c <= kMaxChoice; }
+bool is_tma_choice(int c, bool tgv) { return !tgv && c >= kFirstTmaChoice && c < kFirst768Choice; }
 void decode_choice(int c, bool tgv, int& depth, int& variant) {
   if (c <= 0) { depth = c; variant = -1; return; }
+  if (!tgv && c >= kFirst768Choice) {
+    depth = 1 + c - kFirst768Choice;
+    variant = PD_TILE_64x48_T768;
+    return;
+  }
   if (is_tma_choice(c, tgv)) {
     depth = 1 + c - kFirstTmaChoice;
     variant = PD_TILE_64_TMA;

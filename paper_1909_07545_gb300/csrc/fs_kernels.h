@@ -21,6 +21,11 @@ enum PDVariant {
 // The TMA-staged footprints of k_pd_tma.cu (64 x 64, 1024 threads of 4 rows,
 // 48 interior columns, depth <= 8): not a PDVariant of launch_pd.
 constexpr int PD_TILE_64_TMA = PD_TILE_COUNT;
+// 64 x 48, 64 x 12 threads of 4 rows (768 threads, up to 80 registers):
+// a launch_pd variant numbered after the TMA footprints.  A 512 x 512 level
+// at depth 6 has 150 of them, one per SM, where 64 x 64 footprints leave
+// 31 SMs idle.
+constexpr int PD_TILE_64x48_T768 = PD_TILE_COUNT + 1;
 enum PDClusterVariant { PD_CLUSTER_16 = 0, PD_CLUSTER_32 = 1 };
 
 __global__ void k_trajectory(DevCamDF cam, df tx, df ty, df tz, LevelView L);

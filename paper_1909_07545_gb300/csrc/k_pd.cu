@@ -222,6 +222,7 @@ static cudaError_t launch_pd_s(int variant, const LevelView& L, const PDState& i
     // are latency-bound, not issue-bound)
     case PD_TILE_32_T1024: return launch_pd_t<32, 32, 1, S>(L, in, out, pp, B, n, chained, st);
     case PD_TILE_32_T512: return launch_pd_t<32, 16, 2, S>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_64x48_T768: return launch_pd_t<64, 12, 4, S>(L, in, out, pp, B, n, chained, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -238,6 +239,7 @@ static cudaError_t launch_pd_acc(int variant, const LevelView& L, const PDState&
     case PD_TILE_64_T1024: return launch_pd_t<64, 16, 4, ST_F32, true>(L, in, out, pp, B, n, chained, st);
     case PD_TILE_32_T1024: return launch_pd_t<32, 32, 1, ST_F32, true>(L, in, out, pp, B, n, chained, st);
     case PD_TILE_32_T512: return launch_pd_t<32, 16, 2, ST_F32, true>(L, in, out, pp, B, n, chained, st);
+    case PD_TILE_64x48_T768: return launch_pd_t<64, 12, 4, ST_F32, true>(L, in, out, pp, B, n, chained, st);
     default: return cudaErrorInvalidValue;
   }
 }

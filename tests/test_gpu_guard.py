@@ -82,10 +82,11 @@ def test_guarded_solves_match_unguarded(small, prm):
 
 
 @pytest.mark.parametrize("choice", [1, 5, 8, 9, 12, 16, 17, 20, 24, 25, 29, 32, 33, 37, 40,
-                                    41, 45, 48, 49, 55, 56, 60, 63])
+                                    41, 45, 48, 49, 55, 56, 60, 63, 64, 69])
 def test_guarded_footprints_and_depths(small, choice):
     # every temporal-blocking footprint (64x64 of 512 and of 1024 threads; 32x32
-    # of 256, 512 and 1024 threads; 64x32; the TMA-staged 64x64) at several depths
+    # of 256, 512 and 1024 threads; 64x32; the TMA-staged 64x64; 64x48 of 768
+    # threads) at several depths
     sched = lambda s: s.set_schedule([choice] * small["levels"])
     _same(_run(small, True, prep=sched), _run(small, False, prep=sched))
 

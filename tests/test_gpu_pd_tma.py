@@ -127,7 +127,7 @@ def test_tma_footprints_in_a_graph_and_a_batch(kb):
 def test_tma_footprints_are_tried_by_the_autotuner(small):
     s = make_solver(small)
     choice = s.autotune(iters=6)
-    assert all(-1 <= c <= 63 for c in choice)
+    assert all(-1 <= c <= 71 for c in choice)
     s.close()
 
 

@@ -320,7 +320,7 @@ def test_set_schedule_reproduces_a_tuned_schedule(small):
     d3, _ = s2.solve(small["I0"], small["I1"], 2, 11)
     assert np.array_equal(np64(d1), np64(d3))
     with pytest.raises(fsb.FsError):
-        s2.set_schedule([64, -1, -1])
+        s2.set_schedule([72, -1, -1])
     s1.close()
     s2.close()
 

@@ -432,7 +432,7 @@ def test_pd_footprints_are_bit_exact(which, small, ragged):
     pair = small if which == "small" else ragged
     outs = []
     for choice in (-1, 3, 8, 12, 16, 19, 24, 26, 31, 32, 34, 40, 43, 48, 49, 52, 55, 56, 60,
-                   62, 63):
+                   62, 63, 64, 67, 70, 71):
         rng = np.random.default_rng(12)
         u, uw, p, Iu, rho0 = _pd_inputs(pair, rng)
         s = make_solver(pair)
@@ -480,7 +480,7 @@ def test_pd_footprints_agree_across_chained_launches(storage):
     # read through L1 then came from a launch two steps back.)
     p = f32pair(synth.plain_small(0, W=64, H=64))
     outs = []
-    for choice in (5, 13, 21, 29, 37, 45, 60):   # depth 5 on footprints 0..5 and the TMA one
+    for choice in (5, 13, 21, 29, 37, 45, 60, 68):   # depth 5 on every footprint
         s = make_solver(p, levels=1, storage=storage, pd_schedule=1)
         s.set_schedule([choice])
         s.solve(p["I0"], p["I1"], 1, 14)

@@ -73,5 +73,8 @@ def test_schedule_labels_decode_the_tuner_encoding():
     import re
     src = open(os.path.join(os.path.dirname(bench.__file__), "paper_1909_07545_gb300", "csrc",
                             "fs_kernels.h")).read()
-    assert int(re.search(r"PD_TILE_COUNT = (\d+)", src).group(1)) + 1 == len(bench.FOOTPRINTS)
+    assert int(re.search(r"PD_TILE_COUNT = (\d+)", src).group(1)) + 2 == len(bench.FOOTPRINTS)
     assert "constexpr int PD_TILE_64_TMA = PD_TILE_COUNT;" in src
+    assert "constexpr int PD_TILE_64x48_T768 = PD_TILE_COUNT + 1;" in src
+    assert bench.schedule_label(70) == "blocking x7 (64x48 footprints, 768 threads)"
+    assert bench.interior(7, 6) == (52, 36)
