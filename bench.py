@@ -34,7 +34,7 @@ PD_BYTES_PER_PX_ITER = 52.0   # unblocked FP32 traffic of one pixel-iteration (9
 # (cold L2, the mean of two consecutive launches; commands and figures in
 # profiles/k_pd_level0_kb1024.md and profiles/k_pd_tma_level0_kb1024.md).  A
 # choice without a capture of the current kernel reports traffic null.
-PD_L0_DRAM_BYTES_PER_LAUNCH = {31: 47.51e6, 61: 47.65e6}
+PD_L0_DRAM_BYTES_PER_LAUNCH = {7: 47.44e6, 31: 47.44e6, 61: 47.65e6}
 # FP32 instructions of one pixel-iteration of the primal-dual step as written
 # in pd_math.cuh, an FMA counted as one: dual 24 (2 differences, 7 products,
 # 9 FMAs, the reciprocal square root, a min and 4 mask selects), divergence 3,
