@@ -210,6 +210,92 @@ k_tgv_blocked(LevelView L, TgvState in, TgvState out, TgvParams tp, int B, int n
   __syncthreads();
 
   const int txr = min(tx + 1, FW - 1), txl = max(tx - 1, 0);
+  if constexpr (R % 2 == 0) {
+    // rows in pairs (j, j + H) on the packed FP32 operations, as in
+    // pd_iterate2: the rows below pair j are pair j + 1, those above it
+    // pair j - 1; the same values in the same order, so the same bits
+    constexpr int H = R / 2;
+    TgvConst2 c2[H];
+    float2 u2[H], ub2[H], v12[H], v22[H], vb12[H], vb22[H], p12[H], p22[H];
+    float2 q112[H], q122[H], q212[H], q222[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      c2[j] = tgv_pair(c[j], c[j + H]);
+      u2[j] = make_float2(u[j], u[j + H]);
+      ub2[j] = make_float2(ub[j], ub[j + H]);
+      v12[j] = make_float2(v1[j], v1[j + H]);
+      v22[j] = make_float2(v2[j], v2[j + H]);
+      vb12[j] = make_float2(vb1[j], vb1[j + H]);
+      vb22[j] = make_float2(vb2[j], vb2[j + H]);
+      p12[j] = make_float2(p1[j], p1[j + H]);
+      p22[j] = make_float2(p2[j], p2[j + H]);
+      q112[j] = make_float2(q11[j], q11[j + H]);
+      q122[j] = make_float2(q12[j], q12[j + H]);
+      q212[j] = make_float2(q21[j], q21[j + H]);
+      q222[j] = make_float2(q22[j], q22[j + H]);
+    }
+    const float2 th2 = make_float2(tp.theta, tp.theta);
+    float2 t12[H], t22[H], qx12[H], qx22[H], qy12[H], qy22[H];
+    const int fnext = min(ty * R + R, FH - 1);     // the thread below's first row
+    const int fprev = max(ty * R - 1, 0);          // the thread above's last row
+#pragma unroll 1
+    for (int it = 0; it < n_iters; ++it) {
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        const int f0 = ty * R + j, f1 = f0 + H;
+        const bool last = j + 1 == H;
+        const float2 ub_b = last ? make_float2(ub2[0].y, s_ub[fnext][tx]) : ub2[j + 1];
+        const float2 vb1_b = last ? make_float2(vb12[0].y, s_vb1[fnext][tx]) : vb12[j + 1];
+        const float2 vb2_b = last ? make_float2(vb22[0].y, s_vb2[fnext][tx]) : vb22[j + 1];
+        tgv_px_dual2(mb >> (3 * j), mb >> (3 * (j + H)), ub2[j],
+                     make_float2(s_ub[f0][txr], s_ub[f1][txr]), ub_b, vb12[j],
+                     make_float2(s_vb1[f0][txr], s_vb1[f1][txr]), vb1_b, vb22[j],
+                     make_float2(s_vb2[f0][txr], s_vb2[f1][txr]), vb2_b, c2[j], tp, p12[j],
+                     p22[j], q112[j], q122[j], q212[j], q222[j], t12[j], t22[j], qx12[j],
+                     qx22[j], qy12[j], qy22[j]);
+        s_t1[f0][tx] = t12[j].x;   s_t1[f1][tx] = t12[j].y;
+        s_t2[f0][tx] = t22[j].x;   s_t2[f1][tx] = t22[j].y;
+        s_qx1[f0][tx] = qx12[j].x; s_qx1[f1][tx] = qx12[j].y;
+        s_qx2[f0][tx] = qx22[j].x; s_qx2[f1][tx] = qx22[j].y;
+        s_qy1[f0][tx] = qy12[j].x; s_qy1[f1][tx] = qy12[j].y;
+        s_qy2[f0][tx] = qy22[j].x; s_qy2[f1][tx] = qy22[j].y;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        const int f0 = ty * R + j, f1 = f0 + H;
+        // above: the previous pair, or for the first pair the thread above's
+        // last row (the footprint's top row reads itself) and row H - 1
+        const float2 t2_u = j > 0 ? t22[j - 1] : make_float2(s_t2[fprev][tx], t22[H - 1].x);
+        const float2 qy1_u = j > 0 ? qy12[j - 1] : make_float2(s_qy1[fprev][tx], qy12[H - 1].x);
+        const float2 qy2_u = j > 0 ? qy22[j - 1] : make_float2(s_qy2[fprev][tx], qy22[H - 1].x);
+        tgv_px_primal2(t12[j], make_float2(s_t1[f0][txl], s_t1[f1][txl]), t22[j], t2_u,
+                       qx12[j], make_float2(s_qx1[f0][txl], s_qx1[f1][txl]), qy12[j], qy1_u,
+                       qx22[j], make_float2(s_qx2[f0][txl], s_qx2[f1][txl]), qy22[j], qy2_u,
+                       p12[j], p22[j], c2[j], th2, u2[j], ub2[j], v12[j], v22[j], vb12[j],
+                       vb22[j]);
+        s_ub[f0][tx] = ub2[j].x;   s_ub[f1][tx] = ub2[j].y;
+        s_vb1[f0][tx] = vb12[j].x; s_vb1[f1][tx] = vb12[j].y;
+        s_vb2[f0][tx] = vb22[j].x; s_vb2[f1][tx] = vb22[j].y;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      u[j] = u2[j].x;     u[j + H] = u2[j].y;
+      ub[j] = ub2[j].x;   ub[j + H] = ub2[j].y;
+      v1[j] = v12[j].x;   v1[j + H] = v12[j].y;
+      v2[j] = v22[j].x;   v2[j + H] = v22[j].y;
+      vb1[j] = vb12[j].x; vb1[j + H] = vb12[j].y;
+      vb2[j] = vb22[j].x; vb2[j + H] = vb22[j].y;
+      p1[j] = p12[j].x;   p1[j + H] = p12[j].y;
+      p2[j] = p22[j].x;   p2[j + H] = p22[j].y;
+      q11[j] = q112[j].x; q11[j + H] = q112[j].y;
+      q12[j] = q122[j].x; q12[j + H] = q122[j].y;
+      q21[j] = q212[j].x; q21[j + H] = q212[j].y;
+      q22[j] = q222[j].x; q22[j + H] = q222[j].y;
+    }
+  } else {
   float t1[R], t2[R], qx1[R], qx2[R], qy1[R], qy2[R];
 #pragma unroll 1
   for (int it = 0; it < n_iters; ++it) {
@@ -246,6 +332,7 @@ k_tgv_blocked(LevelView L, TgvState in, TgvState out, TgvParams tp, int B, int n
       s_vb2[fy][tx] = vb2[r];
     }
     __syncthreads();
+  }
   }
 
   if (!col_in || tx < B || tx >= FW - B) return;
