@@ -915,6 +915,10 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "traffic_note": "ncu DRAM read + write bytes of one level-0 launch of "
                                      "this schedule, cold L2 (null: no capture of it)",
+                     # the measured DRAM bytes over the same warm launch time: what
+                     # the kernel actually draws from HBM (L2 serves the halo overlap)
+                     "traffic_gbs": traffic / launch_s / 1e9 if traffic else None,
+                     "traffic_frac": traffic / launch_s / 1e9 / peak if traffic else None,
                      "kernel": ("k_pd_tma" if dec is not None and dec[1] == TMA_FOOTPRINT
                                 else "k_pd") + " level 0 (1024x1024), " + (
                          schedule_label(l0_choice) if l0_choice is not None else "default"),
