@@ -375,7 +375,9 @@ def serve_leg(rigs, sizes, seed, seconds, rate, inflight, warm_mode=1, storage="
     open_loop = srv.stats(reset=True)
 
     # saturated: keep every rig's ring full for a fixed number of requests
-    n_sat = 8 * n_rigs
+    # (64 per rig, about a second: long enough that the ramp-up and the
+    # drain do not decide the rate)
+    n_sat = 64 * n_rigs
     t1 = time.perf_counter()
     for i in range(n_sat):
         done_q.put(submit(i % n_rigs))
@@ -471,6 +473,7 @@ def uneven_batch_leg(seed, stream, steps, warmup, storage="f16", per_size=16,
 
     sols, tuned = handles(storage)
     bt = Batch(sols, stream=stream)
+    coarse = bt.autotune(100)          # the coarse levels' schedule for throughput
     res = {}
     for k in (0, 1, 2, 4):
         bt.set_finest_limit(k)
@@ -510,6 +513,7 @@ def uneven_batch_leg(seed, stream, steps, warmup, storage="f16", per_size=16,
                                      "ms_per_64": plain_ms},
             "schedule_per_size": {str(W): [schedule_label(c) for c in t]
                                   for W, t in tuned.items()},
+            "batch_coarse_schedule": "each pair's own" if coarse < 0 else schedule_label(coarse),
             "render_s": render_s}
 
 
@@ -557,6 +561,7 @@ def batch_1024_leg(seed, stream, tuned, steps, warmup, n=8, storage="f16"):
     outs_d = [torch.empty_like(a) for a in I0s]
     outs_z = [torch.empty_like(a) for a in I0s]
     bt = Batch(sols, stream=stream)
+    coarse = bt.autotune(100)          # the coarse levels' schedule for throughput
     res = {}
     for k in (0, 1, 2):
         bt.set_finest_limit(k)
@@ -579,6 +584,7 @@ def batch_1024_leg(seed, stream, tuned, steps, warmup, n=8, storage="f16"):
     return {"workload": f"{n} distinct 1024x1024 Kannala-Brandt pairs (seeds +100..), 5 levels "
                         f"x 10 warps x 100 iterations, {storage} storage, one graph",
             "by_finest_limit": res,
+            "batch_coarse_schedule": "each pair's own" if coarse < 0 else schedule_label(coarse),
             "best_frames_per_s": max(r["frames_per_s"] for r in res.values())}
 
 

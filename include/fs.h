@@ -266,6 +266,22 @@ fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0, const float* con
  * fs_batch_solve, which captures a new graph.  FS_EINVAL for k < 0. */
 fs_status fs_batch_set_finest_limit(fs_batch* b, int k);
 
+/* Tune the batch for throughput.  fs_autotune times a pair alone, so it
+ * gives the coarse levels (latency-bound) short dependent chains per launch;
+ * many pairs sharing the GPU want few, large footprints with little halo
+ * instead.  Every handle keeps its own schedule for its two finest levels;
+ * for its coarser levels (level 2 and up) this tries, besides every
+ * handle's own choices, one common schedule for all pairs from a fixed set
+ * (fs_autotune encoding 32, 69, 8, 45), timing `iters` primal-dual
+ * iterations on every coarse level of every pair with all pairs at once
+ * on the batch's streams, and keeps the fastest (written into the handles,
+ * as fs_set_schedule would).  choice (may be NULL): the common coarse
+ * choice kept, or -1 for the handles' own.  Results are unchanged (every
+ * schedule gives the same bits).  Overwrites the coarse levels' state and
+ * synchronises the batch stream; FS_EINVAL for TGV handles or iters < 1.
+ * A batch graph is recaptured after any schedule change of its handles. */
+fs_status fs_batch_autotune(fs_batch* b, int iters, int* choice);
+
 /* Free the batch (its streams, events and graph; not the handles). */
 fs_status fs_batch_destroy(fs_batch* b);
 

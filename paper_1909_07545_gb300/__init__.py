@@ -46,6 +46,7 @@ EXPORTED = ["fs_default_params", "fs_create", "fs_set_pose", "fs_level_size",
             "fs_buffer_read", "fs_buffer_write", "fs_run_stage", "fs_stage_prerotate",
             "fs_stage_depth", "fs_timing_enable", "fs_timing_read", "fs_pd_iterate_noalloc",
             "fs_batch_create", "fs_batch_solve", "fs_batch_set_finest_limit",
+            "fs_batch_autotune",
             "fs_batch_destroy", "fs_autotune", "fs_set_schedule", "fs_energy", "fs_state_bytes",
             "fs_guard_check", "fs_guard_clobber", "fs_set_wait_limit", "fs_persist_stall",
             "fs_check_waits",
@@ -141,6 +142,7 @@ def load_library():
         "fs_batch_solve": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), i, i,
                            ctypes.POINTER(_P), ctypes.POINTER(_P)],
         "fs_batch_set_finest_limit": [_P, i],
+        "fs_batch_autotune": [_P, i, ctypes.POINTER(ctypes.c_int)],
         "fs_batch_destroy": [_P],
         "fs_autotune": [_P, i, _P],
         "fs_set_schedule": [_P, _P],
@@ -442,6 +444,13 @@ class Batch:
     def set_finest_limit(self, k):
         """At most k pairs on their finest level at once (0: no bound)."""
         _check(self.lib.fs_batch_set_finest_limit(self.b, int(k)))
+
+    def autotune(self, iters=100):
+        """fs_batch_autotune: the coarse levels' common schedule for throughput;
+        returns the choice kept (-1: the handles' own)."""
+        c = ctypes.c_int(-1)
+        _check(self.lib.fs_batch_autotune(self.b, int(iters), ctypes.byref(c)))
+        return c.value
 
     def solve(self, I0s, I1s, warps, iters, inits=None, disps=None, depths=None):
         """Device tensors per pair; returns lists of (disparity, depth) tensors."""

@@ -290,6 +290,9 @@ struct fs_handle {
   PersistPlan* plan = nullptr;
   unsigned long long wait_ns = 2000000000ull;
   int persist_stall = 0;
+  // bumped whenever a launch argument a captured graph holds changes (the
+  // schedule, the wait bound, the stall aid): batches key their graphs on it
+  unsigned sched_gen = 0;
   // set to FS_ETIMEOUT by a TMA-staged primal-dual launch whose copy wait
   // ran out (in the arena; read and cleared by fs_check_waits)
   int* pd_status = nullptr;
@@ -1519,12 +1522,13 @@ extern "C" fs_status fs_batch_solve(fs_batch* b, const float* const* d_I0,
   if (warps < 1 || iters < 1) return fail(FS_EINVAL, "warps and iters must be >= 1");
   const int n = (int)b->h.size();
   std::vector<const void*> key;
-  key.reserve(6 * n);
+  key.reserve(7 * n);
   for (int i = 0; i < n; ++i) {
     if (!d_I0[i] || !d_I1[i]) return fail(FS_EINVAL, "null input image for pair %d", i);
     fs_status s;
     if ((s = ensure_schedule(b->h[i], iters)) != FS_OK) return s;
     key.push_back(b->h[i]->sched);
+    key.push_back((const void*)(uintptr_t)b->h[i]->sched_gen);
     key.push_back(d_I0[i]);
     key.push_back(d_I1[i]);
     key.push_back(d_init ? d_init[i] : nullptr);
@@ -1631,6 +1635,118 @@ extern "C" fs_status fs_batch_set_finest_limit(fs_batch* b, int k) {
   }
   b->finest_limit = k;
   return FS_OK;
+}
+
+// The common coarse-level schedules fs_batch_autotune tries besides every
+// handle's own: blocking depth 8 on 64 x 64 footprints of 1024 threads,
+// depth 6 on 64 x 48 of 768, depth 8 on 64 x 64 of 512, depth 5 on 32 x 32
+// of 512 -- few, large footprints with little halo, which is what many
+// pairs sharing the GPU want, where a pair alone wants short dependent
+// chains per launch.
+static const int kBatchCoarseChoices[] = {32, 69, 8, 45};
+
+extern "C" fs_status fs_batch_autotune(fs_batch* b, int iters, int* choice) {
+  if (!b) return fail(FS_EINVAL, "null batch");
+  if (iters < 1) return fail(FS_EINVAL, "iters must be >= 1");
+  if (choice) *choice = -1;
+  const int n = (int)b->h.size();
+  // every handle's own coarse choices (to restore when they win)
+  std::vector<std::vector<std::pair<int, int>>> own(n);
+  bool any = false;
+  for (int i = 0; i < n; ++i) {
+    fs_handle* h = b->h[i];
+    if (h->prm.regularizer == FS_REG_TGV)
+      return fail(FS_EINVAL, "fs_batch_autotune: TGV handles are tuned alone (fs_autotune)");
+    fs_status s;
+    if ((s = ensure_schedule(h, iters)) != FS_OK) return s;
+    for (int l = 2; l < h->L; ++l) {
+      own[i].push_back({h->lv[l].tuned, h->lv[l].tuned_variant});
+      any = true;
+    }
+  }
+  if (!any) return FS_OK;
+  FS_CUDA(cudaStreamSynchronize(b->stream));
+  if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+  auto apply = [&](int c) {
+    for (int i = 0; i < n; ++i) {
+      fs_handle* h = b->h[i];
+      if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+      ++h->sched_gen;
+      h->has_state = false;                     // the trials overwrite the coarse levels
+      for (int l = 2; l < h->L; ++l) {
+        HostLevel& L = h->lv[l];
+        if (c < 0) {
+          L.tuned = own[i][l - 2].first;
+          L.tuned_variant = own[i][l - 2].second;
+        } else {
+          decode_choice(c, false, L.tuned, L.tuned_variant);
+        }
+      }
+    }
+  };
+  // `iters` iterations on every coarse level of every pair, each pair on its
+  // own lane (coarsest first), all pairs at once: one graph per candidate,
+  // best of three replays after one
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FS_CUDA(cudaEventCreate(&e0));
+  FS_CUDA(cudaEventCreate(&e1));
+  auto time_it = [&](float& best) -> fs_status {
+    for (int i = 0; i < n; ++i)                 // constants current before the capture
+      for (int l = 2; l < b->h[i]->L; ++l) b->h[i]->lv[l].consts_stale = true;
+    FS_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    fs_status s = FS_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->origin);
+    for (int i = 0; i < n && s == FS_OK && e == cudaSuccess; ++i) {
+      e = cudaStreamWaitEvent(b->lanes[i], b->fork, 0);
+      for (int l = b->h[i]->L - 1; l >= 2 && s == FS_OK && e == cudaSuccess; --l)
+        s = run_pd(b->h[i], l, iters, b->lanes[i]);
+      if (s == FS_OK && e == cudaSuccess) e = cudaEventRecord(b->joins[i], b->lanes[i]);
+      if (s == FS_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->joins[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->origin, &g);
+    if (s != FS_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return fail(FS_ECUDA, "fs_batch_autotune capture: %s",
+                  cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(FS_ECUDA, "fs_batch_autotune: %s", cudaGetErrorString(e));
+    best = 3.4e38f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, b->stream);
+      if (e == cudaSuccess) e = cudaGraphLaunch(x, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && rep > 0 && ms < best) best = ms;
+    }
+    cudaGraphExecDestroy(x);
+    if (e != cudaSuccess) return fail(FS_ECUDA, "fs_batch_autotune: %s", cudaGetErrorString(e));
+    return FS_OK;
+  };
+  fs_status st = FS_OK;
+  float best_ms = 3.4e38f;
+  int best_c = -1;
+  const int n_cand = 1 + (int)(sizeof(kBatchCoarseChoices) / sizeof(int));
+  for (int k = 0; k < n_cand && st == FS_OK; ++k) {
+    const int c = k == 0 ? -1 : kBatchCoarseChoices[k - 1];
+    apply(c);
+    float ms = 0.f;
+    if ((st = time_it(ms)) == FS_OK && ms < best_ms) {
+      best_ms = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  apply(st == FS_OK ? best_c : -1);
+  if (st == FS_OK && choice) *choice = best_c;
+  return st;
 }
 
 extern "C" fs_status fs_batch_destroy(fs_batch* b) {
@@ -1808,6 +1924,7 @@ extern "C" fs_status fs_autotune(fs_handle* h, int iters, int* choice) {
   if (iters < 1) return fail(FS_EINVAL, "iters must be >= 1");
   if ((s = ensure_schedule(h, iters)) != FS_OK) return s;
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  ++h->sched_gen;
   h->has_state = false;   // the trial runs overwrite every level's state
   cudaEvent_t e0, e1;
   FS_CUDA(cudaEventCreate(&e0));
@@ -1903,6 +2020,7 @@ extern "C" fs_status fs_set_schedule(fs_handle* h, const int* choice) {
       return fail(FS_EINVAL, "level %d: no tensor maps for the TMA footprints", l);
   }
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  ++h->sched_gen;
   for (int l = 0; l < h->L; ++l) {
     int c = choice[l];
     HostLevel& L = h->lv[l];
@@ -1917,6 +2035,7 @@ extern "C" fs_status fs_set_wait_limit(fs_handle* h, double seconds) {
   if (!(seconds > 0 && seconds <= 3600)) return fail(FS_EINVAL, "wait limit must be in (0, 3600] s");
   h->wait_ns = (unsigned long long)(seconds * 1e9);
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // captured the old bound
+  ++h->sched_gen;
   return FS_OK;
 }
 
@@ -1925,6 +2044,7 @@ extern "C" fs_status fs_persist_stall(fs_handle* h, int stall) {
   if ((s = check_handle(h)) != FS_OK) return s;
   h->persist_stall = stall ? 1 : 0;
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  ++h->sched_gen;
   return FS_OK;
 }
 
