@@ -106,6 +106,18 @@ def test_host_side_validation(lib):
     assert lib.fs_create(None, None, 64, 64, 1, None, None, ctypes.byref(h)) == -1
 
 
+@pytest.mark.parametrize("W,H", [(0, 64), (64, 0), (0, 0), (3, 64), (64, 3), (-8, 64),
+                                 (32769, 64), (64, 32769)])
+def test_empty_and_out_of_range_sizes_are_rejected_on_the_host(lib, W, H):
+    # an empty image, one below the 4-pixel minimum of the coarsest level, or
+    # one past the 32768-pixel row limit of the 32-bit plane indexing
+    st, msg = _create([EQ, EQ], W=W, H=H, levels=1)
+    assert st == -1 and "image size" in msg
+    n = ctypes.c_size_t(123)
+    assert lib.fs_state_bytes(W, H, 1, None, ctypes.byref(n)) == -1
+    assert n.value == 123 and "image size" in lib.fs_last_error().decode()
+
+
 def test_state_bytes_counts_the_level_planes(lib):
     # mask bytes + 11 FP32 planes + 10 storage-typed planes + 3 float2 planes
     # per level (pitch = width rounded up to 32, planes on 256-byte
