@@ -116,7 +116,9 @@ fs_status fs_server_submit(fs_server* s, int rig, const float* h_I0, const float
 /* Wait up to timeout_s seconds (< 0: no limit) for a request.  On
  * completion returns the request's own status (FS_OK or the error it met),
  * forgets the request, and sets *latency_ms (may be NULL).  FS_ETIMEOUT if
- * it is still pending (it stays known); FS_EINVAL for an unknown id. */
+ * it is still pending (it stays known); FS_EINVAL for an unknown id, or
+ * while another thread is already waiting for the same request (threads
+ * may wait for different requests at once). */
 fs_status fs_server_wait(fs_server* s, long long req_id, double timeout_s, double* latency_ms);
 
 /* Cancel a request that is still queued: it will not run, and

@@ -107,6 +107,7 @@ struct Request {
   float* depth = nullptr;
   Clock::time_point t_submit, t_done;
   bool done = false;
+  bool waited = false;            // a thread is in fs_server_wait for it
   fs_status status = FS_OK;
   std::string msg;
 };
@@ -451,16 +452,22 @@ fs_status fs_server_wait(fs_server* s, long long req_id, double timeout_s, doubl
   auto it = s->known.find(req_id);
   if (it == s->known.end()) return set_error(FS_EINVAL, "unknown request %lld", req_id);
   Request* r = it->second;
+  // one waiter per request: the one that sees it done deletes it
+  if (r->waited) return set_error(FS_EINVAL, "request %lld is already being waited for", req_id);
+  r->waited = true;
   auto ready = [&] { return r->done; };
   if (timeout_s < 0) {
     s->cv_done.wait(lk, ready);
   } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) {
+    r->waited = false;
     return set_error(FS_ETIMEOUT, "request %lld still pending", req_id);
   }
   if (latency_ms) *latency_ms = ms_between(r->t_submit, r->t_done);
   st = r->status;
   std::string msg = r->msg;
-  s->known.erase(it);
+  // by key: a submission while this thread slept may have rehashed the map
+  // and invalidated the iterator found above
+  s->known.erase(req_id);
   delete r;
   lk.unlock();
   if (st != FS_OK) return set_error(st, "request %lld: %s", req_id, msg.c_str());

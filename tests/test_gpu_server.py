@@ -121,6 +121,63 @@ def test_served_in_a_mix_equals_served_alone_and_lone_handle(rigs, warm_mode):
         alone.close()
 
 
+def test_concurrent_waiters_while_submitting(rigs):
+    # one waiter thread per rig sits in fs_server_wait while the main thread
+    # keeps submitting, so the server's request table grows (and rehashes)
+    # under the sleeping waiters; every request completes, with the bits of
+    # the same requests waited for one by one from a single thread
+    import queue
+    import threading
+    seq = [0, 1, 2, 1, 0, 1, 2, 1]
+
+    def run(concurrent):
+        srv = _server(max_inflight=2)
+        ids = [_add(srv, q) for q in rigs]
+        outs, reqs, errs = {}, [], []
+        qs = [queue.Queue() for _ in rigs]
+
+        def waiter(i):
+            while True:
+                x = qs[i].get()
+                if x is None:
+                    return
+                try:
+                    srv.wait(x)
+                except Exception as e:        # reported below
+                    errs.append(e)
+
+        ths = [threading.Thread(target=waiter, args=(i,)) for i in range(len(rigs))]
+        if concurrent:
+            for t in ths:
+                t.start()
+        for k, f in enumerate(seq):
+            for i, (r, q) in enumerate(zip(ids, rigs)):
+                d, z = _outs(q)
+                I0, I1, _ = q["frames"][f]
+                x = srv.submit(r, _pinned(I0), _pinned(I1), d, z)
+                outs[(i, k)] = (d, z)
+                (qs[i].put if concurrent else reqs.append)(x)
+        if concurrent:
+            for qq in qs:
+                qq.put(None)
+            for t in ths:
+                t.join()
+        else:
+            for x in reqs:
+                srv.wait(x)
+        st = srv.stats()
+        srv.close()
+        return outs, st, errs
+
+    a, st, errs = run(True)
+    assert not errs, errs
+    assert st["completed"] == len(seq) * len(rigs) and st["failed"] == 0
+    b, _, _ = run(False)
+    for key in a:
+        assert np.array_equal(a[key][0].numpy(), b[key][0].numpy()), key
+        assert np.array_equal(a[key][1].numpy(), b[key][1].numpy(), equal_nan=True), key
+
+
 def test_served_under_guard_bands(rigs, monkeypatch):
     # FS_GUARD_BANDS=1: every rig handle the server makes has guard bands and
     # every served solve ends with fs_guard_check, whose failure fails the
