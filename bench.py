@@ -15,6 +15,7 @@ the data path).  Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import subprocess
@@ -336,43 +337,65 @@ def serve_leg(rigs, sizes, seed, seconds, rate, inflight, warm_mode=1, storage="
         I0, I1 = frames[r][cycle[pos[r] % len(cycle)]]
         pos[r] += 1
         d, z = outs[r][slot]
-        return srv.submit(ids[r], I0, I1, d, z), r, slot
+        return srv.submit(ids[r], I0, I1, d, z), slot
 
-    done_q = queue.Queue()
+    # one waiter thread per rig returns the rig's result buffers as its
+    # requests complete (a rig's requests run in order): a single waiter
+    # taking requests in submission order would hold a rig's finished slot
+    # behind another rig's slower request, and the generator, needing that
+    # slot, would stall
+    done_q = [queue.Queue() for _ in range(n_rigs)]
 
-    def waiter():
+    def waiter(r):
         while True:
-            item = done_q.get()
+            item = done_q[r].get()
             if item is None:
                 return
-            req, r, slot = item
+            req, slot = item
             srv.wait(req)
             free[r].put(slot)
 
-    th = threading.Thread(target=waiter, daemon=True)
-    th.start()
+    ths = [threading.Thread(target=waiter, args=(r,), daemon=True) for r in range(n_rigs)]
+    for th in ths:
+        th.start()
     # warm-up: every rig's cold first frame, then two warm frames each
     for _ in range(3):
         for r in range(n_rigs):
-            done_q.put(submit(r))
+            done_q[r].put(submit(r))
     srv.drain()
     srv.stats(reset=True)
 
-    # open loop at the offered rate
+    # open loop at the offered rate.  The generator runs with Python's
+    # cyclic collector frozen and off: a collection pass over the process's
+    # objects stops this thread for milliseconds, and the arrivals it holds
+    # back would reach the server as one burst.  late = how long after its
+    # scheduled arrival each request's submission returned (the generator's
+    # own delay, which the server's latency figures do not include).
     arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds * 1.2) + 16))
     arr = arr[arr < seconds]
-    which = rng.integers(0, n_rigs, size=len(arr))
-    start = time.perf_counter()
-    stalls = 0
-    for ta, r in zip(arr, which):
-        now = time.perf_counter() - start
-        if ta > now:
-            time.sleep(ta - now)
-        if free[int(r)].empty():
-            stalls += 1
-        done_q.put(submit(int(r)))
-    srv.drain()
+    which = [int(r) for r in rng.integers(0, n_rigs, size=len(arr))]
+    arr = [float(a) for a in arr]
+    late = np.zeros(len(arr))
+    gc.collect()
+    gc.freeze()
+    gc.disable()
+    try:
+        start = time.perf_counter()
+        stalls = 0
+        for k, (ta, r) in enumerate(zip(arr, which)):
+            now = time.perf_counter() - start
+            if ta > now:
+                time.sleep(ta - now)
+            if free[r].empty():
+                stalls += 1
+            done_q[r].put(submit(r))
+            late[k] = time.perf_counter() - start - ta
+        srv.drain()
+    finally:
+        gc.enable()
+        gc.unfreeze()
     open_loop = srv.stats(reset=True)
+    late_ms = 1e3 * late
 
     # saturated: keep every rig's ring full for a fixed number of requests
     # (64 per rig, about a second: long enough that the ramp-up and the
@@ -380,12 +403,14 @@ def serve_leg(rigs, sizes, seed, seconds, rate, inflight, warm_mode=1, storage="
     n_sat = 64 * n_rigs
     t1 = time.perf_counter()
     for i in range(n_sat):
-        done_q.put(submit(i % n_rigs))
+        done_q[i % n_rigs].put(submit(i % n_rigs))
     srv.drain()
     sat = srv.stats(reset=True)
     sat_wall = time.perf_counter() - t1
-    done_q.put(None)
-    th.join()
+    for q in done_q:
+        q.put(None)
+    for th in ths:
+        th.join()
     srv.close()
     px = {W: W * W for W in set(sizes)}
     mean_px = float(np.mean([px[W] for W in sizes]))
@@ -400,6 +425,9 @@ def serve_leg(rigs, sizes, seed, seconds, rate, inflight, warm_mode=1, storage="
         "frames_per_s": open_loop["frames_per_s"], "p50_ms": open_loop["p50_ms"],
         "p99_ms": open_loop["p99_ms"], "max_ms": open_loop["max_ms"],
         "mean_ms": open_loop["mean_ms"], "submit_stalls": stalls,
+        "submit_late_ms": {"p50": float(np.percentile(late_ms, 50)),
+                           "p99": float(np.percentile(late_ms, 99)),
+                           "max": float(late_ms.max()) if len(late_ms) else 0.0},
         "cold": int(open_loop["cold"]), "evictions": int(open_loop["evictions"]),
         "resident_gb": open_loop["resident_bytes"] / 1e9,
         "saturated_frames_per_s": sat["frames_per_s"], "saturated_requests": n_sat,
