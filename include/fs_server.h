@@ -140,7 +140,10 @@ fs_status fs_server_stats_read(fs_server* s, fs_server_stats* out, int reset);
 fs_status fs_server_evict_all(fs_server* s);
 
 /* Stop the dispatcher, wait for in-flight work, free everything.  Requests
- * still queued are dropped. */
+ * still queued are dropped.  No other thread may be inside any fs_server_*
+ * call on s (fs_server_wait and fs_server_drain included) when it is called,
+ * or call one afterwards: a dropped request never completes, and s is freed.
+ * Wait for or drain what you submitted first. */
 fs_status fs_server_destroy(fs_server* s);
 
 #ifdef __cplusplus
