@@ -41,6 +41,19 @@ def test_kb_zero_coefficients_is_equidistant():
     assert np.allclose(project(kb0, X), project(EQ, X), atol=1e-12)
 
 
+def test_kb_polynomial_at_one_and_two_radians():
+    # at theta = 1 every odd power is 1, so r = 1 + k1 + k2 + k3 + k4; at
+    # theta = 2 the powers are 8, 32, 128 and 512 (worked by hand for the
+    # coefficients 0.03, -0.01, 0.004, 0.001): a dropped term, a wrong power
+    # or two coefficients swapped changes one of the two values
+    assert float(radial(KB, 1.0)) == pytest.approx(1.025, abs=1e-14)
+    assert float(radial(KB, 2.0)) == pytest.approx(2.944, abs=1e-13)
+    # a ray 1 rad off the axis towards +x lands fx r(1) right of the centre
+    x = project(KB, np.array([math.sin(1.0), 0.0, math.cos(1.0)]))
+    assert x[0] == pytest.approx(511.5 + 320.0 * 1.025, abs=1e-10)
+    assert x[1] == pytest.approx(512.5, abs=1e-12)
+
+
 @pytest.mark.parametrize("cam", [EQ, KB, PH, UCM, EUCM])
 def test_round_trip(cam):
     rng = np.random.default_rng(1)

@@ -123,6 +123,21 @@ def test_prerotation_of_identity_is_identity():
     assert np.abs(prerotate(I1, np.zeros((40, 50, 2))) - I1).max() == 0.0
 
 
+def test_prerotation_samples_the_second_image_at_x_plus_c():
+    # I1'(x) = I1(x + c(x)) (Sec. IV-A); bilinear sampling reproduces an
+    # affine image exactly, so a constant field (0.25, -0.5) shifts a ramp
+    H, W = 12, 16
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    I1 = 1.0 + 2.0 * px + 3.0 * py
+    cf = np.zeros((H, W, 2))
+    cf[..., 0] = 0.25
+    cf[..., 1] = -0.5
+    out = prerotate(I1, cf)
+    ref = 1.0 + 2.0 * (px + 0.25) + 3.0 * (py - 0.5)
+    inner = (px + 0.25 <= W - 1) & (py - 0.5 >= 0)
+    assert np.abs(out - ref)[inner].max() < 1e-12
+
+
 @pytest.mark.parametrize("cam", [EQ, KB, PH])
 def test_triangulation_recovers_known_points(cam):
     rng = np.random.default_rng(6)
@@ -144,8 +159,11 @@ def test_triangulation_recovers_known_points(cam):
 def test_virtual_translation_is_rt_t():
     a = math.radians(1.5)
     R = np.array([[1, 0, 0], [0, math.cos(a), -math.sin(a)], [0, math.sin(a), math.cos(a)]])
-    t = np.array([-0.12, 0.0, 0.0])
+    # t off the rotation axis: along x alone R t = R^T t, and a transposed R
+    # would pass
+    t = np.array([-0.12, 0.02, 0.01])
     tp = virtual_translation(R, t)
+    assert np.abs(tp - R @ t).max() > 1e-4
     # a point seen by camera 1 (X1 = R X0 + t) is R X1' in the virtual frame
     X0 = np.array([0.3, -0.2, 2.0])
     assert np.allclose(R @ (X0 + tp), R @ X0 + t, atol=1e-15)

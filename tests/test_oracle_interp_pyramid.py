@@ -75,6 +75,17 @@ def test_downsample_definition_and_constants():
     assert np.abs(d - (0.1 * (2 * X + 0.5) + 0.3 * (2 * Y + 0.5))).max() < 1e-13
 
 
+def test_downsample_averages_only_the_children_inside_the_mask():
+    # one parent over the block [[1, 2], [3, 4]]: with the top row in the
+    # mask the mean is (1 + 2) / 2, with one child only that child, and with
+    # no child in the mask all four count
+    img = np.array([[1.0, 2.0], [3.0, 4.0]])
+    for f in (downsample, downsample_fast):
+        assert f(img, np.array([[True, True], [False, False]]), 1, 1)[0, 0] == 1.5
+        assert f(img, np.array([[False, False], [False, True]]), 1, 1)[0, 0] == 4.0
+        assert f(img, np.zeros((2, 2), bool), 1, 1)[0, 0] == 2.5
+
+
 def test_upsample_linear_interior_and_mask():
     Hc = Wc = 10
     Y, X = np.mgrid[0:Hc, 0:Wc].astype(float)

@@ -1,0 +1,185 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case below plants one slip in the oracle (on the CPU, for the duration
+of the case): a dropped term, a flipped sign, a transposed operand, a wrong
+constant or a forgotten clamp, in the function of the paper's step it
+names.  Then it runs the pins that guard that step and requires at least one
+of them to fail.  A slip that every pin let through would mean that the
+oracle could carry it unnoticed into every parity test.
+
+The slip is planted in every loaded module that holds the function (the
+oracle's own modules and the pin modules that imported it by name), so the
+pins see it wherever they call it.
+"""
+import dataclasses
+import importlib
+import sys
+
+import numpy as np
+import pytest
+
+import test_oracle_camera as cam_pins
+import test_oracle_geometry as geo_pins
+import test_oracle_interp_pyramid as ip_pins
+import test_oracle_tgv as tgv_pins
+import test_oracle_variational as var_pins
+from oracle.camera import KANNALA_BRANDT
+
+
+def _plant(monkeypatch, modname, name, make):
+    mod = importlib.import_module(modname)
+    orig = getattr(mod, name)
+    mutant = make(orig)
+    for mname, m in list(sys.modules.items()):
+        if m is None or not mname.startswith(("oracle", "test_oracle", "synth")):
+            continue
+        if getattr(m, name, None) is orig:
+            monkeypatch.setattr(m, name, mutant)
+
+
+def _kb_without_k4(orig):
+    def radial(calib, theta):
+        if calib.model == KANNALA_BRANDT:
+            calib = dataclasses.replace(calib, k=tuple(calib.k[:3]) + (0.0,))
+        return orig(calib, theta)
+    return radial
+
+
+def _kb_k3_k4_swapped(orig):
+    def radial(calib, theta):
+        if calib.model == KANNALA_BRANDT:
+            k = tuple(calib.k)
+            calib = dataclasses.replace(calib, k=(k[0], k[1], k[3], k[2]))
+        return orig(calib, theta)
+    return radial
+
+
+def _shrink_as_printed(orig):
+    # Eq. 13 as printed: +rho_bar / I_u in the third case
+    def shrink(uh, Iu, rho0, u_w, tau, lam):
+        out = orig(uh, Iu, rho0, u_w, tau, lam)
+        Iu = np.asarray(Iu, dtype=np.float64)
+        r = rho0 + Iu * (uh - u_w)
+        thr = tau * lam * Iu * Iu
+        inner = (np.abs(r) <= thr) & (Iu != 0.0)
+        return np.where(inner, uh + r / np.where(Iu != 0.0, Iu, 1.0), out)
+    return shrink
+
+
+def _negate_third(orig):
+    def f(*a, **k):
+        Iu, rho0, g = orig(*a, **k)
+        return Iu, -rho0, g
+    return f
+
+
+def _negate_first(orig):
+    def f(*a, **k):
+        Iu, rho0, g = orig(*a, **k)
+        return -Iu, rho0, g
+    return f
+
+
+# (paper step, oracle module, function, slip, pins that must catch it)
+CASES = [
+    ("Kannala-Brandt r(theta): k4 theta^9 dropped", "oracle.camera", "radial",
+     _kb_without_k4, [cam_pins.test_kb_polynomial_at_one_and_two_radians]),
+    ("Kannala-Brandt r(theta): k3 and k4 transposed", "oracle.camera", "radial",
+     _kb_k3_k4_swapped, [cam_pins.test_kb_polynomial_at_one_and_two_radians]),
+    ("pi: fx and fy transposed", "oracle.camera", "project",
+     lambda o: lambda c, X: o(dataclasses.replace(c, fx=c.fy, fy=c.fx), X),
+     [cam_pins.test_pinhole_closed_form]),
+    ("pi^-1: y component of the ray negated", "oracle.camera", "unproject",
+     lambda o: lambda c, px, py: o(c, px, py) * np.array([1.0, -1.0, 1.0]),
+     [lambda: cam_pins.test_round_trip(cam_pins.KB)]),
+    ("Eq. 6-7 trajectory field: direction reversed", "oracle.geometry", "trajectory_vector",
+     lambda o: lambda *a, **k: -o(*a, **k),
+     [geo_pins.test_equidistant_centre_row_points_left,
+      geo_pins.test_pinhole_forward_translation_is_radial_from_epipole]),
+    ("Sec. IV-A calibration field: R used untransposed", "oracle.geometry",
+     "calibration_field",
+     lambda o: lambda c0, c1, R, *a, **k: o(c0, c1, np.asarray(R).reshape(3, 3).T, *a, **k),
+     [geo_pins.test_calibration_field_identity_and_axis_roll]),
+    ("Sec. IV-A pre-rotation: I1 sampled at x - c", "oracle.geometry", "prerotate",
+     lambda o: lambda I1, cf: o(I1, -cf),
+     [geo_pins.test_prerotation_samples_the_second_image_at_x_plus_c]),
+    ("Sec. IV-A virtual translation: R t instead of R^T t", "oracle.geometry",
+     "virtual_translation",
+     lambda o: lambda R, t: np.asarray(R, float).reshape(3, 3) @ np.asarray(t, float).reshape(3),
+     [geo_pins.test_virtual_translation_is_rt_t]),
+    ("Sec. III-D triangulation: camera-1 centre at +t'", "oracle.geometry", "triangulate_range",
+     lambda o: lambda c, px, py, wx, wy, tp: o(c, px, py, wx, wy, -np.asarray(tp)),
+     [lambda: geo_pins.test_triangulation_recovers_known_points(geo_pins.EQ)]),
+    ("Eq. 9 bilinear warp: x and y transposed", "oracle.interp", "bilinear",
+     lambda o: lambda img, x, y: o(img, y, x),
+     [ip_pins.test_bilinear_reproduces_affine_and_samples]),
+    ("bicubic trajectory sampling: Keys a = -0.75", "oracle.interp", "keys_weight",
+     lambda o: lambda s, a=-0.5: o(s, -0.75),
+     [ip_pins.test_keys_kernel_partition_of_unity_and_quadratic_reproduction]),
+    ("Sec. IV-B pyramid: the mask ignored in the box mean", "oracle.pyramid", "downsample_fast",
+     lambda o: lambda img, m, Wc, Hc: o(img, np.ones_like(m, dtype=bool), Wc, Hc),
+     [ip_pins.test_downsample_averages_only_the_children_inside_the_mask]),
+    ("Sec. IV-B upsampling: disparity not doubled", "oracle.pyramid", "upsample",
+     lambda o: lambda v, mc, Wf, Hf, mf, scale=2.0: o(v, mc, Wf, Hf, mf, 1.0),
+     [ip_pins.test_upsample_linear_interior_and_mask]),
+    ("Sec. IV-B scaled calibration: pixel-centre offset dropped", "oracle.pyramid",
+     "scaled_calib",
+     lambda o: lambda c, lv: dataclasses.replace(o(c, lv), cx=c.cx * 0.5 ** lv,
+                                                 cy=c.cy * 0.5 ** lv),
+     [ip_pins.test_level_sizes_and_scaled_calibration]),
+    ("Eq. 11 gradient: components transposed", "oracle.variational", "grad",
+     lambda o: lambda u, m1, m2: o(u, m1, m2)[::-1],
+     [var_pins.test_grad_forward_difference_and_neumann]),
+    ("Eq. 11 divergence: sign flipped", "oracle.variational", "div",
+     lambda o: lambda q1, q2, m1, m2: -o(q1, q2, m1, m2),
+     [var_pins.test_div_is_negative_adjoint_of_grad]),
+    ("Eq. 12 tensor: n and n_perp entries transposed", "oracle.variational", "tensor_sqrt",
+     lambda o: lambda *a: o(*a)[::-1],
+     [var_pins.test_tensor_eigenstructure]),
+    ("Eq. 11 dual step: Huber term dropped", "oracle.variational", "dual_step",
+     lambda o: lambda *a: o(*a[:-1], 0.0),
+     [var_pins.test_dual_step_is_huber_conjugate_prox]),
+    ("Eq. 13 shrinkage: third case with the printed sign", "oracle.variational", "shrink",
+     _shrink_as_printed, [var_pins.test_shrink_is_data_term_prox]),
+    ("Eq. 11 primal step: divergence with the wrong sign", "oracle.variational", "primal_step",
+     lambda o: lambda u, p1, p2, *a: o(u, -p1, -p2, *a),
+     [lambda: var_pins.test_energy_descends_over_a_warp(2)]),
+    ("Eq. 3/5 linearisation: rho0 = I0 - I1(x + w)", "oracle.variational", "warp_linearize",
+     _negate_third, [var_pins.test_warp_linearize_on_affine_image]),
+    ("Eq. 7 derivative: taken along -gamma'", "oracle.variational", "warp_linearize",
+     _negate_first, [var_pins.test_warp_linearize_on_affine_image]),
+    ("Algorithm 1 clip: delta-u not clamped", "oracle.variational", "clip_update",
+     lambda o: lambda u, uw, w, g, du, M: o(u, uw, w, g, np.inf, M),
+     [var_pins.test_clip_update_cases]),
+    ("diagonal steps: tau and sigma exchanged", "oracle.variational", "precondition",
+     lambda o: lambda *a, **k: (lambda t, s1, s2: (s1, t, t.copy()))(*o(*a, **k)),
+     [var_pins.test_preconditioned_steps_bound_the_operator]),
+    ("accelerated steps: factor 2 of theta_k dropped", "oracle.variational", "accel_schedule",
+     lambda o: lambda g, n, *a, **k: o(0.5 * g, n, *a, **k),
+     [var_pins.test_accel_schedule_recursion]),
+    ("Eq. 10 TGV: divergence of q with the wrong sign", "oracle.tgv", "div_q",
+     lambda o: lambda *a: tuple(-x for x in o(*a)),
+     [tgv_pins.test_jacobian_divergence_adjoint]),
+]
+
+
+@pytest.mark.parametrize("step,modname,name,make,pins", CASES, ids=[c[0] for c in CASES])
+def test_a_planted_mistake_fails_a_pin(monkeypatch, step, modname, name, make, pins):
+    _plant(monkeypatch, modname, name, make)
+    caught = []
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, ValueError, IndexError, FloatingPointError) as e:
+            caught.append((getattr(pin, "__name__", "pin"), type(e).__name__))
+    assert caught, f"no pin caught: {step}"
+
+
+def test_the_pins_pass_on_the_oracle_as_it_is():
+    # the same pins without a planted mistake
+    seen = set()
+    for _, _, _, _, pins in CASES:
+        for pin in pins:
+            if pin not in seen:
+                seen.add(pin)
+                pin()
