@@ -86,6 +86,25 @@ def test_warm_start_walks_the_trajectory_field():
     sel = nd.binary_erosion(Mc, iterations=12)
     assert np.abs(coarse - fine)[sel].max() < 0.05
     assert np.abs(np.linalg.norm(fine, axis=-1)[sel] - 4.0).max() < 0.05
+    # and the limit is the epipolar curve itself (Sec. III-B): the point 4 px
+    # along the projected 3-D line pi(r0 + s t^), s >= 0, traced by brute
+    # force (a single straight step d gamma'(x) misses it where the curve bends)
+    that = np.array([-0.1, 0.02, 0.0]) / np.hypot(0.1, 0.02)
+    ys, xs = np.nonzero(sel)
+    rng = np.random.default_rng(7)
+    off_straight = 0.0
+    for k in rng.choice(len(xs), 24, replace=False):
+        x0 = np.array([xs[k], ys[k]], float)
+        r0 = oracle.unproject(cam, x0[0], x0[1])
+        sv = np.linspace(0.0, 0.5, 20001)
+        pts = oracle.project(cam, r0[None, :] + sv[:, None] * that[None, :])
+        arc = np.concatenate([[0.0], np.cumsum(np.linalg.norm(np.diff(pts, axis=0), axis=-1))])
+        j = int(np.searchsorted(arc, 4.0))
+        f = (4.0 - arc[j - 1]) / (arc[j] - arc[j - 1])
+        ref = pts[j - 1] + f * (pts[j] - pts[j - 1]) - x0
+        assert np.linalg.norm(fine[ys[k], xs[k]] - ref) < 0.02, (xs[k], ys[k])
+        off_straight = max(off_straight, float(np.linalg.norm(4.0 * g[ys[k], xs[k]] - ref)))
+    assert off_straight > 0.05            # the sample reaches where the curves bend
 
 
 def test_continuation_with_the_rebuilt_field_is_the_disparity_warm_start():

@@ -19,6 +19,7 @@ import numpy as np
 import pytest
 
 import test_oracle_camera as cam_pins
+import test_oracle_end_to_end as e2e_pins
 import test_oracle_geometry as geo_pins
 import test_oracle_interp_pyramid as ip_pins
 import test_oracle_tgv as tgv_pins
@@ -160,6 +161,16 @@ CASES = [
     ("Eq. 10 TGV: divergence of q with the wrong sign", "oracle.tgv", "div_q",
      lambda o: lambda *a: tuple(-x for x in o(*a)),
      [tgv_pins.test_jacobian_divergence_adjoint]),
+    ("Eq. 10 TGV: duals projected on the unit ball, not alpha1 / alpha0", "oracle.tgv",
+     "_project", lambda o: lambda r, *c: o(1.0, *c),
+     [lambda: tgv_pins.test_fixed_point_satisfies_the_saddle_point_conditions(
+         True, (17.0, 1.2, 2.0))]),
+    ("Eq. 10 TGV steps: sigma_q doubled", "oracle.tgv", "tgv_steps",
+     lambda o: lambda *a, **k: (lambda tu, tv, sp, sq: (tu, tv, sp, 2.0 * sq))(*o(*a, **k)),
+     [tgv_pins.test_preconditioned_steps_bound_the_operator]),
+    ("warm start: the whole disparity in one step along gamma'", "oracle.solve",
+     "warm_start_w", lambda o: lambda d, g, M, du: o(d, g, M, 1e9),
+     [e2e_pins.test_warm_start_walks_the_trajectory_field]),
 ]
 
 
