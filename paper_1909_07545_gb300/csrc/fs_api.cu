@@ -120,21 +120,20 @@ DevCamDF dev_cam_df(const fs_calib& c, double fx, double fy, double cx, double c
 }
 
 // cuTensorMapEncodeTiled, looked up once through the runtime (the library
-// links the runtime only); null if the driver does not provide it.
+// links the runtime only); null if the driver does not provide it.  The
+// lookup is a function-local static's initialiser, which C++ runs once even
+// when several threads create handles at the same time.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool looked = false;
-  if (!looked) {
-    looked = true;
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    else
-      cudaGetLastError();
-  }
+      return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    cudaGetLastError();
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
