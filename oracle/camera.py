@@ -51,7 +51,8 @@ class Calib:
 
 
 def calib_from_dict(d) -> Calib:
-    """Build a Calib from the plain-dict interchange format of the generators."""
+    """Build a Calib from the plain-dict interchange format of the generators
+    (the camera models Sec. III-B admits)."""
     if isinstance(d, Calib):
         return d
     m = d["model"]
@@ -63,7 +64,8 @@ def calib_from_dict(d) -> Calib:
 
 
 def radial(calib: Calib, theta):
-    """Normalised image radius r(theta) of the model."""
+    """Normalised image radius r(theta) of the model: the radial part of the
+    projection pi that Sec. III-B needs (any model with a defined pi)."""
     theta = np.asarray(theta, dtype=np.float64)
     if calib.model == PINHOLE:
         return np.tan(theta)
@@ -81,12 +83,14 @@ def radial(calib: Calib, theta):
 
 
 def fov_radius(calib: Calib) -> float:
-    """Normalised radius of the FOV circle, r(theta_max)."""
+    """Normalised radius of the FOV circle, r(theta_max) (the image region
+    the method works on, Sec. IV-B's mask)."""
     return float(radial(calib, calib.theta_max))
 
 
 def project(calib: Calib, X):
-    """pi: 3-D points (..., 3) in the camera frame -> pixels (..., 2)."""
+    """pi: 3-D points (..., 3) in the camera frame -> pixels (..., 2)
+    (Sec. III-A, III-B)."""
     X = np.asarray(X, dtype=np.float64)
     x, y, z = X[..., 0], X[..., 1], X[..., 2]
     rho = np.hypot(x, y)
@@ -99,7 +103,8 @@ def project(calib: Calib, X):
 
 
 def _theta_of_radius(calib: Calib, rn):
-    """Solve r(theta) = rn for theta in [0, theta_max] by bisection (FP64).
+    """Solve r(theta) = rn for theta in [0, theta_max] by bisection (FP64): the
+    inverse radial map behind pi^-1 (Sec. III-D).
 
     rn beyond r(theta_max) returns theta_max (callers mask such pixels out).
     """
@@ -119,7 +124,8 @@ def _theta_of_radius(calib: Calib, rn):
 
 
 def unproject(calib: Calib, px, py):
-    """pi^-1: pixel coordinates -> unit rays (..., 3) in the camera frame."""
+    """pi^-1: pixel coordinates -> unit rays (..., 3) in the camera frame
+    (Sec. III-B, III-D)."""
     px = np.asarray(px, dtype=np.float64)
     py = np.asarray(py, dtype=np.float64)
     mx = (px - calib.cx) / calib.fx
@@ -134,6 +140,7 @@ def unproject(calib: Calib, px, py):
 
 
 def is_monotone(calib: Calib, samples: int = 10000) -> bool:
-    """True when r(theta) strictly increases on [0, theta_max] (sampled)."""
+    """True when r(theta) strictly increases on [0, theta_max] (sampled): where
+    pi^-1 of Sec. III-D is defined."""
     th = np.linspace(0.0, calib.theta_max, samples)
     return bool(np.all(np.diff(radial(calib, th)) > 0.0))

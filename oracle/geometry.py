@@ -50,7 +50,8 @@ def trajectory_vector(calib, tprime, px, py, depth=1.0, s=SMALL_MOTION):
 
 
 def trajectory_field(calib, tprime, W, H, mask):
-    """Trajectory field (H, W, 2) of one pyramid level; 0 outside the mask."""
+    """Trajectory field (H, W, 2) of one pyramid level; 0 outside the mask
+    (Sec. III-B, Eq. 6-7)."""
     py, px = np.mgrid[0:H, 0:W].astype(np.float64)
     g = trajectory_vector(calib, tprime, px, py)
     return np.where(mask[..., None], g, 0.0)
@@ -74,7 +75,8 @@ def prerotate(I1, cfield):
 
 
 def triangulate_range(calib, px, py, wx, wy, tprime):
-    """Range along the camera-0 ray of x, triangulated with the ray of x + w.
+    """Range along the camera-0 ray of x, triangulated with the ray of x + w
+    (Sec. III-D).
 
     Least-squares midpoint of the lines l0 * r0 and C + l1 * r1 with unit
     rays r0 = pi^-1(x), r1 = pi^-1(x + w) and the virtual camera-1 centre

@@ -20,11 +20,14 @@ KEYS_A = -0.5
 
 
 def _clamp_pos(v, n):
+    """Sample positions clamped to the image: the clamp-to-edge sampling of
+    the warp (Eq. 9) and of the trajectory field (Sec. III-B)."""
     return np.clip(np.asarray(v, dtype=np.float64), 0.0, float(n - 1))
 
 
 def bilinear(img, x, y):
-    """Bilinear sample of img (H, W[, C]) at positions x, y (same shape)."""
+    """Bilinear sample of img (H, W[, C]) at positions x, y (same shape): the
+    warp of I1 along w (Eq. 9, Sec. III-C)."""
     img = np.asarray(img, dtype=np.float64)
     H, W = img.shape[:2]
     xc = _clamp_pos(x, W)
@@ -43,7 +46,8 @@ def bilinear(img, x, y):
 
 
 def keys_weight(s, a: float = KEYS_A):
-    """Keys (1981) cubic convolution kernel."""
+    """Keys (1981) cubic convolution kernel, for the bicubic interpolation of
+    the trajectory field (Sec. III-B)."""
     s = np.abs(np.asarray(s, dtype=np.float64))
     w_in = ((a + 2.0) * s - (a + 3.0)) * s * s + 1.0
     w_out = ((a * s - 5.0 * a) * s + 8.0 * a) * s - 4.0 * a
@@ -51,7 +55,8 @@ def keys_weight(s, a: float = KEYS_A):
 
 
 def bicubic(img, x, y):
-    """Keys-bicubic sample of img (H, W[, C]) at positions x, y."""
+    """Keys-bicubic sample of img (H, W[, C]) at positions x, y: the trajectory
+    field read at x + w (Sec. III-B)."""
     img = np.asarray(img, dtype=np.float64)
     H, W = img.shape[:2]
     xc = _clamp_pos(x, W)

@@ -26,6 +26,7 @@ from .camera import Calib, radial
 
 
 def level_sizes(W, H, levels):
+    """Level sizes of the coarse-to-fine pyramid at scale 0.5 (Sec. IV-B)."""
     sizes = [(int(W), int(H))]
     for _ in range(1, levels):
         w, h = sizes[-1]
@@ -34,6 +35,8 @@ def level_sizes(W, H, levels):
 
 
 def scaled_calib(calib: Calib, level: int) -> Calib:
+    """Calibration of pyramid level `level`: focal lengths and principal
+    point scaled by 2^-level about pixel centres (Sec. IV-B)."""
     s = 0.5 ** level
     return Calib(calib.model, calib.fx * s, calib.fy * s,
                  (calib.cx + 0.5) * s - 0.5, (calib.cy + 0.5) * s - 0.5,
@@ -41,14 +44,16 @@ def scaled_calib(calib: Calib, level: int) -> Calib:
 
 
 def fov_mask(calib: Calib, W, H):
-    """Pixels whose ray lies within the FOV half-angle (bool, (H, W))."""
+    """Pixels whose ray lies within the FOV half-angle (bool, (H, W)): the
+    mask of each pyramid level (Sec. IV-B)."""
     py, px = np.mgrid[0:H, 0:W].astype(np.float64)
     rn = np.hypot((px - calib.cx) / calib.fx, (py - calib.cy) / calib.fy)
     return rn <= float(radial(calib, calib.theta_max))
 
 
 def downsample(img, mask_fine, Wc, Hc):
-    """2x2 box mean over in-mask children (all children if none is in mask)."""
+    """2x2 box mean over in-mask children (all children if none is in mask):
+    one pyramid step (Sec. IV-B)."""
     img = np.asarray(img, dtype=np.float64)
     Hf, Wf = img.shape
     out = np.zeros((Hc, Wc))
@@ -63,7 +68,8 @@ def downsample(img, mask_fine, Wc, Hc):
 
 
 def downsample_fast(img, mask_fine, Wc, Hc):
-    """Vectorised twin of :func:`downsample` (same arithmetic per parent)."""
+    """Vectorised twin of :func:`downsample` (same arithmetic per parent; one
+    pyramid step of Sec. IV-B)."""
     img = np.asarray(img, dtype=np.float64)
     Hf, Wf = img.shape
     s_in = np.zeros((Hc, Wc)); n_in = np.zeros((Hc, Wc))
@@ -85,7 +91,8 @@ def downsample_fast(img, mask_fine, Wc, Hc):
 
 
 def upsample(v, mask_c, Wf, Hf, mask_f, scale=2.0):
-    """Masked bilinear x2 upsampling of a (Hc, Wc[, C]) field to (Hf, Wf[, C])."""
+    """Masked bilinear x2 upsampling of a (Hc, Wc[, C]) field to (Hf, Wf[, C]):
+    u and w carried to the next finer level and doubled (Sec. IV-B)."""
     v = np.asarray(v, dtype=np.float64)
     Hc, Wc = v.shape[:2]
     py, px = np.mgrid[0:Hf, 0:Wf].astype(np.float64)

@@ -35,6 +35,8 @@ from .variational import (Params, check_accel, clip_update, grad_masks, pd_itera
 
 
 def level_data(I0l, M, prm: Params):
+    """Per-level constants: T^1/2 (Eq. 12), the gradient masks and the
+    diagonal steps of the primal-dual iterations (Sec. III-D)."""
     a, b, c = tensor_sqrt(I0l, M, prm.beta, prm.eta)
     m1, m2 = grad_masks(M)
     tau, sig1, sig2 = precondition(a, b, c, M, m1, m2, prm.precond)
@@ -55,7 +57,8 @@ def tgv_zero_state(shape):
 
 def solve_level_warps(I0l, I1l, gamma, lv, u, w, p1, p2, warps, iters,
                       prm: Params, on_iter=None, level=0, tgv=None):
-    """Run `warps` warps of `iters` primal-dual iterations on one level.
+    """Run `warps` warps of `iters` primal-dual iterations on one level
+    (Algorithm 1).
 
     tgv: for the TGV-L1 energy, the dict of v and q (TGV_STATE), carried
     across the warps like p and updated in place."""
@@ -106,7 +109,9 @@ def warm_start_w(d, gamma, M, du_max):
 
 def solve(I0, I1, cam0, cam1, R, t, levels, warps, iters, prm: Params = Params(),
           on_iter=None, keep_levels=False, level_hook=None, d_init=None, w_init=None):
-    """Full method on one pair; returns disparity (px), range (m), w and more.
+    """Full method on one pair; returns disparity (px), range (m), w and more:
+    Algorithm 1 inside the pre-rotation of Sec. IV-A and the coarse-to-fine
+    scheme of Sec. IV-B, then the triangulation of Sec. III-D.
 
     level_hook(level, I0_l, I1_l) -> (I0_l, I1_l), when given, may replace
     each level's images after the pyramid is built (a probe for how the

@@ -44,19 +44,22 @@ from .variational import apply_T, div, grad, precondition, shrink
 
 
 def grad_v(v1, v2, m1, m2):
-    """Jacobian of v: (dv1/dx, dv1/dy, dv2/dx, dv2/dy), masked forward differences."""
+    """Jacobian of v: (dv1/dx, dv1/dy, dv2/dx, dv2/dy), masked forward differences
+    (the second-order term of Eq. 10)."""
     a, b = grad(v1, m1, m2)
     c, d = grad(v2, m1, m2)
     return a, b, c, d
 
 
 def div_q(q11, q12, q21, q22, m1, m2):
-    """Exact negative adjoint of :func:`grad_v`: one divergence per row of q."""
+    """Exact negative adjoint of :func:`grad_v`: one divergence per row of q
+    (Eq. 11)."""
     return div(q11, q12, m1, m2), div(q21, q22, m1, m2)
 
 
 def tgv_steps(a, b, c, M, m1, m2, precond=True):
-    """(tau_u, tau_v, sigma_p, sigma_q) for K(u, v) = (T^1/2 grad u - v, grad v)."""
+    """(tau_u, tau_v, sigma_p, sigma_q) for K(u, v) = (T^1/2 grad u - v, grad v):
+    the preconditioned steps of Sec. III-D for Eq. 10-11."""
     M = np.asarray(M, dtype=bool)
     if not precond:
         s = 1.0 / np.sqrt(12.0)
@@ -75,6 +78,7 @@ def tgv_steps(a, b, c, M, m1, m2, precond=True):
 
 
 def _project(r, *comps):
+    """Projection onto the ball of radius r (the dual constraints of Eq. 11)."""
     n = np.maximum(1.0, np.sqrt(sum(c * c for c in comps)) / r) if r > 0 else None
     if n is None:
         return tuple(np.zeros_like(c) for c in comps)
@@ -82,7 +86,8 @@ def _project(r, *comps):
 
 
 def tgv_iteration(st, lv, prm):
-    """One iteration on state st (u, ubar, v1, v2, vb1, vb2, p1, p2, q11, q12,
+    """One iteration of Eq. 11 (TGV-L1) on state st (u, ubar, v1, v2, vb1, vb2,
+    p1, p2, q11, q12,
     q21, q22, Iu, rho0, u_w) with level data lv (a, b, c, m1, m2, M and the
     TGV steps tau_u, tau_v, sig_p, sig_q)."""
     a, b, c, m1, m2, M = lv["a"], lv["b"], lv["c"], lv["m1"], lv["m2"], lv["M"]

@@ -63,7 +63,8 @@ class Params:
 
 
 def grad_masks(M):
-    """Neumann masks m1, m2: forward difference along x / y is inside M."""
+    """Neumann masks m1, m2: forward difference along x / y is inside M (the
+    discrete gradient of Eq. 11)."""
     M = np.asarray(M, dtype=bool)
     m1 = np.zeros_like(M)
     m2 = np.zeros_like(M)
@@ -73,7 +74,7 @@ def grad_masks(M):
 
 
 def grad(u, m1, m2):
-    """Masked forward-difference gradient (g1 along x, g2 along y)."""
+    """Masked forward-difference gradient (g1 along x, g2 along y) of Eq. 11."""
     g1 = np.zeros_like(u, dtype=np.float64)
     g2 = np.zeros_like(u, dtype=np.float64)
     g1[:, :-1] = u[:, 1:] - u[:, :-1]
@@ -82,7 +83,8 @@ def grad(u, m1, m2):
 
 
 def div(q1, q2, m1, m2):
-    """Exact negative adjoint of :func:`grad`: <grad u, q> = -<u, div q>."""
+    """Exact negative adjoint of :func:`grad`: <grad u, q> = -<u, div q>, the
+    divergence of Eq. 11."""
     a = np.where(m1, q1, 0.0)
     b = np.where(m2, q2, 0.0)
     d = a + b
@@ -136,7 +138,8 @@ def tensor_sqrt(I0, M, beta, eta):
 
 
 def precondition(a, b, c, M, m1, m2, precond=True):
-    """Diagonal step sizes (tau, sigma1, sigma2) for K = T^1/2 grad."""
+    """Diagonal step sizes (tau, sigma1, sigma2) for K = T^1/2 grad: the
+    preconditioning of Sec. III-D (Pock-Chambolle, alpha = 1)."""
     if not precond:
         s = 1.0 / np.sqrt(8.0)
         f = np.full(a.shape, s)
@@ -158,11 +161,12 @@ def precondition(a, b, c, M, m1, m2, precond=True):
 
 
 def apply_T(a, b, c, v1, v2):
+    """T^1/2 = [[a, b], [b, c]] applied to the field (v1, v2) (Eq. 12)."""
     return a * v1 + b * v2, b * v1 + c * v2
 
 
 def dual_step(p1, p2, ubar, a, b, c, m1, m2, sig1, sig2, eps):
-    """Dual ascent with the Huber resolvent and the projection P."""
+    """Dual ascent with the Huber resolvent and the projection P (Eq. 11)."""
     g1, g2 = grad(ubar, m1, m2)
     k1, k2 = apply_T(a, b, c, g1, g2)
     q1 = (p1 + sig1 * k1) / (1.0 + sig1 * eps)
@@ -185,7 +189,8 @@ def shrink(uh, Iu, rho0, u_w, tau, lam):
 
 
 def primal_step(u, p1, p2, a, b, c, m1, m2, tau, Iu, rho0, u_w, lam, M):
-    """Primal descent u + tau div(T^1/2 p), then the pointwise shrinkage."""
+    """Primal descent u + tau div(T^1/2 p), then the pointwise shrinkage
+    (Eq. 11, 13)."""
     q1, q2 = apply_T(a, b, c, p1, p2)
     uh = u + tau * div(q1, q2, m1, m2)
     return np.where(M, shrink(uh, Iu, rho0, u_w, tau, lam), u)
@@ -208,6 +213,8 @@ def accel_schedule(gamma, n, tau0=1.0 / np.sqrt(8.0), sig0=1.0 / np.sqrt(8.0)):
 
 
 def check_accel(prm: Params):
+    """The conditions of the accelerated step schedule (Sec. III-D's theta
+    updated every iteration): finite gamma >= 0, scalar steps, Huber-TV."""
     if prm.accel_gamma < 0 or not np.isfinite(prm.accel_gamma):
         raise ValueError("accel_gamma must be finite and >= 0")
     if prm.accel_gamma > 0 and (prm.precond or prm.regularizer != "huber_tv"):
@@ -216,7 +223,8 @@ def check_accel(prm: Params):
 
 
 def pd_iteration(st, lv, prm: Params):
-    """One iteration on state dict st (u, ubar, p1, p2) with level data lv.
+    """One iteration of Eq. 11 on state dict st (u, ubar, p1, p2) with level
+    data lv.
 
     With prm.accel_gamma > 0 the scalar steps and the relaxation follow
     accel_schedule, restarted at every warp: st["k"] counts the warp's
@@ -284,12 +292,14 @@ def clip_update(u, u_w, w, g, du_max, M):
 
 
 def huber(z1, z2, eps):
+    """Huber norm h_eps of the first-order regulariser (Eq. 10 with v = 0)."""
     n = np.hypot(z1, z2)
     return np.where(n <= eps, n * n / (2.0 * eps), n - eps / 2.0)
 
 
 def energy(u, u_w, Iu, rho0, a, b, c, m1, m2, M, lam, eps):
-    """E_w(u) of the linearised problem of one warp."""
+    """E_w(u) of the linearised problem of one warp (Eq. 10 with v = 0, the
+    data term of Eq. 5)."""
     g1, g2 = grad(u, m1, m2)
     k1, k2 = apply_T(a, b, c, g1, g2)
     data = lam * np.abs(rho0 + Iu * (u - u_w))
