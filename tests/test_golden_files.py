@@ -62,3 +62,19 @@ def test_paper_parameters_fixture_cites_the_paper():
     import oracle
     prm = oracle.Params()
     assert prm.alpha0 == g["alpha0"]["value"] and prm.alpha1 == g["alpha1"]["value"]
+
+
+def test_every_oracle_function_cites_its_passage():
+    # each function of the oracle names the section, equation or algorithm of
+    # the paper it follows
+    import ast
+    import glob
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    missing = []
+    for f in sorted(glob.glob(os.path.join(root, "oracle", "*.py"))):
+        for n in ast.parse(open(f).read()).body:
+            if isinstance(n, ast.FunctionDef):
+                d = ast.get_docstring(n) or ""
+                if not any(k in d for k in ("Sec.", "Eq.", "Algorithm")):
+                    missing.append(f"{os.path.basename(f)}:{n.name}")
+    assert not missing, missing
