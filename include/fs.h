@@ -158,7 +158,9 @@ typedef struct fs_handle fs_handle;
 
 /* Fill *out with the defaults (lambda 50, eps 0.01, du_max 0.2, beta 9,
  * eta 0.85, theta 1, precond 1, block_iters 0, use_graph 0, Huber-TV,
- * alpha0 17, alpha1 1.2, deriv FS_DERIV_FORWARD, accel_gamma 0). */
+ * alpha0 17, alpha1 1.2, deriv FS_DERIV_FORWARD, accel_gamma 0).  du_max,
+ * beta, eta, alpha0 and alpha1 are the values of Sec. IV-C; the paper
+ * states no lambda and no Huber eps.  FS_EINVAL for a null out. */
 fs_status fs_default_params(fs_params* out);
 
 /* Create the per-rig state for W x H pairs and `levels` pyramid levels
@@ -174,7 +176,9 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H,
                     int levels, const fs_params* prm, void* cuda_stream,
                     fs_handle** out);
 
-/* Device bytes fs_create would allocate for a handle of this size, level
+/* (No counterpart in the paper: memory planning, as the server's admission
+ * by memory budget uses it.)
+ * Device bytes fs_create would allocate for a handle of this size, level
  * count and storage (prm NULL = defaults), without allocating: the pyramid's
  * planes (FP32 state, the 16-bit-capable planes in the storage type, float2
  * fields, mask bytes) and the calibration field.  fs_solve_host adds 5
@@ -182,10 +186,16 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H,
  * fs_create rejects. */
 fs_status fs_state_bytes(int W, int H, int levels, const fs_params* prm, size_t* out);
 
-/* Replace the pose; recomputes the calibration and trajectory fields. */
+/* Replace the pose (exp(xi_1) of Sec. III-A) for the following solves:
+ * recomputes, on the handle's stream, the calibration field of Sec. IV-A
+ * and the trajectory field of every level (Sec. III-B).  FS_EINVAL for a
+ * null pose or a non-finite entry; the previous pose stays in force when
+ * the call fails. */
 fs_status fs_set_pose(fs_handle* h, const fs_pose* pose);
 
-/* Size of pyramid level `level` (0 = full resolution). */
+/* Size of pyramid level `level` (0 = full resolution; each level halves
+ * the one above, rounding up, Sec. IV-B).  W or H may be NULL.  FS_EINVAL
+ * for a level outside [0, levels). */
 fs_status fs_level_size(const fs_handle* h, int level, int* W, int* H);
 
 /* Copy the trajectory field gamma' of a level (Sec. III-B, Eq. 7) to d_out:
@@ -204,7 +214,9 @@ fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1,
                    const float* d_init, int warps, int iters,
                    float* d_disp, float* d_depth);
 
-/* Warm start of the next frame of a video stream from the handle's own last
+/* (The paper runs each frame from scratch; this continuation is a serving
+ * extension.)  Warm start of the next frame of a video stream from the
+ * handle's own last
  * result, with no disparity round trip: the finest level's u and its 2-D
  * correspondence field w, as the last fs_solve / fs_solve_continue of this
  * handle left them, initialise the finest level (u_w = ubar = u, p = 0) and
@@ -216,20 +228,25 @@ fs_status fs_solve(fs_handle* h, const float* d_I0, const float* d_I1,
 fs_status fs_solve_continue(fs_handle* h, const float* d_I0, const float* d_I1, int warps,
                             int iters, float* d_disp, float* d_depth);
 
-/* fs_solve from HOST buffers: copies the inputs to the device, solves,
+/* (No counterpart in the paper: the end-to-end host entry point.)
+ * fs_solve from HOST buffers: copies the inputs to the device, solves,
  * copies the outputs back and synchronises the handle's stream before
  * returning.  Host buffers may be pageable or pinned (pinned is faster). */
 fs_status fs_solve_host(fs_handle* h, const float* h_I0, const float* h_I1,
                         const float* h_init, int warps, int iters,
                         float* h_disp, float* h_depth);
 
-/* Free the handle and its device memory (synchronises its stream). */
+/* Free the handle and its device memory (synchronises its stream).  A null
+ * handle is a no-op.  (No counterpart in the paper.) */
 fs_status fs_destroy(fs_handle* h);
 
-/* Message for the last failing call of this thread ("" if none). */
+/* Message for the last failing call of this thread ("" if none); owned by
+ * the library, valid until this thread's next call.  (No counterpart in the
+ * paper.) */
 const char* fs_last_error(void);
 
 /* ---- Batches: many independent pairs per call -------------------------
+ * (No counterpart in the paper, which solves one pair at a time.)
  * A batch groups n handles (each from fs_create: any sizes, calibrations
  * and poses, all on one device) and solves one pair per handle at once.
  * Handle i's work runs on its own internal stream, forked from the batch

@@ -6,6 +6,11 @@
  * level's buffers, run a single stage and read the result.  Same
  * conventions as fs.h: dense row-major device buffers (pitch = width of the
  * level), caller-owned, work on the handle's stream.
+ *
+ * Each stage cites the passage it computes.  The calls after the stages --
+ * kernel timing, the autotuner and fs_set_schedule, the energy reduction,
+ * the guard-band check, the wait limits -- have no counterpart in the
+ * paper: they measure, tune and test the implementation.
  */
 #ifndef FS_STAGES_H
 #define FS_STAGES_H

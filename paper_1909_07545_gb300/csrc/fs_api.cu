@@ -1229,6 +1229,9 @@ fs_status fs_set_pose(fs_handle* h, const fs_pose* pose) {
   fs_status s;
   if ((s = check_handle(h)) != FS_OK) return s;
   if (!pose) return fail(FS_EINVAL, "null pose");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(i < 9 ? pose->R[i] : pose->t[i - 9]))
+      return fail(FS_EINVAL, "pose has a non-finite entry");
   fs_pose old = h->pose;
   h->pose = *pose;
   if ((s = build_fields(h)) != FS_OK) {
