@@ -1080,8 +1080,9 @@ fs_status fs_create(const fs_calib cam[2], const fs_pose* pose, int W, int H, in
     L.W = l == 0 ? W : (h->lv[l - 1].W + 1) / 2;
     L.H = l == 0 ? H : (h->lv[l - 1].H + 1) / 2;
     if (L.W < 4 || L.H < 4) {
+      const int lw = L.W, lh = L.H;    // L lives in *h
       delete h;
-      return fail(FS_EINVAL, "level %d would be %dx%d (< 4x4): too many levels", l, L.W, L.H);
+      return fail(FS_EINVAL, "level %d would be %dx%d (< 4x4): too many levels", l, lw, lh);
     }
     L.P = (int)align_up((size_t)L.W, 32);
     double sc = std::ldexp(1.0, -l);
