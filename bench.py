@@ -352,7 +352,10 @@ def serve_leg(rigs, sizes, seed, seconds, rate, inflight, warm_mode=1, storage="
             if item is None:
                 return
             req, slot = item
-            srv.wait(req)
+            try:
+                srv.wait(req)
+            except Exception:          # a failed request: the server counts it
+                pass
             free[r].put(slot)
 
     ths = [threading.Thread(target=waiter, args=(r,), daemon=True) for r in range(n_rigs)]

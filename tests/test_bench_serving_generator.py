@@ -18,7 +18,8 @@ class _StandInServer:
     a rig's requests run one after another (0.3 ms each here), rigs run side
     by side, and a request may be waited for once only."""
 
-    def __init__(self, **cfg):
+    def __init__(self, fail_every=0, **cfg):
+        self.fail_every = fail_every
         self.cfg = cfg
         self.mu = threading.Condition()
         self.next_id = 0
@@ -67,6 +68,8 @@ class _StandInServer:
             assert rid in self.rig_of and rid not in self.waited, rid
             self.waited.add(rid)
             self.mu.wait_for(lambda: rid in self.done)
+        if self.fail_every and rid % self.fail_every == 0:
+            raise RuntimeError(f"request {rid} failed")
         return 0.0
 
     def drain(self):
@@ -90,13 +93,16 @@ class _StandInServer:
         self.closed = True
 
 
-def test_generator_waits_each_request_once_per_rig(monkeypatch):
+@pytest.mark.parametrize("fail_every", [0, 7])
+def test_generator_waits_each_request_once_per_rig(monkeypatch, fail_every):
+    # fail_every = 7: every seventh request fails when it is waited for; its
+    # rig's buffer still comes back and the run completes
     import bench
     import paper_1909_07545_gb300 as pkg
     made = []
 
     def server(**cfg):
-        made.append(_StandInServer(**cfg))
+        made.append(_StandInServer(fail_every=fail_every, **cfg))
         return made[-1]
 
     monkeypatch.setattr(pkg, "Server", server)
