@@ -349,9 +349,14 @@ class Solver:
 
     def autotune(self, iters=20):
         """Pick the primal-dual schedule per level by timing (fs_autotune).
-        Returns per level 0 = cluster, 1..8 = temporal-blocking depth on
-        64x64 footprints, 9..16 = depth (value - 8) on 32x32 footprints,
-        17..24 = depth (value - 16) on 64x32 footprints."""
+        Returns per level the choice kept, in fs_autotune's encoding
+        (include/fs_stages.h): 0 = the whole-level cluster; 8 v + d =
+        temporal-blocking depth d (1..8) on footprint v (0..5: 64x64 of 512
+        threads, 32x32 of 256, 64x32 of 256, 64x64 of 1024, 32x32 of 1024,
+        32x32 of 512), so 1..48; 49..55 = depth 9..15 on 32x32 of 1024
+        threads; 56..63 = depth 1..8 on the TMA-staged 64x64 footprints;
+        64..71 = depth 1..8 on 64x48 of 768 threads.  TGV handles: 0 = a
+        launch per step, 8 v + d = depth d on the five TGV footprints."""
         out = (ctypes.c_int * 8)()
         _check(self.lib.fs_autotune(self.h, int(iters), out))
         return [out[l] for l in range(self.levels)]
