@@ -78,3 +78,30 @@ def test_every_oracle_function_cites_its_passage():
                 if not any(k in d for k in ("Sec.", "Eq.", "Algorithm")):
                     missing.append(f"{os.path.basename(f)}:{n.name}")
     assert not missing, missing
+
+
+def test_profile_summaries_are_text_and_name_committed_commands():
+    # profiles/ holds short text summaries only, and every command they give
+    # runs a module or script of this repository
+    import re
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pdir = os.path.join(root, "profiles")
+    names = sorted(os.listdir(pdir))
+    assert names and all(n.endswith((".md", ".txt")) for n in names), names
+    try:
+        tracked = set(subprocess.run(["git", "ls-files"], cwd=root, capture_output=True,
+                                     text=True).stdout.split())
+    except OSError:                   # no git: check the files exist instead
+        tracked = set()
+    for n in names:
+        text = open(os.path.join(pdir, n)).read()
+        assert len(text) < 16384, n
+        cmds = re.findall(r"python -m ([\w.]+)|python ([\w/]+\.py)", text)
+        assert cmds, f"{n} gives no command"
+        for mod, script in cmds:
+            path = mod.replace(".", "/") + ".py" if mod else script
+            if tracked:
+                assert path in tracked, (n, path)
+            else:
+                assert os.path.exists(os.path.join(root, path)), (n, path)
