@@ -863,7 +863,7 @@ def main():
                                       "bit_identical_to_main": bool(torch.equal(
                                           disp, torch.as_tensor(main_disp, device="cuda")))}
         x.close()
-    # the benchmark spec's comparison at 1024 x 1024: 8 distinct pairs of the workload
+    # the batched path against the plain one at 1024 x 1024: 8 distinct pairs of the workload
     # (seeds seed+100 ..), FP16 storage, one fs_batch graph, against the
     # plain FP32 single-pair figure above
     batch1024 = None

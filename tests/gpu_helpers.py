@@ -119,7 +119,7 @@ def oracle_sensitivity(pair, ref, levels=None, warps=None, iters=None, d_init=No
 
 
 # Disparity parity gate, GPU FP32 vs FP64 oracle (same float32 inputs,
-# pyramid, warps and iterations), at the tolerance the benchmark spec states: max
+# pyramid, warps and iterations), at the stated parity tolerance: max
 # |dd| <= 5e-3 px and mean |dd| <= 1e-4 px.
 #   mean |dd| over the whole FOV mask <= 1e-4 px;
 #   max |dd| <= 5e-3 px over the well-conditioned pixels, those that none of

@@ -10,7 +10,7 @@ storage, all arithmetic FP32:
   iterations), beside the FP32 path.
 
 Gates at the sampled pixels:
-  FP32        the benchmark spec's: mean |dd| <= 1e-4 px; max |dd| <= 5e-3 px where
+  FP32        the stated tolerance: mean |dd| <= 1e-4 px; max |dd| <= 5e-3 px where
               the oracle's own five FP32-sized probes move it by <= 1e-3 px;
               elsewhere within max(5e-3, 2 x that pixel's probe response).
   FP16, BF16  mean |dd| <= MEAN_16[kind] px and 99th percentile

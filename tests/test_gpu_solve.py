@@ -386,7 +386,7 @@ def test_bench_configuration_at_full_counts(fixture):
     # At ten warps per level the solve is chaotic at a fraction of the
     # pixels, noise or not: the FP64 oracle itself moves there by up to a few
     # pixels under FP32-sized perturbations (the five probes of the
-    # fixture), mostly at occlusion boundaries, so the benchmark spec's per-pixel
+    # fixture), mostly at occlusion boundaries, so the stated per-pixel
     # bound cannot hold for any FP32 implementation at this count.  The gate
     # compares distributions with the oracle's own: mean, 99.8th percentile
     # and maximum of |dd| at the sampled pixels no more than twice the
@@ -430,7 +430,7 @@ def test_bench_configuration_at_full_counts(fixture):
     assert rep["max"] <= max(5e-3, 2 * ps["max"]), rep
     assert rep["n_over"] <= 2 * rep["n_over_probe"] + 4, rep
     if "clean" in fixture:
-        # without image noise, the benchmark spec's bound holds at full count on the
+        # without image noise, the stated bound holds at full count on the
         # samples that no probe moves by more than 1e-3 px
         assert rep["max_well"] <= 5e-3, rep
     qs = np.quantile(d[M], gold["quantile_levels"])
