@@ -74,6 +74,29 @@ def _negate_third(orig):
     return f
 
 
+def _no_renormalisation(orig):
+    # Eq. 7's step along the bicubic sample of gamma' as it is, not
+    # renormalised to unit length
+    import oracle.variational as V
+
+    def warp_linearize(I0, I1, w, gamma, M, deriv="forward"):
+        if deriv not in ("forward", "central"):
+            raise ValueError(deriv)
+        H, W = I0.shape
+        py, px = np.mgrid[0:H, 0:W].astype(np.float64)
+        xs, ys = px + w[..., 0], py + w[..., 1]
+        g = V.bicubic(gamma, xs, ys)
+        I1w = V.bilinear(I1, xs, ys)
+        I1g = V.bilinear(I1, xs + g[..., 0], ys + g[..., 1])
+        if deriv == "forward":
+            Iu = I1g - I1w
+        else:
+            Iu = 0.5 * (I1g - V.bilinear(I1, xs - g[..., 0], ys - g[..., 1]))
+        return (np.where(M, Iu, 0.0), np.where(M, I1w - I0, 0.0),
+                np.where(M[..., None], g, 0.0))
+    return warp_linearize
+
+
 def _negate_first(orig):
     def f(*a, **k):
         Iu, rho0, g = orig(*a, **k)
@@ -149,6 +172,9 @@ CASES = [
      _negate_third, [var_pins.test_warp_linearize_on_affine_image]),
     ("Eq. 7 derivative: taken along -gamma'", "oracle.variational", "warp_linearize",
      _negate_first, [var_pins.test_warp_linearize_on_affine_image]),
+    ("Eq. 7 derivative: g not renormalised to unit length", "oracle.variational",
+     "warp_linearize", _no_renormalisation,
+     [var_pins.test_warp_linearize_renormalises_the_sampled_field]),
     ("Algorithm 1 clip: delta-u not clamped", "oracle.variational", "clip_update",
      lambda o: lambda u, uw, w, g, du, M: o(u, uw, w, g, np.inf, M),
      [var_pins.test_clip_update_cases]),

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 from scipy.optimize import minimize_scalar
 
+from oracle.interp import bicubic
 from oracle.variational import (Params, apply_T, clip_update, div, dual_step, energy,
                                 grad, grad_masks, pd_iteration, precondition, shrink,
                                 tensor_sqrt, warp_linearize)
@@ -306,6 +307,27 @@ def test_warp_linearize_derivatives_on_quadratic_image():
     assert np.array_equal(rho_f, rho_c)
     with pytest.raises(ValueError):
         warp_linearize(I0, I1, w, gam, M, "backward")
+
+
+def test_warp_linearize_renormalises_the_sampled_field():
+    # a unit field that turns 0.9 rad per pixel: its bicubic sample half-way
+    # between pixels is shorter than 1, and g is that sample renormalised to
+    # unit length; on an affine I1 the forward I_u is then grad(I1) . g exactly
+    H, W = 10, 24
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    phi = 0.9 * px
+    gam = np.stack([np.cos(phi), np.sin(phi)], -1)
+    I1 = 0.3 + 0.02 * px - 0.01 * py
+    I0 = np.zeros((H, W))
+    w = np.zeros((H, W, 2))
+    w[..., 0] = 0.5
+    M = np.zeros((H, W), bool)
+    M[2:8, 2:20] = True
+    Iu, rho0, g = warp_linearize(I0, I1, w, gam, M)
+    raw = bicubic(gam, px + 0.5, py)
+    assert np.hypot(raw[..., 0], raw[..., 1])[M].max() < 0.999     # the sample is short
+    assert np.abs(np.hypot(g[..., 0], g[..., 1])[M] - 1.0).max() < 1e-12
+    assert np.abs(Iu - (0.02 * g[..., 0] - 0.01 * g[..., 1]))[M].max() < 1e-13
 
 
 def test_warp_linearize_noise_correlation():
