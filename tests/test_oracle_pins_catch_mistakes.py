@@ -97,6 +97,42 @@ def _no_renormalisation(orig):
     return warp_linearize
 
 
+def _sigma_from_first_row(orig):
+    # one sigma from the first component's row sum instead of the larger one
+    def precondition(a, b, c, M, m1, m2, precond=True):
+        tau, s1, s2 = orig(a, b, c, M, m1, m2, precond)
+        if not precond:
+            return tau, s1, s2
+        r1 = 2.0 * (np.abs(a) * m1 + np.abs(b) * m2)
+        sig = np.where(r1 > 0, 1.0 / np.where(r1 > 0, r1, 1.0), 0.0)
+        return tau, sig, sig.copy()
+    return precondition
+
+
+def _clip_each_component(orig):
+    # the dual projected onto the square |q1|, |q2| <= 1 instead of the disc
+    import oracle.variational as V
+
+    def dual_step(p1, p2, ubar, a, b, c, m1, m2, sig1, sig2, eps):
+        g1, g2 = V.grad(ubar, m1, m2)
+        k1, k2 = V.apply_T(a, b, c, g1, g2)
+        q1 = (p1 + sig1 * k1) / (1.0 + sig1 * eps)
+        q2 = (p2 + sig2 * k2) / (1.0 + sig2 * eps)
+        return np.clip(q1, -1.0, 1.0), np.clip(q2, -1.0, 1.0)
+    return dual_step
+
+
+def _threshold_one_iu(orig):
+    # Eq. 13's thresholds tau lam I_u^2 written with one factor I_u
+    def shrink(uh, Iu, rho0, u_w, tau, lam):
+        r = rho0 + Iu * (uh - u_w)
+        thr = tau * lam * np.abs(Iu)
+        step = tau * lam * Iu
+        inner = np.where(Iu != 0.0, -r / np.where(Iu != 0.0, Iu, 1.0), 0.0)
+        return uh + np.where(r < -thr, step, np.where(r > thr, -step, inner))
+    return shrink
+
+
 def _negate_first(orig):
     def f(*a, **k):
         Iu, rho0, g = orig(*a, **k)
@@ -184,6 +220,29 @@ CASES = [
     ("accelerated steps: factor 2 of theta_k dropped", "oracle.variational", "accel_schedule",
      lambda o: lambda g, n, *a, **k: o(0.5 * g, n, *a, **k),
      [var_pins.test_accel_schedule_recursion]),
+    ("Eq. 12 tensor: exponent eta dropped", "oracle.variational", "tensor_sqrt",
+     lambda o: lambda I0, M, beta, eta: o(I0, M, beta, 1.0),
+     [var_pins.test_tensor_eigenstructure]),
+    ("diagonal steps: sigma from the first row only", "oracle.variational", "precondition",
+     _sigma_from_first_row, [var_pins.test_preconditioned_steps_bound_the_operator]),
+    ("Eq. 11: over-relaxation dropped (theta = 0)", "oracle.variational", "pd_iteration",
+     lambda o: lambda st, lv, prm: o(st, lv, dataclasses.replace(prm, theta=0.0)),
+     [lambda: var_pins.test_energy_descends_over_a_warp(2),
+      var_pins.test_accel_iteration_reduces_to_theta_one_and_settles]),
+    ("linearised energy: lambda dropped", "oracle.variational", "energy",
+     lambda o: lambda *a: o(*a[:-2], 1.0, a[-1]),
+     [lambda: var_pins.test_energy_descends_over_a_warp(2)]),
+    ("Huber norm: quadratic branch n^2 / eps", "oracle.variational", "huber",
+     lambda o: lambda z1, z2, eps: np.where(np.hypot(z1, z2) <= eps, np.hypot(z1, z2) ** 2 / eps,
+                                            np.hypot(z1, z2) - eps / 2.0),
+     [lambda: var_pins.test_energy_descends_over_a_warp(2)]),
+    ("Eq. 11 dual projection: per component", "oracle.variational", "dual_step",
+     _clip_each_component, [var_pins.test_dual_step_is_huber_conjugate_prox]),
+    ("Eq. 13 thresholds: one factor I_u", "oracle.variational", "shrink",
+     _threshold_one_iu, [var_pins.test_shrink_is_data_term_prox]),
+    ("Eq. 10 TGV: Jacobian of v with the wrong sign", "oracle.tgv", "grad_v",
+     lambda o: lambda *a: tuple(-x for x in o(*a)),
+     [tgv_pins.test_jacobian_divergence_adjoint]),
     ("Eq. 10 TGV: divergence of q with the wrong sign", "oracle.tgv", "div_q",
      lambda o: lambda *a: tuple(-x for x in o(*a)),
      [tgv_pins.test_jacobian_divergence_adjoint]),
