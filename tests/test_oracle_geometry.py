@@ -117,6 +117,18 @@ def test_calibration_field_identity_and_axis_roll():
     assert np.abs(cf[..., 1][sel] - ey[sel]).max() < 1e-8
 
 
+def test_calibration_field_between_cameras_of_different_focal_length():
+    # no rotation, two equidistant cameras with one principal point and focal
+    # lengths f and 1.1 f: c(x) = pi_1(X) - pi_0(X) = 0.1 (x - c) exactly
+    cam1 = Calib(EQUIDISTANT, 88.0, 88.0, 127.5, 127.5, fov_deg=180.0)
+    W = H = 256
+    M = fov_mask(EQ, W, H)
+    cf = calibration_field(EQ, cam1, np.eye(3), W, H, M)
+    py, px = np.mgrid[0:H, 0:W].astype(float)
+    assert np.abs(cf[..., 0] - 0.1 * (px - 127.5))[M].max() < 1e-9
+    assert np.abs(cf[..., 1] - 0.1 * (py - 127.5))[M].max() < 1e-9
+
+
 def test_prerotation_of_identity_is_identity():
     rng = np.random.default_rng(5)
     I1 = rng.uniform(0, 1, (40, 50))

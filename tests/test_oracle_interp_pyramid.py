@@ -45,6 +45,12 @@ def test_level_sizes_and_scaled_calibration():
     c1 = scaled_calib(cam, 1)
     # centre of a 256 image maps to the centre of the 128 image
     assert c1.cx == pytest.approx(63.5) and c1.fx == pytest.approx(40.0)
+    # both axes: pixel centres on integers, so c_l = (c + 0.5) 2^-l - 0.5
+    # (Sec. IV-B; an off-centre principal point and fx != fy)
+    cam2 = Calib(EQUIDISTANT, 80.0, 60.0, 100.0, 140.0, fov_deg=180.0)
+    c2 = scaled_calib(cam2, 2)
+    assert (c2.fx, c2.fy) == (20.0, 15.0)
+    assert (c2.cx, c2.cy) == (24.625, 34.625)
 
 
 def test_analytic_mask_matches_nearest_neighbour_rescale():
@@ -57,6 +63,16 @@ def test_analytic_mask_matches_nearest_neighbour_rescale():
     assert np.all(M1[allin]) and not np.any(M1[allout])
     assert (allin | allout).mean() > 0.97
     assert 0.7 < M0.mean() < 0.8                # 180 deg circle of radius ~125.7 px
+
+
+def test_fov_mask_follows_both_focal_lengths():
+    # fx = 60, fy = 80: the 180 deg FOV boundary r = pi/2 is an ellipse with
+    # semi-axes 94.2 and 125.7 px about (127.5, 127.5); pixel centres half a
+    # pixel off the axes, checked just inside and just outside along each
+    cam = Calib(EQUIDISTANT, 60.0, 80.0, 127.5, 127.5, fov_deg=180.0)
+    M = fov_mask(cam, 256, 256)
+    assert M[128, 34] and not M[128, 32]          # dx = -93.5 in, -95.5 out
+    assert M[3, 128] and not M[1, 128]            # dy = -124.5 in, -126.5 out
 
 
 def test_downsample_definition_and_constants():

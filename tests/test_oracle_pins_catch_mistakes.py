@@ -160,6 +160,9 @@ CASES = [
      "calibration_field",
      lambda o: lambda c0, c1, R, *a, **k: o(c0, c1, np.asarray(R).reshape(3, 3).T, *a, **k),
      [geo_pins.test_calibration_field_identity_and_axis_roll]),
+    ("Sec. IV-A calibration field: camera 0's model for camera 1", "oracle.geometry",
+     "calibration_field", lambda o: lambda c0, c1, R, *a, **k: o(c0, c0, R, *a, **k),
+     [geo_pins.test_calibration_field_between_cameras_of_different_focal_length]),
     ("Sec. IV-A pre-rotation: I1 sampled at x - c", "oracle.geometry", "prerotate",
      lambda o: lambda I1, cf: o(I1, -cf),
      [geo_pins.test_prerotation_samples_the_second_image_at_x_plus_c]),
@@ -179,6 +182,12 @@ CASES = [
     ("Sec. IV-B pyramid: the mask ignored in the box mean", "oracle.pyramid", "downsample_fast",
      lambda o: lambda img, m, Wc, Hc: o(img, np.ones_like(m, dtype=bool), Wc, Hc),
      [ip_pins.test_downsample_averages_only_the_children_inside_the_mask]),
+    ("Sec. IV-B FOV mask: fy ignored", "oracle.pyramid", "fov_mask",
+     lambda o: lambda c, W, H: o(dataclasses.replace(c, fy=c.fx), W, H),
+     [ip_pins.test_fov_mask_follows_both_focal_lengths]),
+    ("Sec. IV-B scaled calibration: cy without the pixel-centre offset", "oracle.pyramid",
+     "scaled_calib", lambda o: lambda c, lv: dataclasses.replace(o(c, lv), cy=c.cy * 0.5 ** lv),
+     [ip_pins.test_level_sizes_and_scaled_calibration]),
     ("Sec. IV-B upsampling: disparity not doubled", "oracle.pyramid", "upsample",
      lambda o: lambda v, mc, Wf, Hf, mf, scale=2.0: o(v, mc, Wf, Hf, mf, 1.0),
      [ip_pins.test_upsample_linear_interior_and_mask]),
