@@ -37,6 +37,17 @@ def test_keys_kernel_partition_of_unity_and_quadratic_reproduction():
     assert np.abs(bicubic(img, px, py) - img).max() < 1e-13
 
 
+def test_bicubic_clamps_to_the_edge():
+    # a ramp v = x sampled at x = 0.5: the taps at -1, 0, 1, 2 weigh -0.0625,
+    # 0.5625, 0.5625, -0.0625 (Keys, a = -0.5), and the tap at -1 reads the
+    # edge value v(0) = 0, so the sample is 0.5625 - 0.125 = 0.4375 (0.5 for
+    # an unclamped ramp); at the far end, x = 3.5 on 0..4 gives 3.5625
+    img = np.tile(np.arange(5.0), (4, 1))
+    assert bicubic(img, np.array([0.5]), np.array([1.0]))[0] == pytest.approx(0.4375, abs=1e-15)
+    assert bicubic(img, np.array([3.5]), np.array([1.0]))[0] == pytest.approx(3.5625, abs=1e-15)
+    assert bicubic(img, np.array([2.5]), np.array([1.0]))[0] == pytest.approx(2.5, abs=1e-15)
+
+
 def test_level_sizes_and_scaled_calibration():
     assert level_sizes(1024, 1024, 5)[-1] == (64, 64)
     assert level_sizes(1280, 1280, 6)[-1] == (40, 40)

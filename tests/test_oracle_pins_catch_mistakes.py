@@ -24,7 +24,7 @@ import test_oracle_geometry as geo_pins
 import test_oracle_interp_pyramid as ip_pins
 import test_oracle_tgv as tgv_pins
 import test_oracle_variational as var_pins
-from oracle.camera import KANNALA_BRANDT
+from oracle.camera import ENHANCED_UNIFIED, KANNALA_BRANDT, UNIFIED
 
 
 def _plant(monkeypatch, modname, name, make):
@@ -53,6 +53,74 @@ def _kb_k3_k4_swapped(orig):
             calib = dataclasses.replace(calib, k=(k[0], k[1], k[3], k[2]))
         return orig(calib, theta)
     return radial
+
+
+def _unified_xi_halved(orig):
+    def radial(calib, theta):
+        if calib.model == UNIFIED:
+            th = np.asarray(theta, dtype=np.float64)
+            return np.sin(th) / (np.cos(th) + 0.5 * calib.k[0])
+        return orig(calib, theta)
+    return radial
+
+
+def _enhanced_beta_on_cos(orig):
+    def radial(calib, theta):
+        if calib.model == ENHANCED_UNIFIED:
+            th = np.asarray(theta, dtype=np.float64)
+            a, b = calib.k[0], calib.k[1]
+            s, c = np.sin(th), np.cos(th)
+            return s / (a * np.sqrt(s * s + b * c * c) + (1.0 - a) * c)
+        return orig(calib, theta)
+    return radial
+
+
+def _theta_by_atan(orig):
+    # theta = atan(rho / z): wrong beyond 90 degrees off the axis
+    import oracle.camera as C
+
+    def project(calib, X):
+        X = np.asarray(X, dtype=np.float64)
+        x, y, z = X[..., 0], X[..., 1], X[..., 2]
+        rho = np.hypot(x, y)
+        r = C.radial(calib, np.arctan(rho / np.where(z == 0.0, 1e-300, z)))
+        safe = np.where(rho > 0.0, rho, 1.0)
+        mx = np.where(rho > 0.0, r * x / safe, 0.0)
+        my = np.where(rho > 0.0, r * y / safe, 0.0)
+        return np.stack([calib.fx * mx + calib.cx, calib.fy * my + calib.cy], axis=-1)
+    return project
+
+
+def _flow_not_normalised(orig):
+    import oracle.camera as C
+
+    def trajectory_vector(calib, tprime, px, py, depth=1.0, s=1e-5):
+        that = np.asarray(tprime, dtype=np.float64) / np.linalg.norm(tprime)
+        X = depth * C.unproject(calib, px, py)
+        return C.project(calib, X + s * that) - C.project(calib, X - s * that)
+    return trajectory_vector
+
+
+def _bicubic_wraps(orig):
+    # the taps beyond the border wrap around instead of reading the edge
+    import oracle.interp as I
+
+    def bicubic(img, x, y):
+        img = np.asarray(img, dtype=np.float64)
+        H, W = img.shape[:2]
+        xc, yc = I._clamp_pos(x, W), I._clamp_pos(y, H)
+        xi, yi = np.floor(xc).astype(np.int64), np.floor(yc).astype(np.int64)
+        out = 0.0
+        for j in range(-1, 3):
+            wy = I.keys_weight(yc - (yi + j))
+            row = 0.0
+            for i in range(-1, 3):
+                wx = I.keys_weight(xc - (xi + i))
+                v = img[(yi + j) % H, (xi + i) % W]
+                row = row + (wx[..., None] * v if img.ndim == 3 else wx * v)
+            out = out + (wy[..., None] * row if img.ndim == 3 else wy * row)
+        return out
+    return bicubic
 
 
 def _shrink_as_printed(orig):
@@ -146,6 +214,12 @@ CASES = [
      _kb_without_k4, [cam_pins.test_kb_polynomial_at_one_and_two_radians]),
     ("Kannala-Brandt r(theta): k3 and k4 transposed", "oracle.camera", "radial",
      _kb_k3_k4_swapped, [cam_pins.test_kb_polynomial_at_one_and_two_radians]),
+    ("unified model: xi halved", "oracle.camera", "radial", _unified_xi_halved,
+     [cam_pins.test_unified_special_cases]),
+    ("enhanced unified model: beta on cos^2", "oracle.camera", "radial",
+     _enhanced_beta_on_cos, [cam_pins.test_enhanced_unified_special_cases_and_closed_form]),
+    ("pi: theta = atan(rho / z)", "oracle.camera", "project", _theta_by_atan,
+     [lambda: cam_pins.test_round_trip(cam_pins.KB)]),
     ("pi: fx and fy transposed", "oracle.camera", "project",
      lambda o: lambda c, X: o(dataclasses.replace(c, fx=c.fy, fy=c.fx), X),
      [cam_pins.test_pinhole_closed_form]),
@@ -156,6 +230,8 @@ CASES = [
      lambda o: lambda *a, **k: -o(*a, **k),
      [geo_pins.test_equidistant_centre_row_points_left,
       geo_pins.test_pinhole_forward_translation_is_radial_from_epipole]),
+    ("Eq. 7 trajectory field: flow not normalised", "oracle.geometry", "trajectory_vector",
+     _flow_not_normalised, [geo_pins.test_pinhole_lateral_translation_gives_constant_field]),
     ("Sec. IV-A calibration field: R used untransposed", "oracle.geometry",
      "calibration_field",
      lambda o: lambda c0, c1, R, *a, **k: o(c0, c1, np.asarray(R).reshape(3, 3).T, *a, **k),
@@ -179,6 +255,8 @@ CASES = [
     ("bicubic trajectory sampling: Keys a = -0.75", "oracle.interp", "keys_weight",
      lambda o: lambda s, a=-0.5: o(s, -0.75),
      [ip_pins.test_keys_kernel_partition_of_unity_and_quadratic_reproduction]),
+    ("bicubic sampling: wrap-around at the border", "oracle.interp", "bicubic",
+     _bicubic_wraps, [ip_pins.test_bicubic_clamps_to_the_edge]),
     ("Sec. IV-B pyramid: the mask ignored in the box mean", "oracle.pyramid", "downsample_fast",
      lambda o: lambda img, m, Wc, Hc: o(img, np.ones_like(m, dtype=bool), Wc, Hc),
      [ip_pins.test_downsample_averages_only_the_children_inside_the_mask]),
