@@ -123,6 +123,54 @@ def _bicubic_wraps(orig):
     return bicubic
 
 
+def _upsample_from_corners(orig):
+    # fine pixel x read at coarse x / 2 (pixel corners) instead of
+    # (x + 0.5) / 2 - 0.5 (pixel centres)
+    def upsample(v, mask_c, Wf, Hf, mask_f, scale=2.0):
+        v = np.asarray(v, dtype=np.float64)
+        Hc, Wc = v.shape[:2]
+        py, px = np.mgrid[0:Hf, 0:Wf].astype(np.float64)
+        X = np.clip(px * 0.5, 0.0, Wc - 1.0)
+        Y = np.clip(py * 0.5, 0.0, Hc - 1.0)
+        x0 = np.minimum(np.floor(X), max(Wc - 2, 0)).astype(np.int64)
+        y0 = np.minimum(np.floor(Y), max(Hc - 2, 0)).astype(np.int64)
+        x1, y1 = np.minimum(x0 + 1, Wc - 1), np.minimum(y0 + 1, Hc - 1)
+        ax, ay = X - x0, Y - y0
+        num = den = 0.0
+        for wgt, yy, xx in (((1 - ax) * (1 - ay), y0, x0), (ax * (1 - ay), y0, x1),
+                            ((1 - ax) * ay, y1, x0), (ax * ay, y1, x1)):
+            wm = wgt * mask_c[yy, xx]
+            den = den + wm
+            num = num + (wm[..., None] * v[yy, xx] if v.ndim == 3 else wm * v[yy, xx])
+        if v.ndim == 3:
+            out = np.where(den[..., None] > 0, num / np.where(den > 0, den, 1.0)[..., None], 0.0)
+            return np.where(mask_f[..., None], scale * out, 0.0)
+        out = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+        return np.where(mask_f, scale * out, 0.0)
+    return upsample
+
+
+def _central_without_half(orig):
+    # the central difference of I1 along g not halved
+    def warp_linearize(I0, I1, w, gamma, M, deriv="forward"):
+        Iu, rho0, g = orig(I0, I1, w, gamma, M, deriv)
+        return (2.0 * Iu if deriv == "central" else Iu), rho0, g
+    return warp_linearize
+
+
+def _sigma_times_theta(orig):
+    # the accelerated schedule with sigma_{k+1} = sigma_k theta_k
+    def accel_schedule(gamma, n, tau0=1.0 / np.sqrt(8.0), sig0=1.0 / np.sqrt(8.0)):
+        tau, sig, th = np.empty(n), np.empty(n), np.empty(n)
+        t, s = tau0, sig0
+        for k in range(n):
+            tau[k], sig[k] = t, s
+            th[k] = 1.0 / np.sqrt(1.0 + 2.0 * gamma * t)
+            t, s = th[k] * t, s * th[k]
+        return tau, sig, th
+    return accel_schedule
+
+
 def _shrink_as_printed(orig):
     # Eq. 13 as printed: +rho_bar / I_u in the third case
     def shrink(uh, Iu, rho0, u_w, tau, lam):
@@ -249,6 +297,11 @@ CASES = [
     ("Sec. III-D triangulation: camera-1 centre at +t'", "oracle.geometry", "triangulate_range",
      lambda o: lambda c, px, py, wx, wy, tp: o(c, px, py, wx, wy, -np.asarray(tp)),
      [lambda: geo_pins.test_triangulation_recovers_known_points(geo_pins.EQ)]),
+    ("Sec. III-D triangulation: Z returned for the range", "oracle.geometry",
+     "triangulate_range",
+     lambda o: lambda c, px, py, wx, wy, tp: o(c, px, py, wx, wy, tp) * __import__(
+         "oracle").unproject(c, px, py)[..., 2],
+     [lambda: geo_pins.test_triangulation_recovers_known_points(geo_pins.KB)]),
     ("Eq. 9 bilinear warp: x and y transposed", "oracle.interp", "bilinear",
      lambda o: lambda img, x, y: o(img, y, x),
      [ip_pins.test_bilinear_reproduces_affine_and_samples]),
@@ -269,6 +322,8 @@ CASES = [
     ("Sec. IV-B upsampling: disparity not doubled", "oracle.pyramid", "upsample",
      lambda o: lambda v, mc, Wf, Hf, mf, scale=2.0: o(v, mc, Wf, Hf, mf, 1.0),
      [ip_pins.test_upsample_linear_interior_and_mask]),
+    ("Sec. IV-B upsampling: read at pixel corners", "oracle.pyramid", "upsample",
+     _upsample_from_corners, [ip_pins.test_upsample_linear_interior_and_mask]),
     ("Sec. IV-B scaled calibration: pixel-centre offset dropped", "oracle.pyramid",
      "scaled_calib",
      lambda o: lambda c, lv: dataclasses.replace(o(c, lv), cx=c.cx * 0.5 ** lv,
@@ -298,12 +353,20 @@ CASES = [
     ("Eq. 7 derivative: g not renormalised to unit length", "oracle.variational",
      "warp_linearize", _no_renormalisation,
      [var_pins.test_warp_linearize_renormalises_the_sampled_field]),
+    ("central I_u: the factor 1/2 dropped", "oracle.variational", "warp_linearize",
+     _central_without_half, [var_pins.test_warp_linearize_derivatives_on_quadratic_image]),
+    ("Algorithm 1 clip: w moved against g", "oracle.variational", "clip_update",
+     lambda o: lambda u, uw, w, g, du, M: (lambda un, wn: (un, 2.0 * w - wn))(
+         *o(u, uw, w, g, du, M)),
+     [var_pins.test_clip_update_cases]),
     ("Algorithm 1 clip: delta-u not clamped", "oracle.variational", "clip_update",
      lambda o: lambda u, uw, w, g, du, M: o(u, uw, w, g, np.inf, M),
      [var_pins.test_clip_update_cases]),
     ("diagonal steps: tau and sigma exchanged", "oracle.variational", "precondition",
      lambda o: lambda *a, **k: (lambda t, s1, s2: (s1, t, t.copy()))(*o(*a, **k)),
      [var_pins.test_preconditioned_steps_bound_the_operator]),
+    ("accelerated steps: sigma multiplied by theta_k", "oracle.variational", "accel_schedule",
+     _sigma_times_theta, [var_pins.test_accel_schedule_recursion]),
     ("accelerated steps: factor 2 of theta_k dropped", "oracle.variational", "accel_schedule",
      lambda o: lambda g, n, *a, **k: o(0.5 * g, n, *a, **k),
      [var_pins.test_accel_schedule_recursion]),
@@ -337,6 +400,9 @@ CASES = [
      "_project", lambda o: lambda r, *c: o(1.0, *c),
      [lambda: tgv_pins.test_fixed_point_satisfies_the_saddle_point_conditions(
          True, (17.0, 1.2, 2.0))]),
+    ("Eq. 10 TGV steps: tau_v doubled", "oracle.tgv", "tgv_steps",
+     lambda o: lambda *a, **k: (lambda tu, tv, sp, sq: (tu, 2.0 * tv, sp, sq))(*o(*a, **k)),
+     [tgv_pins.test_preconditioned_steps_bound_the_operator]),
     ("Eq. 10 TGV steps: sigma_q doubled", "oracle.tgv", "tgv_steps",
      lambda o: lambda *a, **k: (lambda tu, tv, sp, sq: (tu, tv, sp, 2.0 * sq))(*o(*a, **k)),
      [tgv_pins.test_preconditioned_steps_bound_the_operator]),
