@@ -87,8 +87,8 @@ typedef struct {
   size_t peak_resident_bytes;
 } fs_server_stats;
 
-/* Defaults: 40 GiB budget, 8 in flight, 3 x 50 warm, 10 x 100 cold,
- * warm_mode 1, autotune 1. */
+/* Defaults: 40 GiB budget, 2 in flight, 3 x 50 warm, 10 x 100 cold,
+ * warm_mode 1, autotune 1.  FS_EINVAL for a null out. */
 fs_status fs_server_default_config(fs_server_config* out);
 
 /* Create a server on the calling thread's current CUDA device.  cfg NULL =

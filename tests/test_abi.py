@@ -192,3 +192,36 @@ def test_noalloc_entry_point_rejects_unsupported_options_on_the_host(lib, bad):
                                    ctypes.byref(prm), None)
     assert st == -1, bad
     assert "fs_pd_iterate_noalloc" in lib.fs_last_error().decode()
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    # every field the binding declares sits at the offset the C compiler
+    # gives it, and each struct has the C size (a field added to a header
+    # but not to the binding, or reordered, would shift the rest)
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"fs_calib": fsb.FsCalib, "fs_pose": fsb.FsPose, "fs_params": fsb.FsParams,
+               "fs_server_config": fsb.FsServerConfig, "fs_server_stats": fsb.FsServerStats}
+    cname = lambda f: "lambda" if f == "lambda_" else f
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fs.h"',
+             '#include "fs_server.h"', 'int main(void) {']
+    for s, cls in structs.items():
+        lines.append(f'  printf("{s} sizeof %zu\\n", sizeof({s}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{s} {f} %zu\\n", offsetof({s}, {cname(f)}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in out.splitlines():
+        s, f, v = line.split()
+        cls = structs[s]
+        want = ctypes.sizeof(cls) if f == "sizeof" else getattr(cls, f).offset
+        assert int(v) == want, (s, f, int(v), want)
