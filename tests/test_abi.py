@@ -225,3 +225,44 @@ def test_ctypes_structs_match_the_c_layout(tmp_path):
         cls = structs[s]
         want = ctypes.sizeof(cls) if f == "sizeof" else getattr(cls, f).offset
         assert int(v) == want, (s, f, int(v), want)
+
+
+def _c_signatures():
+    """Every fs_* declaration of include/*.h as (name, [parameter kinds]),
+    a kind being 'ptr' or the scalar C type."""
+    out = {}
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", f)).read(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\**\s*(fs_\w+)\s*\(([^;{]*?)\)\s*;", src,
+                             re.M | re.S):
+            params = [p.strip() for p in m.group(2).split(",")]
+            if params == ["void"]:
+                params = []
+            kinds = []
+            for p in params:
+                if "*" in p or "[" in p:
+                    kinds.append("ptr")
+                else:
+                    kinds.append(" ".join(p.split()[:-1]).replace("const ", ""))
+            out[m.group(1)] = kinds
+    return out
+
+
+def test_binding_argtypes_match_the_c_declarations(lib):
+    # the arity and every scalar type of each entry point as the binding
+    # declares it to ctypes, against the headers
+    scalar = {"int": ctypes.c_int, "double": ctypes.c_double, "float": ctypes.c_float,
+              "size_t": ctypes.c_size_t, "long long": ctypes.c_longlong}
+    sigs = _c_signatures()
+    assert set(sigs) == set(fsb.EXPORTED)
+    for name, kinds in sigs.items():
+        args = getattr(lib, name).argtypes
+        assert args is not None and len(args) == len(kinds), (name, kinds, args)
+        for k, a in zip(kinds, args):
+            if k == "ptr":
+                assert a in (ctypes.c_void_p, ctypes.c_char_p) \
+                    or issubclass(a, (ctypes._Pointer, ctypes.Array)), (name, k, a)
+            else:
+                assert a is scalar[k], (name, k, a)
