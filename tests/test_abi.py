@@ -266,3 +266,41 @@ def test_binding_argtypes_match_the_c_declarations(lib):
                     or issubclass(a, (ctypes._Pointer, ctypes.Array)), (name, k, a)
             else:
                 assert a is scalar[k], (name, k, a)
+
+
+def _c_enum_values():
+    """name -> value of every FS_* enumerator and FS_* #define of include/*.h
+    (the value given, or one past the previous enumerator)."""
+    vals = {}
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", f)).read(), flags=re.S)
+        for body in re.findall(r"enum\s*\{([^}]*)\}", src):
+            nxt = 0
+            for item in [i.strip() for i in body.split(",") if i.strip()]:
+                name, _, v = item.partition("=")
+                nxt = int(v) if v.strip() else nxt
+                vals[name.strip()] = nxt
+                nxt += 1
+        for name, v in re.findall(r"#define\s+(FS_\w+)\s+(-?\d+)\s*$", src, re.M):
+            vals[name] = int(v)
+    return vals
+
+
+def test_binding_constants_match_the_headers():
+    c = _c_enum_values()
+    for name, v in fsb.BUF.items():
+        assert c["FS_BUF_" + name] == v, name
+    for name, v in fsb.STAGE.items():
+        assert c["FS_STAGE_" + name] == v, name
+    for v, name in fsb.STATUS.items():
+        assert c[name] == v, name
+    assert [c[k] for k in ("FS_PINHOLE", "FS_EQUIDISTANT", "FS_KANNALA_BRANDT", "FS_UNIFIED",
+                           "FS_ENHANCED_UNIFIED")] == \
+        [fsb.MODELS[k] for k in ("pinhole", "equidistant", "kb", "ucm", "eucm")]
+    assert (c["FS_REG_HUBER_TV"], c["FS_REG_TGV"]) == (fsb.REGULARIZER["huber_tv"],
+                                                       fsb.REGULARIZER["tgv"])
+    assert (c["FS_DERIV_FORWARD"], c["FS_DERIV_CENTRAL"]) == (fsb.DERIV["forward"],
+                                                              fsb.DERIV["central"])
+    assert c["FS_SCHED_PERSISTENT"] == fsb.SCHEDULE["persistent"]
