@@ -304,3 +304,12 @@ def test_binding_constants_match_the_headers():
     assert (c["FS_DERIV_FORWARD"], c["FS_DERIV_CENTRAL"]) == (fsb.DERIV["forward"],
                                                               fsb.DERIV["central"])
     assert c["FS_SCHED_PERSISTENT"] == fsb.SCHEDULE["persistent"]
+
+
+def test_buffer_plane_counts_match_the_header():
+    # fs_stages.h gives each buffer's plane count at the head of its comment
+    src = open(os.path.join(ROOT, "include", "fs_stages.h")).read()
+    found = re.findall(r"FS_BUF_\w+\s*=\s*(\d+),?\s*/\*\s*(\d+):", src)
+    assert len(found) == len(fsb.BUF)
+    for v, planes in found:
+        assert fsb.BUF_PLANES[int(v)] == int(planes), v
