@@ -41,6 +41,15 @@ def test_default_params_match_paper(lib):
     p = fsb.default_params()
     assert p.beta == pytest.approx(9.0) and p.eta == pytest.approx(0.85)
     assert p.du_max == pytest.approx(0.2) and p.theta == 1.0 and p.precond == 1
+    # and the rest of the defaults fs.h lists for fs_default_params, read from
+    # the library itself
+    q = fsb.FsParams()
+    assert lib.fs_default_params(ctypes.byref(q)) == 0
+    assert q.lambda_ == pytest.approx(50.0) and q.huber_eps == pytest.approx(0.01)
+    assert (q.block_iters, q.use_graph, q.regularizer, q.deriv, q.storage) == (0, 0, 0, 0, 0)
+    assert q.alpha0 == pytest.approx(17.0) and q.alpha1 == pytest.approx(1.2)
+    assert q.accel_gamma == 0.0 and q.pd_schedule == 0
+    assert lib.fs_default_params(None) == -1
 
 
 def _create(cams, W=64, H=64, levels=2, prm=None):
