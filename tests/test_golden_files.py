@@ -105,3 +105,25 @@ def test_profile_summaries_are_text_and_name_committed_commands():
                 assert path in tracked, (n, path)
             else:
                 assert os.path.exists(os.path.join(root, path)), (n, path)
+
+
+def test_fixture_scripts_use_only_the_oracle_and_the_input_generators():
+    # the stored expected values are written by scripts that import the
+    # oracle and the seeded inputs, never the CUDA path or torch
+    import ast
+    import glob
+    allowed = {"oracle", "synth", "numpy", "json", "multiprocessing", "os", "sys", "time",
+               "math", "argparse", "__future__", "hashlib"}
+    scripts = sorted(glob.glob(os.path.join(HERE, "make_*.py")))
+    assert scripts
+    for f in scripts:
+        tree = ast.parse(open(f).read())
+        for n in ast.walk(tree):
+            if isinstance(n, ast.Import):
+                mods = [a.name.split(".")[0] for a in n.names]
+            elif isinstance(n, ast.ImportFrom):
+                mods = [(n.module or "").split(".")[0]]
+            else:
+                continue
+            for m in mods:
+                assert m in allowed, (os.path.basename(f), m)
