@@ -127,3 +127,25 @@ def test_fixture_scripts_use_only_the_oracle_and_the_input_generators():
                 continue
             for m in mods:
                 assert m in allowed, (os.path.basename(f), m)
+
+
+def test_oracle_and_gpu_path_import_nothing_of_each_other():
+    # the oracle imports neither the library nor torch; the library's package
+    # imports no oracle; the seeded inputs import neither
+    import ast
+    import glob
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    banned = {"oracle": {"paper_1909_07545_gb300", "torch"},
+              "paper_1909_07545_gb300": {"oracle"},
+              "synth": {"oracle", "paper_1909_07545_gb300", "torch"}}
+    for pkg, bad in banned.items():
+        for f in sorted(glob.glob(os.path.join(root, pkg, "*.py"))):
+            for n in ast.walk(ast.parse(open(f).read())):
+                if isinstance(n, ast.Import):
+                    mods = [a.name.split(".")[0] for a in n.names]
+                elif isinstance(n, ast.ImportFrom) and n.level == 0:
+                    mods = [(n.module or "").split(".")[0]]
+                else:
+                    continue
+                for m in mods:
+                    assert m not in bad, (pkg, os.path.basename(f), m)
