@@ -322,3 +322,19 @@ def test_buffer_plane_counts_match_the_header():
     assert len(found) == len(fsb.BUF)
     for v, planes in found:
         assert fsb.BUF_PLANES[int(v)] == int(planes), v
+
+
+def test_no_cpu_fallback(monkeypatch, tmp_path):
+    # without a CUDA device the product classes refuse to run, and without
+    # the built library loading it raises: nothing falls back to the CPU
+    import torch
+    cam = dict(model="equidistant", fx=20.0, fy=20.0, cx=31.5, cy=31.5, fov_deg=180.0)
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: False)
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        fsb.Solver(cam, cam, np.eye(3), [-0.1, 0, 0], 64, 64, 2)
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        fsb.Server()
+    monkeypatch.setattr(fsb, "_lib", None)
+    monkeypatch.setattr(fsb, "LIB_PATH", str(tmp_path / "libfs.so"))
+    with pytest.raises(ImportError, match="missing"):
+        fsb.load_library()
