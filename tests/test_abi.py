@@ -338,3 +338,30 @@ def test_no_cpu_fallback(monkeypatch, tmp_path):
     monkeypatch.setattr(fsb, "LIB_PATH", str(tmp_path / "libfs.so"))
     with pytest.raises(ImportError, match="missing"):
         fsb.load_library()
+
+
+def test_create_rejects_fuzzed_arguments_without_crashing(lib):
+    # seeded random and degenerate calibrations and sizes (NaN, infinities,
+    # zero, negative, out-of-range models and fields of view): every call
+    # returns an error status and no handle.  The pose always holds a NaN,
+    # which fs_create checks after the sizes, levels and calibrations, so
+    # every draw runs those checks and none reaches the device.
+    import random
+    rng = random.Random(11)
+    vals = [0.0, -1.0, 1e-300, 1e300, float("nan"), float("inf"), -float("inf"), 1.0, 80.0]
+    for _ in range(1500):
+        cams = []
+        for _ in range(2):
+            c = fsb.FsCalib()
+            c.model = rng.choice([-1, 0, 1, 2, 3, 4, 5, 99])
+            c.fx, c.fy, c.cx, c.cy = (rng.choice(vals) for _ in range(4))
+            for i in range(4):
+                c.k[i] = rng.choice(vals + [0.03, -0.05])
+            c.fov_deg = rng.choice([0.0, -10.0, 179.9, 190.0, 360.0, 720.0, float("nan")])
+            cams.append(c)
+        pose = fsb._pose(np.eye(3), [-0.1, 0.0, float("nan")])
+        h = ctypes.c_void_p()
+        st = lib.fs_create((fsb.FsCalib * 2)(*cams), ctypes.byref(pose),
+                           rng.choice([0, 3, 64, 100000]), rng.choice([0, 64]),
+                           rng.choice([-1, 0, 1, 2, 9]), None, None, ctypes.byref(h))
+        assert st in (-1, -4) and not h.value, st
